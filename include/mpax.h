@@ -1,0 +1,223 @@
+/*
+ * mpax.h -- C ABI of the GB300 restarted-PDHG library (libmpax_gb300.so).
+ *
+ * The library solves problem (1) of the paper (Sec. 2),
+ *
+ *     min  1/2 x^T Q x + c^T x   s.t.   lc <= A x <= uc,   l <= x <= u,
+ *
+ * with r^2HPDHG (Algorithm 1; eqs. 3-4) when Q = 0 and rAPDHG (Algorithm 2;
+ * eqs. 5-6) otherwise, after Ruiz and Pock-Chambolle diagonal scaling (Sec. 3).
+ * Every step of the iteration runs in the library's own sm_103a kernels.
+ *
+ * Conventions for every entry point
+ *   - Every call returns an mpax_status; it never aborts or exits.  On failure
+ *     mpax_last_error() gives a message (thread-local; valid until the calling
+ *     thread's next call into the library).
+ *   - Vectors are dense, contiguous, FP64 unless the name says otherwise.
+ *     Infinite bounds are IEEE +-INFINITY.
+ *   - Sparse matrices are CSR: row_ptr (int64, rows+1 entries, row_ptr[0]=0,
+ *     non-decreasing), col_idx (int32, strictly increasing within a row,
+ *     0 <= col < cols), val (FP64).  nnz must be < 2^31.
+ *   - `kind` says whether pointer arguments are host or device (CUDA) memory.
+ *     Device pointers must belong to the current device.
+ *   - `cuda_stream` is a cudaStream_t (may be NULL = the legacy default
+ *     stream).  The library orders its work after the work already queued on
+ *     that stream and makes that stream wait for the library's results, so a
+ *     caller can treat every call as stream-ordered on `cuda_stream`.
+ *   - Handles are not thread-safe; distinct handles are independent.
+ */
+#ifndef MPAX_H_
+#define MPAX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mpax_status {
+  MPAX_OK = 0,
+  MPAX_ERR_INVALID_ARGUMENT = 1, /* bad sizes, unsorted CSR, NaN data, l > u ... */
+  MPAX_ERR_CUDA = 2,             /* a CUDA runtime call failed                   */
+  MPAX_ERR_OUT_OF_MEMORY = 3,    /* device allocation failed                     */
+  MPAX_ERR_NOT_SOLVED = 4,       /* results requested before mpax_solve          */
+  MPAX_ERR_DEVICE_TIMEOUT = 5,   /* a bounded device-side wait gave up           */
+  MPAX_ERR_NUMERICAL = 6,        /* NaN/Inf appeared in the iterates             */
+  MPAX_ERR_UNSUPPORTED = 7       /* option or input form this build lacks        */
+} mpax_status;
+
+typedef enum mpax_mem_kind { MPAX_MEM_HOST = 0, MPAX_MEM_DEVICE = 1 } mpax_mem_kind;
+
+/* Arithmetic of the iteration.  FP64: matrix, iterates and every vector in
+ * FP64.  MIXED: scaled matrix, iterates and vectors stored and updated in
+ * FP32 (SpMV accumulated in FP32); the KKT, duality-gap and restart
+ * reductions, the step sizes and the primal weight stay FP64. */
+typedef enum mpax_precision { MPAX_PREC_FP64 = 0, MPAX_PREC_MIXED = 1 } mpax_precision;
+
+/* Outcome of a solve (optimal, infeasible, unbounded are the conclusive ones,
+ * Sec. 4.5; the limits and numerical failure are not). */
+typedef enum mpax_termination {
+  MPAX_TERM_UNSOLVED = 0,
+  MPAX_TERM_OPTIMAL = 1,
+  MPAX_TERM_PRIMAL_INFEASIBLE = 2, /* reserved: infeasibility detection not built */
+  MPAX_TERM_DUAL_INFEASIBLE = 3,   /* reserved */
+  MPAX_TERM_ITERATION_LIMIT = 4,
+  MPAX_TERM_TIME_LIMIT = 5,
+  MPAX_TERM_NUMERICAL_ERROR = 6
+} mpax_termination;
+
+/* Solver options.  The first block follows the paper's Appendix A (defaults
+ * there); the second block fixes the rules the paper names but does not state
+ * (Sec. 3: step sizes, restarts, primal weight, scaling).  Always initialise
+ * with mpax_options_default(). */
+typedef struct mpax_options {
+  int32_t verbose;            /* 0: print a line every display_frequency checks */
+  int32_t display_frequency;  /* 10 */
+  int32_t warm_start;         /* informational: x0/y0 of mpax_solve are used when non-NULL */
+  int32_t feasibility_polishing; /* must be 0: not built */
+  double eps_abs;             /* 1e-4 */
+  double eps_rel;             /* 1e-4 */
+  double eps_primal_infeasible; /* 1e-8, reserved */
+  double eps_dual_infeasible;   /* 1e-8, reserved */
+  double eps_feas_polish;       /* 1e-6, reserved */
+  int64_t iteration_limit;      /* INT64_MAX */
+  double time_limit;            /* seconds, +inf */
+
+  int32_t precision;          /* mpax_precision, FP64 */
+  int32_t check_every;        /* 64: iterations between KKT/restart checks (1..1024) */
+  int32_t ruiz_iters;         /* 10 */
+  int32_t pock_chambolle;     /* 1: one Pock-Chambolle round, alpha = 1 */
+  double reflection_gamma;    /* 1.0 (Algorithm 1); eq. 4 allows [0, 1] */
+  double restart_sufficient;  /* 0.2 */
+  double restart_necessary;   /* 0.8 */
+  double restart_artificial;  /* 0.36 */
+  double primal_weight_smoothing; /* 0.5 */
+  double step_safety;         /* 0.998: eta = step_safety / ||A~||_2 */
+  int32_t power_max_iter;     /* 100 */
+  double power_tol;           /* 1e-4 */
+  int32_t use_graphs;         /* 1: replay each check block as one CUDA graph */
+  int32_t profile_kernels;    /* 0: 1 = time every fused SpMV launch with CUDA events
+                                 (no graphs; for measurement only) */
+} mpax_options;
+
+typedef struct mpax_stats {
+  int32_t termination;        /* mpax_termination */
+  int32_t precision;
+  int64_t iterations;         /* PDHG iterations taken */
+  int64_t restarts;
+  int64_t kkt_checks;
+  double primal_obj, dual_obj, gap;  /* unscaled problem, at the returned point */
+  double primal_res, dual_res;       /* ||r_p||_2, ||r_d||_2 */
+  double rel_kkt;                    /* relative KKT error (see mpax_kkt) */
+  double omega, eta, norm_A, norm_Q; /* final primal weight, eta, ||A~||, ||Q~|| */
+  double prepare_seconds;            /* transpose + scaling + norms */
+  double solve_seconds;              /* whole mpax_solve, host wall clock */
+  int64_t kernel_launches;           /* library kernels launched by the last mpax_solve */
+  /* profile_kernels = 1 only: summed CUDA-event milliseconds and launch counts of
+   * [0] primal fused SpMV^T, [1] dual fused SpMV, [2] KKT SpMV, [3] KKT SpMV^T */
+  double profile_ms[4];
+  int64_t profile_launches[4];
+} mpax_stats;
+
+typedef struct mpax_problem mpax_problem;
+
+const char* mpax_version(void);
+const char* mpax_last_error(void);
+const char* mpax_status_string(mpax_status s);
+void mpax_options_default(mpax_options* opts);
+
+/* Create an LP: problem (1) with Q = 0 (Sec. 2).  m rows, n columns, CSR A.
+ * All arrays are copied into library-owned device memory, so the caller may
+ * free or reuse them when the call returns.  Validation: sizes >= 0,
+ * CSR well formed and sorted, no NaN, l <= u, lc <= uc.  m = 0 or nnz = 0 is
+ * allowed.  On success *out owns the problem (free with mpax_destroy). */
+mpax_status mpax_lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                           const int32_t* col_idx, const double* val, const double* c,
+                           const double* lc, const double* uc, const double* l,
+                           const double* u, mpax_mem_kind kind, void* cuda_stream,
+                           mpax_problem** out);
+
+/* Create a convex QP with Q = diag(D) + F F^T (Sec. 2, eq. 1), D >= 0
+ * (n entries), F an n x r CSR matrix (f_row_ptr has n+1 entries).  Other
+ * arguments and ownership as mpax_lp_create. */
+mpax_status mpax_qp_create_diag_lowrank(
+    int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+    const double* val, const double* c, const double* lc, const double* uc, const double* l,
+    const double* u, const double* D, int32_t r, int64_t f_nnz, const int64_t* f_row_ptr,
+    const int32_t* f_col_idx, const double* f_val, mpax_mem_kind kind, void* cuda_stream,
+    mpax_problem** out);
+
+/* Solve from (x0, y0) given in the unscaled space (either may be NULL: zeros,
+ * the paper's default start, Sec. 3.5).  Runs transpose, scaling, norm
+ * estimation and the restarted iteration until the relative KKT test holds,
+ * the iteration limit or the time limit is reached, or NaN appears (status
+ * MPAX_ERR_NUMERICAL).  Returns after the device work is complete. */
+mpax_status mpax_solve(mpax_problem* prob, const mpax_options* opts, const double* x0,
+                       const double* y0, mpax_mem_kind kind);
+
+/* Copy the returned point into caller-owned buffers: x (n), y (m) in the
+ * unscaled space.  For LP that is the PDHG image (x^, y^) of the last
+ * check (Algorithm 1); for QP the weighted averages (Algorithm 2).
+ * Either pointer may be NULL.  MPAX_ERR_NOT_SOLVED before a solve. */
+mpax_status mpax_get_solution(const mpax_problem* prob, double* x, double* y,
+                              mpax_mem_kind kind);
+mpax_status mpax_get_stats(const mpax_problem* prob, mpax_stats* stats);
+
+/* Free everything the handle owns.  NULL is a no-op. */
+void mpax_destroy(mpax_problem* prob);
+
+/* ---- Lower-level entry points (each step of the path on its own) ---------- */
+
+/* Transpose, scaling and norm estimation for `opts` (what mpax_solve does
+ * first).  Needed before the calls below. */
+mpax_status mpax_prepare(mpax_problem* prob, const mpax_options* opts);
+
+/* Scaling factors D_r (m), D_c (n) with A~ = diag(D_r) A diag(D_c), and
+ * info[4] = {||A~||_2 estimate, ||Q~||_2 estimate, eta, omega_0}.  Any
+ * pointer may be NULL. */
+mpax_status mpax_get_scaling(const mpax_problem* prob, double* Dr, double* Dc, double* info,
+                             mpax_mem_kind kind);
+
+/* The device-built transpose of the (unscaled) A as CSR: rowptr_t (n+1),
+ * col_t (nnz), val_t (nnz). */
+mpax_status mpax_get_transpose(const mpax_problem* prob, int64_t* rowptr_t, int32_t* col_t,
+                               double* val_t, mpax_mem_kind kind);
+
+/* Set the iterate in the SCALED space.  LP: (x, y) = z^{n,k}, (x_aux, y_aux)
+ * = the restart anchor z^{n,0}.  QP: (x, y) = current point, (x_aux, y_aux)
+ * = the weighted averages.  k = inner counter, tau/sigma = step sizes. */
+mpax_status mpax_set_iterate(mpax_problem* prob, const double* x, const double* y,
+                             const double* x_aux, const double* y_aux, int64_t k, double tau,
+                             double sigma, mpax_mem_kind kind);
+
+/* Run `iters` plain iterations (no checks, no restarts) from the set iterate. */
+mpax_status mpax_iterate(mpax_problem* prob, int64_t iters);
+
+/* Read the iterate (SCALED space).  LP: (x, y) = z^{n,k} after the run,
+ * (x_hat, y_hat) = the PDHG image of the last step.  QP: (x, y) current,
+ * (x_hat, y_hat) = the weighted averages.  Any pointer may be NULL. */
+mpax_status mpax_get_iterate(const mpax_problem* prob, double* x, double* y, double* x_hat,
+                             double* y_hat, mpax_mem_kind kind);
+
+/* Relative KKT quantities of the UNSCALED problem at (x, y) (unscaled); the
+ * paper names them (primal feasibility, dual feasibility, duality gap; Sec. 3)
+ * and this library evaluates them as
+ *   r_p = A x - proj_[lc,uc](A x);   lam = Q x + c - A^T y;
+ *   r_d = lam - proj_Lambda(lam), Lambda_j = R (both bounds finite), R+ (only
+ *         l_j), R- (only u_j), {0} (neither);
+ *   p = 1/2 x^T Q x + c^T x;
+ *   d = -1/2 x^T Q x + sum(lc y^+ - uc y^-) + sum(l lh^+ - u lh^-), lh the
+ *       projected lam, terms with an infinite bound dropped;
+ *   rel = max(||r_p||/(1+||b||), ||r_d||/(1+||c||), |p-d|/(1+|p|+|d|)),
+ *         b_i the finite one of (lc_i, uc_i) (larger magnitude if both).
+ * out[0] ||r_p||, out[1] ||r_d||, out[2] p, out[3] d, out[4] |p-d|,
+ * out[5] rel.  Needs mpax_prepare. */
+mpax_status mpax_kkt(mpax_problem* prob, const double* x, const double* y, mpax_mem_kind kind,
+                     double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPAX_H_ */

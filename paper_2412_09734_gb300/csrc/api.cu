@@ -1,0 +1,686 @@
+// C ABI of the library (include/mpax.h): argument checks, device copies of the
+// problem data, validation on the device, preprocessing and the solve driver.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.cuh"
+
+using namespace mpax;
+
+namespace {
+
+thread_local std::string g_err;
+
+mpax_status fail(mpax_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+mpax_status cuda_fail(cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(MPAX_ERR_OUT_OF_MEMORY, std::string(where) + ": out of device memory");
+  return fail(MPAX_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define TRY_CUDA(expr, where)                    \
+  do {                                           \
+    cudaError_t e_ = (expr);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+// ---- validation kernels -----------------------------------------------------
+enum : int {
+  V_ROWPTR = 1,
+  V_COL_RANGE = 2,
+  V_COL_ORDER = 4,
+  V_VAL_NAN = 8,
+  V_COST = 16,
+  V_VBOUNDS = 32,
+  V_RBOUNDS = 64,
+  V_DIAG = 128,
+};
+
+__global__ void k_rowptr64_to_32(const long long* __restrict__ src, int* __restrict__ dst,
+                                 int rows, long long nnz, int* flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > rows) return;
+  const long long v = src[i];
+  if (v < 0 || v > nnz || (i == 0 && v != 0) || (i == rows && v != nnz) ||
+      (i < rows && src[i + 1] < v))
+    atomicOr(flags, V_ROWPTR);
+  dst[i] = (int)(v < 0 ? 0 : (v > nnz ? nnz : v));
+}
+
+__global__ void k_check_csr(const int* __restrict__ rp, const int* __restrict__ col,
+                            const double* __restrict__ val, int rows, int cols, int* flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const int b = rp[i], e = rp[i + 1];
+  int prev = -1;
+  for (int p = b; p < e; ++p) {
+    const int c = col[p];
+    if (c < 0 || c >= cols) atomicOr(flags, V_COL_RANGE);
+    if (c <= prev) atomicOr(flags, V_COL_ORDER);
+    prev = c;
+    if (!isfinite(val[p])) atomicOr(flags, V_VAL_NAN);
+  }
+}
+
+__global__ void k_check_vecs(const double* c, const double* l, const double* u, int n,
+                             const double* lc, const double* uc, int m, const double* D,
+                             int* flags) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    if (!isfinite(c[j])) atomicOr(flags, V_COST);
+    const double lo = l[j], hi = u[j];
+    if (isnan(lo) || isnan(hi) || lo > hi || lo == INFINITY || hi == -INFINITY)
+      atomicOr(flags, V_VBOUNDS);
+    if (D && (!isfinite(D[j]) || D[j] < 0.0)) atomicOr(flags, V_DIAG);
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const double lo = lc[i], hi = uc[i];
+    if (isnan(lo) || isnan(hi) || lo > hi || lo == INFINITY || hi == -INFINITY)
+      atomicOr(flags, V_RBOUNDS);
+  }
+}
+
+std::string flags_message(int f) {
+  std::string s;
+  if (f & V_ROWPTR) s += "row_ptr must start at 0, end at nnz and be non-decreasing; ";
+  if (f & V_COL_RANGE) s += "column index out of range; ";
+  if (f & V_COL_ORDER) s += "column indices must be strictly increasing within a row; ";
+  if (f & V_VAL_NAN) s += "matrix values must be finite; ";
+  if (f & V_COST) s += "c must be finite; ";
+  if (f & V_VBOUNDS) s += "variable bounds must satisfy l <= u, l < +inf, u > -inf, no NaN; ";
+  if (f & V_RBOUNDS) s += "row bounds must satisfy lc <= uc, lc < +inf, uc > -inf, no NaN; ";
+  if (f & V_DIAG) s += "D must be finite and non-negative; ";
+  return s;
+}
+
+template <typename T>
+cudaError_t dmalloc(T** p, size_t n) {
+  *p = nullptr;
+  return cudaMalloc(p, sizeof(T) * std::max<size_t>(n, 1));
+}
+
+cudaError_t copy_in(void* dst, const void* src, size_t bytes, mpax_mem_kind kind,
+                    cudaStream_t s) {
+  if (bytes == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes,
+                         kind == MPAX_MEM_HOST ? cudaMemcpyHostToDevice
+                                               : cudaMemcpyDeviceToDevice,
+                         s);
+}
+
+cudaError_t copy_out(void* dst, const void* src, size_t bytes, mpax_mem_kind kind,
+                     cudaStream_t s) {
+  if (bytes == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes,
+                         kind == MPAX_MEM_HOST ? cudaMemcpyDeviceToHost
+                                               : cudaMemcpyDeviceToDevice,
+                         s);
+}
+
+void free_csr(Csr& c) {
+  if (c.rp) cudaFree(c.rp);
+  if (c.col) cudaFree(c.col);
+  c = Csr();
+}
+
+}  // namespace
+
+struct mpax_problem {
+  ProblemData P;
+  cudaStream_t user = nullptr;
+  EngineBase* eng[2] = {nullptr, nullptr};
+  int cur = -1;  // precision of the prepared engine
+  bool prepared = false;
+  bool solved = false;
+  mpax_options last_opts;
+  mpax_stats stats;
+  double* dx = nullptr;  // n FP64 device scratch (host-kind inputs/outputs)
+  double* dy = nullptr;  // m
+  double* dxa = nullptr;
+  double* dya = nullptr;
+  double* d6 = nullptr;  // 8 doubles
+  cudaEvent_t ev = nullptr;
+};
+
+namespace {
+
+cudaError_t order_after_user(mpax_problem* pb) {
+  cudaError_t e = cudaEventRecord(pb->ev, pb->user);
+  if (e) return e;
+  return cudaStreamWaitEvent(pb->P.s, pb->ev, 0);
+}
+
+cudaError_t order_user_after(mpax_problem* pb) {
+  cudaError_t e = cudaEventRecord(pb->ev, pb->P.s);
+  if (e) return e;
+  return cudaStreamWaitEvent(pb->user, pb->ev, 0);
+}
+
+void destroy_problem(mpax_problem* pb) {
+  if (!pb) return;
+  ProblemData& P = pb->P;
+  if (P.s) cudaStreamSynchronize(P.s);
+  for (auto& e : pb->eng) delete e;
+  free_csr(P.A);
+  free_csr(P.At);
+  free_csr(P.F);
+  free_csr(P.Ft);
+  free_schedule(P.schedA);
+  free_schedule(P.schedAt);
+  free_schedule(P.schedF);
+  free_schedule(P.schedFt);
+  double* ds[] = {P.val, P.c,     P.lc,    P.uc,    P.l,   P.u,      P.D,      P.fval,
+                  P.Dr,  P.Dc,    P.invDr, P.invDc, P.val_s, P.fval_s, P.D_s,  P.rowred,
+                  P.colred, P.red, P.red_out, pb->dx, pb->dy, pb->dxa, pb->dya, pb->d6};
+  for (double* d : ds)
+    if (d) cudaFree(d);
+  int* is[] = {P.permT, P.permF, P.tmp_rows, P.tmp_scan};
+  for (int* d : is)
+    if (d) cudaFree(d);
+  if (pb->ev) cudaEventDestroy(pb->ev);
+  if (P.s) cudaStreamDestroy(P.s);
+  delete pb;
+}
+
+bool bad_ptr(const void* p, long long count) { return count > 0 && p == nullptr; }
+
+mpax_status create_common(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                          const int32_t* col_idx, const double* val, const double* c,
+                          const double* lc, const double* uc, const double* l,
+                          const double* u, const double* D, int32_t r, int64_t f_nnz,
+                          const int64_t* f_row_ptr, const int32_t* f_col_idx,
+                          const double* f_val, bool is_qp, mpax_mem_kind kind,
+                          void* cuda_stream, mpax_problem** out) {
+  if (!out) return fail(MPAX_ERR_INVALID_ARGUMENT, "out must not be NULL");
+  *out = nullptr;
+  if (m < 0 || n < 0 || nnz < 0 || r < 0 || f_nnz < 0)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "sizes must be non-negative");
+  if (nnz >= (1LL << 31) || f_nnz >= (1LL << 31))
+    return fail(MPAX_ERR_UNSUPPORTED, "nnz must be < 2^31");
+  if (kind != MPAX_MEM_HOST && kind != MPAX_MEM_DEVICE)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "kind must be MPAX_MEM_HOST or MPAX_MEM_DEVICE");
+  if (bad_ptr(row_ptr, 1) || bad_ptr(col_idx, nnz) || bad_ptr(val, nnz) || bad_ptr(c, n) ||
+      bad_ptr(l, n) || bad_ptr(u, n) || bad_ptr(lc, m) || bad_ptr(uc, m))
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "a required array pointer is NULL");
+  if (is_qp && (bad_ptr(D, n) || bad_ptr(f_row_ptr, 1) || bad_ptr(f_col_idx, f_nnz) ||
+                bad_ptr(f_val, f_nnz)))
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "a required QP array pointer is NULL");
+  if (is_qp && r == 0 && f_nnz > 0)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "F has entries but r = 0");
+
+  mpax_problem* pb = new mpax_problem();
+  ProblemData& P = pb->P;
+  P.m = m;
+  P.n = n;
+  P.nnz = (int)nnz;
+  P.is_qp = is_qp;
+  P.r = r;
+  P.f_nnz = (int)f_nnz;
+  pb->user = (cudaStream_t)cuda_stream;
+  mpax_options_default(&pb->last_opts);
+  std::memset(&pb->stats, 0, sizeof(pb->stats));
+  cudaError_t e = cudaStreamCreateWithFlags(&P.s, cudaStreamNonBlocking);
+  if (!e) e = cudaEventCreateWithFlags(&pb->ev, cudaEventDisableTiming);
+  if (!e) e = order_after_user(pb);
+  const int big = std::max(std::max(m, n), r) + 2;
+  if (!e) e = dmalloc(&P.A.rp, m + 1);
+  if (!e) e = dmalloc(&P.A.col, nnz);
+  if (!e) e = dmalloc(&P.val, nnz);
+  if (!e) e = dmalloc(&P.c, n);
+  if (!e) e = dmalloc(&P.l, n);
+  if (!e) e = dmalloc(&P.u, n);
+  if (!e) e = dmalloc(&P.lc, m);
+  if (!e) e = dmalloc(&P.uc, m);
+  if (!e) e = dmalloc(&P.Dr, m);
+  if (!e) e = dmalloc(&P.Dc, n);
+  if (!e) e = dmalloc(&P.invDr, m);
+  if (!e) e = dmalloc(&P.invDc, n);
+  if (!e) e = dmalloc(&P.val_s, nnz);
+  if (!e) e = dmalloc(&P.rowred, m);
+  if (!e) e = dmalloc(&P.colred, n);
+  if (!e) e = dmalloc(&P.tmp_rows, big);
+  if (!e) e = dmalloc(&P.tmp_scan, scan_tmp_ints(big));
+  if (!e) e = dmalloc(&P.red, kRedBlocks * 8);
+  if (!e) e = dmalloc(&P.red_out, 16);
+  if (!e) e = dmalloc(&P.At.rp, n + 1);
+  if (!e) e = dmalloc(&P.At.col, nnz);
+  if (!e) e = dmalloc(&P.permT, nnz);
+  if (!e) e = dmalloc(&pb->dx, n);
+  if (!e) e = dmalloc(&pb->dy, m);
+  if (!e) e = dmalloc(&pb->dxa, n);
+  if (!e) e = dmalloc(&pb->dya, m);
+  if (!e) e = dmalloc(&pb->d6, 8);
+  if (is_qp) {
+    if (!e) e = dmalloc(&P.D, n);
+    if (!e) e = dmalloc(&P.D_s, n);
+    if (!e) e = dmalloc(&P.F.rp, n + 1);
+    if (!e) e = dmalloc(&P.F.col, f_nnz);
+    if (!e) e = dmalloc(&P.fval, f_nnz);
+    if (!e) e = dmalloc(&P.fval_s, f_nnz);
+    if (!e) e = dmalloc(&P.Ft.rp, r + 1);
+    if (!e) e = dmalloc(&P.Ft.col, f_nnz);
+    if (!e) e = dmalloc(&P.permF, f_nnz);
+  }
+  P.A.rows = m;
+  P.A.cols = n;
+  P.A.nnz = (int)nnz;
+  P.F.rows = n;
+  P.F.cols = r;
+  P.F.nnz = (int)f_nnz;
+  long long* rp64 = nullptr;
+  int* flags = nullptr;
+  if (!e) e = dmalloc(&rp64, (size_t)std::max(m, n) + 1);
+  if (!e) e = dmalloc(&flags, 1);
+  if (!e) e = cudaMemsetAsync(flags, 0, sizeof(int), P.s);
+  cudaStream_t s = P.s;
+  if (!e) e = copy_in(rp64, row_ptr, sizeof(int64_t) * (m + 1), kind, s);
+  if (!e)
+    k_rowptr64_to_32<<<(m + 256) / 256, 256, 0, s>>>(rp64, P.A.rp, m, nnz, flags);
+  if (!e) e = copy_in(P.A.col, col_idx, sizeof(int32_t) * nnz, kind, s);
+  if (!e) e = copy_in(P.val, val, sizeof(double) * nnz, kind, s);
+  if (!e) e = copy_in(P.c, c, sizeof(double) * n, kind, s);
+  if (!e) e = copy_in(P.l, l, sizeof(double) * n, kind, s);
+  if (!e) e = copy_in(P.u, u, sizeof(double) * n, kind, s);
+  if (!e) e = copy_in(P.lc, lc, sizeof(double) * m, kind, s);
+  if (!e) e = copy_in(P.uc, uc, sizeof(double) * m, kind, s);
+  if (is_qp) {
+    if (!e) e = copy_in(P.D, D, sizeof(double) * n, kind, s);
+    if (!e) e = cudaStreamSynchronize(s);  // rp64 reused below
+    if (!e) e = copy_in(rp64, f_row_ptr, sizeof(int64_t) * (n + 1), kind, s);
+    if (!e)
+      k_rowptr64_to_32<<<(n + 256) / 256, 256, 0, s>>>(rp64, P.F.rp, n, f_nnz, flags);
+    if (!e) e = copy_in(P.F.col, f_col_idx, sizeof(int32_t) * f_nnz, kind, s);
+    if (!e) e = copy_in(P.fval, f_val, sizeof(double) * f_nnz, kind, s);
+  }
+  if (!e && m > 0) k_check_csr<<<(m + 255) / 256, 256, 0, s>>>(P.A.rp, P.A.col, P.val, m, n, flags);
+  if (!e && is_qp && n > 0)
+    k_check_csr<<<(n + 255) / 256, 256, 0, s>>>(P.F.rp, P.F.col, P.fval, n, r, flags);
+  if (!e)
+    k_check_vecs<<<std::max(1, std::min(4096, (std::max(m, n) + 255) / 256)), 256, 0, s>>>(
+        P.c, P.l, P.u, n, P.lc, P.uc, m, is_qp ? P.D : nullptr, flags);
+  int hflags = 0;
+  if (!e) e = cudaGetLastError();
+  if (!e) e = cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (rp64) cudaFree(rp64);
+  if (flags) cudaFree(flags);
+  if (e) {
+    destroy_problem(pb);
+    return cuda_fail(e, "create");
+  }
+  if (hflags) {
+    destroy_problem(pb);
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "invalid problem data: " + flags_message(hflags));
+  }
+  *out = pb;
+  return MPAX_OK;
+}
+
+mpax_status check_options(const mpax_options* o) {
+  if (!o) return fail(MPAX_ERR_INVALID_ARGUMENT, "opts must not be NULL");
+  if (o->check_every < 1 || o->check_every > kMaxCheckEvery)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "check_every must be in [1, 1024]");
+  if (o->precision != MPAX_PREC_FP64 && o->precision != MPAX_PREC_MIXED)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "precision must be MPAX_PREC_FP64 or MPAX_PREC_MIXED");
+  if (!(o->eps_abs >= 0) || !(o->eps_rel >= 0))
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "tolerances must be non-negative");
+  if (o->iteration_limit < 1)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "iteration_limit must be >= 1");
+  if (!(o->reflection_gamma >= 0.0 && o->reflection_gamma <= 1.0))
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "reflection_gamma must be in [0, 1]");
+  if (o->ruiz_iters < 0) return fail(MPAX_ERR_INVALID_ARGUMENT, "ruiz_iters must be >= 0");
+  if (!(o->step_safety > 0.0 && o->step_safety < 1.0))
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "step_safety must be in (0, 1)");
+  if (o->power_max_iter < 1) return fail(MPAX_ERR_INVALID_ARGUMENT, "power_max_iter must be >= 1");
+  if (o->feasibility_polishing)
+    return fail(MPAX_ERR_UNSUPPORTED, "feasibility polishing is not built");
+  if (!(o->time_limit >= 0)) return fail(MPAX_ERR_INVALID_ARGUMENT, "time_limit must be >= 0");
+  return MPAX_OK;
+}
+
+mpax_status do_prepare(mpax_problem* pb, const mpax_options* o, long long* launches) {
+  ProblemData& P = pb->P;
+  cudaStream_t s = P.s;
+  // structure: transpose(s) and work-item schedules
+  TRY_CUDA(transpose_csr(P.A, P.At, P.permT, P.tmp_rows, P.tmp_scan, s), "transpose");
+  *launches += 6;
+  if (P.is_qp) {
+    TRY_CUDA(transpose_csr(P.F, P.Ft, P.permF, P.tmp_rows, P.tmp_scan, s), "transpose F");
+    *launches += 6;
+  }
+  P.transposed = true;
+  TRY_CUDA(build_schedule(P.A, P.schedA, s, P.tmp_rows, P.tmp_scan), "schedule A");
+  TRY_CUDA(build_schedule(P.At, P.schedAt, s, P.tmp_rows, P.tmp_scan), "schedule A^T");
+  *launches += 12;
+  if (P.is_qp) {
+    TRY_CUDA(build_schedule(P.F, P.schedF, s, P.tmp_rows, P.tmp_scan), "schedule F");
+    TRY_CUDA(build_schedule(P.Ft, P.schedFt, s, P.tmp_rows, P.tmp_scan), "schedule F^T");
+    *launches += 12;
+  }
+  P.scheduled = true;
+  TRY_CUDA(compute_scaling(P, o->ruiz_iters, o->pock_chambolle != 0), "scaling");
+  *launches += 5 * o->ruiz_iters + 8;
+  TRY_CUDA(bound_and_cost_norms(P), "norms");
+  *launches += 2;
+  const int prec = o->precision;
+  if (!pb->eng[prec]) {
+    cudaError_t e;
+    pb->eng[prec] = make_engine(&P, prec, &e);
+    if (!pb->eng[prec]) return cuda_fail(e, "engine allocation");
+  }
+  EngineBase* eng = pb->eng[prec];
+  TRY_CUDA(eng->load_values(), "load values");
+  *launches += 9;
+  TRY_CUDA(eng->init_state(*o, launches), "init state");
+  pb->cur = prec;
+  pb->prepared = true;
+  pb->last_opts = *o;
+  return MPAX_OK;
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+}  // namespace
+
+// ============================================================================
+// exported functions
+// ============================================================================
+
+extern "C" {
+
+const char* mpax_version(void) { return "mpax-gb300 0.1.0 (sm_103a)"; }
+
+const char* mpax_last_error(void) { return g_err.c_str(); }
+
+const char* mpax_status_string(mpax_status s) {
+  switch (s) {
+    case MPAX_OK: return "ok";
+    case MPAX_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case MPAX_ERR_CUDA: return "CUDA error";
+    case MPAX_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case MPAX_ERR_NOT_SOLVED: return "not solved";
+    case MPAX_ERR_DEVICE_TIMEOUT: return "device timeout";
+    case MPAX_ERR_NUMERICAL: return "numerical error";
+    case MPAX_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+void mpax_options_default(mpax_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->verbose = 0;
+  o->display_frequency = 10;
+  o->warm_start = 0;
+  o->feasibility_polishing = 0;
+  o->eps_abs = 1e-4;
+  o->eps_rel = 1e-4;
+  o->eps_primal_infeasible = 1e-8;
+  o->eps_dual_infeasible = 1e-8;
+  o->eps_feas_polish = 1e-6;
+  o->iteration_limit = INT64_MAX;
+  o->time_limit = INFINITY;
+  o->precision = MPAX_PREC_FP64;
+  o->check_every = 64;
+  o->ruiz_iters = 10;
+  o->pock_chambolle = 1;
+  o->reflection_gamma = 1.0;
+  o->restart_sufficient = 0.2;
+  o->restart_necessary = 0.8;
+  o->restart_artificial = 0.36;
+  o->primal_weight_smoothing = 0.5;
+  o->step_safety = 0.998;
+  o->power_max_iter = 100;
+  o->power_tol = 1e-4;
+  o->use_graphs = 1;
+  o->profile_kernels = 0;
+}
+
+mpax_status mpax_lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                           const int32_t* col_idx, const double* val, const double* c,
+                           const double* lc, const double* uc, const double* l,
+                           const double* u, mpax_mem_kind kind, void* cuda_stream,
+                           mpax_problem** out) {
+  return create_common(m, n, nnz, row_ptr, col_idx, val, c, lc, uc, l, u, nullptr, 0, 0,
+                       nullptr, nullptr, nullptr, false, kind, cuda_stream, out);
+}
+
+mpax_status mpax_qp_create_diag_lowrank(
+    int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+    const double* val, const double* c, const double* lc, const double* uc, const double* l,
+    const double* u, const double* D, int32_t r, int64_t f_nnz, const int64_t* f_row_ptr,
+    const int32_t* f_col_idx, const double* f_val, mpax_mem_kind kind, void* cuda_stream,
+    mpax_problem** out) {
+  return create_common(m, n, nnz, row_ptr, col_idx, val, c, lc, uc, l, u, D, r, f_nnz,
+                       f_row_ptr, f_col_idx, f_val, true, kind, cuda_stream, out);
+}
+
+mpax_status mpax_prepare(mpax_problem* pb, const mpax_options* opts) {
+  if (!pb) return fail(MPAX_ERR_INVALID_ARGUMENT, "problem is NULL");
+  mpax_status st = check_options(opts);
+  if (st) return st;
+  TRY_CUDA(order_after_user(pb), "stream order");
+  long long launches = 0;
+  st = do_prepare(pb, opts, &launches);
+  if (st) return st;
+  TRY_CUDA(cudaStreamSynchronize(pb->P.s), "prepare");
+  TRY_CUDA(order_user_after(pb), "stream order");
+  return MPAX_OK;
+}
+
+mpax_status mpax_solve(mpax_problem* pb, const mpax_options* opts, const double* x0,
+                       const double* y0, mpax_mem_kind kind) {
+  if (!pb) return fail(MPAX_ERR_INVALID_ARGUMENT, "problem is NULL");
+  mpax_status st = check_options(opts);
+  if (st) return st;
+  if (kind != MPAX_MEM_HOST && kind != MPAX_MEM_DEVICE)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "bad memory kind");
+  ProblemData& P = pb->P;
+  const double t0 = now_s();
+  TRY_CUDA(order_after_user(pb), "stream order");
+  long long launches = 0;
+  st = do_prepare(pb, opts, &launches);
+  if (st) return st;
+  TRY_CUDA(cudaStreamSynchronize(P.s), "prepare");
+  const double t1 = now_s();
+  const double* x0d = nullptr;
+  const double* y0d = nullptr;
+  if (x0) {
+    if (kind == MPAX_MEM_HOST) {
+      TRY_CUDA(copy_in(pb->dx, x0, sizeof(double) * P.n, kind, P.s), "copy x0");
+      x0d = pb->dx;
+    } else {
+      x0d = x0;
+    }
+  }
+  if (y0) {
+    if (kind == MPAX_MEM_HOST) {
+      TRY_CUDA(copy_in(pb->dy, y0, sizeof(double) * P.m, kind, P.s), "copy y0");
+      y0d = pb->dy;
+    } else {
+      y0d = y0;
+    }
+  }
+  EngineBase* eng = pb->eng[pb->cur];
+  TRY_CUDA(eng->init_iterate(x0d, y0d), "init iterate");
+  launches += 15;
+  RunInfo info;
+  cudaError_t e = eng->run(*opts, &info);
+  if (e) return cuda_fail(e, "solve");
+  DevState h;
+  TRY_CUDA(eng->read_state(&h), "read state");
+  TRY_CUDA(order_user_after(pb), "stream order");
+  mpax_stats& S = pb->stats;
+  std::memset(&S, 0, sizeof(S));
+  S.termination = info.termination;
+  S.precision = opts->precision;
+  S.iterations = info.iterations;
+  S.restarts = info.restarts;
+  S.kkt_checks = info.checks;
+  S.primal_obj = h.pobj;
+  S.dual_obj = h.dobj;
+  S.gap = h.gap;
+  S.primal_res = h.primal_res;
+  S.dual_res = h.dual_res;
+  S.rel_kkt = h.rel_kkt;
+  S.omega = h.omega;
+  S.eta = h.eta;
+  S.norm_A = h.norm_A;
+  S.norm_Q = h.norm_Q;
+  S.prepare_seconds = t1 - t0;
+  S.solve_seconds = now_s() - t0;
+  S.kernel_launches = launches + info.launches;
+  for (int i = 0; i < 4; ++i) {
+    S.profile_ms[i] = info.profile_ms[i];
+    S.profile_launches[i] = info.profile_launches[i];
+  }
+  pb->solved = true;
+  pb->last_opts = *opts;
+  if (info.termination == MPAX_TERM_NUMERICAL_ERROR)
+    return fail(MPAX_ERR_NUMERICAL, "NaN or Inf appeared in the iteration");
+  return MPAX_OK;
+}
+
+mpax_status mpax_get_solution(const mpax_problem* cpb, double* x, double* y,
+                              mpax_mem_kind kind) {
+  mpax_problem* pb = const_cast<mpax_problem*>(cpb);
+  if (!pb) return fail(MPAX_ERR_INVALID_ARGUMENT, "problem is NULL");
+  if (!pb->solved) return fail(MPAX_ERR_NOT_SOLVED, "call mpax_solve first");
+  const ProblemData& P = pb->P;
+  EngineBase* eng = pb->eng[pb->cur];
+  TRY_CUDA(eng->get_solution(pb->dx, pb->dy), "get solution");
+  if (x) TRY_CUDA(copy_out(x, pb->dx, sizeof(double) * P.n, kind, P.s), "copy x");
+  if (y) TRY_CUDA(copy_out(y, pb->dy, sizeof(double) * P.m, kind, P.s), "copy y");
+  TRY_CUDA(cudaStreamSynchronize(P.s), "get solution");
+  return MPAX_OK;
+}
+
+mpax_status mpax_get_stats(const mpax_problem* pb, mpax_stats* stats) {
+  if (!pb || !stats) return fail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  *stats = pb->stats;
+  if (!pb->solved) return fail(MPAX_ERR_NOT_SOLVED, "call mpax_solve first");
+  return MPAX_OK;
+}
+
+void mpax_destroy(mpax_problem* pb) { destroy_problem(pb); }
+
+mpax_status mpax_get_scaling(const mpax_problem* cpb, double* Dr, double* Dc, double* info,
+                             mpax_mem_kind kind) {
+  mpax_problem* pb = const_cast<mpax_problem*>(cpb);
+  if (!pb) return fail(MPAX_ERR_INVALID_ARGUMENT, "problem is NULL");
+  if (!pb->prepared) return fail(MPAX_ERR_NOT_SOLVED, "call mpax_prepare first");
+  const ProblemData& P = pb->P;
+  if (Dr) TRY_CUDA(copy_out(Dr, P.Dr, sizeof(double) * P.m, kind, P.s), "copy Dr");
+  if (Dc) TRY_CUDA(copy_out(Dc, P.Dc, sizeof(double) * P.n, kind, P.s), "copy Dc");
+  if (info) {
+    DevState h;
+    TRY_CUDA(pb->eng[pb->cur]->read_state(&h), "read state");
+    const double v[4] = {h.norm_A, h.norm_Q, h.eta, h.omega};
+    if (kind == MPAX_MEM_HOST) std::memcpy(info, v, sizeof(v));
+    else TRY_CUDA(cudaMemcpyAsync(info, v, sizeof(v), cudaMemcpyHostToDevice, P.s), "copy info");
+  }
+  TRY_CUDA(cudaStreamSynchronize(P.s), "get scaling");
+  return MPAX_OK;
+}
+
+mpax_status mpax_get_transpose(const mpax_problem* cpb, int64_t* rowptr_t, int32_t* col_t,
+                               double* val_t, mpax_mem_kind kind) {
+  mpax_problem* pb = const_cast<mpax_problem*>(cpb);
+  if (!pb) return fail(MPAX_ERR_INVALID_ARGUMENT, "problem is NULL");
+  if (!pb->P.transposed) return fail(MPAX_ERR_NOT_SOLVED, "call mpax_prepare first");
+  const ProblemData& P = pb->P;
+  cudaStream_t s = P.s;
+  double* v = nullptr;
+  cudaError_t e = dmalloc(&v, P.nnz);
+  if (!e && P.nnz > 0) e = gather_cast<double>(P.val, P.permT, v, P.nnz, s);
+  if (!e) {
+    // widen the row pointers on the host side of the copy
+    std::vector<int> h(P.n + 1);
+    e = cudaMemcpyAsync(h.data(), P.At.rp, sizeof(int) * (P.n + 1), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    std::vector<long long> h64(h.begin(), h.end());
+    if (!e && rowptr_t) {
+      if (kind == MPAX_MEM_HOST) std::memcpy(rowptr_t, h64.data(), sizeof(long long) * (P.n + 1));
+      else e = cudaMemcpyAsync(rowptr_t, h64.data(), sizeof(long long) * (P.n + 1), cudaMemcpyHostToDevice, s);
+    }
+  }
+  if (!e && col_t) e = copy_out(col_t, P.At.col, sizeof(int) * P.nnz, kind, s);
+  if (!e && val_t) e = copy_out(val_t, v, sizeof(double) * P.nnz, kind, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (v) cudaFree(v);
+  if (e) return cuda_fail(e, "get transpose");
+  return MPAX_OK;
+}
+
+mpax_status mpax_set_iterate(mpax_problem* pb, const double* x, const double* y,
+                             const double* x_aux, const double* y_aux, int64_t k, double tau,
+                             double sigma, mpax_mem_kind kind) {
+  if (!pb) return fail(MPAX_ERR_INVALID_ARGUMENT, "problem is NULL");
+  if (!pb->prepared) return fail(MPAX_ERR_NOT_SOLVED, "call mpax_prepare first");
+  if (k < 0 || !(tau > 0) || !(sigma > 0))
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "k >= 0, tau > 0 and sigma > 0 required");
+  const ProblemData& P = pb->P;
+  if (bad_ptr(x, P.n) || bad_ptr(x_aux, P.n) || bad_ptr(y, P.m) || bad_ptr(y_aux, P.m))
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "NULL iterate array");
+  TRY_CUDA(copy_in(pb->dx, x, sizeof(double) * P.n, kind, P.s), "copy x");
+  TRY_CUDA(copy_in(pb->dxa, x_aux, sizeof(double) * P.n, kind, P.s), "copy x_aux");
+  TRY_CUDA(copy_in(pb->dy, y, sizeof(double) * P.m, kind, P.s), "copy y");
+  TRY_CUDA(copy_in(pb->dya, y_aux, sizeof(double) * P.m, kind, P.s), "copy y_aux");
+  TRY_CUDA(pb->eng[pb->cur]->set_iterate(pb->dx, pb->dy, pb->dxa, pb->dya, k, tau, sigma,
+                                         pb->last_opts.reflection_gamma),
+           "set iterate");
+  TRY_CUDA(cudaStreamSynchronize(P.s), "set iterate");
+  return MPAX_OK;
+}
+
+mpax_status mpax_iterate(mpax_problem* pb, int64_t iters) {
+  if (!pb) return fail(MPAX_ERR_INVALID_ARGUMENT, "problem is NULL");
+  if (!pb->prepared) return fail(MPAX_ERR_NOT_SOLVED, "call mpax_prepare first");
+  if (iters < 0) return fail(MPAX_ERR_INVALID_ARGUMENT, "iters must be >= 0");
+  TRY_CUDA(pb->eng[pb->cur]->iterate(iters), "iterate");
+  TRY_CUDA(cudaStreamSynchronize(pb->P.s), "iterate");
+  return MPAX_OK;
+}
+
+mpax_status mpax_get_iterate(const mpax_problem* cpb, double* x, double* y, double* x_hat,
+                             double* y_hat, mpax_mem_kind kind) {
+  mpax_problem* pb = const_cast<mpax_problem*>(cpb);
+  if (!pb) return fail(MPAX_ERR_INVALID_ARGUMENT, "problem is NULL");
+  if (!pb->prepared) return fail(MPAX_ERR_NOT_SOLVED, "call mpax_prepare first");
+  const ProblemData& P = pb->P;
+  TRY_CUDA(pb->eng[pb->cur]->get_iterate(pb->dx, pb->dy, pb->dxa, pb->dya), "get iterate");
+  if (x) TRY_CUDA(copy_out(x, pb->dx, sizeof(double) * P.n, kind, P.s), "copy");
+  if (y) TRY_CUDA(copy_out(y, pb->dy, sizeof(double) * P.m, kind, P.s), "copy");
+  if (x_hat) TRY_CUDA(copy_out(x_hat, pb->dxa, sizeof(double) * P.n, kind, P.s), "copy");
+  if (y_hat) TRY_CUDA(copy_out(y_hat, pb->dya, sizeof(double) * P.m, kind, P.s), "copy");
+  TRY_CUDA(cudaStreamSynchronize(P.s), "get iterate");
+  return MPAX_OK;
+}
+
+mpax_status mpax_kkt(mpax_problem* pb, const double* x, const double* y, mpax_mem_kind kind,
+                     double* out) {
+  if (!pb || !out) return fail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  if (!pb->prepared) return fail(MPAX_ERR_NOT_SOLVED, "call mpax_prepare first");
+  const ProblemData& P = pb->P;
+  if (bad_ptr(x, P.n) || bad_ptr(y, P.m)) return fail(MPAX_ERR_INVALID_ARGUMENT, "NULL x or y");
+  TRY_CUDA(copy_in(pb->dx, x, sizeof(double) * P.n, kind, P.s), "copy x");
+  TRY_CUDA(copy_in(pb->dy, y, sizeof(double) * P.m, kind, P.s), "copy y");
+  TRY_CUDA(pb->eng[pb->cur]->kkt_at(pb->dx, pb->dy, pb->d6), "kkt");
+  TRY_CUDA(copy_out(out, pb->d6, sizeof(double) * 6, kind, P.s), "copy kkt");
+  TRY_CUDA(cudaStreamSynchronize(P.s), "kkt");
+  return MPAX_OK;
+}
+
+}  // extern "C"

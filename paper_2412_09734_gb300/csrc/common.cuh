@@ -1,0 +1,152 @@
+// Internal definitions shared by the library's translation units.
+//
+// Layout in HBM (one problem):
+//   A    : CSR, int32 row_ptr (m+1), int32 col (nnz), values (FP64 original +
+//          scaled copy in the iteration precision)
+//   A^T  : second CSR built on the device (int32 row_ptr (n+1), int32 col,
+//          int32 perm mapping each A^T entry to its A entry), values in the
+//          iteration precision
+//   work items of each CSR (int4 each, see Sched), partial-sum slots (FP64)
+//   vectors: originals in FP64; scaled data and iterates in the iteration
+//          precision; scaling factors in FP64
+//   DevState: scalars of the restarted iteration (step sizes, primal weight,
+//          counters, Halpern coefficient table), device resident
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+namespace mpax {
+
+constexpr int kWarp = 32;
+constexpr int kWarpsPerBlock = 8;
+constexpr int kBlock = kWarp * kWarpsPerBlock;
+// Work decomposition of a CSR matrix into warp items.
+constexpr int kSliceNnz = 256;  // nonzeros of one slice of a long row
+constexpr int kLongRow = 64;    // rows longer than this are cut into slices
+constexpr int kItemRows = 64;   // at most this many short rows per item
+constexpr int kShortCap = kSliceNnz + kLongRow;  // nonzeros of a packed item, upper bound
+constexpr int kMaxCheckEvery = 1024;
+
+// Number of FP64 partial-sum quantities kept per work item.
+constexpr int kPartQ = 6;
+
+// Work item encoding (int4):
+//   packed short rows: {r0, r1, -1, 0}    rows [r0, r1), every row <= kLongRow nnz
+//   slice of a long row: {r, s, S, first}  slice s of S, `first` = index of slice 0
+struct Sched {
+  int rows = 0;
+  int n_items = 0;
+  int4* items = nullptr;
+  int* cnt = nullptr;      // arrival counters of sliced rows (self-resetting)
+  void* carry = nullptr;   // per-item partial row sums of sliced rows (8 bytes each)
+  double* part = nullptr;  // kPartQ * n_items FP64 partials
+};
+
+struct Csr {
+  int rows = 0, cols = 0, nnz = 0;
+  int* rp = nullptr;
+  int* col = nullptr;
+};
+
+// Scalars of the iteration, device resident.  Written by the finalize kernel
+// at every check, read by every fused kernel.
+struct DevState {
+  double tau, sigma, inv_sigma, omega, eta, gamma;
+  double norm_A, norm_Q, step_safety;
+  double r_anchor, r_prev;
+  double eps_abs, eps_rel, r_suff, r_nec, r_art, pw_smooth;
+  double b_norm, c_norm;
+  double primal_res, dual_res, pobj, dobj, gap, rel_kkt;
+  double last_restart_metric;
+  double pw_scale, pw_nu;  // power iteration: 1/||g|| of the last round, estimate
+  long long total, k_base, restarts, checks, iter_limit;
+  int pw_done, pw_iters, pad2, pad3;
+  int done, restart_flag, termination, have_anchor;
+  int check_every, is_qp, nan_seen, pad;
+  // Halpern / averaging coefficient table for the current block:
+  // coef_a[i], coef_b[i] for inner counter k' = k_base - 1 + i (i = 0..block).
+  double coef_a[kMaxCheckEvery + 2];
+  double coef_b[kMaxCheckEvery + 2];
+};
+
+// Host-visible mirror written by the finalize kernel (pinned, mapped).
+struct HostStatus {
+  volatile long long total;
+  volatile long long restarts;
+  volatile long long checks;
+  volatile int done;
+  volatile int termination;
+  volatile double rel_kkt;
+  volatile double pobj, dobj, primal_res, dual_res, gap, omega;
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T clampv(T v, T lo, T hi) {
+  return fmin(fmax(v, lo), hi);
+}
+template <>
+__device__ __forceinline__ float clampv<float>(float v, float lo, float hi) {
+  return fminf(fmaxf(v, lo), hi);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T* p) {
+  return __ldcs(p);
+}
+template <typename T>
+__device__ __forceinline__ T ld_ro(const T* p) {
+  return __ldg(p);
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch helpers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+
+// Exclusive scan of `n` int32 counts into out[0..n] (out[n] = total).
+// `tmp` must hold scan_tmp_ints(n) ints.
+size_t scan_tmp_ints(int n);
+cudaError_t scan_exclusive(const int* in, int* out, int n, int* tmp, cudaStream_t s);
+
+// Build the warp-item schedule of a CSR (device); sched.items etc. allocated here.
+cudaError_t build_schedule(const Csr& A, Sched& sched, cudaStream_t s, int* tmp_rows,
+                           int* tmp_scan);
+void free_schedule(Sched& sched);
+
+// Device transpose: At.rp/At.col/perm allocated by the caller (n+1, nnz, nnz).
+cudaError_t transpose_csr(const Csr& A, Csr& At, int* perm, int* tmp_cnt, int* tmp_scan,
+                          cudaStream_t s);
+
+}  // namespace mpax
+
+namespace mpax {
+
+// Fixed-order block reduction (result valid in thread 0).  `sh` holds 32 values.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : T(0);
+    v = warp_sum(v);
+  }
+  return v;
+}
+
+}  // namespace mpax

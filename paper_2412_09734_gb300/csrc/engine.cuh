@@ -1,0 +1,43 @@
+// Iteration engine interface (one instance per problem and precision).
+#pragma once
+
+#include "../../include/mpax.h"
+#include "problem.cuh"
+
+namespace mpax {
+
+struct RunInfo {
+  int termination = 0;
+  long long iterations = 0, restarts = 0, checks = 0;
+  long long launches = 0;
+  double profile_ms[4] = {0, 0, 0, 0};
+  long long profile_launches[4] = {0, 0, 0, 0};
+  bool time_limit_hit = false;
+};
+
+class EngineBase {
+ public:
+  virtual ~EngineBase() = default;
+  // Scaled matrix values and vectors in the iteration precision (after
+  // compute_scaling and bound_and_cost_norms).
+  virtual cudaError_t load_values() = 0;
+  // Power iterations for ||A~|| (and ||Q~||), initial primal weight, step
+  // sizes, counters; Halpern/averaging tables for the first block.
+  virtual cudaError_t init_state(const mpax_options& o, long long* launches) = 0;
+  // Starting point from unscaled FP64 device vectors (nullable = zeros).
+  virtual cudaError_t init_iterate(const double* x0, const double* y0) = 0;
+  virtual cudaError_t run(const mpax_options& o, RunInfo* info) = 0;
+  // Lower-level access (scaled space, FP64 device vectors).
+  virtual cudaError_t set_iterate(const double* x, const double* y, const double* xa,
+                                  const double* ya, long long k, double tau, double sigma,
+                                  double gamma) = 0;
+  virtual cudaError_t iterate(long long iters) = 0;
+  virtual cudaError_t get_iterate(double* x, double* y, double* xh, double* yh) = 0;
+  virtual cudaError_t get_solution(double* x, double* y) = 0;  // unscaled
+  virtual cudaError_t kkt_at(const double* x, const double* y, double* out6) = 0;  // unscaled
+  virtual cudaError_t read_state(DevState* h) = 0;
+};
+
+EngineBase* make_engine(ProblemData* P, int precision, cudaError_t* err);
+
+}  // namespace mpax

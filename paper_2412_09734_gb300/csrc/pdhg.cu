@@ -1,0 +1,916 @@
+// Restarted PDHG iteration on the device: r^2HPDHG (Algorithm 1) for LP and
+// rAPDHG (Algorithm 2) for QP, in FP64 or mixed precision.
+//
+// A check block of `check_every` iterations is a fixed launch sequence
+//   [F~^T x_md (QP)], primal fused SpMV^T, dual fused SpMV     (per iteration)
+//   [F~^T xavg (QP)], KKT SpMV, KKT SpMV^T, finalize, restart (per check)
+// captured once as a CUDA graph and replayed.  The finalize kernel (one CTA)
+// reduces the FP64 partials in a fixed order, evaluates the relative KKT test,
+// the restart rule and the primal-weight update, and refreshes the device
+// state; a host thread only reads a mapped status word one block behind.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <map>
+#include <vector>
+
+#include "engine.cuh"
+#include "epilogues.cuh"
+#include "kernels.cuh"
+
+namespace mpax {
+
+namespace {
+
+int grid1(long long k) { return (int)std::max(1LL, std::min(4096LL, (k + 255) / 256)); }
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_fill(T* v, int n, T val) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    v[i] = val;
+}
+
+template <typename T>
+__global__ void k_copy(T* __restrict__ d, const T* __restrict__ s, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    d[i] = s[i];
+}
+
+// dst = src / D (src nullable: zeros), cast to T
+template <typename T>
+__global__ void k_div_in(const double* __restrict__ src, const double* __restrict__ D,
+                         T* __restrict__ dst, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = src ? (T)(src[i] / D[i]) : (T)0;
+}
+
+template <typename T>
+__global__ void k_to_double(const T* __restrict__ v, const double* __restrict__ D,
+                            double* __restrict__ out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = D ? D[i] * (double)v[i] : (double)v[i];
+}
+
+template <typename T>
+__global__ void k_from_double(const double* __restrict__ v, T* __restrict__ out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = (T)v[i];
+}
+
+// x^{n,k} rebuilt from (w, anchor) with coefficient slot idx (see EpiPrimalLP)
+template <typename T>
+__global__ void k_materialize_lp(T* __restrict__ out, const T* __restrict__ w,
+                                 const T* __restrict__ xa, const DevState* st, int idx, int n) {
+  const T a = (T)st->coef_a[idx], b = (T)st->coef_b[idx];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    out[j] = (a == (T)0) ? xa[j] : a * w[j] + b * xa[j];
+}
+
+// Halpern (LP) or averaging (QP) coefficients for a block starting at k_base.
+__device__ void fill_table(DevState* st, int len) {
+  const long long kb = st->k_base;
+  for (int i = threadIdx.x; i <= len + 1 && i < kMaxCheckEvery + 2; i += blockDim.x) {
+    if (st->is_qp) {
+      const double k = (double)(kb + i);
+      st->coef_a[i] = 2.0 / (k + 2.0);
+      st->coef_b[i] = 0.0;
+    } else {
+      const double kp = (double)(kb - 1 + i);
+      st->coef_a[i] = (kp + 1.0) / (kp + 2.0);
+      st->coef_b[i] = 1.0 / (kp + 2.0);
+    }
+  }
+}
+
+__global__ void k_set_table(DevState* st, long long k_base, int len) {
+  if (threadIdx.x == 0) st->k_base = k_base;
+  __syncthreads();
+  fill_table(st, len);
+}
+
+__global__ void k_set_steps(DevState* st, double tau, double sigma, double gamma) {
+  st->tau = tau;
+  st->sigma = sigma;
+  st->inv_sigma = 1.0 / sigma;
+  st->gamma = gamma;
+  st->done = 0;
+}
+
+__device__ void set_step_sizes(DevState* st) {
+  if (st->is_qp) {
+    const double sigma = st->eta * st->omega;
+    const double denom = st->norm_Q + sigma * st->norm_A * st->norm_A;
+    st->sigma = sigma;
+    st->tau = denom > 0.0 ? st->step_safety / denom : 1.0;
+  } else {
+    st->tau = st->eta / st->omega;
+    st->sigma = st->eta * st->omega;
+  }
+  st->inv_sigma = 1.0 / st->sigma;
+}
+
+struct InitParams {
+  double eps_abs, eps_rel, r_suff, r_nec, r_art, pw_smooth, step_safety, gamma;
+  long long iter_limit;
+  int check_every, is_qp;
+};
+
+// red: [0] ||c~||, [1] ||b~||, [2] ||c||, [3] ||b||  (norm_A, norm_Q already in st)
+__global__ void k_init_state(DevState* st, InitParams p, const double* red) {
+  if (threadIdx.x == 0) {
+    st->eps_abs = p.eps_abs;
+    st->eps_rel = p.eps_rel;
+    st->r_suff = p.r_suff;
+    st->r_nec = p.r_nec;
+    st->r_art = p.r_art;
+    st->pw_smooth = p.pw_smooth;
+    st->step_safety = p.step_safety;
+    st->gamma = p.gamma;
+    st->iter_limit = p.iter_limit;
+    st->check_every = p.check_every;
+    st->is_qp = p.is_qp;
+    const double nc = red[0], nb = red[1];
+    st->omega = (nc > 1e-10 && nb > 1e-10) ? nc / nb : 1.0;
+    st->c_norm = red[2];
+    st->b_norm = red[3];
+    st->eta = st->norm_A > 0.0 ? p.step_safety / st->norm_A : 1.0;
+    set_step_sizes(st);
+    st->total = 0;
+    st->k_base = 0;
+    st->restarts = 0;
+    st->checks = 0;
+    st->done = 0;
+    st->restart_flag = 0;
+    st->termination = 0;
+    st->have_anchor = 0;
+    st->r_anchor = 0.0;
+    st->r_prev = 0.0;
+    st->rel_kkt = INFINITY;
+  }
+  __syncthreads();
+  fill_table(st, p.check_every);
+}
+
+__global__ void k_power_start(DevState* st) {
+  st->pw_scale = 1.0;
+  st->pw_nu = 0.0;
+  st->pw_done = 0;
+  st->pw_iters = 0;
+}
+
+// One power-iteration round done: sum of squares of g in part[0..n).
+// mode 0 (A~^T A~): nu = sqrt(||g||); mode 1 (Q~): nu = ||g||.  v_next = g/||g||
+// through pw_scale.  Writes the estimate to norm_A or norm_Q.
+__global__ void k_power_finalize(const double* __restrict__ part, int n, DevState* st, int t,
+                                 double tol, int mode) {
+  __shared__ double sh[32];
+  if (st->pw_done) return;
+  double v = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) {
+    const double nrm = sqrt(v);
+    if (nrm == 0.0) {
+      st->pw_nu = 0.0;
+      st->pw_done = 1;
+    } else {
+      const double nu = (mode == 0) ? sqrt(nrm) : nrm;
+      const double prev = st->pw_nu;
+      st->pw_scale = 1.0 / nrm;
+      st->pw_nu = nu;
+      if (t > 1 && fabs(nu - prev) <= tol * nu) st->pw_done = 1;
+    }
+    st->pw_iters = t;
+    if (mode == 0) st->norm_A = st->pw_nu;
+    else st->norm_Q = st->pw_nu;
+  }
+}
+
+__device__ double sum_slot(const double* part, int q, int n, double* sh) {
+  double v = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[(size_t)q * n + i];
+  return block_sum(v, sh);
+}
+
+// Check of Algorithm 1 / 2 after a block of `len` iterations.
+//   partAt slots: 0 sum(x^-x)^2, 1 sum(x^-x_anchor)^2 (QP: averages), 2..5 KKT column terms
+//   partA  slots: 0 sum(y^-y)^2, 1 sum(y^-y_anchor)^2, 2..3 KKT row terms
+__global__ void k_finalize_check(const double* __restrict__ partAt, int nAt,
+                                 const double* __restrict__ partA, int nA, DevState* st,
+                                 HostStatus* hs, int len, int next_len) {
+  __shared__ double sh[32];
+  __shared__ double vals[10];
+  if (st->done) return;
+  for (int q = 0; q < 6; ++q) {
+    const double v = sum_slot(partAt, q, nAt, sh);
+    if (threadIdx.x == 0) vals[q] = v;
+  }
+  for (int q = 0; q < 4; ++q) {
+    const double v = sum_slot(partA, q, nA, sh);
+    if (threadIdx.x == 0) vals[6 + q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double P0 = vals[0], P1 = vals[1], C0 = vals[2], C1 = vals[3], C2 = vals[4],
+                 C3 = vals[5], D0 = vals[6], D1 = vals[7], K0 = vals[8], K1 = vals[9];
+    st->total += len;
+    st->checks += 1;
+    const double nrp = sqrt(K0), nrd = sqrt(C0);
+    const double pobj = C1 + 0.5 * C3;
+    const double dobj = K1 + C2 - 0.5 * C3;
+    const double gap = fabs(pobj - dobj);
+    const double bn = st->b_norm, cn = st->c_norm;
+    const double rel = fmax(fmax(nrp / (1.0 + bn), nrd / (1.0 + cn)),
+                            gap / (1.0 + fabs(pobj) + fabs(dobj)));
+    st->primal_res = nrp;
+    st->dual_res = nrd;
+    st->pobj = pobj;
+    st->dobj = dobj;
+    st->gap = gap;
+    st->rel_kkt = rel;
+    const double ea = st->eps_abs, er = st->eps_rel;
+    const bool conv = nrp <= ea + er * bn && nrd <= ea + er * cn &&
+                      gap <= ea + er * (fabs(pobj) + fabs(dobj));
+    int term = 0;
+    if (!isfinite(rel) || !isfinite(P0) || !isfinite(D0) || !isfinite(P1) || !isfinite(D1))
+      term = MPAX_TERM_NUMERICAL_ERROR;
+    else if (conv) term = MPAX_TERM_OPTIMAL;
+    else if (st->total >= st->iter_limit) term = MPAX_TERM_ITERATION_LIMIT;
+    st->restart_flag = 0;
+    if (term) {
+      st->termination = term;
+      st->done = 1;
+    } else {
+      const double r = st->is_qp ? rel : sqrt(st->omega * P0 + D0 / st->omega);
+      const long long kc = st->k_base + len;
+      const bool restart = !st->have_anchor || r <= st->r_suff * st->r_anchor ||
+                           (r <= st->r_nec * st->r_anchor && r > st->r_prev) ||
+                           (double)kc >= st->r_art * (double)st->total;
+      st->last_restart_metric = r;
+      if (restart) {
+        const double dx = sqrt(P1), dy = sqrt(D1);
+        if (dx > 1e-10 && dy > 1e-10) {
+          const double th = st->pw_smooth;
+          st->omega = exp(th * log(dy / dx) + (1.0 - th) * log(st->omega));
+        }
+        set_step_sizes(st);
+        st->k_base = 0;
+        st->have_anchor = 1;
+        st->r_anchor = r;
+        st->r_prev = r;
+        st->restarts += 1;
+        st->restart_flag = 1;
+      } else {
+        st->r_prev = r;
+        st->k_base = kc;
+      }
+    }
+    hs->total = st->total;
+    hs->restarts = st->restarts;
+    hs->checks = st->checks;
+    hs->rel_kkt = rel;
+    hs->pobj = pobj;
+    hs->dobj = dobj;
+    hs->primal_res = nrp;
+    hs->dual_res = nrd;
+    hs->gap = gap;
+    hs->omega = st->omega;
+    hs->termination = st->termination;
+    __threadfence_system();
+    hs->done = st->done;
+    __threadfence_system();
+  }
+  __syncthreads();
+  if (!st->done) fill_table(st, next_len);
+}
+
+// Restart of Algorithm 1: anchor and iterate <- (x^, y^).
+template <typename T>
+__global__ void k_restart_lp(const DevState* st, int n, int m, const T* __restrict__ xhat,
+                             T* __restrict__ xa, T* __restrict__ xbar, T* __restrict__ wbuf,
+                             const T* __restrict__ yhat, T* __restrict__ ya, T* __restrict__ y) {
+  if (st->done || !st->restart_flag) return;
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    const T v = xhat[j];
+    xa[j] = v;
+    xbar[j] = v;
+    wbuf[j] = v;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const T v = yhat[i];
+    ya[i] = v;
+    y[i] = v;
+  }
+}
+
+// Restart of Algorithm 2: x, anchor <- xavg; y, anchor <- yavg.
+template <typename T>
+__global__ void k_restart_qp(const DevState* st, int n, int m, const T* __restrict__ xavg,
+                             T* __restrict__ x, T* __restrict__ xanc,
+                             const T* __restrict__ yavg, T* __restrict__ y,
+                             T* __restrict__ yanc) {
+  if (st->done || !st->restart_flag) return;
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    const T v = xavg[j];
+    x[j] = v;
+    xanc[j] = v;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const T v = yavg[i];
+    y[i] = v;
+    yanc[i] = v;
+  }
+}
+
+__global__ void k_kkt_finalize(const double* __restrict__ partAt, int nAt,
+                               const double* __restrict__ partA, int nA, const DevState* st,
+                               double* out) {
+  __shared__ double sh[32];
+  __shared__ double vals[6];
+  for (int q = 0; q < 4; ++q) {
+    const double v = sum_slot(partAt, 2 + q, nAt, sh);
+    if (threadIdx.x == 0) vals[q] = v;
+  }
+  for (int q = 0; q < 2; ++q) {
+    const double v = sum_slot(partA, 2 + q, nA, sh);
+    if (threadIdx.x == 0) vals[4 + q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double nrp = sqrt(vals[4]), nrd = sqrt(vals[0]);
+    const double pobj = vals[1] + 0.5 * vals[3];
+    const double dobj = vals[5] + vals[2] - 0.5 * vals[3];
+    const double gap = fabs(pobj - dobj);
+    out[0] = nrp;
+    out[1] = nrd;
+    out[2] = pobj;
+    out[3] = dobj;
+    out[4] = gap;
+    out[5] = fmax(fmax(nrp / (1.0 + st->b_norm), nrd / (1.0 + st->c_norm)),
+                  gap / (1.0 + fabs(pobj) + fabs(dobj)));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch helper
+// ---------------------------------------------------------------------------
+
+template <typename T, class In, class Epi>
+void launch_spmv(const Sched& sc, const Csr& K, const T* val, In in, Epi epi, int q0,
+                 cudaStream_t s) {
+  if (sc.n_items == 0) return;
+  SpmvArgs<T> a;
+  a.items = sc.items;
+  a.n_items = sc.n_items;
+  a.rp = K.rp;
+  a.col = K.col;
+  a.val = val;
+  a.cnt = sc.cnt;
+  a.carry = reinterpret_cast<T*>(sc.carry);
+  a.part = sc.part;
+  a.q0 = q0;
+  const int grid = (sc.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  spmv_fused<T, In, Epi><<<grid, kBlock, 0, s>>>(a, in, epi);
+}
+
+template <typename T>
+T* dalloc(size_t n, cudaError_t* e) {
+  T* p = nullptr;
+  if (*e == cudaSuccess) *e = cudaMalloc(&p, sizeof(T) * std::max<size_t>(n, 1));
+  return p;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Engine
+// ---------------------------------------------------------------------------
+
+template <typename T>
+class Engine final : public EngineBase {
+ public:
+  Engine(ProblemData* P, cudaError_t* e) : P_(P) {
+    const int m = P->m, n = P->n;
+    valA_ = dalloc<T>(P->nnz, e);
+    valAt_ = dalloc<T>(P->nnz, e);
+    c_ = dalloc<T>(n, e);
+    l_ = dalloc<T>(n, e);
+    u_ = dalloc<T>(n, e);
+    lc_ = dalloc<T>(m, e);
+    uc_ = dalloc<T>(m, e);
+    xbar_ = dalloc<T>(n, e);
+    wbuf_ = dalloc<T>(n, e);
+    xa_ = dalloc<T>(n, e);
+    xhat_ = dalloc<T>(n, e);
+    xprev_ = dalloc<T>(n, e);
+    pv_ = dalloc<T>(n, e);
+    pg_ = dalloc<T>(n, e);
+    y_ = dalloc<T>(m, e);
+    ya_ = dalloc<T>(m, e);
+    yhat_ = dalloc<T>(m, e);
+    yprev_ = dalloc<T>(m, e);
+    pw_ = dalloc<T>(m, e);
+    if (P->is_qp) {
+      x_ = dalloc<T>(n, e);
+      xavg_ = dalloc<T>(n, e);
+      xref_ = dalloc<T>(n, e);
+      xanc_ = dalloc<T>(n, e);
+      yavg_ = dalloc<T>(m, e);
+      yanc_ = dalloc<T>(m, e);
+      Ds_ = dalloc<T>(n, e);
+      fval_ = dalloc<T>(P->f_nnz, e);
+      ftval_ = dalloc<T>(P->f_nnz, e);
+      uvec_ = dalloc<T>(P->r, e);
+      uvec2_ = dalloc<T>(P->r, e);
+    }
+    st_ = dalloc<DevState>(1, e);
+    if (*e == cudaSuccess) *e = cudaHostAlloc(&hs_, sizeof(HostStatus), cudaHostAllocMapped);
+    if (*e == cudaSuccess) *e = cudaHostGetDevicePointer((void**)&hs_dev_, hs_, 0);
+    if (*e == cudaSuccess) *e = cudaMemsetAsync(st_, 0, sizeof(DevState), P->s);
+  }
+
+  ~Engine() override {
+    for (auto& kv : graphs_) cudaGraphExecDestroy(kv.second);
+    for (auto& ev : prof_ev_) cudaEventDestroy(ev);
+    void* bufs[] = {valA_, valAt_, c_,    l_,    u_,    lc_,   uc_,    xbar_, wbuf_,
+                    xa_,   xhat_,  xprev_, pv_,  pg_,   y_,    ya_,    yhat_, yprev_,
+                    pw_,   x_,     xavg_, xref_, xanc_, yavg_, yanc_,  Ds_,   fval_,
+                    ftval_, uvec_, uvec2_, st_};
+    for (void* b : bufs)
+      if (b) cudaFree(b);
+    if (hs_) cudaFreeHost(hs_);
+  }
+
+  cudaError_t load_values() override {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    cudaError_t e;
+    if ((e = cast_vec<T>(P.val_s, valA_, P.nnz, s))) return e;
+    if ((e = gather_cast<T>(P.val_s, P.permT, valAt_, P.nnz, s))) return e;
+    if ((e = scale_cast<T>(P.c, P.Dc, false, c_, P.n, s))) return e;
+    if ((e = scale_cast<T>(P.l, P.Dc, true, l_, P.n, s))) return e;
+    if ((e = scale_cast<T>(P.u, P.Dc, true, u_, P.n, s))) return e;
+    if ((e = scale_cast<T>(P.lc, P.Dr, false, lc_, P.m, s))) return e;
+    if ((e = scale_cast<T>(P.uc, P.Dr, false, uc_, P.m, s))) return e;
+    if (P.is_qp) {
+      if ((e = cast_vec<T>(P.D_s, Ds_, P.n, s))) return e;
+      if ((e = cast_vec<T>(P.fval_s, fval_, P.f_nnz, s))) return e;
+      if ((e = gather_cast<T>(P.fval_s, P.permF, ftval_, P.f_nnz, s))) return e;
+    }
+    return cudaGetLastError();
+  }
+
+  // ---- norms by power iteration -------------------------------------------
+  cudaError_t power(int mode, const mpax_options& o, long long* launches) {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    const int n = P.n;
+    k_power_start<<<1, 1, 0, s>>>(st_);
+    k_fill<T><<<grid1(n), 256, 0, s>>>(pv_, n, (T)(1.0 / std::sqrt((double)std::max(n, 1))));
+    *launches += 2;
+    T* v = pv_;
+    T* g = pg_;
+    const int* skip = &st_->pw_done;
+    for (int t = 1; t <= o.power_max_iter; ++t) {
+      EpiStore<T> e1{skip, nullptr, &st_->pw_scale, nullptr, nullptr, nullptr, 0};
+      EpiStore<T> e2{skip, g, nullptr, nullptr, nullptr, nullptr, 1};
+      if (mode == 0) {
+        e1.out = pw_;
+        launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{v}, e1, 0, s);
+        launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{pw_}, e2, 0, s);
+        k_power_finalize<<<1, 256, 0, s>>>(P.schedAt.part, P.schedAt.n_items, st_, t,
+                                           o.power_tol, 0);
+      } else {
+        e1.out = uvec_;
+        launch_spmv<T>(P.schedFt, P.Ft, ftval_, InPlain<T>{v}, e1, 0, s);
+        e2.diag = Ds_;
+        e2.din = v;
+        e2.d_scale = &st_->pw_scale;
+        launch_spmv<T>(P.schedF, P.F, fval_, InPlain<T>{uvec_}, e2, 0, s);
+        k_power_finalize<<<1, 256, 0, s>>>(P.schedF.part, P.schedF.n_items, st_, t,
+                                           o.power_tol, 1);
+      }
+      *launches += 3;
+      std::swap(v, g);
+      if (t % 8 == 0) {
+        int done = 0;
+        cudaError_t e = cudaMemcpyAsync(&done, &st_->pw_done, sizeof(int),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e) return e;
+        if (done) break;
+      }
+    }
+    return cudaGetLastError();
+  }
+
+  cudaError_t init_state(const mpax_options& o, long long* launches) override {
+    ProblemData& P = *P_;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(st_, 0, sizeof(DevState), P.s))) return e;
+    if (P.m > 0 && P.nnz > 0) {
+      if ((e = power(0, o, launches))) return e;
+    }
+    if (P.is_qp) {
+      if ((e = power(1, o, launches))) return e;
+    }
+    InitParams ip;
+    ip.eps_abs = o.eps_abs;
+    ip.eps_rel = o.eps_rel;
+    ip.r_suff = o.restart_sufficient;
+    ip.r_nec = o.restart_necessary;
+    ip.r_art = o.restart_artificial;
+    ip.pw_smooth = o.primal_weight_smoothing;
+    ip.step_safety = o.step_safety;
+    ip.gamma = o.reflection_gamma;
+    ip.iter_limit = o.iteration_limit;
+    ip.check_every = o.check_every;
+    ip.is_qp = P.is_qp ? 1 : 0;
+    k_init_state<<<1, 256, 0, P.s>>>(st_, ip, P.red_out);
+    *launches += 1;
+    gamma_one_ = (o.reflection_gamma == 1.0);
+    return cudaGetLastError();
+  }
+
+  cudaError_t init_iterate(const double* x0, const double* y0) override {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    const int n = P.n, m = P.m;
+    if (n) k_div_in<T><<<grid1(n), 256, 0, s>>>(x0, P.Dc, xhat_, n);
+    if (m) k_div_in<T><<<grid1(m), 256, 0, s>>>(y0, P.Dr, yhat_, m);
+    T* xs[] = {xa_, xbar_, wbuf_, xprev_, x_, xavg_, xref_, xanc_};
+    T* ys[] = {ya_, y_, yprev_, yavg_, yanc_};
+    for (T* d : xs)
+      if (d && n) k_copy<T><<<grid1(n), 256, 0, s>>>(d, xhat_, n);
+    for (T* d : ys)
+      if (d && m) k_copy<T><<<grid1(m), 256, 0, s>>>(d, yhat_, m);
+    use_xsrc_ = false;
+    return cudaGetLastError();
+  }
+
+  // ---- one block -------------------------------------------------------------
+  void launch_block(int len, bool plain, bool record_all, bool prof) {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    const bool qp = P.is_qp;
+    for (int it = 0; it < len; ++it) {
+      const bool last = (it == len - 1) && !plain;
+      const int rec = (record_all || last) ? 1 : 0;
+      const int chk = last ? 1 : 0;
+      if (!qp) {
+        EpiPrimalLP<T> ep{st_, xbar_, gamma_one_ ? xbar_ : wbuf_, xa_, c_, l_, u_,
+                          (it == 0 && use_xsrc_) ? xprev_ : nullptr, xhat_, xprev_, it, rec,
+                          chk};
+        prof_begin(prof, 0);
+        launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{y_}, ep, 0, s);
+        prof_end(prof, 0);
+        EpiDualLP<T> ed{st_, y_, ya_, lc_, uc_, yhat_, yprev_, it, rec, chk};
+        prof_begin(prof, 1);
+        launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{xbar_}, ed, 0, s);
+        prof_end(prof, 1);
+        launches_ += 2;
+      } else {
+        if (P.f_nnz > 0) {
+          EpiStore<T> eu{&st_->done, uvec_, nullptr, nullptr, nullptr, nullptr, 0};
+          launch_spmv<T>(P.schedFt, P.Ft, ftval_, InMomentum<T>{x_, xavg_, st_, it}, eu, 0, s);
+          launches_ += 1;
+        }
+        EpiPrimalQP<T> ep{st_, x_,  xavg_,    xref_,    xanc_,  c_,     l_,    u_,
+                          Ds_, P.F.rp, P.F.col, fval_, uvec_, xprev_, it,    rec, chk};
+        prof_begin(prof, 0);
+        launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{y_}, ep, 0, s);
+        prof_end(prof, 0);
+        EpiDualQP<T> ed{st_, y_, yavg_, yanc_, lc_, uc_, it, chk};
+        prof_begin(prof, 1);
+        launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{xref_}, ed, 0, s);
+        prof_end(prof, 1);
+        launches_ += 2;
+      }
+    }
+    use_xsrc_ = false;
+    if (plain) return;
+    kkt_launch(&st_->done, prof);
+    k_finalize_check<<<1, 512, 0, s>>>(P.schedAt.part, P.schedAt.n_items, P.schedA.part,
+                                       P.schedA.n_items, st_, hs_dev_, len, block_);
+    if (!qp) {
+      k_restart_lp<T><<<grid1(std::max(P.n, P.m)), 256, 0, s>>>(
+          st_, P.n, P.m, xhat_, xa_, xbar_, gamma_one_ ? xbar_ : wbuf_, yhat_, ya_, y_);
+    } else {
+      k_restart_qp<T><<<grid1(std::max(P.n, P.m)), 256, 0, s>>>(st_, P.n, P.m, xavg_, x_,
+                                                                 xanc_, yavg_, y_, yanc_);
+    }
+    launches_ += 2;
+  }
+
+  // KKT SpMVs at (x^, y^) (LP) or (xavg, yavg) (QP), partial slots 2..
+  void kkt_launch(const int* skip, bool prof) {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    const bool qp = P.is_qp;
+    const T* xv = qp ? xavg_ : xhat_;
+    const T* yv = qp ? yavg_ : yhat_;
+    if (qp && P.f_nnz > 0) {
+      EpiStore<T> eu{skip, uvec2_, nullptr, nullptr, nullptr, nullptr, 0};
+      launch_spmv<T>(P.schedFt, P.Ft, ftval_, InPlain<T>{xv}, eu, 0, s);
+      launches_ += 1;
+    }
+    EpiKktRow<T> er{skip, P.invDr, P.Dr, P.lc, P.uc, yv, 1};
+    prof_begin(prof, 2);
+    launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{xv}, er, 2, s);
+    prof_end(prof, 2);
+    EpiKktCol<T> ec{skip, P.invDc, P.Dc, P.c, P.l, P.u, xv, qp ? 1 : 0, P.D_s,
+                    P.F.rp, P.F.col, P.fval_s, uvec2_, 1};
+    prof_begin(prof, 3);
+    launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{yv}, ec, 2, s);
+    prof_end(prof, 3);
+    launches_ += 2;
+  }
+
+  // ---- profiling with CUDA events (no graphs) ---------------------------------
+  void prof_begin(bool prof, int cls) {
+    if (!prof) return;
+    if (prof_used_ + 2 > prof_ev_.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t ev;
+        cudaEventCreate(&ev);
+        prof_ev_.push_back(ev);
+      }
+    }
+    cudaEventRecord(prof_ev_[prof_used_], P_->s);
+    prof_cls_.push_back(cls);
+  }
+  void prof_end(bool prof, int) {
+    if (!prof) return;
+    cudaEventRecord(prof_ev_[prof_used_ + 1], P_->s);
+    prof_used_ += 2;
+  }
+  void prof_collect(RunInfo* info) {
+    for (size_t i = 0; i < prof_cls_.size(); ++i) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, prof_ev_[2 * i], prof_ev_[2 * i + 1]);
+      info->profile_ms[prof_cls_[i]] += ms;
+      info->profile_launches[prof_cls_[i]] += 1;
+    }
+    prof_cls_.clear();
+    prof_used_ = 0;
+  }
+
+  cudaError_t block_graph(int len, cudaGraphExec_t* out) {
+    auto itg = graphs_.find(len);
+    if (itg != graphs_.end()) {
+      *out = itg->second;
+      return cudaSuccess;
+    }
+    cudaStream_t s = P_->s;
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e) return e;
+    const long long before = launches_;
+    launch_block(len, false, false, false);
+    graph_launches_[len] = launches_ - before;
+    launches_ = before;
+    e = cudaStreamEndCapture(s, &g);
+    if (e) return e;
+    cudaGraphExec_t ge;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e) return e;
+    graphs_[len] = ge;
+    *out = ge;
+    return cudaSuccess;
+  }
+
+  cudaError_t run(const mpax_options& o, RunInfo* info) override {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    cudaError_t e;
+    block_ = o.check_every;
+    hs_->done = 0;
+    hs_->total = 0;
+    hs_->checks = 0;
+    launches_ = 0;
+    const bool prof = o.profile_kernels != 0;
+    const bool graphs = o.use_graphs != 0 && !prof;
+    const long long limit = o.iteration_limit;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaEvent_t ev[2];
+    cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+    long long launched = 0;
+    long long last_print = -1;
+    bool stop = false;
+    for (long long b = 0; !stop; ++b) {
+      const int len = (int)std::min<long long>(block_, limit - launched);
+      if (graphs) {
+        cudaGraphExec_t ge;
+        if ((e = block_graph(len, &ge))) break;
+        if ((e = cudaGraphLaunch(ge, s))) break;
+        launches_ += graph_launches_[len];
+      } else {
+        launch_block(len, false, false, prof);
+      }
+      if ((e = cudaEventRecord(ev[b & 1], s))) break;
+      launched += len;
+      if (prof) {
+        if ((e = cudaEventSynchronize(ev[b & 1]))) break;
+        prof_collect(info);
+        stop = hs_->done != 0;
+      } else if (b >= 1) {
+        if ((e = cudaEventSynchronize(ev[(b - 1) & 1]))) break;
+        stop = hs_->done != 0;
+      }
+      if (o.verbose && hs_->checks != last_print &&
+          hs_->checks % std::max(1, o.display_frequency) == 0) {
+        last_print = hs_->checks;
+        std::printf("mpax  iter %10lld  rel_kkt %.3e  pobj %+.8e  dobj %+.8e  omega %.3e\n",
+                    (long long)hs_->total, (double)hs_->rel_kkt, (double)hs_->pobj,
+                    (double)hs_->dobj, (double)hs_->omega);
+        std::fflush(stdout);
+      }
+      if (!stop && launched >= limit) {
+        if ((e = cudaEventSynchronize(ev[b & 1]))) break;
+        stop = true;
+      }
+      if (!stop && o.time_limit < INFINITY) {
+        const double el =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el >= o.time_limit) {
+          info->time_limit_hit = true;
+          stop = true;
+        }
+      }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e) return e;
+    if ((e = cudaStreamSynchronize(s))) return e;
+    DevState h;
+    if ((e = read_state(&h))) return e;
+    info->termination = h.termination;
+    if (!h.done && info->time_limit_hit) info->termination = MPAX_TERM_TIME_LIMIT;
+    info->iterations = h.total;
+    info->restarts = h.restarts;
+    info->checks = h.checks;
+    info->launches = launches_;
+    return cudaSuccess;
+  }
+
+  // ---- lower-level access -----------------------------------------------------
+  cudaError_t set_iterate(const double* x, const double* y, const double* xa, const double* ya,
+                          long long k, double tau, double sigma, double gamma) override {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    const int n = P.n, m = P.m;
+    gamma_one_ = (gamma == 1.0);
+    if (!P.is_qp) {
+      if (n) {
+        k_from_double<T><<<grid1(n), 256, 0, s>>>(x, xprev_, n);
+        k_from_double<T><<<grid1(n), 256, 0, s>>>(x, xbar_, n);
+        k_from_double<T><<<grid1(n), 256, 0, s>>>(x, wbuf_, n);
+        k_from_double<T><<<grid1(n), 256, 0, s>>>(xa, xa_, n);
+      }
+      if (m) {
+        k_from_double<T><<<grid1(m), 256, 0, s>>>(y, y_, m);
+        k_from_double<T><<<grid1(m), 256, 0, s>>>(ya, ya_, m);
+      }
+      use_xsrc_ = true;
+    } else {
+      if (n) {
+        k_from_double<T><<<grid1(n), 256, 0, s>>>(x, x_, n);
+        k_from_double<T><<<grid1(n), 256, 0, s>>>(xa, xavg_, n);
+        k_from_double<T><<<grid1(n), 256, 0, s>>>(xa, xanc_, n);
+      }
+      if (m) {
+        k_from_double<T><<<grid1(m), 256, 0, s>>>(y, y_, m);
+        k_from_double<T><<<grid1(m), 256, 0, s>>>(ya, yavg_, m);
+        k_from_double<T><<<grid1(m), 256, 0, s>>>(ya, yanc_, m);
+      }
+    }
+    st_is_qp_kernel();
+    k_set_steps<<<1, 1, 0, s>>>(st_, tau, sigma, gamma);
+    k_cur_ = k;
+    return cudaGetLastError();
+  }
+
+  void st_is_qp_kernel() {
+    // is_qp flag for the coefficient tables when set_iterate runs before a solve
+    InitParams ip{};
+    (void)ip;
+    const int v = P_->is_qp ? 1 : 0;
+    cudaMemcpyAsync(&st_->is_qp, &v, sizeof(int), cudaMemcpyHostToDevice, P_->s);
+    cudaStreamSynchronize(P_->s);
+  }
+
+  cudaError_t iterate(long long iters) override {
+    cudaStream_t s = P_->s;
+    while (iters > 0) {
+      const int len = (int)std::min<long long>(iters, kMaxCheckEvery);
+      k_set_table<<<1, 256, 0, s>>>(st_, k_cur_, len);
+      launch_block(len, true, true, false);
+      k_cur_ += len;
+      iters -= len;
+    }
+    return cudaGetLastError();
+  }
+
+  cudaError_t get_iterate(double* x, double* y, double* xh, double* yh) override {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    const int n = P.n, m = P.m;
+    if (!P.is_qp) {
+      k_set_table<<<1, 256, 0, s>>>(st_, k_cur_, 1);
+      if (n) {
+        k_materialize_lp<T><<<grid1(n), 256, 0, s>>>(pv_, gamma_one_ ? xbar_ : wbuf_, xa_, st_,
+                                                     0, n);
+        if (x) k_to_double<T><<<grid1(n), 256, 0, s>>>(pv_, nullptr, x, n);
+        if (xh) k_to_double<T><<<grid1(n), 256, 0, s>>>(xhat_, nullptr, xh, n);
+      }
+      if (m) {
+        if (y) k_to_double<T><<<grid1(m), 256, 0, s>>>(y_, nullptr, y, m);
+        if (yh) k_to_double<T><<<grid1(m), 256, 0, s>>>(yhat_, nullptr, yh, m);
+      }
+    } else {
+      if (n && x) k_to_double<T><<<grid1(n), 256, 0, s>>>(x_, nullptr, x, n);
+      if (n && xh) k_to_double<T><<<grid1(n), 256, 0, s>>>(xavg_, nullptr, xh, n);
+      if (m && y) k_to_double<T><<<grid1(m), 256, 0, s>>>(y_, nullptr, y, m);
+      if (m && yh) k_to_double<T><<<grid1(m), 256, 0, s>>>(yavg_, nullptr, yh, m);
+    }
+    return cudaGetLastError();
+  }
+
+  cudaError_t get_solution(double* x, double* y) override {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    const T* xv = P.is_qp ? xavg_ : xhat_;
+    const T* yv = P.is_qp ? yavg_ : yhat_;
+    if (x && P.n) k_to_double<T><<<grid1(P.n), 256, 0, s>>>(xv, P.Dc, x, P.n);
+    if (y && P.m) k_to_double<T><<<grid1(P.m), 256, 0, s>>>(yv, P.Dr, y, P.m);
+    return cudaGetLastError();
+  }
+
+  cudaError_t kkt_at(const double* x, const double* y, double* out6) override {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    T* xv = P.is_qp ? xavg_ : xhat_;
+    T* yv = P.is_qp ? yavg_ : yhat_;
+    if (P.n) k_div_in<T><<<grid1(P.n), 256, 0, s>>>(x, P.Dc, xv, P.n);
+    if (P.m) k_div_in<T><<<grid1(P.m), 256, 0, s>>>(y, P.Dr, yv, P.m);
+    // zero the partial slots so empty schedules contribute nothing
+    if (P.schedA.part) cudaMemsetAsync(P.schedA.part, 0, sizeof(double) * kPartQ * std::max(P.schedA.n_items, 1), s);
+    if (P.schedAt.part) cudaMemsetAsync(P.schedAt.part, 0, sizeof(double) * kPartQ * std::max(P.schedAt.n_items, 1), s);
+    kkt_launch(nullptr, false);
+    k_kkt_finalize<<<1, 256, 0, s>>>(P.schedAt.part, P.schedAt.n_items, P.schedA.part,
+                                     P.schedA.n_items, st_, out6);
+    return cudaGetLastError();
+  }
+
+  cudaError_t read_state(DevState* h) override {
+    cudaError_t e = cudaMemcpyAsync(h, st_, sizeof(DevState), cudaMemcpyDeviceToHost, P_->s);
+    if (e) return e;
+    return cudaStreamSynchronize(P_->s);
+  }
+
+ private:
+  ProblemData* P_;
+  T *valA_ = nullptr, *valAt_ = nullptr;
+  T *c_ = nullptr, *l_ = nullptr, *u_ = nullptr, *lc_ = nullptr, *uc_ = nullptr;
+  T *xbar_ = nullptr, *wbuf_ = nullptr, *xa_ = nullptr, *xhat_ = nullptr, *xprev_ = nullptr;
+  T *pv_ = nullptr, *pg_ = nullptr, *pw_ = nullptr;
+  T *y_ = nullptr, *ya_ = nullptr, *yhat_ = nullptr, *yprev_ = nullptr;
+  T *x_ = nullptr, *xavg_ = nullptr, *xref_ = nullptr, *xanc_ = nullptr;
+  T *yavg_ = nullptr, *yanc_ = nullptr;
+  T *Ds_ = nullptr, *fval_ = nullptr, *ftval_ = nullptr, *uvec_ = nullptr, *uvec2_ = nullptr;
+  DevState* st_ = nullptr;
+  HostStatus* hs_ = nullptr;
+  HostStatus* hs_dev_ = nullptr;
+  bool gamma_one_ = true;
+  bool use_xsrc_ = false;
+  long long k_cur_ = 0;
+  int block_ = 64;
+  long long launches_ = 0;
+  std::map<int, cudaGraphExec_t> graphs_;
+  std::map<int, long long> graph_launches_;
+  std::vector<cudaEvent_t> prof_ev_;
+  std::vector<int> prof_cls_;
+  size_t prof_used_ = 0;
+};
+
+EngineBase* make_engine(ProblemData* P, int precision, cudaError_t* err) {
+  *err = cudaSuccess;
+  EngineBase* e;
+  if (precision == MPAX_PREC_FP64) e = new Engine<double>(P, err);
+  else e = new Engine<float>(P, err);
+  if (*err != cudaSuccess) {
+    delete e;
+    return nullptr;
+  }
+  return e;
+}
+
+}  // namespace mpax

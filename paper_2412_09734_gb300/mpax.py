@@ -1,0 +1,329 @@
+"""Thin ctypes binding of libmpax_gb300.so (include/mpax.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  Functions keep the C names.  Array arguments may be numpy arrays
+(host memory, kind=MPAX_MEM_HOST) or CUDA torch tensors (device memory,
+kind=MPAX_MEM_DEVICE); the kind is inferred from the first array argument.
+A missing library raises at import of this module: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpax_gb300.so")
+
+MPAX_OK = 0
+MPAX_MEM_HOST = 0
+MPAX_MEM_DEVICE = 1
+MPAX_PREC_FP64 = 0
+MPAX_PREC_MIXED = 1
+TERMINATION = {0: "unsolved", 1: "optimal", 2: "primal_infeasible", 3: "dual_infeasible",
+               4: "iteration_limit", 5: "time_limit", 6: "numerical_error"}
+
+EXPORTED = ["mpax_version", "mpax_last_error", "mpax_status_string", "mpax_options_default",
+            "mpax_lp_create", "mpax_qp_create_diag_lowrank", "mpax_solve", "mpax_get_solution",
+            "mpax_get_stats", "mpax_destroy", "mpax_prepare", "mpax_get_scaling",
+            "mpax_get_transpose", "mpax_set_iterate", "mpax_iterate", "mpax_get_iterate",
+            "mpax_kkt"]
+
+
+class MpaxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"mpax status {status}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("verbose", ctypes.c_int32), ("display_frequency", ctypes.c_int32),
+        ("warm_start", ctypes.c_int32), ("feasibility_polishing", ctypes.c_int32),
+        ("eps_abs", ctypes.c_double), ("eps_rel", ctypes.c_double),
+        ("eps_primal_infeasible", ctypes.c_double), ("eps_dual_infeasible", ctypes.c_double),
+        ("eps_feas_polish", ctypes.c_double), ("iteration_limit", ctypes.c_int64),
+        ("time_limit", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("check_every", ctypes.c_int32),
+        ("ruiz_iters", ctypes.c_int32), ("pock_chambolle", ctypes.c_int32),
+        ("reflection_gamma", ctypes.c_double), ("restart_sufficient", ctypes.c_double),
+        ("restart_necessary", ctypes.c_double), ("restart_artificial", ctypes.c_double),
+        ("primal_weight_smoothing", ctypes.c_double), ("step_safety", ctypes.c_double),
+        ("power_max_iter", ctypes.c_int32), ("power_tol", ctypes.c_double),
+        ("use_graphs", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("termination", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("iterations", ctypes.c_int64), ("restarts", ctypes.c_int64),
+        ("kkt_checks", ctypes.c_int64),
+        ("primal_obj", ctypes.c_double), ("dual_obj", ctypes.c_double), ("gap", ctypes.c_double),
+        ("primal_res", ctypes.c_double), ("dual_res", ctypes.c_double),
+        ("rel_kkt", ctypes.c_double),
+        ("omega", ctypes.c_double), ("eta", ctypes.c_double), ("norm_A", ctypes.c_double),
+        ("norm_Q", ctypes.c_double),
+        ("prepare_seconds", ctypes.c_double), ("solve_seconds", ctypes.c_double),
+        ("kernel_launches", ctypes.c_int64),
+        ("profile_ms", ctypes.c_double * 4), ("profile_launches", ctypes.c_int64 * 4),
+    ]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        d["termination_name"] = TERMINATION.get(self.termination, "?")
+        return d
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is not built; run `python -m paper_2412_09734_gb300.build` "
+        "(or __graft_entry__.build()) first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_P = ctypes.c_void_p
+_I32, _I64, _D, _INT = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+_sig = {
+    "mpax_version": ([], ctypes.c_char_p),
+    "mpax_last_error": ([], ctypes.c_char_p),
+    "mpax_status_string": ([_INT], ctypes.c_char_p),
+    "mpax_options_default": ([ctypes.POINTER(Options)], None),
+    "mpax_lp_create": ([_I32, _I32, _I64] + [_P] * 8 + [_INT, _P, ctypes.POINTER(_P)], _INT),
+    "mpax_qp_create_diag_lowrank": ([_I32, _I32, _I64] + [_P] * 9 + [_I32, _I64, _P, _P, _P,
+                                                                       _INT, _P,
+                                                                       ctypes.POINTER(_P)],
+                                    _INT),
+    "mpax_solve": ([_P, ctypes.POINTER(Options), _P, _P, _INT], _INT),
+    "mpax_get_solution": ([_P, _P, _P, _INT], _INT),
+    "mpax_get_stats": ([_P, ctypes.POINTER(Stats)], _INT),
+    "mpax_destroy": ([_P], None),
+    "mpax_prepare": ([_P, ctypes.POINTER(Options)], _INT),
+    "mpax_get_scaling": ([_P, _P, _P, _P, _INT], _INT),
+    "mpax_get_transpose": ([_P, _P, _P, _P, _INT], _INT),
+    "mpax_set_iterate": ([_P, _P, _P, _P, _P, _I64, _D, _D, _INT], _INT),
+    "mpax_iterate": ([_P, _I64], _INT),
+    "mpax_get_iterate": ([_P, _P, _P, _P, _P, _INT], _INT),
+    "mpax_kkt": ([_P, _P, _P, _INT, _P], _INT),
+}
+for _name, (_args, _res) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def _check(status):
+    if status != MPAX_OK:
+        raise MpaxError(status, _lib.mpax_last_error().decode())
+
+
+# ---------------------------------------------------------------------------
+# marshalling
+# ---------------------------------------------------------------------------
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _kind_of(*arrays):
+    for a in arrays:
+        if a is None:
+            continue
+        if _is_torch(a):
+            return MPAX_MEM_DEVICE if a.is_cuda else MPAX_MEM_HOST
+        return MPAX_MEM_HOST
+    return MPAX_MEM_HOST
+
+
+class _Keep:
+    """Holds converted arrays alive for the duration of a call."""
+
+    def __init__(self, kind):
+        self.kind = kind
+        self.refs = []
+
+    def ptr(self, a, dtype):
+        if a is None:
+            return None
+        if _is_torch(a):
+            import torch
+            tdt = {np.float64: torch.float64, np.int64: torch.int64,
+                   np.int32: torch.int32}[dtype]
+            if self.kind == MPAX_MEM_DEVICE and not a.is_cuda:
+                raise ValueError("mixed host/device arguments")
+            if self.kind == MPAX_MEM_HOST and a.is_cuda:
+                raise ValueError("mixed host/device arguments")
+            t = a.to(tdt).contiguous()
+            self.refs.append(t)
+            return t.data_ptr() if t.numel() else None
+        if self.kind == MPAX_MEM_DEVICE:
+            raise ValueError("mixed host/device arguments")
+        arr = np.ascontiguousarray(a, dtype=dtype)
+        self.refs.append(arr)
+        return arr.ctypes.data if arr.size else None
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# C names
+# ---------------------------------------------------------------------------
+
+def mpax_version():
+    return _lib.mpax_version().decode()
+
+
+def mpax_last_error():
+    return _lib.mpax_last_error().decode()
+
+
+def mpax_options_default(**overrides):
+    o = Options()
+    _lib.mpax_options_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def mpax_lp_create(m, n, row_ptr, col_idx, val, c, lc, uc, l, u, stream=None):
+    kind = _kind_of(row_ptr, val)
+    k = _Keep(kind)
+    nnz = int(len(val)) if not _is_torch(val) else int(val.numel())
+    h = _P()
+    _check(_lib.mpax_lp_create(m, n, nnz, k.ptr(row_ptr, np.int64), k.ptr(col_idx, np.int32),
+                               k.ptr(val, np.float64), k.ptr(c, np.float64),
+                               k.ptr(lc, np.float64), k.ptr(uc, np.float64),
+                               k.ptr(l, np.float64), k.ptr(u, np.float64), kind,
+                               _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def mpax_qp_create_diag_lowrank(m, n, row_ptr, col_idx, val, c, lc, uc, l, u, D, r,
+                                f_row_ptr, f_col_idx, f_val, stream=None):
+    kind = _kind_of(row_ptr, val)
+    k = _Keep(kind)
+    nnz = int(len(val)) if not _is_torch(val) else int(val.numel())
+    f_nnz = int(len(f_val)) if not _is_torch(f_val) else int(f_val.numel())
+    h = _P()
+    _check(_lib.mpax_qp_create_diag_lowrank(
+        m, n, nnz, k.ptr(row_ptr, np.int64), k.ptr(col_idx, np.int32), k.ptr(val, np.float64),
+        k.ptr(c, np.float64), k.ptr(lc, np.float64), k.ptr(uc, np.float64),
+        k.ptr(l, np.float64), k.ptr(u, np.float64), k.ptr(D, np.float64), r, f_nnz,
+        k.ptr(f_row_ptr, np.int64), k.ptr(f_col_idx, np.int32), k.ptr(f_val, np.float64),
+        kind, _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def mpax_solve(h, opts, x0=None, y0=None):
+    kind = _kind_of(x0, y0)
+    k = _Keep(kind)
+    _check(_lib.mpax_solve(h, ctypes.byref(opts), k.ptr(x0, np.float64),
+                           k.ptr(y0, np.float64), kind))
+
+
+def mpax_prepare(h, opts):
+    _check(_lib.mpax_prepare(h, ctypes.byref(opts)))
+
+
+def _out(n, like):
+    if like is not None and _is_torch(like) and like.is_cuda:
+        import torch
+        return torch.empty(n, dtype=torch.float64, device=like.device), MPAX_MEM_DEVICE
+    return np.empty(n, dtype=np.float64), MPAX_MEM_HOST
+
+
+def _ptr_out(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        return a.data_ptr() if a.numel() else None
+    return a.ctypes.data if a.size else None
+
+
+def mpax_get_solution(h, m, n, device=None):
+    """Returns (x, y) as numpy arrays, or CUDA tensors when `device` is a CUDA
+    tensor used as a template."""
+    x, kind = _out(n, device)
+    y, _ = _out(m, device)
+    _check(_lib.mpax_get_solution(h, _ptr_out(x), _ptr_out(y), kind))
+    return x, y
+
+
+def mpax_get_stats(h):
+    s = Stats()
+    _check(_lib.mpax_get_stats(h, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def mpax_destroy(h):
+    if h:
+        _lib.mpax_destroy(h)
+
+
+def mpax_get_scaling(h, m, n):
+    Dr = np.empty(m)
+    Dc = np.empty(n)
+    info = np.empty(4)
+    _check(_lib.mpax_get_scaling(h, _ptr_out(Dr), _ptr_out(Dc), info.ctypes.data,
+                                 MPAX_MEM_HOST))
+    return Dr, Dc, dict(norm_A=info[0], norm_Q=info[1], eta=info[2], omega=info[3])
+
+
+def mpax_get_transpose(h, n, nnz):
+    rp = np.empty(n + 1, dtype=np.int64)
+    col = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz)
+    _check(_lib.mpax_get_transpose(h, rp.ctypes.data, _ptr_out(col), _ptr_out(val),
+                                   MPAX_MEM_HOST))
+    return rp, col, val
+
+
+def mpax_set_iterate(h, x, y, x_aux, y_aux, k, tau, sigma):
+    kind = _kind_of(x, y)
+    kp = _Keep(kind)
+    _check(_lib.mpax_set_iterate(h, kp.ptr(x, np.float64), kp.ptr(y, np.float64),
+                                 kp.ptr(x_aux, np.float64), kp.ptr(y_aux, np.float64), int(k),
+                                 float(tau), float(sigma), kind))
+
+
+def mpax_iterate(h, iters):
+    _check(_lib.mpax_iterate(h, int(iters)))
+
+
+def mpax_get_iterate(h, m, n):
+    x, y, xh, yh = np.empty(n), np.empty(m), np.empty(n), np.empty(m)
+    _check(_lib.mpax_get_iterate(h, _ptr_out(x), _ptr_out(y), _ptr_out(xh), _ptr_out(yh),
+                                 MPAX_MEM_HOST))
+    return x, y, xh, yh
+
+
+def mpax_kkt(h, x, y):
+    kind = _kind_of(x, y)
+    kp = _Keep(kind)
+    out = np.empty(6)
+    if kind == MPAX_MEM_DEVICE:
+        import torch
+        dout = torch.empty(6, dtype=torch.float64, device=x.device)
+        _check(_lib.mpax_kkt(h, kp.ptr(x, np.float64), kp.ptr(y, np.float64), kind,
+                             dout.data_ptr()))
+        out = dout.cpu().numpy()
+    else:
+        _check(_lib.mpax_kkt(h, kp.ptr(x, np.float64), kp.ptr(y, np.float64), kind,
+                             out.ctypes.data))
+    keys = ("primal_res", "dual_res", "primal_obj", "dual_obj", "gap", "rel_kkt")
+    return dict(zip(keys, out.tolist()))

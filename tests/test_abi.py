@@ -1,0 +1,99 @@
+"""The C-ABI library loads and exports every symbol include/mpax.h declares; host-side
+argument checks that return before any device work.  No GPU needed."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_2412_09734_gb300 import build
+    build.build()
+    from paper_2412_09734_gb300 import mpax
+    return mpax
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "mpax.h")) as fh:
+        src = fh.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(mpax_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(C):
+    lib = ctypes.CDLL(C.LIB_PATH)
+    decl = declared_functions()
+    assert len(decl) >= 17
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(C.EXPORTED) == decl
+
+
+def test_version_and_defaults(C):
+    assert "sm_103a" in C.mpax_version()
+    o = C.mpax_options_default()
+    # Appendix A defaults
+    assert o.eps_abs == 1e-4 and o.eps_rel == 1e-4
+    assert o.eps_primal_infeasible == 1e-8 and o.eps_dual_infeasible == 1e-8
+    assert o.eps_feas_polish == 1e-6
+    assert o.display_frequency == 10 and o.verbose == 0 and o.feasibility_polishing == 0
+    assert o.iteration_limit == 2**63 - 1
+    # rules fixed by this library
+    assert o.check_every == 64 and o.ruiz_iters == 10 and o.pock_chambolle == 1
+    assert o.reflection_gamma == 1.0 and o.step_safety == 0.998
+    assert (o.restart_sufficient, o.restart_necessary, o.restart_artificial) == (0.2, 0.8, 0.36)
+
+
+def test_struct_layout_matches_header(C, tmp_path):
+    """Field offsets of the ctypes mirrors equal the C compiler's for mpax.h."""
+    import subprocess
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mpax.h"', 'int main(void){']
+    for cname, cls in (("mpax_options", C.Options), ("mpax_stats", C.Stats)):
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for cname, cls in (("mpax_options", C.Options), ("mpax_stats", C.Stats)):
+        assert got[(cname, "size")] == ctypes.sizeof(cls)
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_invalid_sizes_rejected_before_device_work(C):
+    h = ctypes.c_void_p()
+    st = C._lib.mpax_lp_create(-1, 3, 0, None, None, None, None, None, None, None, None, 0,
+                               None, ctypes.byref(h))
+    assert st == 1 and "non-negative" in C.mpax_last_error()
+    st = C._lib.mpax_lp_create(2, 3, 1 << 31, None, None, None, None, None, None, None, None,
+                               0, None, ctypes.byref(h))
+    assert st == 7
+    rp = np.array([0, 1, 2], dtype=np.int64)
+    st = C._lib.mpax_lp_create(2, 3, 2, rp.ctypes.data, None, None, None, None, None, None,
+                               None, 0, None, ctypes.byref(h))
+    assert st == 1 and "NULL" in C.mpax_last_error()
+    st = C._lib.mpax_lp_create(2, 3, 2, rp.ctypes.data, None, None, None, None, None, None,
+                               None, 5, None, ctypes.byref(h))
+    assert st == 1
+    assert C._lib.mpax_get_stats(None, None) == 1
+    C.mpax_destroy(None)
+
+
+def test_status_strings(C):
+    for s in range(8):
+        assert C._lib.mpax_status_string(s).decode() != "unknown status"
