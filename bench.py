@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-iters", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="only run short solves (128 iterations, mixed then FP64) as an ncu target")
     return ap.parse_args()
 
 
@@ -376,8 +378,29 @@ def run_ours(args):
     return 0
 
 
+def run_profile_target(args):
+    """Short solves of the bench workload for an ncu capture: 128 iterations in
+    mixed precision, then 128 in FP64 (two check blocks each)."""
+    import torch
+    torch.cuda.init()
+    from paper_2412_09734_gb300 import mpax as C
+    d, _ = workload(args.workload)
+    m, n, _ = WORKLOADS[args.workload]
+    keys = ("row_ptr", "col", "val", "c", "lc", "uc", "l", "u")
+    dev = {k: torch.from_numpy(np.ascontiguousarray(d[k])).cuda() for k in keys}
+    h = C.mpax_lp_create(m, n, *[dev[k] for k in keys])
+    for prec in (C.MPAX_PREC_MIXED, C.MPAX_PREC_FP64):
+        C.mpax_solve(h, C.mpax_options_default(precision=prec, iteration_limit=128))
+        print(json.dumps({"precision": prec, **{k: v for k, v in C.mpax_get_stats(h).items()
+                                                if k in ("iterations", "kernel_launches")}}))
+    C.mpax_destroy(h)
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_run:
+        return run_profile_target(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -16,8 +16,10 @@ implements the same written rules.  The readings are:
     computing from the current scaled matrix K the row factors
     1/sqrt(max_j |K_ij|) and column factors 1/sqrt(max_i |K_ij|) (1 for an
     empty row/column) and applying both; then one Pock-Chambolle round with
-    alpha = 1: factors 1/sqrt(sum_j |K_ij|) and 1/sqrt(sum_i |K_ij|).  Only A
-    drives the factors; Q is scaled congruently (Q~ = D_c Q D_c).
+    alpha = 1: factors 1/sqrt(sum_j |K_ij|) and 1/sqrt(sum_i |K_ij|).  For a QP
+    the scaled diagonal Q~_jj joins column j's norm (max in the Ruiz rounds,
+    sum in the Pock-Chambolle round) in place of Q's part of the KKT matrix;
+    Q is scaled congruently (Q~ = D_c Q D_c).
     Scaled data: A~ = D_r A D_c, c~ = D_c c, Q~ = D_c Q D_c, [l~, u~] = [l, u]/D_c,
     [lc~, uc~] = D_r [lc, uc]; x = D_c x~, y = D_r y~.
   * Step sizes: eta = 0.998 / ||A~||_2 with ||A~||_2 from power iteration on
@@ -82,6 +84,9 @@ class DiagLowRankQ:
         """diag(d) Q diag(d)."""
         return DiagLowRankQ(d * d * self.D, sp.diags(d) @ self.F)
 
+    def diagonal(self):
+        return self.D + np.asarray(self.F.multiply(self.F).sum(axis=1)).ravel()
+
     def dense(self):
         return np.diag(self.D) + (self.F @ self.F.T).toarray()
 
@@ -95,6 +100,9 @@ class SparseQ:
 
     def congruent(self, d):
         return SparseQ(sp.diags(d) @ self.Q @ sp.diags(d))
+
+    def diagonal(self):
+        return self.Q.diagonal()
 
     def dense(self):
         return self.Q.toarray()
@@ -164,8 +172,14 @@ def _inv_sqrt_or_one(v):
     return out
 
 
-def scaling_factors(A: sp.csr_matrix, ruiz_iters: int = 10, pock_chambolle: bool = True):
-    """Diagonal factors (D_r, D_c) such that A~ = diag(D_r) A diag(D_c)."""
+def scaling_factors(A: sp.csr_matrix, ruiz_iters: int = 10, pock_chambolle: bool = True,
+                    qdiag=None):
+    """Diagonal factors (D_r, D_c) such that A~ = diag(D_r) A diag(D_c).
+
+    For a QP, `qdiag` is the diagonal of Q; the scaled diagonal
+    Q~_jj = D_c,j^2 Q_jj joins column j's norm (max with the column's
+    infinity-norm in a Ruiz round, added to its 1-norm in the Pock-Chambolle
+    round), standing in for Q's part of the KKT matrix."""
     m, n = A.shape
     Dr = np.ones(m)
     Dc = np.ones(n)
@@ -174,6 +188,8 @@ def scaling_factors(A: sp.csr_matrix, ruiz_iters: int = 10, pock_chambolle: bool
         absK = abs(K)
         row_max = np.asarray(absK.max(axis=1).todense()).ravel() if m and n else np.zeros(m)
         col_max = np.asarray(absK.max(axis=0).todense()).ravel() if m and n else np.zeros(n)
+        if qdiag is not None:
+            col_max = np.maximum(col_max, Dc * Dc * qdiag)
         dr = _inv_sqrt_or_one(row_max)
         dc = _inv_sqrt_or_one(col_max)
         K = sp.csr_matrix(sp.diags(dr) @ K @ sp.diags(dc))
@@ -183,6 +199,8 @@ def scaling_factors(A: sp.csr_matrix, ruiz_iters: int = 10, pock_chambolle: bool
         absK = abs(K)
         row_sum = np.asarray(absK.sum(axis=1)).ravel()
         col_sum = np.asarray(absK.sum(axis=0)).ravel()
+        if qdiag is not None:
+            col_sum = col_sum + Dc * Dc * qdiag
         dr = _inv_sqrt_or_one(row_sum)
         dc = _inv_sqrt_or_one(col_sum)
         Dr *= dr
@@ -369,7 +387,8 @@ class Result:
 
 def prepare(p: Problem, opts: Options):
     """Scaling, operator norms and the initial primal weight."""
-    Dr, Dc = scaling_factors(p.A, opts.ruiz_iters, opts.pock_chambolle)
+    qd = None if p.Q is None else p.Q.diagonal()
+    Dr, Dc = scaling_factors(p.A, opts.ruiz_iters, opts.pock_chambolle, qd)
     ps = scale_problem(p, Dr, Dc)
     nA, _ = power_norm_A(ps.A, opts.power_max_iter, opts.power_tol)
     nQ, _ = power_norm_Q(ps.Q, ps.n, opts.power_max_iter, opts.power_tol)

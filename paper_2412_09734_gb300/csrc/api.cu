@@ -180,7 +180,7 @@ void destroy_problem(mpax_problem* pb) {
   free_schedule(P.schedFt);
   double* ds[] = {P.val, P.c,     P.lc,    P.uc,    P.l,   P.u,      P.D,      P.fval,
                   P.Dr,  P.Dc,    P.invDr, P.invDc, P.val_s, P.fval_s, P.D_s,  P.rowred,
-                  P.colred, P.red, P.red_out, pb->dx, pb->dy, pb->dxa, pb->dya, pb->d6};
+                  P.colred, P.red, P.red_out, P.qdiag, pb->dx, pb->dy, pb->dxa, pb->dya, pb->d6};
   for (double* d : ds)
     if (d) cudaFree(d);
   int* is[] = {P.permT, P.permF, P.tmp_rows, P.tmp_scan};
@@ -233,7 +233,7 @@ mpax_status create_common(int32_t m, int32_t n, int64_t nnz, const int64_t* row_
   if (!e) e = order_after_user(pb);
   const int big = std::max(std::max(m, n), r) + 2;
   if (!e) e = dmalloc(&P.A.rp, m + 1);
-  if (!e) e = dmalloc(&P.A.col, nnz);
+  if (!e) e = dmalloc(&P.A.col, nnz + kPad);
   if (!e) e = dmalloc(&P.val, nnz);
   if (!e) e = dmalloc(&P.c, n);
   if (!e) e = dmalloc(&P.l, n);
@@ -252,7 +252,7 @@ mpax_status create_common(int32_t m, int32_t n, int64_t nnz, const int64_t* row_
   if (!e) e = dmalloc(&P.red, kRedBlocks * 8);
   if (!e) e = dmalloc(&P.red_out, 16);
   if (!e) e = dmalloc(&P.At.rp, n + 1);
-  if (!e) e = dmalloc(&P.At.col, nnz);
+  if (!e) e = dmalloc(&P.At.col, nnz + kPad);
   if (!e) e = dmalloc(&P.permT, nnz);
   if (!e) e = dmalloc(&pb->dx, n);
   if (!e) e = dmalloc(&pb->dy, m);
@@ -262,12 +262,13 @@ mpax_status create_common(int32_t m, int32_t n, int64_t nnz, const int64_t* row_
   if (is_qp) {
     if (!e) e = dmalloc(&P.D, n);
     if (!e) e = dmalloc(&P.D_s, n);
+    if (!e) e = dmalloc(&P.qdiag, n);
     if (!e) e = dmalloc(&P.F.rp, n + 1);
-    if (!e) e = dmalloc(&P.F.col, f_nnz);
+    if (!e) e = dmalloc(&P.F.col, f_nnz + kPad);
     if (!e) e = dmalloc(&P.fval, f_nnz);
     if (!e) e = dmalloc(&P.fval_s, f_nnz);
     if (!e) e = dmalloc(&P.Ft.rp, r + 1);
-    if (!e) e = dmalloc(&P.Ft.col, f_nnz);
+    if (!e) e = dmalloc(&P.Ft.col, f_nnz + kPad);
     if (!e) e = dmalloc(&P.permF, f_nnz);
   }
   P.A.rows = m;

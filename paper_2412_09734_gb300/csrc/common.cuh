@@ -34,8 +34,10 @@ constexpr int kMaxCheckEvery = 1024;
 constexpr int kPartQ = 6;
 
 // Work item encoding (int4):
-//   packed short rows: {r0, r1, -1, 0}    rows [r0, r1), every row <= kLongRow nnz
-//   slice of a long row: {r, s, S, first}  slice s of S, `first` = index of slice 0
+//   packed short rows:   {r0, r1, base, end}        rows [r0, r1), nonzeros [base, end),
+//                                                    every row <= kLongRow nonzeros
+//   slice of a long row: {-(r+1), p0, p1, s<<16|S}  nonzeros [p0, p1) of row r, slice s
+//                                                    of S; slice 0 is item (this - s)
 struct Sched {
   int rows = 0;
   int n_items = 0;
@@ -125,6 +127,12 @@ cudaError_t scan_exclusive(const int* in, int* out, int n, int* tmp, cudaStream_
 cudaError_t build_schedule(const Csr& A, Sched& sched, cudaStream_t s, int* tmp_rows,
                            int* tmp_scan);
 void free_schedule(Sched& sched);
+// Incremented whenever schedule buffers are (re)allocated; CUDA graphs that
+// captured older buffers must be rebuilt.
+extern unsigned long long sched_generation;
+// Elements of padding allocated past the end of every value and column array
+// (the L2 bulk prefetch rounds its range out to 16 bytes).
+constexpr int kPad = 16;
 
 // Device transpose: At.rp/At.col/perm allocated by the caller (n+1, nnz, nnz).
 cudaError_t transpose_csr(const Csr& A, Csr& At, int* perm, int* tmp_cnt, int* tmp_scan,

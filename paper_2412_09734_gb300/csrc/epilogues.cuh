@@ -1,9 +1,15 @@
 // Row epilogues of the fused SpMV kernels: the elementwise half of each PDHG
 // half-step, fused with the SpMV that produces its row sums.
 //
-// Each epilogue is called once per row with s = (K v)_row, accumulates up to
-// NQ FP64 partial sums when `check` is set, and reads its scalars from the
-// device-resident DevState in load().
+// Interface: load() reads the DevState scalars once per warp; pre(r, p) issues
+// the loads of row r's operands (called before the SpMV loads so that they are
+// in flight together); row(r, s, p, acc) receives s = (K v)_r, computes, stores
+// and, when `check` is set, accumulates NQ FP64 partial sums.
+//
+// Weighted sums of two points are written as anchor-relative affine updates,
+// v + b (anchor - v), so the two weights sum to one exactly in any precision;
+// with separately rounded FP32 weights (k+1)/(k+2) and 1/(k+2) the iterate
+// would drift by ~1e-7 relatively per iteration over long restart cycles.
 #pragma once
 
 #include "common.cuh"
@@ -13,7 +19,7 @@ namespace mpax {
 // ---- r^2HPDHG (Algorithm 1) -------------------------------------------------
 //
 // Storage of the Halpern iterate: the current primal iterate of the cycle,
-//   x^{n,k} = a_k w^k + b_k x^{n,0},  a_k = k/(k+1), b_k = 1/(k+1),
+//   x^{n,k} = w^k + (1/(k+1)) (x^{n,0} - w^k),
 // is rebuilt from the stored reflected point w^k = (1+gamma) x^ - gamma x of the
 // previous step and the anchor x^{n,0} (eq. 4 rewritten), so a primal
 // half-step reads (w, anchor, c, l, u) and writes only w (plus xbar = 2x^ - x,
@@ -26,6 +32,9 @@ namespace mpax {
 template <typename T>
 struct EpiPrimalLP {
   static constexpr int NQ = 2;
+  struct Pre {
+    T w, x0, c, l, u, xs;
+  };
   const DevState* st;
   T* xbar;
   T* wbuf;  // == xbar when gamma == 1
@@ -37,23 +46,26 @@ struct EpiPrimalLP {
   T* xhat;
   T* xprev;
   int it, record, check;
-  T tau, ra, rb, g;
+  T tau, rb, g;
   __device__ __forceinline__ bool skip() const { return st->done != 0; }
   __device__ __forceinline__ void load() {
     tau = (T)st->tau;
-    ra = (T)st->coef_a[it];
     rb = (T)st->coef_b[it];
     g = (T)st->gamma;
   }
-  __device__ __forceinline__ void row(int j, T t, double* acc) {
-    const T x0 = xa[j];
+  __device__ __forceinline__ void pre(int j, Pre& p) const {
+    p.w = wbuf[j];
+    p.x0 = xa[j];
+    p.c = c[j];
+    p.l = l[j];
+    p.u = u[j];
+    p.xs = xsrc ? xsrc[j] : (T)0;
+  }
+  __device__ __forceinline__ void row(int j, T t, const Pre& p, double* acc) {
     T x;
-    if (xsrc) {
-      x = xsrc[j];
-    } else {
-      x = (ra == (T)0) ? x0 : ra * wbuf[j] + rb * x0;
-    }
-    const T xh = clampv<T>(x - tau * (c[j] - t), l[j], u[j]);
+    if (xsrc) x = p.xs;
+    else x = (rb == (T)1) ? p.x0 : p.w + rb * (p.x0 - p.w);
+    const T xh = clampv<T>(x - tau * (p.c - t), p.l, p.u);
     xbar[j] = (T)2 * xh - x;
     if (wbuf != xbar) wbuf[j] = ((T)1 + g) * xh - g * x;
     if (record) {
@@ -61,7 +73,7 @@ struct EpiPrimalLP {
       xprev[j] = x;
     }
     if (check) {
-      const double d0 = (double)xh - (double)x, d1 = (double)xh - (double)x0;
+      const double d0 = (double)xh - (double)x, d1 = (double)xh - (double)p.x0;
       acc[0] += d0 * d0;
       acc[1] += d1 * d1;
     }
@@ -71,11 +83,14 @@ struct EpiPrimalLP {
 // Dual half-step over the rows of A (one row per constraint i), s = (A xbar)_i:
 //   v = y/sigma - s;  y^ = sigma (v - proj_[-uc,-lc](v))   (eq. 3, second line;
 //   y - sigma s = sigma v)
-//   y+ = a ((1+gamma) y^ - gamma y) + b y^{n,0}            (eq. 4)
+//   y+ = z + b (y^{n,0} - z),  z = (1+gamma) y^ - gamma y, b = 1/(k+2)   (eq. 4)
 // check partials: [0] sum (y^ - y)^2, [1] sum (y^ - y^{n,0})^2
 template <typename T>
 struct EpiDualLP {
   static constexpr int NQ = 2;
+  struct Pre {
+    T y, ya, lc, uc;
+  };
   const DevState* st;
   T* y;
   const T* ya;
@@ -84,27 +99,31 @@ struct EpiDualLP {
   T* yhat;
   T* yprev;
   int it, record, check;
-  T sigma, inv_sigma, ha, hb, g;
+  T sigma, inv_sigma, hb, g;
   __device__ __forceinline__ bool skip() const { return st->done != 0; }
   __device__ __forceinline__ void load() {
     sigma = (T)st->sigma;
     inv_sigma = (T)st->inv_sigma;
-    ha = (T)st->coef_a[it + 1];
     hb = (T)st->coef_b[it + 1];
     g = (T)st->gamma;
   }
-  __device__ __forceinline__ void row(int i, T s, double* acc) {
-    const T y0 = y[i];
-    const T y0a = ya[i];
-    const T v = y0 * inv_sigma - s;
-    const T yh = sigma * (v - clampv<T>(v, -uc[i], -lc[i]));
-    y[i] = ha * (((T)1 + g) * yh - g * y0) + hb * y0a;
+  __device__ __forceinline__ void pre(int i, Pre& p) const {
+    p.y = y[i];
+    p.ya = ya[i];
+    p.lc = lc[i];
+    p.uc = uc[i];
+  }
+  __device__ __forceinline__ void row(int i, T s, const Pre& p, double* acc) {
+    const T v = p.y * inv_sigma - s;
+    const T yh = sigma * (v - clampv<T>(v, -p.uc, -p.lc));
+    const T z = ((T)1 + g) * yh - g * p.y;
+    y[i] = z + hb * (p.ya - z);
     if (record) {
       yhat[i] = yh;
-      yprev[i] = y0;
+      yprev[i] = p.y;
     }
     if (check) {
-      const double d0 = (double)yh - (double)y0, d1 = (double)yh - (double)y0a;
+      const double d0 = (double)yh - (double)p.y, d1 = (double)yh - (double)p.ya;
       acc[0] += d0 * d0;
       acc[1] += d1 * d1;
     }
@@ -116,13 +135,17 @@ struct EpiDualLP {
 // u = F~^T x_md computed by the SpMV launched just before.
 
 // Primal step over the rows of A^T, t = (A^T y)_j:
-//   x_md = (1-beta) xavg + beta x;  q = Ds x_md + (F~ u)_j
+//   x_md = xavg + beta (x - xavg);  q = Ds x_md + (F~ u)_j
 //   x+ = proj_[l,u](x - tau (q + c - t))            (eq. 6)
-//   xref = 2 x+ - x;  xavg+ = (1-theta) xavg + theta x+
+//   xref = 2 x+ - x;  xavg+ = xavg + theta (x+ - xavg)
 // check partials: [1] sum (xavg+ - x_anchor)^2
 template <typename T>
 struct EpiPrimalQP {
   static constexpr int NQ = 2;
+  struct Pre {
+    T x, xa, xn, c, l, u, d;
+    int f0, f1;
+  };
   const DevState* st;
   T* x;
   T* xavg;
@@ -144,20 +167,29 @@ struct EpiPrimalQP {
     tau = (T)st->tau;
     beta = (T)st->coef_a[it];
   }
-  __device__ __forceinline__ void row(int j, T t, double* acc) {
-    const T x0 = x[j];
-    const T xa = xavg[j];
-    const T xmd = ((T)1 - beta) * xa + beta * x0;
-    T q = Ds[j] * xmd;
-    for (int p = frp[j]; p < frp[j + 1]; ++p) q += fval[p] * uvec[fcol[p]];
-    const T xn = clampv<T>(x0 - tau * (q + c[j] - t), l[j], u[j]);
-    xref[j] = (T)2 * xn - x0;
+  __device__ __forceinline__ void pre(int j, Pre& p) const {
+    p.x = x[j];
+    p.xa = xavg[j];
+    p.xn = check ? xanc[j] : (T)0;
+    p.c = c[j];
+    p.l = l[j];
+    p.u = u[j];
+    p.d = Ds[j];
+    p.f0 = frp[j];
+    p.f1 = frp[j + 1];
+  }
+  __device__ __forceinline__ void row(int j, T t, const Pre& p, double* acc) {
+    const T xmd = p.xa + beta * (p.x - p.xa);
+    T q = p.d * xmd;
+    for (int k = p.f0; k < p.f1; ++k) q += fval[k] * uvec[fcol[k]];
+    const T xn = clampv<T>(p.x - tau * (q + p.c - t), p.l, p.u);
+    xref[j] = (T)2 * xn - p.x;
     x[j] = xn;
-    const T xan = ((T)1 - beta) * xa + beta * xn;
+    const T xan = p.xa + beta * (xn - p.xa);
     xavg[j] = xan;
-    if (record) xprev[j] = x0;
+    if (record) xprev[j] = p.x;
     if (check) {
-      const double d1 = (double)xan - (double)xanc[j];
+      const double d1 = (double)xan - (double)p.xn;
       acc[1] += d1 * d1;
     }
   }
@@ -168,6 +200,9 @@ struct EpiPrimalQP {
 template <typename T>
 struct EpiDualQP {
   static constexpr int NQ = 2;
+  struct Pre {
+    T y, ya, yn, lc, uc;
+  };
   const DevState* st;
   T* y;
   T* yavg;
@@ -182,15 +217,21 @@ struct EpiDualQP {
     inv_sigma = (T)st->inv_sigma;
     theta = (T)st->coef_a[it];
   }
-  __device__ __forceinline__ void row(int i, T s, double* acc) {
-    const T y0 = y[i];
-    const T v = y0 * inv_sigma - s;
-    const T yn = sigma * (v - clampv<T>(v, -uc[i], -lc[i]));
+  __device__ __forceinline__ void pre(int i, Pre& p) const {
+    p.y = y[i];
+    p.ya = yavg[i];
+    p.yn = check ? yanc[i] : (T)0;
+    p.lc = lc[i];
+    p.uc = uc[i];
+  }
+  __device__ __forceinline__ void row(int i, T s, const Pre& p, double* acc) {
+    const T v = p.y * inv_sigma - s;
+    const T yn = sigma * (v - clampv<T>(v, -p.uc, -p.lc));
     y[i] = yn;
-    const T yan = ((T)1 - theta) * yavg[i] + theta * yn;
+    const T yan = p.ya + theta * (yn - p.ya);
     yavg[i] = yan;
     if (check) {
-      const double d1 = (double)yan - (double)yanc[i];
+      const double d1 = (double)yan - (double)p.yn;
       acc[1] += d1 * d1;
     }
   }
@@ -203,6 +244,10 @@ struct EpiDualQP {
 template <typename T>
 struct EpiKktRow {
   static constexpr int NQ = 2;
+  struct Pre {
+    double idr, dr, lc, uc;
+    T yv;
+  };
   const int* skipf;
   const double* invDr;
   const double* Dr;
@@ -212,15 +257,21 @@ struct EpiKktRow {
   int check;
   __device__ __forceinline__ bool skip() const { return skipf && *skipf != 0; }
   __device__ __forceinline__ void load() {}
-  __device__ __forceinline__ void row(int i, T s, double* acc) {
-    const double ax = (double)s * invDr[i];
-    const double lo = lc[i], hi = uc[i];
-    const double rp = ax - fmin(fmax(ax, lo), hi);
+  __device__ __forceinline__ void pre(int i, Pre& p) const {
+    p.idr = invDr[i];
+    p.dr = Dr[i];
+    p.lc = lc[i];
+    p.uc = uc[i];
+    p.yv = yv[i];
+  }
+  __device__ __forceinline__ void row(int i, T s, const Pre& p, double* acc) {
+    const double ax = (double)s * p.idr;
+    const double rp = ax - fmin(fmax(ax, p.lc), p.uc);
     acc[0] += rp * rp;
-    const double y = Dr[i] * (double)yv[i];
+    const double y = p.dr * (double)p.yv;
     double term = 0.0;
-    if (y > 0.0 && isfinite(lo)) term = lo * y;
-    if (y < 0.0 && isfinite(hi)) term = hi * y;
+    if (y > 0.0 && isfinite(p.lc)) term = p.lc * y;
+    if (y < 0.0 && isfinite(p.uc)) term = p.uc * y;
     acc[1] += term;
   }
 };
@@ -231,6 +282,10 @@ struct EpiKktRow {
 template <typename T>
 struct EpiKktCol {
   static constexpr int NQ = 4;
+  struct Pre {
+    double idc, dc, c, l, u;
+    T xv;
+  };
   const int* skipf;
   const double* invDc;
   const double* Dc;
@@ -247,19 +302,26 @@ struct EpiKktCol {
   int check;
   __device__ __forceinline__ bool skip() const { return skipf && *skipf != 0; }
   __device__ __forceinline__ void load() {}
-  __device__ __forceinline__ void row(int j, T t, double* acc) {
-    const double aty = (double)t * invDc[j];
-    const double xs = (double)xv[j];
-    const double x = Dc[j] * xs;
+  __device__ __forceinline__ void pre(int j, Pre& p) const {
+    p.idc = invDc[j];
+    p.dc = Dc[j];
+    p.c = c[j];
+    p.l = l[j];
+    p.u = u[j];
+    p.xv = xv[j];
+  }
+  __device__ __forceinline__ void row(int j, T t, const Pre& p, double* acc) {
+    const double aty = (double)t * p.idc;
+    const double xs = (double)p.xv;
+    const double x = p.dc * xs;
     double qx = 0.0;
     if (is_qp) {
       double q = Ds[j] * xs;
-      for (int p = frp[j]; p < frp[j + 1]; ++p) q += fval[p] * (double)uvec[fcol[p]];
-      qx = q * invDc[j];
+      for (int k = frp[j]; k < frp[j + 1]; ++k) q += fval[k] * (double)uvec[fcol[k]];
+      qx = q * p.idc;
     }
-    const double lam = qx + c[j] - aty;
-    const double lo = l[j], hi = u[j];
-    const bool lf = isfinite(lo), uf = isfinite(hi);
+    const double lam = qx + p.c - aty;
+    const bool lf = isfinite(p.l), uf = isfinite(p.u);
     double lh;
     if (lf && uf) lh = lam;
     else if (lf) lh = fmax(lam, 0.0);
@@ -267,8 +329,8 @@ struct EpiKktCol {
     else lh = 0.0;
     const double rd = lam - lh;
     acc[0] += rd * rd;
-    acc[1] += c[j] * x;
-    acc[2] += (lf ? lo * fmax(lh, 0.0) : 0.0) + (uf ? hi * fmin(lh, 0.0) : 0.0);
+    acc[1] += p.c * x;
+    acc[2] += (lf ? p.l * fmax(lh, 0.0) : 0.0) + (uf ? p.u * fmin(lh, 0.0) : 0.0);
     acc[3] += x * qx;
   }
 };
@@ -278,6 +340,9 @@ struct EpiKktCol {
 template <typename T>
 struct EpiStore {
   static constexpr int NQ = 1;
+  struct Pre {
+    T d, di;
+  };
   const int* skipf;
   T* out;
   const double* s_scale;  // nullable: 1
@@ -291,9 +356,13 @@ struct EpiStore {
     ss = s_scale ? (T)*s_scale : (T)1;
     ds = d_scale ? (T)*d_scale : (T)1;
   }
-  __device__ __forceinline__ void row(int r, T s, double* acc) {
+  __device__ __forceinline__ void pre(int r, Pre& p) const {
+    p.d = diag ? diag[r] : (T)0;
+    p.di = diag ? din[r] : (T)0;
+  }
+  __device__ __forceinline__ void row(int r, T s, const Pre& p, double* acc) {
     T v = s * ss;
-    if (diag) v += diag[r] * (din[r] * ds);
+    if (diag) v += p.d * (p.di * ds);
     out[r] = v;
     if (check) acc[0] += (double)v * (double)v;
   }

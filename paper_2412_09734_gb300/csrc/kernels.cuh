@@ -9,16 +9,27 @@
 // warp arrives last at its counter; it sums the slices' partials in slice
 // order, so every result is independent of scheduling.  No floating-point
 // atomics are used anywhere: every reduction has a fixed order.
+//
+// Latency: a warp issues every independent load of its item at once (item
+// descriptor, state scalars, row pointers and epilogue operands of its rows,
+// all matrix values and column indices), then the gathers of the input vector,
+// then computes.  Lane 0 also issues a TMA bulk prefetch into L2
+// (cp.async.bulk.prefetch.L2) of the values and column indices of the item one
+// resident wave ahead, so most matrix loads of later waves hit L2.
 #pragma once
 
 #include "common.cuh"
 
 namespace mpax {
 
+constexpr int kShortLoads = (kShortCap + kWarp - 1) / kWarp;  // per lane, packed rows
+constexpr int kSliceLoads = kSliceNnz / kWarp;                // per lane, one slice
+
 template <typename T>
 struct SpmvArgs {
   const int4* items;
   int n_items;
+  int pf_dist;  // prefetch distance in items (0 = off)
   const int* rp;
   const int* col;
   const T* val;
@@ -36,7 +47,7 @@ struct InPlain {
   __device__ __forceinline__ T operator()(int j) const { return ld_ro(x + j); }
 };
 
-// x_md = (1 - beta) xavg + beta x, beta = coef_a[it] (rAPDHG momentum point, eq. 6)
+// x_md = xavg + beta (x - xavg), beta = coef_a[it] (rAPDHG momentum point, eq. 6)
 template <typename T>
 struct InMomentum {
   const T* x;
@@ -46,52 +57,94 @@ struct InMomentum {
   T beta;
   __device__ __forceinline__ void load() { beta = (T)st->coef_a[it]; }
   __device__ __forceinline__ T operator()(int j) const {
-    return ((T)1 - beta) * ld_ro(xavg + j) + beta * ld_ro(x + j);
+    const T a = ld_ro(xavg + j);
+    return a + beta * (ld_ro(x + j) - a);
   }
 };
+
+__device__ __forceinline__ int item_row(const int4& it) { return it.x >= 0 ? it.x : -(it.x + 1); }
+
+__device__ __forceinline__ void item_range(const int4& it, int& p0, int& p1) {
+  if (it.x >= 0) {
+    p0 = it.z;
+    p1 = it.w;
+  } else {
+    p0 = it.y;
+    p1 = it.z;
+  }
+}
+
+// TMA bulk prefetch of [p, p + bytes) into L2 (16-byte aligned, rounded out;
+// arrays carry at least 16 bytes of padding past their end).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  if (bytes == 0) return;
+  const unsigned long long a0 = (unsigned long long)p & ~15ull;
+  const unsigned long long a1 = ((unsigned long long)p + bytes + 15ull) & ~15ull;
+  const unsigned size = (unsigned)(a1 - a0);
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"(size) : "memory");
+}
 
 template <typename T, class In, class Epi>
 __global__ void __launch_bounds__(kBlock) spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
   __shared__ T sbuf[kWarpsPerBlock][kShortCap];
-  if (epi.skip()) return;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int item = blockIdx.x * kWarpsPerBlock + wib;
   if (item >= a.n_items) return;
+  const int4 it = a.items[item];
+  if (epi.skip()) return;
   in.load();
   epi.load();
   double acc[Epi::NQ];
 #pragma unroll
   for (int q = 0; q < Epi::NQ; ++q) acc[q] = 0.0;
-  const int4 it = a.items[item];
-  if (it.z < 0) {
-    // packed short rows [r0, r1): stage the products, then one lane per row
-    const int r0 = it.x, r1 = it.y;
-    const int base = a.rp[r0], end = a.rp[r1];
-    T* buf = sbuf[wib];
-    for (int p = base + lane; p < end; p += 4 * kWarp) {
-      T v[4];
-      int c[4];
+  const bool do_pf = (lane == 0) && a.pf_dist > 0 && item + a.pf_dist < a.n_items;
+
+  if (it.x >= 0) {
+    // ---- packed short rows [r0, r1), nonzeros [base, end) ----------------
+    const int r0 = it.x, r1 = it.y, base = it.z, end = it.w;
+    const int ra = r0 + lane, rb = r0 + kWarp + lane;
+    const bool ha = ra < r1, hb = rb < r1;
+    const int sa = ha ? ra : r0, sb = hb ? rb : r0;  // always-valid rows
+    const int pa0 = a.rp[sa], pa1 = a.rp[sa + 1];
+    const int pb0 = a.rp[sb], pb1 = a.rp[sb + 1];
+    typename Epi::Pre pra, prb;
+    epi.pre(sa, pra);
+    epi.pre(sb, prb);
+    T v[kShortLoads];
+    int c[kShortLoads];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = p + u * kWarp;
-        if (q < end) {
-          v[u] = ld_stream(a.val + q);
-          c[u] = ld_stream(a.col + q);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = p + u * kWarp;
-        if (q < end) buf[q - base] = v[u] * in(c[u]);
+    for (int u = 0; u < kShortLoads; ++u) {
+      const int q = base + lane + u * kWarp;
+      if (q < end) {
+        v[u] = ld_stream(a.val + q);
+        c[u] = ld_stream(a.col + q);
       }
     }
+    int4 ft;
+    if (do_pf) ft = a.items[item + a.pf_dist];
+    T* buf = sbuf[wib];
+#pragma unroll
+    for (int u = 0; u < kShortLoads; ++u) {
+      const int q = base + lane + u * kWarp;
+      if (q < end) buf[q - base] = v[u] * in(c[u]);
+    }
+    if (do_pf) {
+      int q0, q1;
+      item_range(ft, q0, q1);
+      prefetch_l2(a.val + q0, sizeof(T) * (size_t)(q1 - q0));
+      prefetch_l2(a.col + q0, sizeof(int) * (size_t)(q1 - q0));
+    }
     __syncwarp();
-    for (int r = r0 + lane; r < r1; r += kWarp) {
-      const int q0 = a.rp[r] - base, q1 = a.rp[r + 1] - base;
+    if (ha) {
       T s = 0;
-      for (int q = q0; q < q1; ++q) s += buf[q];
-      epi.row(r, s, acc);
+      for (int q = pa0; q < pa1; ++q) s += buf[q - base];
+      epi.row(ra, s, pra, acc);
+    }
+    if (hb) {
+      T s = 0;
+      for (int q = pb0; q < pb1; ++q) s += buf[q - base];
+      epi.row(rb, s, prb, acc);
     }
     if (Epi::NQ > 0 && epi.check) {
 #pragma unroll
@@ -102,31 +155,41 @@ __global__ void __launch_bounds__(kBlock) spmv_fused(SpmvArgs<T> a, In in, Epi e
     }
     return;
   }
-  // slice s of S of the long row r
-  const int r = it.x, si = it.y, S = it.z, first = it.w;
-  const int rb = a.rp[r];
-  const int p0 = rb + si * kSliceNnz;
-  const int p1 = min(p0 + kSliceNnz, a.rp[r + 1]);
-  T v[kSliceNnz / kWarp];
-  int c[kSliceNnz / kWarp];
+
+  // ---- slice s of S of the long row r: nonzeros [p0, p1) ------------------
+  const int r = -(it.x + 1), p0 = it.y, p1 = it.z;
+  const int si = it.w >> 16, S = it.w & 0xffff;
+  const int first = item - si;
+  typename Epi::Pre pr;
+  epi.pre(r, pr);
+  T v[kSliceLoads];
+  int c[kSliceLoads];
 #pragma unroll
-  for (int u = 0; u < kSliceNnz / kWarp; ++u) {
+  for (int u = 0; u < kSliceLoads; ++u) {
     const int q = p0 + lane + u * kWarp;
     if (q < p1) {
       v[u] = ld_stream(a.val + q);
       c[u] = ld_stream(a.col + q);
     }
   }
+  int4 ft;
+  if (do_pf) ft = a.items[item + a.pf_dist];
   T s = 0;
 #pragma unroll
-  for (int u = 0; u < kSliceNnz / kWarp; ++u) {
+  for (int u = 0; u < kSliceLoads; ++u) {
     const int q = p0 + lane + u * kWarp;
     if (q < p1) s += v[u] * in(c[u]);
+  }
+  if (do_pf) {
+    int q0, q1;
+    item_range(ft, q0, q1);
+    prefetch_l2(a.val + q0, sizeof(T) * (size_t)(q1 - q0));
+    prefetch_l2(a.col + q0, sizeof(int) * (size_t)(q1 - q0));
   }
   s = warp_sum(s);
   if (S == 1) {
     if (lane == 0) {
-      epi.row(r, s, acc);
+      epi.row(r, s, pr, acc);
       if (Epi::NQ > 0 && epi.check) {
 #pragma unroll
         for (int q = 0; q < Epi::NQ; ++q) a.part[(a.q0 + q) * a.n_items + item] = acc[q];
@@ -138,13 +201,13 @@ __global__ void __launch_bounds__(kBlock) spmv_fused(SpmvArgs<T> a, In in, Epi e
     a.carry[item] = s;
     __threadfence();
     const int prev = atomicAdd(a.cnt + first, 1);
-    bool last = (prev == S - 1);
+    const bool last = (prev == S - 1);
     if (last) {
       __threadfence();
       T tot = 0;
       for (int t = 0; t < S; ++t) tot += __ldcg(a.carry + first + t);
       a.cnt[first] = 0;  // ready for the next launch
-      epi.row(r, tot, acc);
+      epi.row(r, tot, pr, acc);
     }
     if (Epi::NQ > 0 && epi.check) {
       // the finished row's contribution always lands in slot `first`; the

@@ -65,9 +65,9 @@ __global__ void k_from_double(const double* __restrict__ v, T* __restrict__ out,
 template <typename T>
 __global__ void k_materialize_lp(T* __restrict__ out, const T* __restrict__ w,
                                  const T* __restrict__ xa, const DevState* st, int idx, int n) {
-  const T a = (T)st->coef_a[idx], b = (T)st->coef_b[idx];
+  const T b = (T)st->coef_b[idx];
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-    out[j] = (a == (T)0) ? xa[j] : a * w[j] + b * xa[j];
+    out[j] = (b == (T)1) ? xa[j] : w[j] + b * (xa[j] - w[j]);
 }
 
 // Halpern (LP) or averaging (QP) coefficients for a block starting at k_base.
@@ -361,6 +361,20 @@ __global__ void k_kkt_finalize(const double* __restrict__ partAt, int nAt,
 // launch helper
 // ---------------------------------------------------------------------------
 
+// Warps of spmv_fused<T, In, Epi> resident on the whole GPU (one wave).
+template <typename T, class In, class Epi>
+int resident_warps() {
+  static int w = -1;
+  if (w < 0) {
+    int blocks = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, spmv_fused<T, In, Epi>, kBlock, 0);
+    w = std::max(1, blocks) * sms * kWarpsPerBlock;
+  }
+  return w;
+}
+
 template <typename T, class In, class Epi>
 void launch_spmv(const Sched& sc, const Csr& K, const T* val, In in, Epi epi, int q0,
                  cudaStream_t s) {
@@ -368,6 +382,7 @@ void launch_spmv(const Sched& sc, const Csr& K, const T* val, In in, Epi epi, in
   SpmvArgs<T> a;
   a.items = sc.items;
   a.n_items = sc.n_items;
+  a.pf_dist = resident_warps<T, In, Epi>();
   a.rp = K.rp;
   a.col = K.col;
   a.val = val;
@@ -397,8 +412,8 @@ class Engine final : public EngineBase {
  public:
   Engine(ProblemData* P, cudaError_t* e) : P_(P) {
     const int m = P->m, n = P->n;
-    valA_ = dalloc<T>(P->nnz, e);
-    valAt_ = dalloc<T>(P->nnz, e);
+    valA_ = dalloc<T>((size_t)P->nnz + kPad, e);
+    valAt_ = dalloc<T>((size_t)P->nnz + kPad, e);
     c_ = dalloc<T>(n, e);
     l_ = dalloc<T>(n, e);
     u_ = dalloc<T>(n, e);
@@ -424,8 +439,8 @@ class Engine final : public EngineBase {
       yavg_ = dalloc<T>(m, e);
       yanc_ = dalloc<T>(m, e);
       Ds_ = dalloc<T>(n, e);
-      fval_ = dalloc<T>(P->f_nnz, e);
-      ftval_ = dalloc<T>(P->f_nnz, e);
+      fval_ = dalloc<T>((size_t)P->f_nnz + kPad, e);
+      ftval_ = dalloc<T>((size_t)P->f_nnz + kPad, e);
       uvec_ = dalloc<T>(P->r, e);
       uvec2_ = dalloc<T>(P->r, e);
     }
@@ -662,7 +677,14 @@ class Engine final : public EngineBase {
   }
 
   cudaError_t block_graph(int len, cudaGraphExec_t* out) {
-    auto itg = graphs_.find(len);
+    if (graph_gen_ != sched_generation) {
+      for (auto& kv : graphs_) cudaGraphExecDestroy(kv.second);
+      graphs_.clear();
+      graph_launches_.clear();
+      graph_gen_ = sched_generation;
+    }
+    const long long key = (long long)len + 4096LL * block_ + (gamma_one_ ? (1LL << 40) : 0);
+    auto itg = graphs_.find(key);
     if (itg != graphs_.end()) {
       *out = itg->second;
       return cudaSuccess;
@@ -673,7 +695,7 @@ class Engine final : public EngineBase {
     if (e) return e;
     const long long before = launches_;
     launch_block(len, false, false, false);
-    graph_launches_[len] = launches_ - before;
+    graph_launches_[key] = launches_ - before;
     launches_ = before;
     e = cudaStreamEndCapture(s, &g);
     if (e) return e;
@@ -681,7 +703,8 @@ class Engine final : public EngineBase {
     e = cudaGraphInstantiate(&ge, g, 0);
     cudaGraphDestroy(g);
     if (e) return e;
-    graphs_[len] = ge;
+    graphs_[key] = ge;
+    graph_key_ = key;
     *out = ge;
     return cudaSuccess;
   }
@@ -711,7 +734,7 @@ class Engine final : public EngineBase {
         cudaGraphExec_t ge;
         if ((e = block_graph(len, &ge))) break;
         if ((e = cudaGraphLaunch(ge, s))) break;
-        launches_ += graph_launches_[len];
+        launches_ += graph_launches_[graph_key_];
       } else {
         launch_block(len, false, false, prof);
       }
@@ -894,8 +917,10 @@ class Engine final : public EngineBase {
   long long k_cur_ = 0;
   int block_ = 64;
   long long launches_ = 0;
-  std::map<int, cudaGraphExec_t> graphs_;
-  std::map<int, long long> graph_launches_;
+  std::map<long long, cudaGraphExec_t> graphs_;
+  std::map<long long, long long> graph_launches_;
+  unsigned long long graph_gen_ = 0;
+  long long graph_key_ = 0;
   std::vector<cudaEvent_t> prof_ev_;
   std::vector<int> prof_cls_;
   size_t prof_used_ = 0;

@@ -30,10 +30,18 @@ __global__ void row_absreduce(const int* __restrict__ rp, const double* __restri
 }
 
 // d_i = 1/sqrt(norm_i) (1 for an empty row/column); D_i *= d_i.  d overwrites norm.
-__global__ void factor_update(double* __restrict__ norm, int k, double* __restrict__ D) {
+// With qdiag (QP columns) the current scaled diagonal D_i^2 qdiag_i joins the
+// norm first: max with it (Ruiz, SUM = false) or added to it (Pock-Chambolle).
+template <bool SUM>
+__global__ void factor_update(double* __restrict__ norm, int k, double* __restrict__ D,
+                              const double* __restrict__ qdiag) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= k) return;
-  const double v = norm[i];
+  double v = norm[i];
+  if (qdiag) {
+    const double q = D[i] * D[i] * qdiag[i];
+    v = SUM ? v + q : fmax(v, q);
+  }
   const double d = (v > 0.0) ? 1.0 / sqrt(v) : 1.0;
   norm[i] = d;
   D[i] *= d;
@@ -51,6 +59,16 @@ __global__ void apply_scale(const int* __restrict__ rp, const int* __restrict__ 
     for (int p = rp[i] + lane; p < rp[i + 1]; p += 32)
       dst[p] = dc ? (src[p] * ri) * dc[col[p]] : src[p] * ri;
   }
+}
+
+// diag(Q)_j = D_j + sum_r F_jr^2 for Q = diag(D) + F F^T
+__global__ void q_diagonal(const int* __restrict__ frp, const double* __restrict__ fval,
+                           const double* __restrict__ D, int n, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = D[j];
+  for (int p = frp[j]; p < frp[j + 1]; ++p) s += fval[p] * fval[p];
+  out[j] = s;
 }
 
 __global__ void fill_ones(double* a, int k) {
@@ -83,19 +101,33 @@ cudaError_t compute_scaling(ProblemData& P, int ruiz_iters, bool pock_chambolle)
   if (n) fill_ones<<<grid_for(n), 256, 0, s>>>(P.Dc, n);
   if (P.nnz) cudaMemcpyAsync(P.val_s, P.val, sizeof(double) * P.nnz, cudaMemcpyDeviceToDevice, s);
   const bool have = (P.nnz > 0 && m > 0 && n > 0);
-  for (int t = 0; have && t < ruiz_iters; ++t) {
-    row_absreduce<false><<<warp_grid(m), 256, 0, s>>>(P.A.rp, P.val_s, nullptr, m, P.rowred);
-    row_absreduce<false><<<warp_grid(n), 256, 0, s>>>(P.At.rp, P.val_s, P.permT, n, P.colred);
-    factor_update<<<grid_for(m), 256, 0, s>>>(P.rowred, m, P.Dr);
-    factor_update<<<grid_for(n), 256, 0, s>>>(P.colred, n, P.Dc);
-    apply_scale<<<warp_grid(m), 256, 0, s>>>(P.A.rp, P.A.col, P.val_s, P.val_s, m, P.rowred,
-                                              P.colred);
+  const double* qd = nullptr;
+  if (P.is_qp && n) {
+    q_diagonal<<<grid_for(n), 256, 0, s>>>(P.F.rp, P.fval, P.D, n, P.qdiag);
+    qd = P.qdiag;
   }
-  if (have && pock_chambolle) {
-    row_absreduce<true><<<warp_grid(m), 256, 0, s>>>(P.A.rp, P.val_s, nullptr, m, P.rowred);
-    row_absreduce<true><<<warp_grid(n), 256, 0, s>>>(P.At.rp, P.val_s, P.permT, n, P.colred);
-    factor_update<<<grid_for(m), 256, 0, s>>>(P.rowred, m, P.Dr);
-    factor_update<<<grid_for(n), 256, 0, s>>>(P.colred, n, P.Dc);
+  for (int t = 0; (have || qd) && t < ruiz_iters; ++t) {
+    if (have) {
+      row_absreduce<false><<<warp_grid(m), 256, 0, s>>>(P.A.rp, P.val_s, nullptr, m, P.rowred);
+      row_absreduce<false><<<warp_grid(n), 256, 0, s>>>(P.At.rp, P.val_s, P.permT, n, P.colred);
+    } else {
+      cudaMemsetAsync(P.colred, 0, sizeof(double) * n, s);
+    }
+    if (have) factor_update<false><<<grid_for(m), 256, 0, s>>>(P.rowred, m, P.Dr, nullptr);
+    factor_update<false><<<grid_for(n), 256, 0, s>>>(P.colred, n, P.Dc, qd);
+    if (have)
+      apply_scale<<<warp_grid(m), 256, 0, s>>>(P.A.rp, P.A.col, P.val_s, P.val_s, m, P.rowred,
+                                                P.colred);
+  }
+  if ((have || qd) && pock_chambolle) {
+    if (have) {
+      row_absreduce<true><<<warp_grid(m), 256, 0, s>>>(P.A.rp, P.val_s, nullptr, m, P.rowred);
+      row_absreduce<true><<<warp_grid(n), 256, 0, s>>>(P.At.rp, P.val_s, P.permT, n, P.colred);
+      factor_update<true><<<grid_for(m), 256, 0, s>>>(P.rowred, m, P.Dr, nullptr);
+    } else {
+      cudaMemsetAsync(P.colred, 0, sizeof(double) * n, s);
+    }
+    factor_update<true><<<grid_for(n), 256, 0, s>>>(P.colred, n, P.Dc, qd);
   }
   // the scaled matrix from the original values and the accumulated factors
   if (have)

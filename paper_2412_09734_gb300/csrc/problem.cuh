@@ -37,6 +37,7 @@ struct ProblemData {
   double* val_s = nullptr;    // scaled A values, FP64 (A order)
   double* fval_s = nullptr;   // scaled F values (diag(Dc) F), FP64
   double* D_s = nullptr;      // scaled D (Dc^2 D)
+  double* qdiag = nullptr;    // diag(Q) = D + row sums of F^2 (QP)
   double* rowred = nullptr;   // m work
   double* colred = nullptr;   // n work
 

@@ -7,6 +7,8 @@
 
 namespace mpax {
 
+unsigned long long sched_generation = 0;
+
 // ---------------------------------------------------------------------------
 // Exclusive scan (three passes: block sums, scan of block sums, block scans)
 // ---------------------------------------------------------------------------
@@ -114,27 +116,43 @@ __global__ void sched_count(const int* __restrict__ rp, int rows, int* __restric
 }
 
 __global__ void sched_fill(const int* __restrict__ rp, int rows, const int* __restrict__ cnt,
-                           const int* __restrict__ off, int4* __restrict__ items) {
+                           const int* __restrict__ off, int4* __restrict__ items,
+                           int* __restrict__ err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const int c = cnt[i];
   if (c == 0) return;
-  const int len = rp[i + 1] - rp[i];
+  const int b = rp[i], len = rp[i + 1] - b;
   const int o = off[i];
   if (len > kLongRow) {
-    for (int s = 0; s < c; ++s) items[o + s] = make_int4(i, s, c, o);
+    if (c > 0xffff) {  // slice index and count are packed in 16 bits each
+      atomicOr(err, 1);
+      return;
+    }
+    for (int s = 0; s < c; ++s) {
+      const int p0 = b + s * kSliceNnz;
+      items[o + s] = make_int4(-(i + 1), p0, min(p0 + kSliceNnz, b + len), (s << 16) | c);
+    }
   } else {
-    items[o] = make_int4(i, -1, -1, 0);
+    items[o] = make_int4(i, -1, b, -1);
   }
 }
 
 // A packed item ends where the next item begins.
-__global__ void sched_fix(int4* __restrict__ items, int n_items, int rows) {
+__global__ void sched_fix(int4* __restrict__ items, int n_items, int rows,
+                          const int* __restrict__ rp) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_items) return;
   int4 it = items[k];
-  if (it.z < 0) {
-    it.y = (k + 1 < n_items) ? items[k + 1].x : rows;
+  if (it.x >= 0) {
+    int next = rows;
+    if (k + 1 < n_items) {
+      // only the .x field of the next item is read; this kernel never writes it
+      const int nx = reinterpret_cast<const int*>(items + k + 1)[0];
+      next = nx >= 0 ? nx : -(nx + 1);
+    }
+    it.y = next;
+    it.w = rp[next];
     items[k] = it;
   }
 }
@@ -149,15 +167,20 @@ void free_schedule(Sched& sc) {
 
 cudaError_t build_schedule(const Csr& A, Sched& sc, cudaStream_t s, int* tmp_rows,
                            int* tmp_scan) {
-  // tmp_rows: rows+1 ints (counts, then offsets in place of a second buffer)
-  free_schedule(sc);
+  // tmp_rows: rows + 2 ints.  Buffers of an existing schedule with the same
+  // item count are reused, so device pointers captured in CUDA graphs stay valid.
   sc.rows = A.rows;
   cudaError_t e;
-  if (A.rows == 0) return cudaSuccess;
+  if (A.rows == 0) {
+    free_schedule(sc);
+    return cudaSuccess;
+  }
   int* cnt = tmp_rows;
   int* off = nullptr;
-  e = cudaMallocAsync(&off, sizeof(int) * (A.rows + 1), s);
-  if (e) return e;
+  int* err = nullptr;
+  if ((e = cudaMallocAsync(&off, sizeof(int) * (A.rows + 2), s))) return e;
+  err = off + A.rows + 1;
+  if ((e = cudaMemsetAsync(err, 0, sizeof(int), s))) return e;
   const int g = (A.rows + 255) / 256;
   sched_count<<<g, 256, 0, s>>>(A.rp, A.rows, cnt);
   if ((e = scan_exclusive(cnt, off, A.rows, tmp_scan, s))) return e;
@@ -165,16 +188,26 @@ cudaError_t build_schedule(const Csr& A, Sched& sc, cudaStream_t s, int* tmp_row
   if ((e = cudaMemcpyAsync(&n_items, off + A.rows, sizeof(int), cudaMemcpyDeviceToHost, s)))
     return e;
   if ((e = cudaStreamSynchronize(s))) return e;
-  sc.n_items = n_items;
-  if ((e = cudaMalloc(&sc.items, sizeof(int4) * std::max(n_items, 1)))) return e;
-  if ((e = cudaMalloc(&sc.cnt, sizeof(int) * std::max(n_items, 1)))) return e;
-  if ((e = cudaMalloc(&sc.carry, sizeof(double) * std::max(n_items, 1)))) return e;
-  if ((e = cudaMalloc(&sc.part, sizeof(double) * kPartQ * std::max(n_items, 1)))) return e;
-  cudaMemsetAsync(sc.cnt, 0, sizeof(int) * std::max(n_items, 1), s);
-  cudaMemsetAsync(sc.part, 0, sizeof(double) * kPartQ * std::max(n_items, 1), s);
-  sched_fill<<<g, 256, 0, s>>>(A.rp, A.rows, cnt, off, sc.items);
-  if (n_items > 0) sched_fix<<<(n_items + 255) / 256, 256, 0, s>>>(sc.items, n_items, A.rows);
+  if (sc.items == nullptr || sc.n_items != n_items) {
+    free_schedule(sc);
+    sc.rows = A.rows;
+    sc.n_items = n_items;
+    if ((e = cudaMalloc(&sc.items, sizeof(int4) * std::max(n_items, 1)))) return e;
+    if ((e = cudaMalloc(&sc.cnt, sizeof(int) * std::max(n_items, 1)))) return e;
+    if ((e = cudaMalloc(&sc.carry, sizeof(double) * std::max(n_items, 1)))) return e;
+    if ((e = cudaMalloc(&sc.part, sizeof(double) * kPartQ * std::max(n_items, 1)))) return e;
+    cudaMemsetAsync(sc.cnt, 0, sizeof(int) * std::max(n_items, 1), s);
+    cudaMemsetAsync(sc.part, 0, sizeof(double) * kPartQ * std::max(n_items, 1), s);
+    ++sched_generation;
+  }
+  sched_fill<<<g, 256, 0, s>>>(A.rp, A.rows, cnt, off, sc.items, err);
+  if (n_items > 0)
+    sched_fix<<<(n_items + 255) / 256, 256, 0, s>>>(sc.items, n_items, A.rows, A.rp);
+  int herr = 0;
+  if ((e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s))) return e;
+  if ((e = cudaStreamSynchronize(s))) return e;
   cudaFreeAsync(off, s);
+  if (herr) return cudaErrorInvalidValue;  // a row longer than 65535 slices
   return cudaGetLastError();
 }
 
