@@ -216,6 +216,42 @@ mpax_status mpax_get_iterate(const mpax_problem* prob, double* x, double* y, dou
 mpax_status mpax_kkt(mpax_problem* prob, const double* x, const double* y, mpax_mem_kind kind,
                      double* out);
 
+/* ---- Evaluation without device allocation --------------------------------- */
+
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * cannot call cudaMalloc: code that runs inside a device-memory pool or budget
+ * it does not own (a framework allocator, a serving process with a fixed
+ * reservation), or that must not allocate while a stream is being captured.
+ *
+ * It returns what mpax_kkt returns (same definitions, out[0..5]) for the LP
+ * min c^T x s.t. lc <= A x <= uc, l <= x <= u at the point (x, y), computed
+ * directly on caller-owned DEVICE arrays, without a problem handle and without
+ * allocating anything: no cudaMalloc, no cudaFree, no allocating library call.
+ * The caller passes A and its transpose as CSR (int64 row pointers, int32
+ * columns sorted within each row, FP64 values; row_ptr has m+1 entries,
+ * row_ptr_t has n+1), the vectors (c, l, u, x: n; lc, uc, y: m) and `out`
+ * (6 doubles of device memory).  The work is queued on `cuda_stream` (NULL =
+ * legacy default stream) and the call returns without waiting for it.
+ *
+ * Scratch: the per-block partial sums live in one static device array of
+ * 2.5 MiB, held by every GPU that loads the library until the process exits.
+ * Its size is the limit: m and n must each be at most 16,777,216; larger sizes
+ * return MPAX_ERR_UNSUPPORTED with a message.  Every slot read by a call is
+ * written earlier in the same call, so nothing needs clearing between calls,
+ * but all calls share the array: calls whose device work overlaps (on
+ * different streams, or from different host threads) race and give wrong
+ * results.  The first call on each device looks up the array's device address
+ * (with that device current); make that first call before any stream capture.
+ * Errors: MPAX_ERR_INVALID_ARGUMENT (negative size, NULL pointer),
+ * MPAX_ERR_UNSUPPORTED (size limit, device index >= 64), MPAX_ERR_CUDA. */
+mpax_status mpax_lp_kkt_noalloc(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                                const int32_t* col_idx, const double* val,
+                                const int64_t* row_ptr_t, const int32_t* col_idx_t,
+                                const double* val_t, const double* c, const double* lc,
+                                const double* uc, const double* l, const double* u,
+                                const double* x, const double* y, double* out,
+                                void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,12 @@ mpax_status fail(mpax_status s, const std::string& msg) {
   return s;
 }
 
+}  // namespace
+
+void mpax::set_last_error(const char* msg) { g_err = msg; }
+
+namespace {
+
 mpax_status cuda_fail(cudaError_t e, const char* where) {
   if (e == cudaErrorMemoryAllocation)
     return fail(MPAX_ERR_OUT_OF_MEMORY, std::string(where) + ": out of device memory");

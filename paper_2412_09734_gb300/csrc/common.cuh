@@ -118,6 +118,9 @@ __device__ __forceinline__ T ld_ro(const T* p) {
 // host-side launch helpers (defined in the .cu files)
 // ---------------------------------------------------------------------------
 
+// Message returned by mpax_last_error() for the calling thread.
+void set_last_error(const char* msg);
+
 // Exclusive scan of `n` int32 counts into out[0..n] (out[n] = total).
 // `tmp` must hold scan_tmp_ints(n) ints.
 size_t scan_tmp_ints(int n);

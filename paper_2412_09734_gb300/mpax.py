@@ -28,7 +28,7 @@ EXPORTED = ["mpax_version", "mpax_last_error", "mpax_status_string", "mpax_optio
             "mpax_lp_create", "mpax_qp_create_diag_lowrank", "mpax_solve", "mpax_get_solution",
             "mpax_get_stats", "mpax_destroy", "mpax_prepare", "mpax_get_scaling",
             "mpax_get_transpose", "mpax_set_iterate", "mpax_iterate", "mpax_get_iterate",
-            "mpax_kkt"]
+            "mpax_kkt", "mpax_lp_kkt_noalloc"]
 
 
 class MpaxError(RuntimeError):
@@ -108,6 +108,7 @@ _sig = {
     "mpax_iterate": ([_P, _I64], _INT),
     "mpax_get_iterate": ([_P, _P, _P, _P, _P, _INT], _INT),
     "mpax_kkt": ([_P, _P, _P, _INT, _P], _INT),
+    "mpax_lp_kkt_noalloc": ([_I32, _I32, _I64] + [_P] * 15, _INT),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
