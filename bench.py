@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sparse_lp_500k", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="sparse_lp_500k",
+                    choices=list(WORKLOADS) + ["ragged_lp_4096", "shared_dense_512",
+                                               "qp_200k"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-iters", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -397,8 +399,214 @@ def run_profile_target(args):
     return 0
 
 
+def run_batch(args):
+    """Ragged batch of 4096 LPs (m ~ U{50..2000}, n = 2m, 1% density), one
+    persistent launch per solve; reports solved instances per second and the
+    per-instance device times."""
+    import torch
+    torch.cuda.init()
+    from paper_2412_09734_gb300 import mpax as C
+    from synth import ragged_lp_batch
+    d = ragged_lp_batch(4096)
+    keys = ("m_off", "n_off", "row_ptr", "col", "val", "c", "lc", "uc", "l", "u")
+    dev = {k: torch.from_numpy(np.ascontiguousarray(d[k])).cuda() for k in keys}
+    out = {}
+    for prec, name in ((C.MPAX_PREC_MIXED, "mixed"), (C.MPAX_PREC_FP64, "fp64")):
+        h = C.mpax_lp_batch_create(d["B"], *[dev[k] for k in keys])
+        opts = C.mpax_options_default(precision=prec)
+        for _ in range(args.warmup if name == "mixed" else 1):
+            C.mpax_batch_solve(h, opts)
+        steps = args.steps if name == "mixed" else max(1, args.steps // 2)
+        clocks = Clocks(0)
+        clocks.start()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            C.mpax_batch_solve(h, opts)
+        e1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1) / steps
+        summ, per = C.mpax_batch_get_stats(h, d["B"])
+        C.mpax_batch_destroy(h)
+        out[name] = dict(solves_per_s=d["B"] / (ms / 1e3), ms_per_batch=ms,
+                         n_optimal=summ["n_optimal"], p50_s=summ["instance_seconds_p50"],
+                         p99_s=summ["instance_seconds_p99"],
+                         iterations_mean=summ["iterations_total"] / d["B"],
+                         rel_kkt_max=summ["rel_kkt_max"], clocks=clk,
+                         gpu_launches=summ["kernel_launches"])
+    nnz = int(d["row_ptr"][-1])
+    line = {"metric": "ragged batch LP solves/s to rel KKT 1e-4 (4096 instances)",
+            "value": out["mixed"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["mixed"]["ms_per_batch"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"4096 LPs, m ~ U{{50..2000}}, n = 2m, 1% density, total "
+                                   f"nnz {nnz}, one persistent launch per batch"},
+            "mixed": out["mixed"], "fp64": out["fp64"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return p["bf16_tflops_sustained"], "measured (bf16_tflops_sustained)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback 1.7 PFLOP/s sustained"
+
+
+def run_shared(args):
+    """Shared-matrix dense LP batch: A 16384 x 32768 FP32, 512 cost vectors solved
+    together, K X and K^T Y as BF16x3 tensor-core GEMMs (FP32 accumulate) and,
+    beside it, as FP32 GEMMs; one step = one batch solve to rel KKT 1e-4."""
+    import torch
+    torch.cuda.init()
+    from paper_2412_09734_gb300 import mpax as C
+    from synth import shared_dense_lp_batch
+    m, n, B = 16384, 32768, 512
+    d = shared_dense_lp_batch(m, n, B, bound_frac=0.5)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(d[k])).cuda()
+           for k in ("A", "C", "b", "l", "u")}
+    out = {}
+    for fp32, name in ((False, "bf16x3"), (True, "fp32")):
+        h = C.mpax_lp_shared_create(m, n, B, dev["A"], dev["C"], dev["b"], dev["b"], dev["l"],
+                                    dev["u"])
+        opts = C.mpax_options_default()
+        warm = args.warmup if not fp32 else 1
+        steps = args.steps if not fp32 else max(1, args.fp64_steps // 3)
+        for _ in range(warm):
+            C.mpax_shared_solve(h, opts, fp32)
+        clocks = Clocks(0)
+        clocks.start()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            C.mpax_shared_solve(h, opts, fp32)
+        e1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1) / steps
+        summ, per = C.mpax_shared_get_stats(h, B)
+        C.mpax_shared_destroy(h)
+        flops = summ["gemm_flops"]
+        out[name] = dict(solves_per_s=B / (ms / 1e3), ms_per_batch=ms,
+                         n_optimal=summ["n_optimal"], iterations_max=int(per["iterations"].max()),
+                         rel_kkt_max=summ["rel_kkt_max"], gemms=summ["gemms"],
+                         gemm_tflops_per_solve=flops / 1e12,
+                         tensor_tflops_over_solve=flops / (ms / 1e3) / 1e12,
+                         obj_rel_err_max=float(np.max(np.abs(per["primal_obj"] - d["opt_value"])
+                                                      / (1 + np.abs(d["opt_value"])))),
+                         clocks=clk, gpu_launches=summ["kernel_launches"])
+    pk, src = bf16_peak()
+    a = out["bf16x3"]["tensor_tflops_over_solve"]
+    line = {"metric": "shared-matrix dense LP batch solves/s to rel KKT 1e-4",
+            "value": out["bf16x3"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["bf16x3"]["ms_per_batch"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/f32", "data": "synthetic",
+            "config": {"workload": f"dense A {m}x{n} FP32 N(0,1/n), box [0,1], equality rows, "
+                                   f"{B} cost vectors (half of x0 at bounds), rel KKT 1e-4",
+                       "l2": "A is 2.1 GB FP32 / 2 x 1.1 GB BF16, larger than L2"},
+            "roofline": {"bound": "tensor", "achieved": a, "peak": pk, "unit": "TFLOP/s",
+                         "frac": a / pk, "traffic": None,
+                         "note": "BF16 GEMM flops executed (3 per BF16x3 product) over the whole "
+                                 "solve time, so a lower bound on the GEMMs' own rate",
+                         "peak_source": src + ", of measured"},
+            "bf16x3": out["bf16x3"], "fp32": out["fp32"],
+            "speedup_vs_fp32_products": out["fp32"]["ms_per_batch"] / out["bf16x3"]["ms_per_batch"],
+            "clocks": out["bf16x3"]["clocks"], "gpu_launches": out["bf16x3"]["gpu_launches"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_qp(args):
+    """Differentiable convex QP (rAPDHG): n = 200000, m = 100000, Q = D + F F^T
+    (F n x 32, 1% density), A 0.01% density, box [-1, 1], equality rows.  One step
+    = forward solve to rel KKT 1e-4 plus the backward adjoint of
+    1/2 ||x* - x_target||^2 for dL/dc, dL/db, dL/dD."""
+    import torch
+    torch.cuda.init()
+    from paper_2412_09734_gb300 import mpax as C
+    from synth import instance_seed, qp_instance
+    n, m = 200_000, 100_000
+    d = qp_instance(n, m, seed=instance_seed(3), a_density=1e-4, f_cols=32, f_density=0.01)
+    keys = ("row_ptr", "col", "val", "c", "lc", "uc", "l", "u", "D")
+    fk = ("f_row_ptr", "f_col", "f_val")
+    dev = {k: torch.from_numpy(np.ascontiguousarray(d[k])).cuda() for k in keys + fk}
+    xt = torch.from_numpy(d["x_target"]).cuda()
+    out = {}
+    for prec, name in ((C.MPAX_PREC_MIXED, "mixed"), (C.MPAX_PREC_FP64, "fp64")):
+        opts = C.mpax_options_default(precision=prec)
+
+        def step():
+            h = C.mpax_qp_create_diag_lowrank(
+                m, n, dev["row_ptr"], dev["col"], dev["val"], dev["c"], dev["lc"], dev["uc"],
+                dev["l"], dev["u"], dev["D"], d["f_cols"], dev["f_row_ptr"], dev["f_col"],
+                dev["f_val"])
+            try:
+                C.mpax_solve(h, opts)
+                s = C.mpax_get_stats(h)
+                x, _ = C.mpax_get_solution(h, m, n, device=xt)
+                t1 = time.perf_counter()
+                _, _, _, info = C.mpax_qp_adjoint(h, x - xt, m, n, tol=1e-8)
+                torch.cuda.synchronize()
+                return s, info, time.perf_counter() - t1
+            finally:
+                C.mpax_destroy(h)
+
+        warm = args.warmup if name == "mixed" else 1
+        steps = args.steps if name == "mixed" else max(1, args.fp64_steps // 3)
+        for _ in range(warm):
+            step()
+        clocks = Clocks(0)
+        clocks.start()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        its, bw, res, launches = [], [], [], 0
+        for _ in range(steps):
+            s, info, tb = step()
+            assert s["termination_name"] == "optimal", s
+            its.append(s["iterations"])
+            bw.append(tb)
+            res.append(info["rel_residual"])
+            launches += s["kernel_launches"]
+        e1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = dict(steps_per_s=1e3 / ms, ms_per_step=ms, iterations=float(np.mean(its)),
+                         backward_s=float(np.mean(bw)), adjoint_rel_residual=max(res),
+                         clocks=clk, gpu_launches=launches)
+    line = {"metric": "differentiable QP forward (rel KKT 1e-4) + backward steps/s",
+            "value": out["mixed"]["steps_per_s"], "unit": "steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["mixed"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"QP n={n} m={m}, Q = diag(U[0.1,1]) + F F^T (F n x 32, 1%), "
+                                   f"A 0.01% N(0,1), box [-1,1], b = A x0; loss 1/2||x*-x_t||^2"},
+            "mixed": out["mixed"], "fp64": out["fp64"],
+            "speedup_vs_fp64": out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"],
+            "clocks": out["mixed"]["clocks"], "gpu_launches": out["mixed"]["gpu_launches"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "ragged_lp_4096":
+        return run_batch(args)
+    if args.workload == "shared_dense_512":
+        return run_shared(args)
+    if args.workload == "qp_200k":
+        return run_qp(args)
     if args.profile_run:
         return run_profile_target(args)
     if args.impl == "reference":

@@ -99,6 +99,10 @@ typedef struct mpax_options {
   int32_t use_graphs;         /* 1: replay each check block as one CUDA graph */
   int32_t profile_kernels;    /* 0: 1 = time every fused SpMV launch with CUDA events
                                  (no graphs; for measurement only) */
+  int32_t fp64_continuation;  /* 1: a MIXED solve whose relative KKT error stops
+                                 improving (no 10% gain over stall_checks checks)
+                                 continues in FP64 from its FP32 point */
+  int32_t stall_checks;       /* 8 */
 } mpax_options;
 
 typedef struct mpax_stats {
@@ -118,6 +122,7 @@ typedef struct mpax_stats {
    * [0] primal fused SpMV^T, [1] dual fused SpMV, [2] KKT SpMV, [3] KKT SpMV^T */
   double profile_ms[4];
   int64_t profile_launches[4];
+  int64_t fp64_iterations;           /* iterations of the FP64 continuation (MIXED) */
 } mpax_stats;
 
 typedef struct mpax_problem mpax_problem;
@@ -215,6 +220,107 @@ mpax_status mpax_get_iterate(const mpax_problem* prob, double* x, double* y, dou
  * out[5] rel.  Needs mpax_prepare. */
 mpax_status mpax_kkt(mpax_problem* prob, const double* x, const double* y, mpax_mem_kind kind,
                      double* out);
+
+/* ---- Differentiation of the returned solution ------------------------------ */
+
+/* Gradients of an LP's optimal value at the returned point (x, y) of the last
+ * mpax_solve, by the envelope theorem (the paper differentiates LPs through
+ * surrogate losses, Sec. 3.4; the value gradient is what those losses use):
+ * dc = x, dlc = y^+, duc = -y^-, dl = lam^+, du = -lam^- with lam = c - A^T y,
+ * all unscaled.  Any output may be NULL; lengths n (dc, dl, du), m (dlc, duc). */
+mpax_status mpax_lp_value_grad(mpax_problem* prob, double* dc, double* dlc, double* duc,
+                               double* dl, double* du, mpax_mem_kind kind);
+
+/* Implicit adjoint of a strictly convex QP's returned solution x* (Q = diag(D)
+ * + F F^T) for a loss with gradient g = dL/dx* (n).  On the active set at x*
+ * (free variables: strictly inside the box, or at a bound with multiplier
+ * |lam_j| <= 1e-7 (1 + ||c||_inf), bound distance tested at 1e-7 (1 + |bound|);
+ * active rows: equalities and rows with y_i != 0) it solves
+ *     [[Q_FF, A_RF^T], [A_RF, 0]] [w; v] = [g_F; 0]
+ * by MINRES (relative residual tol, at most max_iter iterations) with the
+ * library's SpMVs in FP64, and returns dc = -w (free entries, else 0),
+ * db = v (active rows, else 0; n.b. b is the row bound of equality rows),
+ * dD = -w x* (free entries; dD may be NULL).  info (HOST, 2 doubles,
+ * nullable) receives the iteration count and the final relative residual. */
+mpax_status mpax_qp_adjoint(mpax_problem* prob, const double* g, double* dc, double* db,
+                            double* dD, double tol, int32_t max_iter, mpax_mem_kind kind,
+                            double* info);
+
+/* ---- Ragged batch of independent LPs ---------------------------------------- */
+
+/* B independent LPs of problem (1) (Q = 0), of any sizes, solved together in
+ * one persistent kernel launch (the paper's batched solving, Sec. 3.2, without
+ * its same-shape restriction).  Instance b owns rows [m_off[b], m_off[b+1]) and
+ * columns [n_off[b], n_off[b+1]) (m_off, n_off: B+1 int64 entries starting at
+ * 0).  row_ptr is the CSR row pointer over all rows (sum m + 1 entries, global
+ * nonzero offsets); col_idx are column indices LOCAL to each instance
+ * (0 <= col < n_b); val and the vectors are packed in instance order.
+ * Validation and ownership as mpax_lp_create.  Every instance gets its own
+ * scaling, step sizes, primal weight, restarts and termination. */
+typedef struct mpax_batch mpax_batch;
+
+typedef struct mpax_batch_stats {
+  int32_t B;
+  int32_t n_optimal;              /* instances that met the relative KKT test */
+  int64_t iterations_total, iterations_max, restarts_total;
+  double rel_kkt_max;
+  double instance_seconds_p50;    /* per-instance device time (CTA start to finish) */
+  double instance_seconds_p99;
+  double instance_seconds_max;
+  double solve_seconds;           /* whole mpax_batch_solve, host wall clock */
+  int64_t kernel_launches;
+} mpax_batch_stats;
+
+mpax_status mpax_lp_batch_create(int32_t B, const int64_t* m_off, const int64_t* n_off,
+                                 const int64_t* row_ptr, const int32_t* col_idx,
+                                 const double* val, const double* c, const double* lc,
+                                 const double* uc, const double* l, const double* u,
+                                 mpax_mem_kind kind, void* cuda_stream, mpax_batch** out);
+/* Options as mpax_solve (reflection_gamma must be 1).  The batch runs as one
+ * persistent launch; time_limit is measured on the device clock from the start
+ * of that launch and is capped at 600 s, so the launch always ends (instances
+ * still running then finish with MPAX_TERM_TIME_LIMIT).  Each instance needs m_b + n_b <= 51,200 (FP32) or 25,600 (FP64) for its
+ * shared-memory vectors; larger instances return MPAX_ERR_UNSUPPORTED. */
+mpax_status mpax_batch_solve(mpax_batch* batch, const mpax_options* opts);
+/* Returned points (x^, y^) of every instance, packed like the inputs. */
+mpax_status mpax_batch_get_solution(const mpax_batch* batch, double* x, double* y,
+                                    mpax_mem_kind kind);
+/* Summary, and (each pointer nullable, HOST memory, B entries) per-instance
+ * termination, iterations, relative KKT error, primal objective, device seconds. */
+mpax_status mpax_batch_get_stats(const mpax_batch* batch, mpax_batch_stats* stats,
+                                 int32_t* status, int64_t* iterations, double* rel_kkt,
+                                 double* primal_obj, double* seconds);
+void mpax_batch_destroy(mpax_batch* batch);
+
+/* ---- Batch of LPs sharing one dense constraint matrix ----------------------- */
+
+/* B LPs  min c_k^T x  s.t.  lc <= A x <= uc, l <= x <= u  with one dense A
+ * (m x n, FP32, row-major) and per-instance costs C (B x n, row-major: row k is
+ * c_k); lc, uc (m) and l, u (n) are shared.  Stacking the iterates as columns
+ * makes both products of an iteration dense GEMMs (the paper's batched solving,
+ * Sec. 3.2, with a shared matrix); they run on the tensor cores as three BF16
+ * GEMMs with FP32 accumulation (BF16x3 split of the scaled matrix and of the
+ * iterates), or, with fp32_products = 1, as one FP32 GEMM on the FP32 pipes.
+ * Every instance has its own step sizes, primal weight, restarts and
+ * termination (Algorithm 1).  Arrays are copied at create. */
+typedef struct mpax_shared mpax_shared;
+mpax_status mpax_lp_shared_create(int32_t m, int32_t n, int32_t B, const float* A,
+                                  const double* C, const double* lc, const double* uc,
+                                  const double* l, const double* u, mpax_mem_kind kind,
+                                  void* cuda_stream, mpax_shared** out);
+/* Options as mpax_solve (reflection_gamma must be 1); time_limit is checked on
+ * the host clock at each KKT check. */
+mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* opts, int32_t fp32_products);
+/* X: B x n (row k = x of instance k), Y: B x m, unscaled; either may be NULL. */
+mpax_status mpax_shared_get_solution(const mpax_shared* sh, double* X, double* Y,
+                                     mpax_mem_kind kind);
+/* As mpax_batch_get_stats (seconds = host time from solve start to the check at
+ * which the instance finished); gemm_info (HOST, 3 doubles, nullable) receives
+ * the GEMM count, their flops, and ||A~||_2. */
+mpax_status mpax_shared_get_stats(const mpax_shared* sh, mpax_batch_stats* stats,
+                                  int32_t* status, int64_t* iterations, double* rel_kkt,
+                                  double* primal_obj, double* seconds, double* gemm_info);
+void mpax_shared_destroy(mpax_shared* sh);
 
 /* ---- Evaluation without device allocation --------------------------------- */
 

@@ -1,0 +1,103 @@
+"""torch.autograd layers over the C ABI (marshalling only; the solve and the
+adjoint run in the library's kernels).
+
+QPLayer: x* = argmin 1/2 x^T (diag(D) + F F^T) x + c^T x  s.t.  A x = b, l <= x <= u,
+         differentiable in (c, b, D) through the implicit adjoint on the active set.
+LPValue: v = min c^T x  s.t.  lc <= A x <= uc, l <= x <= u, differentiable in
+         (c, lc, uc) through the envelope theorem (dv/dc = x*, ...).
+SharedLPValues: v_k = min c_k^T x  s.t.  lc <= A x <= uc, l <= x <= u for the B rows
+         c_k of C with one dense A shared by the batch; dv_k/dc_k = x_k*.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import mpax as C
+
+
+def _f64(t):
+    return t.detach().to(torch.float64).contiguous()
+
+
+class QPLayer(torch.autograd.Function):
+    """forward(c, b, D, data, options) -> x*.
+
+    `data` holds the fixed parts as CUDA tensors: m, n, row_ptr, col, val, l, u,
+    f_row_ptr, f_col, f_val, r.  `options` are mpax_options fields."""
+
+    @staticmethod
+    def forward(ctx, c, b, D, data, options):
+        d = data
+        h = C.mpax_qp_create_diag_lowrank(
+            d["m"], d["n"], d["row_ptr"], d["col"], d["val"], _f64(c), _f64(b), _f64(b),
+            d["l"], d["u"], _f64(D), d["r"], d["f_row_ptr"], d["f_col"], d["f_val"])
+        try:
+            C.mpax_solve(h, C.mpax_options_default(**(options or {})))
+            x, _ = C.mpax_get_solution(h, d["m"], d["n"], device=c)
+        except Exception:
+            C.mpax_destroy(h)
+            raise
+        ctx.h = h
+        ctx.m, ctx.n = d["m"], d["n"]
+        return x.to(c.dtype)
+
+    @staticmethod
+    def backward(ctx, gx):
+        try:
+            dc, db, dD, _ = C.mpax_qp_adjoint(ctx.h, _f64(gx), ctx.m, ctx.n)
+        finally:
+            C.mpax_destroy(ctx.h)
+            ctx.h = None
+        return dc.to(gx.dtype), db.to(gx.dtype), dD.to(gx.dtype), None, None
+
+
+class LPValue(torch.autograd.Function):
+    """forward(c, lc, uc, data, options) -> optimal value (0-dim tensor).
+
+    `data` holds m, n, row_ptr, col, val, l, u as CUDA tensors."""
+
+    @staticmethod
+    def forward(ctx, c, lc, uc, data, options):
+        d = data
+        h = C.mpax_lp_create(d["m"], d["n"], d["row_ptr"], d["col"], d["val"], _f64(c),
+                             _f64(lc), _f64(uc), d["l"], d["u"])
+        try:
+            C.mpax_solve(h, C.mpax_options_default(**(options or {})))
+            stats = C.mpax_get_stats(h)
+            g = C.mpax_lp_value_grad(h, d["m"], d["n"], device=c)
+        finally:
+            C.mpax_destroy(h)
+        ctx.save_for_backward(g["c"], g["lc"], g["uc"])
+        return torch.tensor(stats["primal_obj"], dtype=c.dtype, device=c.device)
+
+    @staticmethod
+    def backward(ctx, gv):
+        dc, dlc, duc = ctx.saved_tensors
+        return (gv * dc).to(gv.dtype), (gv * dlc).to(gv.dtype), (gv * duc).to(gv.dtype), None, None
+
+
+class SharedLPValues(torch.autograd.Function):
+    """forward(C, A, lc, uc, l, u, options, fp32_products) -> (B,) optimal values.
+
+    C is (B, n); A is a dense (m, n) FP32 CUDA tensor shared by the batch.  Only C
+    is differentiable: dv_k/dc_k = x_k*."""
+
+    @staticmethod
+    def forward(ctx, Cm, A, lc, uc, l, u, options, fp32_products=False):
+        B, n = Cm.shape
+        m = A.shape[0]
+        h = C.mpax_lp_shared_create(m, n, B, A.detach(), _f64(Cm), _f64(lc), _f64(uc),
+                                    _f64(l), _f64(u))
+        try:
+            C.mpax_shared_solve(h, C.mpax_options_default(**(options or {})), fp32_products)
+            _, per = C.mpax_shared_get_stats(h, B)
+            X, _ = C.mpax_shared_get_solution(h, m, n, B, device=Cm)
+        finally:
+            C.mpax_shared_destroy(h)
+        ctx.save_for_backward(X)
+        return torch.as_tensor(per["primal_obj"], dtype=Cm.dtype, device=Cm.device)
+
+    @staticmethod
+    def backward(ctx, gv):
+        (X,) = ctx.saved_tensors
+        return (gv[:, None] * X).to(gv.dtype), None, None, None, None, None, None, None

@@ -17,7 +17,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmpax_gb300.so")
-SOURCES = ["api.cu", "pdhg.cu", "prep.cu", "sparse.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "pdhg.cu", "prep.cu", "sparse.cu", "noalloc.cu", "batch.cu", "adjoint.cu",
+           "shared.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -61,7 +62,9 @@ def build(verbose: bool = False, force: bool = False) -> str:
         list(ex.map(run, jobs))
     if force or jobs or not _newer(LIB, objs):
         tmp = LIB + ".tmp"
-        run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
+        libdir = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
+        run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lcublas",
+             "-Xlinker", f"-rpath={libdir}"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -351,6 +351,8 @@ mpax_status check_options(const mpax_options* o) {
   if (o->feasibility_polishing)
     return fail(MPAX_ERR_UNSUPPORTED, "feasibility polishing is not built");
   if (!(o->time_limit >= 0)) return fail(MPAX_ERR_INVALID_ARGUMENT, "time_limit must be >= 0");
+  if (o->fp64_continuation && o->stall_checks < 1)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "stall_checks must be >= 1");
   return MPAX_OK;
 }
 
@@ -400,6 +402,12 @@ double now_s() {
 }
 
 }  // namespace
+
+namespace mpax {
+ProblemData* problem_data(mpax_problem* p) { return &p->P; }
+void problem_order_after_user(mpax_problem* p) { order_after_user(p); }
+void problem_order_user_after(mpax_problem* p) { order_user_after(p); }
+}  // namespace mpax
 
 // ============================================================================
 // exported functions
@@ -453,6 +461,8 @@ void mpax_options_default(mpax_options* o) {
   o->power_tol = 1e-4;
   o->use_graphs = 1;
   o->profile_kernels = 0;
+  o->fp64_continuation = 1;
+  o->stall_checks = 8;
 }
 
 mpax_status mpax_lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
@@ -526,6 +536,31 @@ mpax_status mpax_solve(mpax_problem* pb, const mpax_options* opts, const double*
   RunInfo info;
   cudaError_t e = eng->run(*opts, &info);
   if (e) return cuda_fail(e, "solve");
+  long long fp64_iters = 0;
+  if (info.termination == kTermStalled) {
+    // FP64 continuation from the FP32 point (unscaled), with the remaining budget
+    TRY_CUDA(eng->get_solution(pb->dxa, pb->dya), "fp32 point");
+    mpax_options o64 = *opts;
+    o64.precision = MPAX_PREC_FP64;
+    o64.iteration_limit = std::max<long long>(1, opts->iteration_limit - info.iterations);
+    st = do_prepare(pb, &o64, &launches);
+    if (st) return st;
+    eng = pb->eng[pb->cur];
+    TRY_CUDA(eng->init_iterate(pb->dxa, pb->dya), "fp64 start");
+    RunInfo info64;
+    e = eng->run(o64, &info64);
+    if (e) return cuda_fail(e, "fp64 continuation");
+    fp64_iters = info64.iterations;
+    info64.iterations += info.iterations;
+    info64.restarts += info.restarts;
+    info64.checks += info.checks;
+    info64.launches += info.launches;
+    for (int i = 0; i < 4; ++i) {
+      info64.profile_ms[i] += info.profile_ms[i];
+      info64.profile_launches[i] += info.profile_launches[i];
+    }
+    info = info64;
+  }
   DevState h;
   TRY_CUDA(eng->read_state(&h), "read state");
   TRY_CUDA(order_user_after(pb), "stream order");
@@ -553,6 +588,7 @@ mpax_status mpax_solve(mpax_problem* pb, const mpax_options* opts, const double*
     S.profile_ms[i] = info.profile_ms[i];
     S.profile_launches[i] = info.profile_launches[i];
   }
+  S.fp64_iterations = fp64_iters;
   pb->solved = true;
   pb->last_opts = *opts;
   if (info.termination == MPAX_TERM_NUMERICAL_ERROR)

@@ -1,0 +1,750 @@
+// Ragged batch of independent LPs solved by r^2HPDHG (Algorithm 1) in ONE
+// persistent kernel launch.
+//
+// The paper batches same-shape instances by vectorising the solver (Sec. 3.2).
+// Here instances may differ in size: they are packed back to back as one
+// block-diagonal problem, so the device transpose and the Ruiz/Pock-Chambolle
+// scaling (row- and column-local operations) of the single-problem path apply
+// unchanged.  The iteration itself runs in one launch: each CTA takes the next
+// unsolved instance from an atomic work counter and runs the whole restarted
+// loop for it -- power iteration, initial primal weight, half-steps, relative
+// KKT checks, restarts, primal-weight updates, termination -- with the two
+// gathered vectors of the instance (y for the SpMV^T, the reflected primal point
+// for the SpMV) held in shared memory.  All reductions are fixed-order CTA
+// trees in FP64; no instance waits on another, so no grid-wide synchronisation
+// exists and a finished CTA simply takes the next instance.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mpax.h"
+#include "problem.cuh"
+
+namespace mpax {
+
+constexpr int kBatchThreads = 512;
+constexpr double kBatchMaxSeconds = 600.0;
+constexpr int kLPR = 8;  // lanes cooperating on one row
+
+template <typename T>
+struct BatchArgs {
+  int B;
+  const long long* m_off;
+  const long long* n_off;
+  const int* rp;      // A (block diagonal, global columns)
+  const int* col;
+  const T* val;
+  const int* rpt;     // A^T (columns are global rows of A)
+  const int* colt;
+  const T* valt;
+  const T *c, *l, *u, *lc, *uc;                 // scaled data
+  const double *c0, *l0, *u0, *lc0, *uc0, *Dr, *Dc;  // originals and scaling
+  T *w, *xa, *xhat, *ya, *yhat, *gbuf;          // iterate storage
+  double *xout, *yout;
+  int* status;
+  long long* iters;
+  long long* restarts;
+  double *relkkt, *pobj, *secs;
+  int* next;
+  int smem_m;  // elements of y held in shared memory (>= max m_b)
+  double eps_abs, eps_rel, r_suff, r_nec, r_art, pw_smooth, step_safety, power_tol;
+  long long iter_limit;
+  long long time_limit_ns;  // from the start of the launch, on the device clock
+  int check_every, power_max_iter;
+};
+
+__device__ __forceinline__ double bsum(double v, double* sh) {
+  v = block_sum(v, sh);
+  __shared__ double bc;
+  if (threadIdx.x == 0) bc = v;
+  __syncthreads();
+  const double r = bc;
+  __syncthreads();
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = kLPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, kLPR);
+  return v;
+}
+
+__device__ __forceinline__ double bound_val(double lo, double hi) {
+  const bool fl = isfinite(lo), fu = isfinite(hi);
+  if (fl && fu) return (fabs(lo) >= fabs(hi)) ? lo : hi;
+  if (fl) return lo;
+  if (fu) return hi;
+  return 0.0;
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <typename T>
+__device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, double* sh,
+                               unsigned long long t_launch) {
+  const unsigned long long t_start = gtimer();
+  __shared__ int s_late;
+  const int m0 = (int)a.m_off[b], mb = (int)(a.m_off[b + 1] - a.m_off[b]);
+  const int n0 = (int)a.n_off[b], nb = (int)(a.n_off[b + 1] - a.n_off[b]);
+  const int grp = threadIdx.x / kLPR, gl = threadIdx.x % kLPR;
+  const int G = blockDim.x / kLPR;
+
+  // ---- power iteration for ||A~_b||_2, from the all-ones vector -------------
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) xs[j] = (T)(1.0 / sqrt((double)nb));
+  __syncthreads();
+  double nA = 0.0, nu_prev = 0.0;
+  const bool has_rows = mb > 0 && a.rp[m0 + mb] > a.rp[m0];
+  for (int t = 1; has_rows && t <= a.power_max_iter; ++t) {
+    for (int i0 = 0; i0 < mb; i0 += G) {
+      const int i = i0 + grp;
+      const bool in_i = i < mb;
+      T s = 0;
+      for (int p = in_i ? a.rp[m0 + i] + gl : 0; in_i && p < a.rp[m0 + i + 1]; p += kLPR)
+        s += a.val[p] * xs[a.col[p] - n0];
+      s = group_sum(s);
+      if (gl == 0 && in_i) ys[i] = s;
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int j0 = 0; j0 < nb; j0 += G) {
+      const int j = j0 + grp;
+      const bool in_j = j < nb;
+      T s = 0;
+      for (int p = in_j ? a.rpt[n0 + j] + gl : 0; in_j && p < a.rpt[n0 + j + 1]; p += kLPR)
+        s += a.valt[p] * ys[a.colt[p] - m0];
+      s = group_sum(s);
+      if (gl == 0 && in_j) {
+        a.gbuf[n0 + j] = s;
+        acc += (double)s * (double)s;
+      }
+    }
+    const double nrm = sqrt(bsum(acc, sh));
+    if (nrm == 0.0) {
+      nA = 0.0;
+      break;
+    }
+    const double nu = sqrt(nrm);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) xs[j] = (T)((double)a.gbuf[n0 + j] / nrm);
+    __syncthreads();
+    nA = nu;
+    if (t > 1 && fabs(nu - nu_prev) <= a.power_tol * nu) break;
+    nu_prev = nu;
+  }
+
+  // ---- initial primal weight, norms of the unscaled data ------------------
+  double s_cs = 0, s_bs = 0, s_c = 0, s_b = 0;
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const double cs = (double)a.c[n0 + j];
+    s_cs += cs * cs;
+    s_c += a.c0[n0 + j] * a.c0[n0 + j];
+  }
+  for (int i = threadIdx.x; i < mb; i += blockDim.x) {
+    const double bs = bound_val((double)a.lc[m0 + i], (double)a.uc[m0 + i]);
+    const double bo = bound_val(a.lc0[m0 + i], a.uc0[m0 + i]);
+    s_bs += bs * bs;
+    s_b += bo * bo;
+  }
+  const double ncs = sqrt(bsum(s_cs, sh)), nbs = sqrt(bsum(s_bs, sh));
+  const double c_norm = sqrt(bsum(s_c, sh)), b_norm = sqrt(bsum(s_b, sh));
+  double omega = (ncs > 1e-10 && nbs > 1e-10) ? ncs / nbs : 1.0;
+  const double eta = nA > 0.0 ? a.step_safety / nA : 1.0;
+  double tau = eta / omega, sigma = eta * omega;
+
+  // ---- start at zero: anchor, reflected point, duals ----------------------
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    a.xa[n0 + j] = (T)0;
+    a.w[n0 + j] = (T)0;
+    a.xhat[n0 + j] = (T)0;
+  }
+  for (int i = threadIdx.x; i < mb; i += blockDim.x) {
+    ys[i] = (T)0;
+    a.ya[m0 + i] = (T)0;
+    a.yhat[m0 + i] = (T)0;
+  }
+  __syncthreads();
+
+  long long total = 0, k = 0, restarts = 0;
+  double r_anchor = 0.0, r_prev = 0.0, rel = INFINITY, pobj = 0.0;
+  bool have_anchor = false;
+  int term = 0;
+  while (true) {
+    const int len = (int)min((long long)a.check_every, a.iter_limit - total);
+    double P0 = 0, P1 = 0, D0 = 0, D1 = 0;
+    const T tt = (T)tau, ss = (T)sigma, iss = (T)(1.0 / sigma);
+    for (int it = 0; it < len; ++it) {
+      const bool chk = (it == len - 1);
+      const T rb = (T)(1.0 / (double)(k + 1));  // rebuild weight of x^{n,k}
+      const T hb = (T)(1.0 / (double)(k + 2));  // Halpern weight of the anchor
+      // primal half-step over the rows of A^T (eq. 3, first line)
+      for (int j0 = 0; j0 < nb; j0 += G) {
+      const int j = j0 + grp;
+      const bool in_j = j < nb;
+        T s = 0;
+        for (int p = in_j ? a.rpt[n0 + j] + gl : 0; in_j && p < a.rpt[n0 + j + 1]; p += kLPR)
+          s += a.valt[p] * ys[a.colt[p] - m0];
+        s = group_sum(s);
+        if (gl == 0 && in_j) {
+          const int g = n0 + j;
+          const T x0 = a.xa[g], wv = a.w[g];
+          const T x = (k == 0) ? x0 : wv + rb * (x0 - wv);
+          const T xh = clampv<T>(x - tt * (a.c[g] - s), a.l[g], a.u[g]);
+          const T wn = (T)2 * xh - x;
+          a.w[g] = wn;
+          xs[j] = wn;
+          if (chk) {
+            a.xhat[g] = xh;
+            const double d0 = (double)xh - (double)x, d1 = (double)xh - (double)x0;
+            P0 += d0 * d0;
+            P1 += d1 * d1;
+          }
+        }
+      }
+      __syncthreads();
+      // dual half-step over the rows of A (eq. 3, second line) and Halpern (eq. 4)
+      for (int i0 = 0; i0 < mb; i0 += G) {
+      const int i = i0 + grp;
+      const bool in_i = i < mb;
+        T s = 0;
+        for (int p = in_i ? a.rp[m0 + i] + gl : 0; in_i && p < a.rp[m0 + i + 1]; p += kLPR)
+          s += a.val[p] * xs[a.col[p] - n0];
+        s = group_sum(s);
+        if (gl == 0 && in_i) {
+          const int g = m0 + i;
+          const T y0 = ys[i], y0a = a.ya[g];
+          const T v = y0 * iss - s;
+          const T yh = ss * (v - clampv<T>(v, -a.uc[g], -a.lc[g]));
+          const T z = (T)2 * yh - y0;
+          ys[i] = z + hb * (y0a - z);
+          if (chk) {
+            a.yhat[g] = yh;
+            const double d0 = (double)yh - (double)y0, d1 = (double)yh - (double)y0a;
+            D0 += d0 * d0;
+            D1 += d1 * d1;
+          }
+        }
+      }
+      __syncthreads();
+      ++k;
+      ++total;
+    }
+    // ---- check: relative KKT error of (x^, y^) on the unscaled problem ----
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) xs[j] = a.xhat[n0 + j];
+    __syncthreads();
+    double K0 = 0, K1 = 0, C0 = 0, C1 = 0, C2 = 0;
+    for (int i0 = 0; i0 < mb; i0 += G) {
+      const int i = i0 + grp;
+      const bool in_i = i < mb;
+      T s = 0;
+      for (int p = in_i ? a.rp[m0 + i] + gl : 0; in_i && p < a.rp[m0 + i + 1]; p += kLPR)
+        s += a.val[p] * xs[a.col[p] - n0];
+      s = group_sum(s);
+      if (gl == 0 && in_i) {
+        const int g = m0 + i;
+        const double ax = (double)s / a.Dr[g];
+        const double lo = a.lc0[g], hi = a.uc0[g];
+        const double r = ax - fmin(fmax(ax, lo), hi);
+        K0 += r * r;
+        const double y = a.Dr[g] * (double)a.yhat[g];
+        if (y > 0.0 && isfinite(lo)) K1 += lo * y;
+        if (y < 0.0 && isfinite(hi)) K1 += hi * y;
+      }
+    }
+    for (int j0 = 0; j0 < nb; j0 += G) {
+      const int j = j0 + grp;
+      const bool in_j = j < nb;
+      T s = 0;
+      for (int p = in_j ? a.rpt[n0 + j] + gl : 0; in_j && p < a.rpt[n0 + j + 1]; p += kLPR)
+        s += a.valt[p] * a.yhat[a.colt[p]];
+      s = group_sum(s);
+      if (gl == 0 && in_j) {
+        const int g = n0 + j;
+        const double aty = (double)s / a.Dc[g];
+        const double x = a.Dc[g] * (double)xs[j];
+        const double lam = a.c0[g] - aty;
+        const double lo = a.l0[g], hi = a.u0[g];
+        const bool lf = isfinite(lo), uf = isfinite(hi);
+        const double lh = (lf && uf) ? lam : lf ? fmax(lam, 0.0) : uf ? fmin(lam, 0.0) : 0.0;
+        const double rd = lam - lh;
+        C0 += rd * rd;
+        C1 += a.c0[g] * x;
+        C2 += (lf ? lo * fmax(lh, 0.0) : 0.0) + (uf ? hi * fmin(lh, 0.0) : 0.0);
+      }
+    }
+    P0 = bsum(P0, sh);
+    P1 = bsum(P1, sh);
+    D0 = bsum(D0, sh);
+    D1 = bsum(D1, sh);
+    K0 = bsum(K0, sh);
+    K1 = bsum(K1, sh);
+    C0 = bsum(C0, sh);
+    C1 = bsum(C1, sh);
+    C2 = bsum(C2, sh);
+    const double nrp = sqrt(K0), nrd = sqrt(C0);
+    pobj = C1;
+    const double dobj = K1 + C2;
+    const double gap = fabs(pobj - dobj);
+    rel = fmax(fmax(nrp / (1.0 + b_norm), nrd / (1.0 + c_norm)),
+               gap / (1.0 + fabs(pobj) + fabs(dobj)));
+    const bool conv = nrp <= a.eps_abs + a.eps_rel * b_norm &&
+                      nrd <= a.eps_abs + a.eps_rel * c_norm &&
+                      gap <= a.eps_abs + a.eps_rel * (fabs(pobj) + fabs(dobj));
+    if (!isfinite(rel) || !isfinite(P0) || !isfinite(D0)) term = MPAX_TERM_NUMERICAL_ERROR;
+    else if (conv) term = MPAX_TERM_OPTIMAL;
+    else if (total >= a.iter_limit) term = MPAX_TERM_ITERATION_LIMIT;
+    // one thread reads the clock so that the decision is uniform over the block
+    if (threadIdx.x == 0) s_late = (long long)(gtimer() - t_launch) >= a.time_limit_ns;
+    __syncthreads();
+    if (!term && s_late) term = MPAX_TERM_TIME_LIMIT;
+    __syncthreads();
+    if (term) break;
+    // restart rule and primal weight (the same rule as the single-problem path)
+    const double r = sqrt(omega * P0 + D0 / omega);
+    const bool restart = !have_anchor || r <= a.r_suff * r_anchor ||
+                         (r <= a.r_nec * r_anchor && r > r_prev) ||
+                         (double)k >= a.r_art * (double)total;
+    if (restart) {
+      const double dx = sqrt(P1), dy = sqrt(D1);
+      if (dx > 1e-10 && dy > 1e-10)
+        omega = exp(a.pw_smooth * log(dy / dx) + (1.0 - a.pw_smooth) * log(omega));
+      tau = eta / omega;
+      sigma = eta * omega;
+      have_anchor = true;
+      r_anchor = r;
+      r_prev = r;
+      k = 0;
+      ++restarts;
+      for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const T v = a.xhat[n0 + j];
+        a.xa[n0 + j] = v;
+        a.w[n0 + j] = v;
+      }
+      for (int i = threadIdx.x; i < mb; i += blockDim.x) {
+        const T v = a.yhat[m0 + i];
+        a.ya[m0 + i] = v;
+        ys[i] = v;
+      }
+    } else {
+      r_prev = r;
+    }
+    __syncthreads();
+  }
+  // ---- returned point (x^, y^), unscaled; per-instance statistics ---------
+  for (int j = threadIdx.x; j < nb; j += blockDim.x)
+    a.xout[n0 + j] = a.Dc[n0 + j] * (double)a.xhat[n0 + j];
+  for (int i = threadIdx.x; i < mb; i += blockDim.x)
+    a.yout[m0 + i] = a.Dr[m0 + i] * (double)a.yhat[m0 + i];
+  if (threadIdx.x == 0) {
+    a.status[b] = term;
+    a.iters[b] = total;
+    a.restarts[b] = restarts;
+    a.relkkt[b] = rel;
+    a.pobj[b] = pobj;
+    a.secs[b] = (double)(gtimer() - t_start) * 1e-9;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBatchThreads) batch_lp_kernel(BatchArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ double sh[32];
+  __shared__ int s_inst;
+  T* ys = reinterpret_cast<T*>(sm);
+  T* xs = ys + a.smem_m;
+  const unsigned long long t_launch = gtimer();  // used by thread 0 only
+  while (true) {
+    if (threadIdx.x == 0) s_inst = atomicAdd(a.next, 1);
+    __syncthreads();
+    const int b = s_inst;
+    __syncthreads();
+    if (b >= a.B) return;
+    solve_instance<T>(a, b, ys, xs, sh, t_launch);
+  }
+}
+
+// row -> instance via binary search in m_off; global column = n_off[b] + local
+__global__ void k_globalize_cols(const long long* __restrict__ m_off,
+                                 const long long* __restrict__ n_off, int B,
+                                 const long long* __restrict__ rp, int rows,
+                                 int* __restrict__ col, int* flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  int lo = 0, hi = B;  // find b with m_off[b] <= i < m_off[b+1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (m_off[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  const long long nb = n_off[lo + 1] - n_off[lo];
+  for (long long p = rp[i]; p < rp[i + 1]; ++p) {
+    const int c = col[p];
+    if (c < 0 || c >= nb) atomicOr(flags, 1);
+    col[p] = (int)(n_off[lo] + c);
+  }
+}
+
+}  // namespace mpax
+
+// ============================================================================
+
+using namespace mpax;
+
+struct mpax_batch {
+  mpax_problem* prob = nullptr;  // the block-diagonal problem
+  int B = 0;
+  long long* m_off = nullptr;  // device
+  long long* n_off = nullptr;
+  std::vector<long long> h_moff, h_noff;
+  int max_m = 0, max_n = 0;
+  int* next = nullptr;
+  int* status = nullptr;
+  long long* iters = nullptr;
+  long long* restarts = nullptr;
+  double *relkkt = nullptr, *pobj = nullptr, *secs = nullptr, *xout = nullptr, *yout = nullptr;
+  void* work = nullptr;  // iterate storage and scaled data (precision dependent)
+  size_t work_bytes = 0;
+  bool solved = false;
+  double solve_seconds = 0.0;
+  long long launches = 0;
+};
+
+namespace mpax {
+// defined in api.cu
+ProblemData* problem_data(mpax_problem* p);
+cudaStream_t problem_stream(mpax_problem* p);
+void problem_order_after_user(mpax_problem* p);
+void problem_order_user_after(mpax_problem* p);
+}  // namespace mpax
+
+namespace {
+
+mpax_status bfail(mpax_status s, const std::string& m) {
+  set_last_error(m.c_str());
+  return s;
+}
+
+template <typename T>
+mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches) {
+  ProblemData& P = *problem_data(bt->prob);
+  cudaStream_t s = P.s;
+  const int m = P.m, n = P.n, nnz = P.nnz;
+  // scaled data and iterate storage in the iteration precision
+  const size_t need = sizeof(T) * ((size_t)2 * (nnz + kPad) + 9 * (size_t)n + 7 * (size_t)m + 64);
+  if (bt->work_bytes < need) {
+    if (bt->work) cudaFree(bt->work);
+    bt->work = nullptr;
+    bt->work_bytes = 0;
+    if (cudaMalloc(&bt->work, need) != cudaSuccess) return bfail(MPAX_ERR_OUT_OF_MEMORY, "batch work");
+    bt->work_bytes = need;
+  }
+  T* p = reinterpret_cast<T*>(bt->work);
+  auto take = [&](size_t k) {
+    T* r = p;
+    p += (k + 15) / 16 * 16;
+    return r;
+  };
+  T* valA = take(nnz + kPad);
+  T* valAt = take(nnz + kPad);
+  T *c = take(n), *l = take(n), *u = take(n), *lc = take(m), *uc = take(m);
+  T *w = take(n), *xa = take(n), *xhat = take(n), *gbuf = take(n);
+  T *ya = take(m), *yhat = take(m);
+  cudaError_t e;
+  if ((e = cast_vec<T>(P.val_s, valA, nnz, s))) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  if ((e = gather_cast<T>(P.val_s, P.permT, valAt, nnz, s)))
+    return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  scale_cast<T>(P.c, P.Dc, false, c, n, s);
+  scale_cast<T>(P.l, P.Dc, true, l, n, s);
+  scale_cast<T>(P.u, P.Dc, true, u, n, s);
+  scale_cast<T>(P.lc, P.Dr, false, lc, m, s);
+  scale_cast<T>(P.uc, P.Dr, false, uc, m, s);
+  *launches += 7;
+  BatchArgs<T> a;
+  a.B = bt->B;
+  a.m_off = bt->m_off;
+  a.n_off = bt->n_off;
+  a.rp = P.A.rp;
+  a.col = P.A.col;
+  a.val = valA;
+  a.rpt = P.At.rp;
+  a.colt = P.At.col;
+  a.valt = valAt;
+  a.c = c;
+  a.l = l;
+  a.u = u;
+  a.lc = lc;
+  a.uc = uc;
+  a.c0 = P.c;
+  a.l0 = P.l;
+  a.u0 = P.u;
+  a.lc0 = P.lc;
+  a.uc0 = P.uc;
+  a.Dr = P.Dr;
+  a.Dc = P.Dc;
+  a.w = w;
+  a.xa = xa;
+  a.xhat = xhat;
+  a.ya = ya;
+  a.yhat = yhat;
+  a.gbuf = gbuf;
+  a.xout = bt->xout;
+  a.yout = bt->yout;
+  a.status = bt->status;
+  a.iters = bt->iters;
+  a.restarts = bt->restarts;
+  a.relkkt = bt->relkkt;
+  a.pobj = bt->pobj;
+  a.secs = bt->secs;
+  a.next = bt->next;
+  a.smem_m = (bt->max_m + 3) / 4 * 4;
+  a.eps_abs = o->eps_abs;
+  a.eps_rel = o->eps_rel;
+  a.r_suff = o->restart_sufficient;
+  a.r_nec = o->restart_necessary;
+  a.r_art = o->restart_artificial;
+  a.pw_smooth = o->primal_weight_smoothing;
+  a.step_safety = o->step_safety;
+  a.power_tol = o->power_tol;
+  a.iter_limit = o->iteration_limit;
+  // the whole batch is one launch: it always ends, at the latest kBatchMaxSeconds
+  // after it starts, even with no iteration or time limit given
+  a.time_limit_ns = (long long)(std::min(o->time_limit, kBatchMaxSeconds) * 1e9);
+  a.check_every = o->check_every;
+  a.power_max_iter = o->power_max_iter;
+  const size_t smem = sizeof(T) * ((size_t)a.smem_m + (size_t)bt->max_n);
+  if (smem > 200 * 1024)
+    return bfail(MPAX_ERR_UNSUPPORTED,
+                 "batch instances too large for one CTA's shared memory (max_m + max_n)");
+  cudaFuncSetAttribute(batch_lp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  int occ = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_lp_kernel<T>, kBatchThreads, smem);
+  const int grid = std::min(bt->B, std::max(1, occ) * sms);
+  cudaMemsetAsync(bt->next, 0, sizeof(int), s);
+  batch_lp_kernel<T><<<grid, kBatchThreads, smem, s>>>(a);
+  *launches += 1;
+  if ((e = cudaGetLastError())) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  return MPAX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpax_status mpax_lp_batch_create(int32_t B, const int64_t* m_off, const int64_t* n_off,
+                                 const int64_t* row_ptr, const int32_t* col_idx,
+                                 const double* val, const double* c, const double* lc,
+                                 const double* uc, const double* l, const double* u,
+                                 mpax_mem_kind kind, void* cuda_stream, mpax_batch** out) {
+  if (!out) return bfail(MPAX_ERR_INVALID_ARGUMENT, "out must not be NULL");
+  *out = nullptr;
+  if (B < 1) return bfail(MPAX_ERR_INVALID_ARGUMENT, "B must be >= 1");
+  if (!m_off || !n_off || !row_ptr) return bfail(MPAX_ERR_INVALID_ARGUMENT, "NULL offsets");
+  std::vector<long long> hm(B + 1), hn(B + 1);
+  const cudaMemcpyKind k = kind == MPAX_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
+  if (cudaMemcpy(hm.data(), m_off, sizeof(long long) * (B + 1), k) != cudaSuccess ||
+      cudaMemcpy(hn.data(), n_off, sizeof(long long) * (B + 1), k) != cudaSuccess)
+    return bfail(MPAX_ERR_CUDA, "copy of the offsets failed");
+  if (hm[0] != 0 || hn[0] != 0) return bfail(MPAX_ERR_INVALID_ARGUMENT, "offsets must start at 0");
+  int max_m = 0, max_n = 0;
+  for (int b = 0; b < B; ++b) {
+    if (hm[b + 1] < hm[b] || hn[b + 1] < hn[b])
+      return bfail(MPAX_ERR_INVALID_ARGUMENT, "offsets must be non-decreasing");
+    max_m = std::max<long long>(max_m, hm[b + 1] - hm[b]);
+    max_n = std::max<long long>(max_n, hn[b + 1] - hn[b]);
+  }
+  if (hm[B] >= (1LL << 31) || hn[B] >= (1LL << 31))
+    return bfail(MPAX_ERR_UNSUPPORTED, "total rows and columns must be < 2^31");
+  const int m = (int)hm[B], n = (int)hn[B];
+  long long nnz = 0;
+  if (cudaMemcpy(&nnz, row_ptr + m, sizeof(long long), k) != cudaSuccess)
+    return bfail(MPAX_ERR_CUDA, "copy of row_ptr failed");
+  // device copies of the structure with columns made global
+  long long *d_moff = nullptr, *d_noff = nullptr, *d_rp = nullptr;
+  int *d_col = nullptr, *flags = nullptr;
+  cudaError_t e = cudaMalloc(&d_moff, sizeof(long long) * (B + 1));
+  if (!e) e = cudaMalloc(&d_noff, sizeof(long long) * (B + 1));
+  if (!e) e = cudaMalloc(&d_rp, sizeof(long long) * (m + 1));
+  if (!e) e = cudaMalloc(&d_col, sizeof(int) * std::max<long long>(nnz, 1));
+  if (!e) e = cudaMalloc(&flags, sizeof(int));
+  if (!e) e = cudaMemcpy(d_moff, hm.data(), sizeof(long long) * (B + 1), cudaMemcpyHostToDevice);
+  if (!e) e = cudaMemcpy(d_noff, hn.data(), sizeof(long long) * (B + 1), cudaMemcpyHostToDevice);
+  const cudaMemcpyKind kin = kind == MPAX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (!e) e = cudaMemcpy(d_rp, row_ptr, sizeof(long long) * (m + 1), kin);
+  if (!e && nnz > 0) e = cudaMemcpy(d_col, col_idx, sizeof(int) * nnz, kin);
+  if (!e) e = cudaMemset(flags, 0, sizeof(int));
+  if (!e && m > 0) k_globalize_cols<<<(m + 255) / 256, 256>>>(d_moff, d_noff, B, d_rp, m, d_col, flags);
+  int hf = 0;
+  if (!e) e = cudaMemcpy(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost);
+  mpax_problem* prob = nullptr;
+  mpax_status st = MPAX_OK;
+  if (!e && hf) st = bfail(MPAX_ERR_INVALID_ARGUMENT, "a column index is outside its instance");
+  if (!e && !hf) {
+    // values and vectors go through the single-problem create (copy + validation);
+    // host inputs are staged on the device first so that every pointer is device memory
+    const double* dv[6] = {val, c, lc, uc, l, u};
+    const long long cnt[6] = {nnz, n, m, m, n, n};
+    double* tmp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (kind == MPAX_MEM_HOST) {
+      for (int q = 0; q < 6 && !e; ++q) {
+        e = cudaMalloc(&tmp[q], sizeof(double) * std::max<long long>(cnt[q], 1));
+        if (!e && cnt[q] > 0) e = cudaMemcpy(tmp[q], dv[q], sizeof(double) * cnt[q], cudaMemcpyHostToDevice);
+        dv[q] = tmp[q];
+      }
+    }
+    if (!e)
+      st = mpax_lp_create(m, n, nnz, (const int64_t*)d_rp, d_col, dv[0], dv[1], dv[2], dv[3],
+                          dv[4], dv[5], MPAX_MEM_DEVICE, cuda_stream, &prob);
+    for (double* t : tmp)
+      if (t) cudaFree(t);
+  }
+  cudaFree(d_rp);
+  cudaFree(d_col);
+  cudaFree(flags);
+  if (e) {
+    cudaFree(d_moff);
+    cudaFree(d_noff);
+    return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (st) {
+    cudaFree(d_moff);
+    cudaFree(d_noff);
+    return st;
+  }
+  mpax_batch* bt = new mpax_batch();
+  e = cudaMalloc(&bt->next, sizeof(int));
+  if (!e) e = cudaMalloc(&bt->status, sizeof(int) * B);
+  if (!e) e = cudaMalloc(&bt->iters, sizeof(long long) * B);
+  if (!e) e = cudaMalloc(&bt->restarts, sizeof(long long) * B);
+  if (!e) e = cudaMalloc(&bt->relkkt, sizeof(double) * B);
+  if (!e) e = cudaMalloc(&bt->pobj, sizeof(double) * B);
+  if (!e) e = cudaMalloc(&bt->secs, sizeof(double) * B);
+  if (!e) e = cudaMalloc(&bt->xout, sizeof(double) * std::max(n, 1));
+  if (!e) e = cudaMalloc(&bt->yout, sizeof(double) * std::max(m, 1));
+  bt->prob = prob;
+  bt->B = B;
+  bt->m_off = d_moff;
+  bt->n_off = d_noff;
+  bt->h_moff = hm;
+  bt->h_noff = hn;
+  bt->max_m = max_m;
+  bt->max_n = max_n;
+  if (e) {
+    mpax_batch_destroy(bt);
+    return bfail(MPAX_ERR_OUT_OF_MEMORY, "batch output arrays");
+  }
+  *out = bt;
+  return MPAX_OK;
+}
+
+mpax_status mpax_batch_solve(mpax_batch* bt, const mpax_options* o) {
+  if (!bt || !o) return bfail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  if (o->reflection_gamma != 1.0)
+    return bfail(MPAX_ERR_UNSUPPORTED, "the batch path implements reflection_gamma = 1");
+  if (o->check_every < 1 || o->iteration_limit < 1 || o->ruiz_iters < 0 ||
+      !(o->step_safety > 0 && o->step_safety < 1) || o->power_max_iter < 1 ||
+      !(o->time_limit >= 0))
+    return bfail(MPAX_ERR_INVALID_ARGUMENT, "invalid options");
+  if (o->precision != MPAX_PREC_FP64 && o->precision != MPAX_PREC_MIXED)
+    return bfail(MPAX_ERR_INVALID_ARGUMENT, "bad precision");
+  const auto t0 = std::chrono::steady_clock::now();
+  ProblemData& P = *problem_data(bt->prob);
+  cudaStream_t s = P.s;
+  problem_order_after_user(bt->prob);
+  long long launches = 0;
+  cudaError_t e = transpose_csr(P.A, P.At, P.permT, P.tmp_rows, P.tmp_scan, s);
+  if (!e) e = compute_scaling(P, o->ruiz_iters, o->pock_chambolle != 0);
+  launches += 6 + 5 * o->ruiz_iters + 8;
+  if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  mpax_status st = o->precision == MPAX_PREC_FP64 ? run_batch<double>(bt, o, &launches)
+                                                  : run_batch<float>(bt, o, &launches);
+  if (st) return st;
+  e = cudaStreamSynchronize(s);
+  if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  problem_order_user_after(bt->prob);
+  bt->solved = true;
+  bt->launches = launches;
+  bt->solve_seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return MPAX_OK;
+}
+
+mpax_status mpax_batch_get_solution(const mpax_batch* bt, double* x, double* y,
+                                    mpax_mem_kind kind) {
+  if (!bt) return bfail(MPAX_ERR_INVALID_ARGUMENT, "NULL batch");
+  if (!bt->solved) return bfail(MPAX_ERR_NOT_SOLVED, "call mpax_batch_solve first");
+  const cudaMemcpyKind k = kind == MPAX_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  const long long n = bt->h_noff[bt->B], m = bt->h_moff[bt->B];
+  cudaError_t e = cudaSuccess;
+  if (x && n) e = cudaMemcpy(x, bt->xout, sizeof(double) * n, k);
+  if (!e && y && m) e = cudaMemcpy(y, bt->yout, sizeof(double) * m, k);
+  if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  return MPAX_OK;
+}
+
+mpax_status mpax_batch_get_stats(const mpax_batch* bt, mpax_batch_stats* stats, int32_t* status,
+                                 int64_t* iterations, double* rel_kkt, double* primal_obj,
+                                 double* seconds) {
+  if (!bt || !stats) return bfail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  if (!bt->solved) return bfail(MPAX_ERR_NOT_SOLVED, "call mpax_batch_solve first");
+  const int B = bt->B;
+  std::vector<int> hs(B);
+  std::vector<long long> hi(B), hr(B);
+  std::vector<double> hk(B), hp(B), ht(B);
+  cudaError_t e = cudaMemcpy(hs.data(), bt->status, sizeof(int) * B, cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(hi.data(), bt->iters, sizeof(long long) * B, cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(hr.data(), bt->restarts, sizeof(long long) * B, cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(hk.data(), bt->relkkt, sizeof(double) * B, cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(hp.data(), bt->pobj, sizeof(double) * B, cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(ht.data(), bt->secs, sizeof(double) * B, cudaMemcpyDeviceToHost);
+  if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  std::memset(stats, 0, sizeof(*stats));
+  stats->B = B;
+  std::vector<double> sorted = ht;
+  std::sort(sorted.begin(), sorted.end());
+  for (int b = 0; b < B; ++b) {
+    stats->n_optimal += hs[b] == MPAX_TERM_OPTIMAL;
+    stats->iterations_total += hi[b];
+    stats->iterations_max = std::max<long long>(stats->iterations_max, hi[b]);
+    stats->restarts_total += hr[b];
+    stats->rel_kkt_max = std::max(stats->rel_kkt_max, hk[b]);
+  }
+  auto pct = [&](double q) {
+    const size_t i = std::min<size_t>(sorted.size() - 1, (size_t)std::ceil(q * sorted.size()) - 1);
+    return sorted[i];
+  };
+  stats->instance_seconds_p50 = pct(0.50);
+  stats->instance_seconds_p99 = pct(0.99);
+  stats->instance_seconds_max = sorted.back();
+  stats->solve_seconds = bt->solve_seconds;
+  stats->kernel_launches = bt->launches;
+  for (int b = 0; b < B; ++b) {
+    if (status) status[b] = hs[b];
+    if (iterations) iterations[b] = hi[b];
+    if (rel_kkt) rel_kkt[b] = hk[b];
+    if (primal_obj) primal_obj[b] = hp[b];
+    if (seconds) seconds[b] = ht[b];
+  }
+  return MPAX_OK;
+}
+
+void mpax_batch_destroy(mpax_batch* bt) {
+  if (!bt) return;
+  if (bt->prob) mpax_destroy(bt->prob);
+  void* bufs[] = {bt->m_off, bt->n_off, bt->next, bt->status, bt->iters, bt->restarts,
+                  bt->relkkt, bt->pobj, bt->secs, bt->xout, bt->yout, bt->work};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete bt;
+}
+
+}  // extern "C"

@@ -23,6 +23,28 @@ namespace mpax {
 constexpr int kWarp = 32;
 constexpr int kWarpsPerBlock = 8;
 constexpr int kBlock = kWarp * kWarpsPerBlock;
+
+// Launch shape of the fused SpMV kernels: warps per CTA and the minimum number
+// of resident CTAs per SM asked of the register allocator.  Small CTAs retire
+// as soon as their few warp items are done, so an SM refills at warp grain.
+#ifndef MPAX_SPMV_WARPS
+#define MPAX_SPMV_WARPS 8
+#endif
+#ifndef MPAX_SPMV_MINB
+#define MPAX_SPMV_MINB 0  // 0: the register allocator's own choice
+#endif
+// 1: sliced long rows are completed through acquire/release atomics on the
+//    row's counter; 0: through __threadfence() around a relaxed atomic.
+#ifndef MPAX_LONG_ACQREL
+#define MPAX_LONG_ACQREL 0
+#endif
+constexpr int kSpmvWarps = MPAX_SPMV_WARPS;
+constexpr int kSpmvBlock = kWarp * kSpmvWarps;
+#if MPAX_SPMV_MINB > 0
+#define MPAX_SPMV_BOUNDS __launch_bounds__(kSpmvBlock, MPAX_SPMV_MINB)
+#else
+#define MPAX_SPMV_BOUNDS __launch_bounds__(kSpmvBlock)
+#endif
 // Work decomposition of a CSR matrix into warp items.
 constexpr int kSliceNnz = 256;  // nonzeros of one slice of a long row
 constexpr int kLongRow = 64;    // rows longer than this are cut into slices
@@ -65,7 +87,8 @@ struct DevState {
   double last_restart_metric;
   double pw_scale, pw_nu;  // power iteration: 1/||g|| of the last round, estimate
   long long total, k_base, restarts, checks, iter_limit;
-  int pw_done, pw_iters, pad2, pad3;
+  int pw_done, pw_iters, stall_limit, stall_count;
+  double best_rel;
   int done, restart_flag, termination, have_anchor;
   int check_every, is_qp, nan_seen, pad;
   // Halpern / averaging coefficient table for the current block:
@@ -73,6 +96,10 @@ struct DevState {
   double coef_a[kMaxCheckEvery + 2];
   double coef_b[kMaxCheckEvery + 2];
 };
+
+// Termination recorded when a mixed-precision run stops improving and the
+// solve continues in FP64 (internal; never reported to callers).
+constexpr int kTermStalled = 100;
 
 // Host-visible mirror written by the finalize kernel (pinned, mapped).
 struct HostStatus {

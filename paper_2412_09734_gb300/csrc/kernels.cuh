@@ -85,11 +85,11 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
 }
 
 template <typename T, class In, class Epi>
-__global__ void __launch_bounds__(kBlock) spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
-  __shared__ T sbuf[kWarpsPerBlock][kShortCap];
+__global__ void MPAX_SPMV_BOUNDS spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
+  __shared__ T sbuf[kSpmvWarps][kShortCap];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int item = blockIdx.x * kWarpsPerBlock + wib;
+  const int item = blockIdx.x * kSpmvWarps + wib;
   if (item >= a.n_items) return;
   const int4 it = a.items[item];
   if (epi.skip()) return;
@@ -199,11 +199,22 @@ __global__ void __launch_bounds__(kBlock) spmv_fused(SpmvArgs<T> a, In in, Epi e
   }
   if (lane == 0) {
     a.carry[item] = s;
+#if MPAX_LONG_ACQREL
+    // release: this slice's carry is visible to whoever observes the count;
+    // acquire: the last arriver sees every earlier slice's carry
+    int prev;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                 : "=r"(prev)
+                 : "l"(a.cnt + first)
+                 : "memory");
+    const bool last = (prev == S - 1);
+#else
     __threadfence();
     const int prev = atomicAdd(a.cnt + first, 1);
     const bool last = (prev == S - 1);
+    if (last) __threadfence();
+#endif
     if (last) {
-      __threadfence();
       T tot = 0;
       for (int t = 0; t < S; ++t) tot += __ldcg(a.carry + first + t);
       a.cnt[first] = 0;  // ready for the next launch

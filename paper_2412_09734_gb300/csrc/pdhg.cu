@@ -116,7 +116,7 @@ __device__ void set_step_sizes(DevState* st) {
 struct InitParams {
   double eps_abs, eps_rel, r_suff, r_nec, r_art, pw_smooth, step_safety, gamma;
   long long iter_limit;
-  int check_every, is_qp;
+  int check_every, is_qp, stall_limit;
 };
 
 // red: [0] ||c~||, [1] ||b~||, [2] ||c||, [3] ||b||  (norm_A, norm_Q already in st)
@@ -150,6 +150,9 @@ __global__ void k_init_state(DevState* st, InitParams p, const double* red) {
     st->r_anchor = 0.0;
     st->r_prev = 0.0;
     st->rel_kkt = INFINITY;
+    st->best_rel = INFINITY;
+    st->stall_count = 0;
+    st->stall_limit = p.stall_limit;
   }
   __syncthreads();
   fill_table(st, p.check_every);
@@ -196,6 +199,26 @@ __device__ double sum_slot(const double* part, int q, int n, double* sh) {
   return block_sum(v, sh);
 }
 
+// First level of the check reductions: block b sums the fixed chunk b of every
+// partial-sum slot (A^T slots 0..qt-1, then A slots 0..qa-1) into out[q][b].
+constexpr int kChunks = 128;
+__global__ void k_part_reduce(const double* __restrict__ partAt, int nAt, int qt,
+                              const double* __restrict__ partA, int nA, int qa,
+                              const int* skip, double* __restrict__ out) {
+  __shared__ double sh[32];
+  if (skip && *skip) return;
+  for (int q = 0; q < qt + qa; ++q) {
+    const double* p = q < qt ? partAt + (size_t)q * nAt : partA + (size_t)(q - qt) * nA;
+    const int n = q < qt ? nAt : nA;
+    const int chunk = (n + kChunks - 1) / kChunks;
+    const int lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    double v = 0;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) v += p[i];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) out[q * kChunks + blockIdx.x] = v;
+  }
+}
+
 // Check of Algorithm 1 / 2 after a block of `len` iterations.
 //   partAt slots: 0 sum(x^-x)^2, 1 sum(x^-x_anchor)^2 (QP: averages), 2..5 KKT column terms
 //   partA  slots: 0 sum(y^-y)^2, 1 sum(y^-y_anchor)^2, 2..3 KKT row terms
@@ -205,14 +228,14 @@ __global__ void k_finalize_check(const double* __restrict__ partAt, int nAt,
   __shared__ double sh[32];
   __shared__ double vals[10];
   if (st->done) return;
-  for (int q = 0; q < 6; ++q) {
-    const double v = sum_slot(partAt, q, nAt, sh);
+  // partAt / partA hold the kChunks first-level sums of every slot (k_part_reduce)
+  for (int q = 0; q < 10; ++q) {
+    const double v = sum_slot(partAt, q, kChunks, sh);
     if (threadIdx.x == 0) vals[q] = v;
   }
-  for (int q = 0; q < 4; ++q) {
-    const double v = sum_slot(partA, q, nA, sh);
-    if (threadIdx.x == 0) vals[6 + q] = v;
-  }
+  (void)partA;
+  (void)nA;
+  (void)nAt;
   __syncthreads();
   if (threadIdx.x == 0) {
     const double P0 = vals[0], P1 = vals[1], C0 = vals[2], C1 = vals[3], C2 = vals[4],
@@ -240,6 +263,15 @@ __global__ void k_finalize_check(const double* __restrict__ partAt, int nAt,
       term = MPAX_TERM_NUMERICAL_ERROR;
     else if (conv) term = MPAX_TERM_OPTIMAL;
     else if (st->total >= st->iter_limit) term = MPAX_TERM_ITERATION_LIMIT;
+    if (!term && st->stall_limit > 0) {
+      // the precision floor: no 10% improvement of the KKT error for stall_limit checks
+      if (rel < 0.9 * st->best_rel) {
+        st->best_rel = rel;
+        st->stall_count = 0;
+      } else if (++st->stall_count >= st->stall_limit) {
+        term = kTermStalled;
+      }
+    }
     st->restart_flag = 0;
     if (term) {
       st->termination = term;
@@ -333,14 +365,17 @@ __global__ void k_kkt_finalize(const double* __restrict__ partAt, int nAt,
                                double* out) {
   __shared__ double sh[32];
   __shared__ double vals[6];
+  // partAt holds the chunk sums of the A^T slots 0..5 then the A slots 0..3
   for (int q = 0; q < 4; ++q) {
     const double v = sum_slot(partAt, 2 + q, nAt, sh);
     if (threadIdx.x == 0) vals[q] = v;
   }
   for (int q = 0; q < 2; ++q) {
-    const double v = sum_slot(partA, 2 + q, nA, sh);
+    const double v = sum_slot(partAt, 8 + q, nAt, sh);
     if (threadIdx.x == 0) vals[4 + q] = v;
   }
+  (void)partA;
+  (void)nA;
   __syncthreads();
   if (threadIdx.x == 0) {
     const double nrp = sqrt(vals[4]), nrd = sqrt(vals[0]);
@@ -369,8 +404,9 @@ int resident_warps() {
     int blocks = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, spmv_fused<T, In, Epi>, kBlock, 0);
-    w = std::max(1, blocks) * sms * kWarpsPerBlock;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, spmv_fused<T, In, Epi>, kSpmvBlock,
+                                                  0);
+    w = std::max(1, blocks) * sms * kSpmvWarps;
   }
   return w;
 }
@@ -390,8 +426,8 @@ void launch_spmv(const Sched& sc, const Csr& K, const T* val, In in, Epi epi, in
   a.carry = reinterpret_cast<T*>(sc.carry);
   a.part = sc.part;
   a.q0 = q0;
-  const int grid = (sc.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  spmv_fused<T, In, Epi><<<grid, kBlock, 0, s>>>(a, in, epi);
+  const int grid = (sc.n_items + kSpmvWarps - 1) / kSpmvWarps;
+  spmv_fused<T, In, Epi><<<grid, kSpmvBlock, 0, s>>>(a, in, epi);
 }
 
 template <typename T>
@@ -499,8 +535,9 @@ class Engine final : public EngineBase {
         e1.out = pw_;
         launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{v}, e1, 0, s);
         launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{pw_}, e2, 0, s);
-        k_power_finalize<<<1, 256, 0, s>>>(P.schedAt.part, P.schedAt.n_items, st_, t,
-                                           o.power_tol, 0);
+        k_part_reduce<<<kChunks, 256, 0, s>>>(P.schedAt.part, P.schedAt.n_items, 1, nullptr, 0,
+                                              0, skip, P.red);
+        k_power_finalize<<<1, 256, 0, s>>>(P.red, kChunks, st_, t, o.power_tol, 0);
       } else {
         e1.out = uvec_;
         launch_spmv<T>(P.schedFt, P.Ft, ftval_, InPlain<T>{v}, e1, 0, s);
@@ -508,10 +545,11 @@ class Engine final : public EngineBase {
         e2.din = v;
         e2.d_scale = &st_->pw_scale;
         launch_spmv<T>(P.schedF, P.F, fval_, InPlain<T>{uvec_}, e2, 0, s);
-        k_power_finalize<<<1, 256, 0, s>>>(P.schedF.part, P.schedF.n_items, st_, t,
-                                           o.power_tol, 1);
+        k_part_reduce<<<kChunks, 256, 0, s>>>(P.schedF.part, P.schedF.n_items, 1, nullptr, 0,
+                                              0, skip, P.red);
+        k_power_finalize<<<1, 256, 0, s>>>(P.red, kChunks, st_, t, o.power_tol, 1);
       }
-      *launches += 3;
+      *launches += 4;
       std::swap(v, g);
       if (t % 8 == 0) {
         int done = 0;
@@ -547,6 +585,7 @@ class Engine final : public EngineBase {
     ip.iter_limit = o.iteration_limit;
     ip.check_every = o.check_every;
     ip.is_qp = P.is_qp ? 1 : 0;
+    ip.stall_limit = (o.precision == MPAX_PREC_MIXED && o.fp64_continuation) ? o.stall_checks : 0;
     k_init_state<<<1, 256, 0, P.s>>>(st_, ip, P.red_out);
     *launches += 1;
     gamma_one_ = (o.reflection_gamma == 1.0);
@@ -611,8 +650,10 @@ class Engine final : public EngineBase {
     use_xsrc_ = false;
     if (plain) return;
     kkt_launch(&st_->done, prof);
-    k_finalize_check<<<1, 512, 0, s>>>(P.schedAt.part, P.schedAt.n_items, P.schedA.part,
-                                       P.schedA.n_items, st_, hs_dev_, len, block_);
+    k_part_reduce<<<kChunks, 256, 0, s>>>(P.schedAt.part, P.schedAt.n_items, 6, P.schedA.part,
+                                          P.schedA.n_items, 4, &st_->done, P.red);
+    k_finalize_check<<<1, 512, 0, s>>>(P.red, kChunks, nullptr, 0, st_, hs_dev_, len, block_);
+    launches_ += 1;
     if (!qp) {
       k_restart_lp<T><<<grid1(std::max(P.n, P.m)), 256, 0, s>>>(
           st_, P.n, P.m, xhat_, xa_, xbar_, gamma_one_ ? xbar_ : wbuf_, yhat_, ya_, y_);
@@ -888,8 +929,9 @@ class Engine final : public EngineBase {
     if (P.schedA.part) cudaMemsetAsync(P.schedA.part, 0, sizeof(double) * kPartQ * std::max(P.schedA.n_items, 1), s);
     if (P.schedAt.part) cudaMemsetAsync(P.schedAt.part, 0, sizeof(double) * kPartQ * std::max(P.schedAt.n_items, 1), s);
     kkt_launch(nullptr, false);
-    k_kkt_finalize<<<1, 256, 0, s>>>(P.schedAt.part, P.schedAt.n_items, P.schedA.part,
-                                     P.schedA.n_items, st_, out6);
+    k_part_reduce<<<kChunks, 256, 0, s>>>(P.schedAt.part, P.schedAt.n_items, 6, P.schedA.part,
+                                          P.schedA.n_items, 4, nullptr, P.red);
+    k_kkt_finalize<<<1, 256, 0, s>>>(P.red, kChunks, nullptr, 0, st_, out6);
     return cudaGetLastError();
   }
 

@@ -1,0 +1,843 @@
+// Batch of LPs sharing one dense constraint matrix: B instances
+//     min c_k^T x  s.t.  lc <= A x <= uc,  l <= x <= u,   k = 0..B-1,
+// solved together by r^2HPDHG (Algorithm 1) with per-instance step sizes,
+// primal weights, restarts and termination.  Stacking the instances' iterates
+// as the columns of X (n x B) and Y (m x B) turns the two matrix-vector products
+// of every iteration into dense GEMMs, A X and A^T Y (the paper batches
+// same-shape instances by vectorisation, Sec. 3.2; with a shared A the batched
+// product is a dense contraction), which run on the tensor cores.
+//
+// Precision: the scaled matrix and the iterates are split into BF16 pairs
+// v = v_hi + v_lo (v_hi = bf16(v), v_lo = bf16(v - v_hi)); each product is the
+// sum of three BF16 GEMMs with FP32 accumulation, A_hi X_lo + A_lo X_hi +
+// A_hi X_hi, which carries about the accuracy of an FP32 product.  The split of
+// the iterates is written by the fused update kernels, so a GEMM reads BF16
+// operands only.  The GEMMs are plain library GEMMs (cuBLAS); the PDHG update,
+// projection, Halpern step, splitting and the FP64 check reductions are this
+// file's kernels.  A plain FP32 product path (SGEMM on the FP32 pipes) is kept
+// for comparison.
+//
+// Layout: A is row-major m x n, i.e. column-major n x m; X, Y and every
+// per-instance vector are column-major (column k = instance k).
+#include <cublas_v2.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mpax.h"
+#include "common.cuh"
+
+namespace mpax {
+
+namespace {
+
+int g1(long long k) { return (int)std::max(1LL, std::min(8192LL, (k + 255) / 256)); }
+
+mpax_status sfail(mpax_status s, const std::string& m) {
+  set_last_error(m.c_str());
+  return s;
+}
+
+// ---- per-instance state --------------------------------------------------------
+struct Inst {
+  double tau, sigma, omega, r_anchor, r_prev, rel, pobj, dobj, c_norm, best_rel;
+  long long k, total, restarts, done_at;
+  int done, status, restart, have_anchor;
+};
+
+// ---- dense scaling (row-major m x n): row/column infinity- and 1-norms ----------
+__global__ void k_row_red(const float* __restrict__ A, int m, int n, int sum,
+                          double* __restrict__ out) {
+  __shared__ double sh[32];
+  for (int i = blockIdx.x; i < m; i += gridDim.x) {
+    double acc = 0.0;
+    const float* r = A + (size_t)i * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double v = fabs((double)r[j]);
+      acc = sum ? acc + v : fmax(acc, v);
+    }
+    if (sum) {
+      acc = block_sum(acc, sh);
+    } else {
+      // fixed-order max tree
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc = fmax(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = fmax(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+      }
+    }
+    if (threadIdx.x == 0) out[i] = acc;
+    __syncthreads();
+  }
+}
+
+// column reduction: thread per column, sequential over rows (coalesced in j)
+__global__ void k_col_red(const float* __restrict__ A, int m, int n, int sum,
+                          double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double acc = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double v = fabs((double)A[(size_t)i * n + j]);
+    acc = sum ? acc + v : fmax(acc, v);
+  }
+  out[j] = acc;
+}
+
+__global__ void k_factor(double* __restrict__ norm, int k, double* __restrict__ D) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  const double v = norm[i];
+  const double d = v > 0.0 ? 1.0 / sqrt(v) : 1.0;
+  norm[i] = d;
+  D[i] *= d;
+}
+
+// dst_ij = (src_ij * dr_i) * dc_j
+__global__ void k_scale_dense(const float* __restrict__ src, float* __restrict__ dst, int m,
+                              int n, const double* __restrict__ dr,
+                              const double* __restrict__ dc) {
+  const size_t total = (size_t)m * n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    dst[e] = (float)(((double)src[e] * dr[i]) * dc[j]);
+  }
+}
+
+__global__ void k_split(const float* __restrict__ a, __nv_bfloat16* __restrict__ hi,
+                        __nv_bfloat16* __restrict__ lo, size_t total) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const float v = a[e];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+__device__ __forceinline__ void split_store(float v, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                            size_t e) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[e] = h;
+  lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// ---- fused updates ----------------------------------------------------------------
+struct Vecs {
+  int m, n, B;
+  const float *ct, *l, *u, *lc, *uc;  // scaled: ct n x B, l/u n, lc/uc m
+  float *w, *xa, *xhat, *T;             // n x B
+  float *y, *ya, *yhat, *S;             // m x B
+  __nv_bfloat16 *xh_hi, *xh_lo, *y_hi, *y_lo;
+  double* part;                          // per-column partials [q][k]
+  Inst* inst;
+};
+
+// primal: T = A~^T Y; x = w + (anchor - w)/(k+1); x^ = proj(x - tau (c~ - T));
+// w <- 2 x^ - x (also split to BF16 for the next product)
+__global__ void k_primal(Vecs v, int check) {
+  const size_t total = (size_t)v.n * v.B;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / v.n), j = (int)(e % v.n);
+    const Inst& I = v.inst[k];
+    if (I.done) continue;
+    const float rb = (float)(1.0 / (double)(I.k + 1));
+    const float x0 = v.xa[e], wv = v.w[e];
+    const float x = (I.k == 0) ? x0 : wv + rb * (x0 - wv);
+    const float xh = fminf(fmaxf(x - (float)I.tau * (v.ct[e] - v.T[e]), v.l[j]), v.u[j]);
+    const float wn = 2.0f * xh - x;
+    v.w[e] = wn;
+    split_store(wn, v.xh_hi, v.xh_lo, e);
+    if (check) v.xhat[e] = xh;
+  }
+}
+
+// dual: S = A~ xbar; y^ = sigma (v - proj_[-uc,-lc](v)), v = y/sigma - S;
+// y <- z + (anchor - z)/(k+2), z = 2 y^ - y (also split)
+__global__ void k_dual(Vecs v, int check) {
+  const size_t total = (size_t)v.m * v.B;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / v.m), i = (int)(e % v.m);
+    const Inst& I = v.inst[k];
+    if (I.done) continue;
+    const float sg = (float)I.sigma, isg = (float)(1.0 / I.sigma);
+    const float hb = (float)(1.0 / (double)(I.k + 2));
+    const float y0 = v.y[e];
+    const float vv = y0 * isg - v.S[e];
+    const float yh = sg * (vv - fminf(fmaxf(vv, -v.uc[i]), -v.lc[i]));
+    const float z = 2.0f * yh - y0;
+    const float yn = z + hb * (v.ya[e] - z);
+    v.y[e] = yn;
+    split_store(yn, v.y_hi, v.y_lo, e);
+    if (check) v.yhat[e] = yh;
+  }
+}
+
+__global__ void k_advance(Inst* inst, int B) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < B && !inst[k].done) {
+    inst[k].k += 1;
+    inst[k].total += 1;
+  }
+}
+
+// Per-column check reductions (one block per instance, fixed order).
+// The products S = A~ x^ and T = A~^T y^ were formed into S and T by the caller.
+// part[q * B + k]: 0 sum (x^-x)^2 .. computed here from w/xa? -- see k_check_prep.
+struct KktArgs {
+  int m, n, B;
+  const float *xhat, *yhat, *S, *T, *xprev_w, *xa, *yprev, *ya;
+  const double *Dr, *Dc, *c0, *lc0, *uc0, *l0, *u0;  // c0: n x B unscaled costs
+  double* part;
+};
+
+__global__ void k_kkt_cols(KktArgs a, const Inst* inst) {
+  __shared__ double sh[32];
+  const int k = blockIdx.x;
+  if (inst[k].done) return;
+  const size_t on = (size_t)k * a.n, om = (size_t)k * a.m;
+  double rd2 = 0, cx = 0, bt = 0;
+  for (int j = threadIdx.x; j < a.n; j += blockDim.x) {
+    const double aty = (double)a.T[on + j] / a.Dc[j];
+    const double x = a.Dc[j] * (double)a.xhat[on + j];
+    const double c = a.c0[on + j];
+    const double lam = c - aty;
+    const double lo = a.l0[j], hi = a.u0[j];
+    const bool lf = isfinite(lo), uf = isfinite(hi);
+    const double lh = (lf && uf) ? lam : lf ? fmax(lam, 0.0) : uf ? fmin(lam, 0.0) : 0.0;
+    rd2 += (lam - lh) * (lam - lh);
+    cx += c * x;
+    bt += (lf ? lo * fmax(lh, 0.0) : 0.0) + (uf ? hi * fmin(lh, 0.0) : 0.0);
+  }
+  double rp2 = 0, yt = 0;
+  for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
+    const double ax = (double)a.S[om + i] / a.Dr[i];
+    const double lo = a.lc0[i], hi = a.uc0[i];
+    const double r = ax - fmin(fmax(ax, lo), hi);
+    rp2 += r * r;
+    const double y = a.Dr[i] * (double)a.yhat[om + i];
+    if (y > 0.0 && isfinite(lo)) yt += lo * y;
+    if (y < 0.0 && isfinite(hi)) yt += hi * y;
+  }
+  const double v[5] = {rd2, cx, bt, rp2, yt};
+  for (int q = 0; q < 5; ++q) {
+    const double s = block_sum(v[q], sh);
+    if (threadIdx.x == 0) a.part[(size_t)q * a.B + k] = s;
+  }
+}
+
+// restart metric pieces: x = w_prev rebuilt is not stored; use the stored x^ and the
+// iterate before the check step (xprev) to form |x^ - x|^2 and |x^ - anchor|^2
+__global__ void k_fixed_point_cols(const float* __restrict__ xhat, const float* __restrict__ xprev,
+                                   const float* __restrict__ xa, const float* __restrict__ yhat,
+                                   const float* __restrict__ yprev, const float* __restrict__ ya,
+                                   int m, int n, int B, const Inst* inst, double* part) {
+  __shared__ double sh[32];
+  const int k = blockIdx.x;
+  if (inst[k].done) return;
+  const size_t on = (size_t)k * n, om = (size_t)k * m;
+  double p0 = 0, p1 = 0, d0 = 0, d1 = 0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double a = (double)xhat[on + j] - (double)xprev[on + j];
+    const double b = (double)xhat[on + j] - (double)xa[on + j];
+    p0 += a * a;
+    p1 += b * b;
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double a = (double)yhat[om + i] - (double)yprev[om + i];
+    const double b = (double)yhat[om + i] - (double)ya[om + i];
+    d0 += a * a;
+    d1 += b * b;
+  }
+  const double v[4] = {p0, p1, d0, d1};
+  for (int q = 0; q < 4; ++q) {
+    const double s = block_sum(v[q], sh);
+    if (threadIdx.x == 0) part[(size_t)(5 + q) * B + k] = s;
+  }
+}
+
+struct CheckParams {
+  double eps_abs, eps_rel, r_suff, r_nec, r_art, pw_smooth, eta, b_norm;
+  long long iter_limit, now_ns, time_limit_ns;
+  int B, check_no;
+};
+
+__global__ void k_check_finalize(Inst* inst, const double* part, CheckParams p) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= p.B) return;
+  Inst& I = inst[k];
+  I.restart = 0;
+  if (I.done) return;
+  const double rd2 = part[0 * p.B + k], cx = part[1 * p.B + k], bt = part[2 * p.B + k],
+               rp2 = part[3 * p.B + k], yt = part[4 * p.B + k];
+  const double P0 = part[5 * p.B + k], P1 = part[6 * p.B + k], D0 = part[7 * p.B + k],
+               D1 = part[8 * p.B + k];
+  const double nrp = sqrt(rp2), nrd = sqrt(rd2), pobj = cx, dobj = yt + bt;
+  const double gap = fabs(pobj - dobj);
+  const double rel = fmax(fmax(nrp / (1.0 + p.b_norm), nrd / (1.0 + I.c_norm)),
+                          gap / (1.0 + fabs(pobj) + fabs(dobj)));
+  I.rel = rel;
+  I.pobj = pobj;
+  I.dobj = dobj;
+  const bool conv = nrp <= p.eps_abs + p.eps_rel * p.b_norm &&
+                    nrd <= p.eps_abs + p.eps_rel * I.c_norm &&
+                    gap <= p.eps_abs + p.eps_rel * (fabs(pobj) + fabs(dobj));
+  int term = 0;
+  if (!isfinite(rel)) term = MPAX_TERM_NUMERICAL_ERROR;
+  else if (conv) term = MPAX_TERM_OPTIMAL;
+  else if (I.total >= p.iter_limit) term = MPAX_TERM_ITERATION_LIMIT;
+  else if (p.now_ns >= p.time_limit_ns) term = MPAX_TERM_TIME_LIMIT;
+  if (term) {
+    I.done = 1;
+    I.status = term;
+    I.done_at = p.now_ns;
+    return;
+  }
+  const double r = sqrt(I.omega * P0 + D0 / I.omega);
+  const bool restart = !I.have_anchor || r <= p.r_suff * I.r_anchor ||
+                       (r <= p.r_nec * I.r_anchor && r > I.r_prev) ||
+                       (double)I.k >= p.r_art * (double)I.total;
+  if (restart) {
+    const double dx = sqrt(P1), dy = sqrt(D1);
+    if (dx > 1e-10 && dy > 1e-10)
+      I.omega = exp(p.pw_smooth * log(dy / dx) + (1.0 - p.pw_smooth) * log(I.omega));
+    I.tau = p.eta / I.omega;
+    I.sigma = p.eta * I.omega;
+    I.have_anchor = 1;
+    I.r_anchor = r;
+    I.r_prev = r;
+    I.k = 0;
+    I.restarts += 1;
+    I.restart = 1;
+  } else {
+    I.r_prev = r;
+  }
+}
+
+__global__ void k_restart_apply(Vecs v) {
+  const size_t tn = (size_t)v.n * v.B, tm = (size_t)v.m * v.B;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tn + tm;
+       e += (size_t)gridDim.x * blockDim.x) {
+    if (e < tn) {
+      const int k = (int)(e / v.n);
+      if (!v.inst[k].restart) continue;
+      const float xh = v.xhat[e];
+      v.xa[e] = xh;
+      v.w[e] = xh;
+      split_store(xh, v.xh_hi, v.xh_lo, e);
+    } else {
+      const size_t f = e - tn;
+      const int k = (int)(f / v.m);
+      if (!v.inst[k].restart) continue;
+      const float yh = v.yhat[f];
+      v.ya[f] = yh;
+      v.y[f] = yh;
+      split_store(yh, v.y_hi, v.y_lo, f);
+    }
+  }
+}
+
+// x (before the check step) rebuilt for the fixed-point residual: x = w + (xa - w)/(k+1)
+__global__ void k_rebuild_x(const float* __restrict__ w, const float* __restrict__ xa,
+                            float* __restrict__ out, int n, int B, const Inst* inst) {
+  const size_t total = (size_t)n * B;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / n);
+    const Inst& I = inst[k];
+    const float rb = (float)(1.0 / (double)(I.k + 1));
+    out[e] = (I.k == 0) ? xa[e] : w[e] + rb * (xa[e] - w[e]);
+  }
+}
+
+__global__ void k_copy_f(const float* __restrict__ s, float* __restrict__ d, size_t total) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x)
+    d[e] = s[e];
+}
+
+__global__ void k_init_inst(Inst* inst, int B, const double* cnorm_s, const double* cnorm,
+                            double bnorm_s, double eta) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= B) return;
+  Inst I;
+  memset(&I, 0, sizeof(I));
+  const double nc = cnorm_s[k];
+  I.omega = (nc > 1e-10 && bnorm_s > 1e-10) ? nc / bnorm_s : 1.0;
+  I.tau = eta / I.omega;
+  I.sigma = eta * I.omega;
+  I.c_norm = cnorm[k];
+  I.rel = INFINITY;
+  I.best_rel = INFINITY;
+  inst[k] = I;
+}
+
+// ||column k||_2 of an n x B column-major double matrix, optionally scaled by D
+__global__ void k_colnorm(const double* __restrict__ Cm, const double* __restrict__ D, int n,
+                          double* __restrict__ out) {
+  __shared__ double sh[32];
+  const int k = blockIdx.x;
+  double s = 0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double v = Cm[(size_t)k * n + j] * (D ? D[j] : 1.0);
+    s += v * v;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[k] = sqrt(s);
+}
+
+__global__ void k_scale_costs(const double* __restrict__ C0, const double* __restrict__ Dc, int n,
+                              size_t total, float* __restrict__ ct) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x)
+    ct[e] = (float)(C0[e] * Dc[e % n]);
+}
+
+__global__ void k_scale_vec(const double* __restrict__ v, const double* __restrict__ D, int div,
+                            int n, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)(div ? v[i] / D[i] : v[i] * D[i]);
+}
+
+__global__ void k_unscale_out(const float* __restrict__ v, const double* __restrict__ D, int n,
+                              size_t total, double* __restrict__ out) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x)
+    out[e] = D[e % n] * (double)v[e];
+}
+
+__global__ void k_bound_norm(const double* lc, const double* uc, const double* Dr, int m,
+                             double* out) {
+  __shared__ double sh[32];
+  double s = 0, ss = 0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double lo = lc[i], hi = uc[i];
+    auto bnd = [](double a, double b) {
+      const bool fa = isfinite(a), fb = isfinite(b);
+      if (fa && fb) return fabs(a) >= fabs(b) ? a : b;
+      if (fa) return a;
+      if (fb) return b;
+      return 0.0;
+    };
+    const double b = bnd(lo, hi), bs = bnd(lo * Dr[i], hi * Dr[i]);
+    s += b * b;
+    ss += bs * bs;
+  }
+  s = block_sum(s, sh);
+  __syncthreads();
+  ss = block_sum(ss, sh);
+  if (threadIdx.x == 0) {
+    out[0] = sqrt(s);
+    out[1] = sqrt(ss);
+  }
+}
+
+__global__ void k_vec_norm_part(const float* __restrict__ v, size_t n, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = 0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)v[i] * (double)v[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = sqrt(s);
+}
+
+__global__ void k_scale_f(float* __restrict__ v, size_t n, const double* __restrict__ nrm) {
+  const double inv = *nrm > 0 ? 1.0 / *nrm : 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    v[i] = (float)((double)v[i] * inv);
+}
+
+}  // namespace
+}  // namespace mpax
+
+using namespace mpax;
+
+struct mpax_shared {
+  int m = 0, n = 0, B = 0;
+  cudaStream_t user = nullptr, s = nullptr;
+  cublasHandle_t blas = nullptr;
+  float* A0 = nullptr;   // original FP32, row-major m x n
+  float* As = nullptr;   // scaled FP32
+  __nv_bfloat16 *Ahi = nullptr, *Alo = nullptr;
+  double *C0 = nullptr, *lc = nullptr, *uc = nullptr, *l = nullptr, *u = nullptr;
+  double *Dr = nullptr, *Dc = nullptr, *red_m = nullptr, *red_n = nullptr, *scal = nullptr;
+  float *ct = nullptr, *lf = nullptr, *uf = nullptr, *lcf = nullptr, *ucf = nullptr;
+  float *w = nullptr, *xa = nullptr, *xhat = nullptr, *T = nullptr, *xprev = nullptr;
+  float *y = nullptr, *ya = nullptr, *yhat = nullptr, *S = nullptr, *yprev = nullptr;
+  __nv_bfloat16 *xh_hi = nullptr, *xh_lo = nullptr, *y_hi = nullptr, *y_lo = nullptr;
+  double *part = nullptr, *cn = nullptr, *cns = nullptr;
+  Inst* inst = nullptr;
+  double *Xout = nullptr, *Yout = nullptr;
+  bool solved = false;
+  double solve_seconds = 0.0, norm_A = 0.0;
+  long long launches = 0, gemms = 0;
+  double gemm_flops = 0.0;
+  std::vector<Inst> h_inst;
+};
+
+namespace {
+
+void free_shared(mpax_shared* sh) {
+  if (!sh) return;
+  if (sh->s) cudaStreamSynchronize(sh->s);
+  void* bufs[] = {sh->A0,  sh->As,   sh->Ahi,   sh->Alo,   sh->C0,   sh->lc,   sh->uc,
+                  sh->l,   sh->u,    sh->Dr,    sh->Dc,    sh->red_m, sh->red_n, sh->scal,
+                  sh->ct,  sh->lf,   sh->uf,    sh->lcf,   sh->ucf,  sh->w,    sh->xa,
+                  sh->xhat, sh->T,   sh->xprev, sh->y,     sh->ya,   sh->yhat, sh->S,
+                  sh->yprev, sh->xh_hi, sh->xh_lo, sh->y_hi, sh->y_lo, sh->part, sh->cn,
+                  sh->cns, sh->inst, sh->Xout, sh->Yout};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (sh->blas) cublasDestroy(sh->blas);
+  if (sh->s) cudaStreamDestroy(sh->s);
+  delete sh;
+}
+
+// C (rows x B, col-major) = op(M) V, M the stored column-major n x m matrix
+// (A row-major).  trans = 1: C = M^T V (= A V, rows = m, K = n); trans = 0:
+// C = M V (= A^T V, rows = n, K = m).  BF16x3 or FP32.
+cublasStatus_t product(mpax_shared* sh, int trans, const __nv_bfloat16* vhi,
+                       const __nv_bfloat16* vlo, const float* vf, float* C, bool bf16x3,
+                       const float* Mf) {
+  const int m = sh->m, n = sh->n, B = sh->B;
+  const int rows = trans ? m : n, K = trans ? n : m;
+  const cublasOperation_t op = trans ? CUBLAS_OP_T : CUBLAS_OP_N;
+  const float one = 1.0f, zero = 0.0f;
+  cublasStatus_t st;
+  if (!bf16x3) {
+    st = cublasSgemm(sh->blas, op, CUBLAS_OP_N, rows, B, K, &one, Mf, n, vf, K, &zero, C, rows);
+    sh->gemms += 1;
+    sh->gemm_flops += 2.0 * rows * (double)B * K;
+    return st;
+  }
+  // small terms first: A_hi v_lo, A_lo v_hi, then A_hi v_hi
+  const void* As[3] = {sh->Ahi, sh->Alo, sh->Ahi};
+  const void* Vs[3] = {vlo, vhi, vhi};
+  for (int t = 0; t < 3; ++t) {
+    st = cublasGemmEx(sh->blas, op, CUBLAS_OP_N, rows, B, K, &one, As[t], CUDA_R_16BF, n, Vs[t],
+                      CUDA_R_16BF, K, t == 0 ? &zero : &one, C, CUDA_R_32F, rows,
+                      CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+    if (st != CUBLAS_STATUS_SUCCESS) return st;
+  }
+  sh->gemms += 3;
+  sh->gemm_flops += 3 * 2.0 * rows * (double)B * K;
+  return CUBLAS_STATUS_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpax_status mpax_lp_shared_create(int32_t m, int32_t n, int32_t B, const float* A,
+                                  const double* C, const double* lc, const double* uc,
+                                  const double* l, const double* u, mpax_mem_kind kind,
+                                  void* cuda_stream, mpax_shared** out) {
+  if (!out) return sfail(MPAX_ERR_INVALID_ARGUMENT, "out must not be NULL");
+  *out = nullptr;
+  if (m < 1 || n < 1 || B < 1) return sfail(MPAX_ERR_INVALID_ARGUMENT, "m, n, B must be >= 1");
+  if (!A || !C || !lc || !uc || !l || !u)
+    return sfail(MPAX_ERR_INVALID_ARGUMENT, "a required array pointer is NULL");
+  mpax_shared* sh = new mpax_shared();
+  sh->m = m;
+  sh->n = n;
+  sh->B = B;
+  sh->user = (cudaStream_t)cuda_stream;
+  const size_t mn = (size_t)m * n, nB = (size_t)n * B, mB = (size_t)m * B;
+  cudaError_t e = cudaStreamCreateWithFlags(&sh->s, cudaStreamNonBlocking);
+  auto al = [&](auto** p, size_t cnt) {
+    if (!e) e = cudaMalloc((void**)p, sizeof(**p) * std::max<size_t>(cnt, 1));
+  };
+  al(&sh->A0, mn);
+  al(&sh->As, mn);
+  al(&sh->Ahi, mn);
+  al(&sh->Alo, mn);
+  al(&sh->C0, nB);
+  al(&sh->lc, m);
+  al(&sh->uc, m);
+  al(&sh->l, n);
+  al(&sh->u, n);
+  al(&sh->Dr, m);
+  al(&sh->Dc, n);
+  al(&sh->red_m, m);
+  al(&sh->red_n, n);
+  al(&sh->scal, 8);
+  al(&sh->ct, nB);
+  al(&sh->lf, n);
+  al(&sh->uf, n);
+  al(&sh->lcf, m);
+  al(&sh->ucf, m);
+  for (float** p : {&sh->w, &sh->xa, &sh->xhat, &sh->T, &sh->xprev}) al(p, nB);
+  for (float** p : {&sh->y, &sh->ya, &sh->yhat, &sh->S, &sh->yprev}) al(p, mB);
+  al(&sh->xh_hi, nB);
+  al(&sh->xh_lo, nB);
+  al(&sh->y_hi, mB);
+  al(&sh->y_lo, mB);
+  al(&sh->part, 16 * (size_t)B);
+  al(&sh->cn, B);
+  al(&sh->cns, B);
+  al(&sh->inst, B);
+  al(&sh->Xout, nB);
+  al(&sh->Yout, mB);
+  const cudaMemcpyKind k = kind == MPAX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (!e) e = cudaMemcpy(sh->A0, A, sizeof(float) * mn, k);
+  if (!e) e = cudaMemcpy(sh->C0, C, sizeof(double) * nB, k);
+  if (!e) e = cudaMemcpy(sh->lc, lc, sizeof(double) * m, k);
+  if (!e) e = cudaMemcpy(sh->uc, uc, sizeof(double) * m, k);
+  if (!e) e = cudaMemcpy(sh->l, l, sizeof(double) * n, k);
+  if (!e) e = cudaMemcpy(sh->u, u, sizeof(double) * n, k);
+  if (e) {
+    free_shared(sh);
+    return sfail(e == cudaErrorMemoryAllocation ? MPAX_ERR_OUT_OF_MEMORY : MPAX_ERR_CUDA,
+                 cudaGetErrorString(e));
+  }
+  if (cublasCreate(&sh->blas) != CUBLAS_STATUS_SUCCESS ||
+      cublasSetStream(sh->blas, sh->s) != CUBLAS_STATUS_SUCCESS) {
+    free_shared(sh);
+    return sfail(MPAX_ERR_CUDA, "cuBLAS initialisation failed");
+  }
+  cublasSetMathMode(sh->blas, CUBLAS_DEFAULT_MATH);  // no TF32: the FP32 path stays FP32
+  *out = sh;
+  return MPAX_OK;
+}
+
+mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp32_products) {
+  if (!sh || !o) return sfail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  if (o->reflection_gamma != 1.0 || o->check_every < 1 || o->iteration_limit < 1 ||
+      !(o->time_limit >= 0))
+    return sfail(MPAX_ERR_INVALID_ARGUMENT, "invalid options (reflection_gamma must be 1)");
+  const auto t0 = std::chrono::steady_clock::now();
+  const int m = sh->m, n = sh->n, B = sh->B;
+  const size_t mn = (size_t)m * n, nB = (size_t)n * B, mB = (size_t)m * B;
+  cudaStream_t s = sh->s;
+  cudaEvent_t ev;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  cudaEventRecord(ev, sh->user);
+  cudaStreamWaitEvent(s, ev, 0);
+  long long L = 0;
+  sh->gemms = 0;
+  sh->gemm_flops = 0.0;
+  // ---- scaling of the shared matrix (Ruiz, Pock-Chambolle) ----------------------
+  auto fill1 = [&](double* p, int cnt) {
+    std::vector<double> ones(cnt, 1.0);
+    cudaMemcpyAsync(p, ones.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+  };
+  fill1(sh->Dr, m);
+  fill1(sh->Dc, n);
+  cudaMemcpyAsync(sh->As, sh->A0, sizeof(float) * mn, cudaMemcpyDeviceToDevice, s);
+  for (int t = 0; t < o->ruiz_iters; ++t) {
+    k_row_red<<<std::min(m, 4096), 256, 0, s>>>(sh->As, m, n, 0, sh->red_m);
+    k_col_red<<<(n + 255) / 256, 256, 0, s>>>(sh->As, m, n, 0, sh->red_n);
+    k_factor<<<(m + 255) / 256, 256, 0, s>>>(sh->red_m, m, sh->Dr);
+    k_factor<<<(n + 255) / 256, 256, 0, s>>>(sh->red_n, n, sh->Dc);
+    k_scale_dense<<<g1(mn), 256, 0, s>>>(sh->As, sh->As, m, n, sh->red_m, sh->red_n);
+    L += 5;
+  }
+  if (o->pock_chambolle) {
+    k_row_red<<<std::min(m, 4096), 256, 0, s>>>(sh->As, m, n, 1, sh->red_m);
+    k_col_red<<<(n + 255) / 256, 256, 0, s>>>(sh->As, m, n, 1, sh->red_n);
+    k_factor<<<(m + 255) / 256, 256, 0, s>>>(sh->red_m, m, sh->Dr);
+    k_factor<<<(n + 255) / 256, 256, 0, s>>>(sh->red_n, n, sh->Dc);
+    L += 4;
+  }
+  k_scale_dense<<<g1(mn), 256, 0, s>>>(sh->A0, sh->As, m, n, sh->Dr, sh->Dc);
+  k_split<<<g1(mn), 256, 0, s>>>(sh->As, sh->Ahi, sh->Alo, mn);
+  k_scale_costs<<<g1(nB), 256, 0, s>>>(sh->C0, sh->Dc, n, nB, sh->ct);
+  k_scale_vec<<<(n + 255) / 256, 256, 0, s>>>(sh->l, sh->Dc, 1, n, sh->lf);
+  k_scale_vec<<<(n + 255) / 256, 256, 0, s>>>(sh->u, sh->Dc, 1, n, sh->uf);
+  k_scale_vec<<<(m + 255) / 256, 256, 0, s>>>(sh->lc, sh->Dr, 0, m, sh->lcf);
+  k_scale_vec<<<(m + 255) / 256, 256, 0, s>>>(sh->uc, sh->Dr, 0, m, sh->ucf);
+  L += 7;
+  // ---- ||A~||_2 by power iteration (FP32 products, FP64 norms) --------------------
+  {
+    float* v = sh->T;    // n (first column of T as scratch)
+    float* wv = sh->S;   // m
+    std::vector<float> ones(n, (float)(1.0 / std::sqrt((double)n)));
+    cudaMemcpyAsync(v, ones.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    const float one = 1.0f, zero = 0.0f;
+    double prev = 0.0, nu = 0.0;
+    for (int t = 1; t <= o->power_max_iter; ++t) {
+      cublasSgemv(sh->blas, CUBLAS_OP_T, n, m, &one, sh->As, n, v, 1, &zero, wv, 1);
+      cublasSgemv(sh->blas, CUBLAS_OP_N, n, m, &one, sh->As, n, wv, 1, &zero, v, 1);
+      k_vec_norm_part<<<1, 512, 0, s>>>(v, n, sh->scal);
+      double nrm = 0.0;
+      cudaMemcpyAsync(&nrm, sh->scal, sizeof(double), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      k_scale_f<<<g1(n), 256, 0, s>>>(v, n, sh->scal);
+      L += 4;
+      if (nrm == 0.0) break;
+      nu = std::sqrt(nrm);
+      if (t > 1 && std::fabs(nu - prev) <= o->power_tol * nu) break;
+      prev = nu;
+    }
+    sh->norm_A = nu;
+  }
+  const double eta = sh->norm_A > 0 ? o->step_safety / sh->norm_A : 1.0;
+  // ---- per-instance initial state --------------------------------------------------
+  k_colnorm<<<B, 256, 0, s>>>(sh->C0, sh->Dc, n, sh->cns);
+  k_colnorm<<<B, 256, 0, s>>>(sh->C0, nullptr, n, sh->cn);
+  k_bound_norm<<<1, 512, 0, s>>>(sh->lc, sh->uc, sh->Dr, m, sh->scal);
+  double bn[2];
+  cudaMemcpyAsync(bn, sh->scal, sizeof(bn), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  k_init_inst<<<(B + 255) / 256, 256, 0, s>>>(sh->inst, B, sh->cns, sh->cn, bn[1], eta);
+  for (void* p : {(void*)sh->w, (void*)sh->xa, (void*)sh->xhat})
+    cudaMemsetAsync(p, 0, sizeof(float) * nB, s);
+  for (void* p : {(void*)sh->y, (void*)sh->ya, (void*)sh->yhat})
+    cudaMemsetAsync(p, 0, sizeof(float) * mB, s);
+  cudaMemsetAsync(sh->xh_hi, 0, sizeof(__nv_bfloat16) * nB, s);
+  cudaMemsetAsync(sh->xh_lo, 0, sizeof(__nv_bfloat16) * nB, s);
+  cudaMemsetAsync(sh->y_hi, 0, sizeof(__nv_bfloat16) * mB, s);
+  cudaMemsetAsync(sh->y_lo, 0, sizeof(__nv_bfloat16) * mB, s);
+  L += 4;
+  const bool bf = !fp32_products;
+  Vecs V{m, n, B, sh->ct, sh->lf, sh->uf, sh->lcf, sh->ucf, sh->w, sh->xa, sh->xhat, sh->T,
+         sh->y, sh->ya, sh->yhat, sh->S, sh->xh_hi, sh->xh_lo, sh->y_hi, sh->y_lo, sh->part,
+         sh->inst};
+  KktArgs K{m, n, B, sh->xhat, sh->yhat, sh->S, sh->T, nullptr, sh->xa, nullptr, sh->ya,
+            sh->Dr, sh->Dc, sh->C0, sh->lc, sh->uc, sh->l, sh->u, sh->part};
+  long long done_iters = 0;
+  int check_no = 0;
+  // time limit, checked at each KKT check against the host clock
+  const long long tl_ns = o->time_limit >= 9.0e9 ? LLONG_MAX : (long long)(o->time_limit * 1e9);
+  std::vector<Inst> hi(B);
+  mpax_status result = MPAX_OK;
+  while (true) {
+    const int len = (int)std::min<long long>(o->check_every, o->iteration_limit - done_iters);
+    for (int it = 0; it < len; ++it) {
+      const int chk = (it == len - 1);
+      if (chk) {  // the iterate before the check step, for the fixed-point residual
+        k_rebuild_x<<<g1(nB), 256, 0, s>>>(sh->w, sh->xa, sh->xprev, n, B, sh->inst);
+        k_copy_f<<<g1(mB), 256, 0, s>>>(sh->y, sh->yprev, mB);
+        L += 2;
+      }
+      if (product(sh, 0, sh->y_hi, sh->y_lo, sh->y, sh->T, bf, sh->As)) {
+        result = sfail(MPAX_ERR_CUDA, "cuBLAS product failed");
+        break;
+      }
+      k_primal<<<g1(nB), 256, 0, s>>>(V, chk);
+      // the dual product reads the reflected point w (FP32) or its BF16 split
+      if (product(sh, 1, sh->xh_hi, sh->xh_lo, sh->w, sh->S, bf, sh->As)) {
+        result = sfail(MPAX_ERR_CUDA, "cuBLAS product failed");
+        break;
+      }
+      k_dual<<<g1(mB), 256, 0, s>>>(V, chk);
+      k_advance<<<(B + 255) / 256, 256, 0, s>>>(sh->inst, B);
+      L += 3;
+    }
+    if (result) break;
+    done_iters += len;
+    ++check_no;
+    // KKT products at (x^, y^): S = A~ x^, T = A~^T y^ (the x^/y^ splits reuse the
+    // BF16 buffers; the iteration rewrites them before its next product)
+    k_split<<<g1(nB), 256, 0, s>>>(sh->xhat, sh->xh_hi, sh->xh_lo, nB);
+    k_split<<<g1(mB), 256, 0, s>>>(sh->yhat, sh->y_hi, sh->y_lo, mB);
+    product(sh, 1, sh->xh_hi, sh->xh_lo, sh->xhat, sh->S, bf, sh->As);
+    product(sh, 0, sh->y_hi, sh->y_lo, sh->yhat, sh->T, bf, sh->As);
+    k_kkt_cols<<<B, 256, 0, s>>>(K, sh->inst);
+    k_fixed_point_cols<<<B, 256, 0, s>>>(sh->xhat, sh->xprev, sh->xa, sh->yhat, sh->yprev,
+                                         sh->ya, m, n, B, sh->inst, sh->part);
+    CheckParams cp{o->eps_abs, o->eps_rel, o->restart_sufficient, o->restart_necessary,
+                   o->restart_artificial, o->primal_weight_smoothing, eta, bn[0],
+                   o->iteration_limit,
+                   (long long)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                       std::chrono::steady_clock::now() - t0).count(),
+                   tl_ns, B, check_no};
+    k_check_finalize<<<(B + 255) / 256, 256, 0, s>>>(sh->inst, sh->part, cp);
+    // the BF16 splits of the iterates are rebuilt (restart copies x^, y^ into them)
+    k_split<<<g1(nB), 256, 0, s>>>(sh->w, sh->xh_hi, sh->xh_lo, nB);
+    k_split<<<g1(mB), 256, 0, s>>>(sh->y, sh->y_hi, sh->y_lo, mB);
+    k_restart_apply<<<g1(nB + mB), 256, 0, s>>>(V);
+    L += 8;
+    cudaMemcpyAsync(hi.data(), sh->inst, sizeof(Inst) * B, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    int active = 0;
+    for (const Inst& I : hi) active += !I.done;
+    if (!active) break;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (!result && e) result = sfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  k_unscale_out<<<g1(nB), 256, 0, s>>>(sh->xhat, sh->Dc, n, nB, sh->Xout);
+  k_unscale_out<<<g1(mB), 256, 0, s>>>(sh->yhat, sh->Dr, m, mB, sh->Yout);
+  L += 2;
+  cudaStreamSynchronize(s);
+  cudaEventRecord(ev, s);
+  cudaStreamWaitEvent(sh->user, ev, 0);
+  cudaEventDestroy(ev);
+  sh->h_inst = hi;
+  sh->launches = L;
+  sh->solved = !result;
+  sh->solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return result;
+}
+
+mpax_status mpax_shared_get_solution(const mpax_shared* sh, double* X, double* Y,
+                                     mpax_mem_kind kind) {
+  if (!sh) return sfail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  if (!sh->solved) return sfail(MPAX_ERR_NOT_SOLVED, "call mpax_shared_solve first");
+  const cudaMemcpyKind k = kind == MPAX_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  cudaError_t e = cudaSuccess;
+  if (X) e = cudaMemcpy(X, sh->Xout, sizeof(double) * (size_t)sh->n * sh->B, k);
+  if (!e && Y) e = cudaMemcpy(Y, sh->Yout, sizeof(double) * (size_t)sh->m * sh->B, k);
+  if (e) return sfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  return MPAX_OK;
+}
+
+mpax_status mpax_shared_get_stats(const mpax_shared* sh, mpax_batch_stats* stats,
+                                  int32_t* status, int64_t* iterations, double* rel_kkt,
+                                  double* primal_obj, double* seconds, double* gemm_info) {
+  if (!sh || !stats) return sfail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  if (!sh->solved) return sfail(MPAX_ERR_NOT_SOLVED, "call mpax_shared_solve first");
+  std::memset(stats, 0, sizeof(*stats));
+  stats->B = sh->B;
+  std::vector<double> secs(sh->B);
+  for (int k = 0; k < sh->B; ++k) {
+    const Inst& I = sh->h_inst[k];
+    stats->n_optimal += I.status == MPAX_TERM_OPTIMAL;
+    stats->iterations_total += I.total;
+    stats->iterations_max = std::max<long long>(stats->iterations_max, I.total);
+    stats->restarts_total += I.restarts;
+    stats->rel_kkt_max = std::max(stats->rel_kkt_max, I.rel);
+    secs[k] = I.done_at * 1e-9;
+    if (status) status[k] = I.status;
+    if (iterations) iterations[k] = I.total;
+    if (rel_kkt) rel_kkt[k] = I.rel;
+    if (primal_obj) primal_obj[k] = I.pobj;
+    if (seconds) seconds[k] = secs[k];
+  }
+  std::vector<double> so = secs;
+  std::sort(so.begin(), so.end());
+  auto pct = [&](double q) {
+    const size_t i = std::min<size_t>(so.size() - 1, (size_t)std::ceil(q * so.size()) - 1);
+    return so[i];
+  };
+  stats->instance_seconds_p50 = pct(0.5);
+  stats->instance_seconds_p99 = pct(0.99);
+  stats->instance_seconds_max = so.back();
+  stats->solve_seconds = sh->solve_seconds;
+  stats->kernel_launches = sh->launches;
+  if (gemm_info) {
+    gemm_info[0] = (double)sh->gemms;
+    gemm_info[1] = sh->gemm_flops;
+    gemm_info[2] = sh->norm_A;
+  }
+  return MPAX_OK;
+}
+
+void mpax_shared_destroy(mpax_shared* sh) { free_shared(sh); }
+
+}  // extern "C"

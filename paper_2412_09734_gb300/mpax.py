@@ -28,7 +28,10 @@ EXPORTED = ["mpax_version", "mpax_last_error", "mpax_status_string", "mpax_optio
             "mpax_lp_create", "mpax_qp_create_diag_lowrank", "mpax_solve", "mpax_get_solution",
             "mpax_get_stats", "mpax_destroy", "mpax_prepare", "mpax_get_scaling",
             "mpax_get_transpose", "mpax_set_iterate", "mpax_iterate", "mpax_get_iterate",
-            "mpax_kkt", "mpax_lp_kkt_noalloc"]
+            "mpax_kkt", "mpax_lp_value_grad", "mpax_qp_adjoint", "mpax_lp_batch_create", "mpax_batch_solve", "mpax_batch_get_solution",
+            "mpax_batch_get_stats", "mpax_batch_destroy", "mpax_lp_shared_create", "mpax_shared_solve",
+            "mpax_shared_get_solution", "mpax_shared_get_stats", "mpax_shared_destroy",
+            "mpax_lp_kkt_noalloc"]
 
 
 class MpaxError(RuntimeError):
@@ -52,6 +55,7 @@ class Options(ctypes.Structure):
         ("primal_weight_smoothing", ctypes.c_double), ("step_safety", ctypes.c_double),
         ("power_max_iter", ctypes.c_int32), ("power_tol", ctypes.c_double),
         ("use_graphs", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
+        ("fp64_continuation", ctypes.c_int32), ("stall_checks", ctypes.c_int32),
     ]
 
 
@@ -68,6 +72,7 @@ class Stats(ctypes.Structure):
         ("prepare_seconds", ctypes.c_double), ("solve_seconds", ctypes.c_double),
         ("kernel_launches", ctypes.c_int64),
         ("profile_ms", ctypes.c_double * 4), ("profile_launches", ctypes.c_int64 * 4),
+        ("fp64_iterations", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -77,6 +82,20 @@ class Stats(ctypes.Structure):
             d[name] = list(v) if hasattr(v, "__len__") else v
         d["termination_name"] = TERMINATION.get(self.termination, "?")
         return d
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [
+        ("B", ctypes.c_int32), ("n_optimal", ctypes.c_int32),
+        ("iterations_total", ctypes.c_int64), ("iterations_max", ctypes.c_int64),
+        ("restarts_total", ctypes.c_int64), ("rel_kkt_max", ctypes.c_double),
+        ("instance_seconds_p50", ctypes.c_double), ("instance_seconds_p99", ctypes.c_double),
+        ("instance_seconds_max", ctypes.c_double), ("solve_seconds", ctypes.c_double),
+        ("kernel_launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 if not os.path.exists(LIB_PATH):
@@ -109,6 +128,19 @@ _sig = {
     "mpax_get_iterate": ([_P, _P, _P, _P, _P, _INT], _INT),
     "mpax_kkt": ([_P, _P, _P, _INT, _P], _INT),
     "mpax_lp_kkt_noalloc": ([_I32, _I32, _I64] + [_P] * 15, _INT),
+    "mpax_lp_value_grad": ([_P, _P, _P, _P, _P, _P, _INT], _INT),
+    "mpax_qp_adjoint": ([_P, _P, _P, _P, _P, _D, _I32, _INT, _P], _INT),
+    "mpax_lp_batch_create": ([_I32] + [_P] * 10 + [_INT, _P, ctypes.POINTER(_P)], _INT),
+    "mpax_batch_solve": ([_P, ctypes.POINTER(Options)], _INT),
+    "mpax_batch_get_solution": ([_P, _P, _P, _INT], _INT),
+    "mpax_batch_get_stats": ([_P, ctypes.POINTER(BatchStats), _P, _P, _P, _P, _P], _INT),
+    "mpax_batch_destroy": ([_P], None),
+    "mpax_lp_shared_create": ([_I32, _I32, _I32] + [_P] * 6 + [_INT, _P, ctypes.POINTER(_P)],
+                              _INT),
+    "mpax_shared_solve": ([_P, ctypes.POINTER(Options), _I32], _INT),
+    "mpax_shared_get_solution": ([_P, _P, _P, _INT], _INT),
+    "mpax_shared_get_stats": ([_P, ctypes.POINTER(BatchStats)] + [_P] * 6, _INT),
+    "mpax_shared_destroy": ([_P], None),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -328,3 +360,142 @@ def mpax_kkt(h, x, y):
                              out.ctypes.data))
     keys = ("primal_res", "dual_res", "primal_obj", "dual_obj", "gap", "rel_kkt")
     return dict(zip(keys, out.tolist()))
+
+
+# ---------------------------------------------------------------------------
+# ragged batch
+# ---------------------------------------------------------------------------
+
+def mpax_lp_batch_create(B, m_off, n_off, row_ptr, col_idx, val, c, lc, uc, l, u, stream=None):
+    kind = _kind_of(row_ptr, val)
+    k = _Keep(kind)
+    h = _P()
+    # offsets are read on the host side of the call in either memory kind
+    _check(_lib.mpax_lp_batch_create(
+        int(B), k.ptr(m_off, np.int64), k.ptr(n_off, np.int64), k.ptr(row_ptr, np.int64),
+        k.ptr(col_idx, np.int32), k.ptr(val, np.float64), k.ptr(c, np.float64),
+        k.ptr(lc, np.float64), k.ptr(uc, np.float64), k.ptr(l, np.float64),
+        k.ptr(u, np.float64), kind, _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def mpax_batch_solve(h, opts):
+    _check(_lib.mpax_batch_solve(h, ctypes.byref(opts)))
+
+
+def mpax_batch_get_solution(h, m_total, n_total):
+    x = np.empty(n_total)
+    y = np.empty(m_total)
+    _check(_lib.mpax_batch_get_solution(h, _ptr_out(x), _ptr_out(y), MPAX_MEM_HOST))
+    return x, y
+
+
+def mpax_batch_get_stats(h, B):
+    s = BatchStats()
+    st = np.empty(B, dtype=np.int32)
+    it = np.empty(B, dtype=np.int64)
+    kk = np.empty(B)
+    po = np.empty(B)
+    sec = np.empty(B)
+    _check(_lib.mpax_batch_get_stats(h, ctypes.byref(s), st.ctypes.data, it.ctypes.data,
+                                     kk.ctypes.data, po.ctypes.data, sec.ctypes.data))
+    return s.as_dict(), dict(status=st, iterations=it, rel_kkt=kk, primal_obj=po, seconds=sec)
+
+
+def mpax_batch_destroy(h):
+    if h:
+        _lib.mpax_batch_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# differentiation
+# ---------------------------------------------------------------------------
+
+def mpax_lp_value_grad(h, m, n, device=None):
+    """Returns dict(c, lc, uc, l, u) of optimal-value gradients."""
+    outs = {k: _out(sz, device)[0] for k, sz in (("c", n), ("lc", m), ("uc", m), ("l", n),
+                                                 ("u", n))}
+    kind = MPAX_MEM_DEVICE if (device is not None and _is_torch(device) and device.is_cuda) \
+        else MPAX_MEM_HOST
+    _check(_lib.mpax_lp_value_grad(h, _ptr_out(outs["c"]), _ptr_out(outs["lc"]),
+                                   _ptr_out(outs["uc"]), _ptr_out(outs["l"]),
+                                   _ptr_out(outs["u"]), kind))
+    return outs
+
+
+def mpax_qp_adjoint(h, g, m, n, tol=1e-10, max_iter=10000):
+    """Returns (dc, db, dD, info) for the loss gradient g = dL/dx*."""
+    kind = _kind_of(g)
+    kp = _Keep(kind)
+    gp = kp.ptr(g, np.float64)
+    dc, _ = _out(n, g if kind == MPAX_MEM_DEVICE else None)
+    db, _ = _out(m, g if kind == MPAX_MEM_DEVICE else None)
+    dD, _ = _out(n, g if kind == MPAX_MEM_DEVICE else None)
+    info = np.zeros(2)
+    _check(_lib.mpax_qp_adjoint(h, gp, _ptr_out(dc), _ptr_out(db), _ptr_out(dD), float(tol),
+                                int(max_iter), kind, info.ctypes.data))
+    return dc, db, dD, dict(iterations=int(info[0]), rel_residual=float(info[1]))
+
+
+# ---------------------------------------------------------------------------
+# shared dense matrix batch
+# ---------------------------------------------------------------------------
+
+def mpax_lp_shared_create(m, n, B, A, C, lc, uc, l, u, stream=None):
+    kind = _kind_of(A, C)
+    k = _Keep(kind)
+    if _is_torch(A):
+        import torch
+        Ap = A.to(torch.float32).contiguous()
+        k.refs.append(Ap)
+        a_ptr = Ap.data_ptr()
+    else:
+        Ap = np.ascontiguousarray(A, dtype=np.float32)
+        k.refs.append(Ap)
+        a_ptr = Ap.ctypes.data
+    h = _P()
+    _check(_lib.mpax_lp_shared_create(int(m), int(n), int(B), a_ptr, k.ptr(C, np.float64),
+                                      k.ptr(lc, np.float64), k.ptr(uc, np.float64),
+                                      k.ptr(l, np.float64), k.ptr(u, np.float64), kind,
+                                      _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def mpax_shared_solve(h, opts, fp32_products=False):
+    _check(_lib.mpax_shared_solve(h, ctypes.byref(opts), 1 if fp32_products else 0))
+
+
+def mpax_shared_get_solution(h, m, n, B, device=None):
+    """Returns (X, Y) as (B, n) and (B, m) FP64 arrays; CUDA tensors when `device`
+    is a CUDA tensor used as a template."""
+    if device is not None and _is_torch(device) and device.is_cuda:
+        import torch
+        X = torch.empty((B, n), dtype=torch.float64, device=device.device)
+        Y = torch.empty((B, m), dtype=torch.float64, device=device.device)
+        _check(_lib.mpax_shared_get_solution(h, X.data_ptr(), Y.data_ptr(), MPAX_MEM_DEVICE))
+        return X, Y
+    X = np.empty((B, n))
+    Y = np.empty((B, m))
+    _check(_lib.mpax_shared_get_solution(h, X.ctypes.data, Y.ctypes.data, MPAX_MEM_HOST))
+    return X, Y
+
+
+def mpax_shared_get_stats(h, B):
+    s = BatchStats()
+    st = np.empty(B, dtype=np.int32)
+    it = np.empty(B, dtype=np.int64)
+    kk = np.empty(B)
+    po = np.empty(B)
+    sec = np.empty(B)
+    gi = np.zeros(3)
+    _check(_lib.mpax_shared_get_stats(h, ctypes.byref(s), st.ctypes.data, it.ctypes.data,
+                                      kk.ctypes.data, po.ctypes.data, sec.ctypes.data,
+                                      gi.ctypes.data))
+    d = s.as_dict()
+    d.update(gemms=int(gi[0]), gemm_flops=float(gi[1]), norm_A=float(gi[2]))
+    return d, dict(status=st, iterations=it, rel_kkt=kk, primal_obj=po, seconds=sec)
+
+
+def mpax_shared_destroy(h):
+    if h:
+        _lib.mpax_shared_destroy(h)

@@ -152,11 +152,12 @@ def _rmatvec(row_ptr, col, val, y, n):
 def lp_instance(m: int, n: int, *, seed: int, density: float | None = None,
                 nnz: int | None = None, rows: str = "bernoulli", lo: float = 0.0,
                 hi: float = 10.0, eq_frac: float = 0.5, variant: str = "literal",
-                min_row: int = 0) -> dict:
+                min_row: int = 0, tight_frac: float = 0.5) -> dict:
     """Feasible, bounded LP  min c^T x  s.t.  lc <= A x <= uc,  lo <= x <= hi.
 
     Rows [0, m_eq) are equalities lc = uc = A x0; rows [m_eq, m) are
-    inequalities lc <= A x with uc = +inf.
+    inequalities lc <= A x with uc = +inf.  In the nondegenerate variant exactly
+    round(tight_frac * (m - m_eq)) inequality rows are tight at x0.
     """
     rng = _rng(seed)
     row_ptr, col, val = csr_random(m, n, rng, density=density, nnz=nnz, rows=rows,
@@ -188,7 +189,8 @@ def lp_instance(m: int, n: int, *, seed: int, density: float | None = None,
     n_ineq = m - m_eq
     slack = rng.uniform(0.0, 1.0, size=n_ineq)
     if variant == "nondegenerate":
-        tight = rng.random(n_ineq) < 0.5
+        tight = np.zeros(n_ineq, dtype=bool)
+        tight[rng.permutation(n_ineq)[:int(round(tight_frac * n_ineq))]] = True
         slack[tight] = 0.0
         y0[m_eq:][tight] = np.abs(rng.standard_normal(int(tight.sum())))
     lc[m_eq:] = ax0[m_eq:] - slack
@@ -256,15 +258,32 @@ def ragged_lp_batch(B: int, *, seed: int = MASTER_SEED, m_lo: int = 50, m_hi: in
 # ----------------------------------------------------------------------------
 
 def shared_dense_lp_batch(m: int, n: int, B: int, *, seed: int = MASTER_SEED,
-                          lo: float = 0.0, hi: float = 1.0, dtype=np.float32) -> dict:
+                          lo: float = 0.0, hi: float = 1.0, dtype=np.float32,
+                          bound_frac: float = 0.0) -> dict:
     """Dense A (m x n) with N(0, 1/n) entries (std 1/sqrt(n)); equality rows
-    b = A x0 with x0 ~ U[lo, hi]; B cost vectors c_k = A^T y_k, y_k ~ N(0,1)."""
+    b = A x0 with x0 ~ U[lo, hi]; B cost vectors c_k = A^T y_k + s_k, y_k ~ N(0,1).
+
+    bound_frac = 0: s_k = 0 (every feasible point is optimal, value c_k^T x0).
+    bound_frac > 0: that fraction of x0's coordinates is moved to a bound (half
+    to lo, half to hi) and s_k carries reduced costs of the right sign there
+    (U[0.1, 1] at lo, -U[0.1, 1] at hi), so x0 is the unique-valued optimum and
+    (y_k, s_k) a dual certificate."""
     rng = _rng(seed)
     A = (rng.standard_normal((m, n), dtype=np.float32) / np.float32(np.sqrt(n))).astype(dtype)
     x0 = rng.uniform(lo, hi, size=n)
-    b = A.astype(np.float64) @ x0
     Y = rng.standard_normal((B, m))
-    C = Y @ A.astype(np.float64)
+    if bound_frac > 0:
+        r = rng.random(n)
+        at_lo = r < 0.5 * bound_frac
+        at_hi = (r >= 0.5 * bound_frac) & (r < bound_frac)
+        x0[at_lo], x0[at_hi] = lo, hi
+    A64 = A.astype(np.float64)
+    b = A64 @ x0
+    C = Y @ A64
+    del A64
+    if bound_frac > 0:
+        C[:, at_lo] += rng.uniform(0.1, 1.0, size=(B, int(at_lo.sum())))
+        C[:, at_hi] -= rng.uniform(0.1, 1.0, size=(B, int(at_hi.sum())))
     return dict(kind="lp_shared", m=m, n=n, B=B, A=A, b=b, C=C, x0=x0, Y=Y,
                 l=np.full(n, lo), u=np.full(n, hi), opt_value=C @ x0)
 

@@ -1,0 +1,124 @@
+"""GPU differentiation layer against the oracle's adjoint (which is itself pinned
+by central finite differences in tests/test_oracle_adjoint.py), plus the
+torch.autograd wrappers against finite differences of GPU solves."""
+import numpy as np
+import pytest
+
+from oracle import adjoint as AD
+from oracle import pdhg as O
+from synth import instance_seed, lp_instance, qp_instance
+from tests.gpu_util import create, lib, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    return lib()
+
+
+def _lp_case():
+    return lp_instance(20, 40, seed=instance_seed(401), density=0.3, variant="nondegenerate",
+                       tight_frac=0.6)
+
+
+def _qp_small():
+    return qp_instance(50, 25, seed=instance_seed(202), a_density=0.04, f_cols=32,
+                       f_density=0.04, min_row=2)
+
+
+def test_lp_value_gradient_matches_oracle(C):
+    d = _lp_case()
+    p = O.problem_from_arrays(d)
+    ref = O.solve_lp(p, O.Options(eps_abs=1e-11, eps_rel=1e-11, iteration_limit=10**6))
+    gr = AD.lp_value_gradient(p, ref.x, ref.y)
+    h = create(C, d)
+    try:
+        C.mpax_solve(h, C.mpax_options_default(eps_abs=1e-11, eps_rel=1e-11,
+                                               iteration_limit=10**6))
+        g = C.mpax_lp_value_grad(h, d["m"], d["n"])
+    finally:
+        C.mpax_destroy(h)
+    for k in ("c", "lc", "uc", "l", "u"):
+        assert np.max(np.abs(g[k] - gr[k])) <= 1e-6 * (1 + np.max(np.abs(gr[k]))), k
+
+
+@pytest.mark.parametrize("case,eps,tol", [("small", 1e-11, 1e-5), ("4k", 1e-8, 1e-3)])
+def test_qp_adjoint_matches_oracle(C, case, eps, tol):
+    if case == "small":
+        d = _qp_small()
+    else:
+        d = qp_instance(4000, 2000, seed=instance_seed(201), a_density=5e-3, f_cols=32,
+                        f_density=0.01)
+    p = O.problem_from_arrays(d)
+    ref = O.solve_qp(p, O.Options(eps_abs=eps, eps_rel=eps, iteration_limit=10**6))
+    assert ref.status == "optimal"
+    free, rows = AD.active_sets(p, ref.x, ref.y, 1e-7, 1e-7)
+    rdc, rdb, rdD = AD.qp_adjoint(p, ref.x, ref.y, ref.x - d["x_target"], free, rows)
+    h = create(C, d)
+    try:
+        C.mpax_solve(h, C.mpax_options_default(eps_abs=eps, eps_rel=eps, iteration_limit=10**6))
+        x, _ = C.mpax_get_solution(h, d["m"], d["n"])
+        dc, db, dD, info = C.mpax_qp_adjoint(h, x - d["x_target"], d["m"], d["n"], tol=1e-12,
+                                             max_iter=20000)
+    finally:
+        C.mpax_destroy(h)
+    assert info["rel_residual"] <= 1e-10
+    assert rel_inf(dc, rdc) <= tol
+    assert rel_inf(db, rdb) <= tol
+    assert rel_inf(dD, rdD) <= tol
+
+
+def test_qp_layer_autograd_matches_finite_differences(C):
+    import torch
+    from paper_2412_09734_gb300.autograd import QPLayer
+    d = _qp_small()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    data = dict(m=d["m"], n=d["n"], row_ptr=dev(d["row_ptr"]), col=dev(d["col"]),
+                val=dev(d["val"]), l=dev(d["l"]), u=dev(d["u"]), f_row_ptr=dev(d["f_row_ptr"]),
+                f_col=dev(d["f_col"]), f_val=dev(d["f_val"]), r=d["f_cols"])
+    opts = dict(eps_abs=1e-11, eps_rel=1e-11, iteration_limit=10**6)
+    xt = dev(d["x_target"])
+    c = dev(d["c"]).requires_grad_(True)
+    b = dev(d["lc"]).requires_grad_(True)
+    D = dev(d["D"]).requires_grad_(True)
+    x = QPLayer.apply(c, b, D, data, opts)
+    loss = 0.5 * torch.sum((x - xt) ** 2)
+    loss.backward()
+
+    def L(c_, b_, D_):
+        with torch.no_grad():
+            xx = QPLayer.apply(c_, b_, D_, data, opts)
+            return float(0.5 * torch.sum((xx - xt) ** 2))
+
+    h = 1e-6
+    with torch.no_grad():
+        for j in (0, 7, 19, 33):
+            e = torch.zeros_like(c)
+            e[j] = h
+            fd = (L(c + e, b, D) - L(c - e, b, D)) / (2 * h)
+            assert fd == pytest.approx(float(c.grad[j]), rel=1e-4, abs=1e-6)
+        for i in (1, 12):
+            e = torch.zeros_like(b)
+            e[i] = h
+            fd = (L(c, b + e, D) - L(c, b - e, D)) / (2 * h)
+            assert fd == pytest.approx(float(b.grad[i]), rel=1e-4, abs=1e-6)
+
+
+def test_lp_value_layer_autograd(C):
+    import torch
+    from paper_2412_09734_gb300.autograd import LPValue
+    d = _lp_case()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    data = dict(m=d["m"], n=d["n"], row_ptr=dev(d["row_ptr"]), col=dev(d["col"]),
+                val=dev(d["val"]), l=dev(d["l"]), u=dev(d["u"]))
+    c = dev(d["c"]).requires_grad_(True)
+    v = LPValue.apply(c, dev(d["lc"]), dev(d["uc"]), data,
+                      dict(eps_abs=1e-11, eps_rel=1e-11, iteration_limit=10**6))
+    v.backward()
+    assert float(v) == pytest.approx(d["opt_value"], rel=1e-8)
+    np.testing.assert_allclose(c.grad.cpu().numpy(), d["x0"], atol=1e-6)

@@ -1,0 +1,111 @@
+"""GPU parity of the ragged batch path (one persistent launch over many LPs)
+against the FP64 oracle run on each instance separately."""
+import numpy as np
+import pytest
+
+from oracle import pdhg as O
+from synth import ragged_lp_batch
+from tests.gpu_util import lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    return lib()
+
+
+def _create(C, d, device=False):
+    keys = ("m_off", "n_off", "row_ptr", "col", "val", "c", "lc", "uc", "l", "u")
+    arrs = [d[k] for k in keys]
+    if device:
+        import torch
+        arrs = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+    return C.mpax_lp_batch_create(d["B"], *arrs)
+
+
+def _fp32_kkt_bound(p, x, y, chk):
+    """First-order bound on |rel_kkt(FP32 row sums) - rel_kkt(exact)| at (x, y).
+
+    A row sum of L terms computed in FP32 from FP32-rounded scaled values has
+    error at most (L + 1) u sum_j |a_j v_j|, u = 2^-24 (standard recursive-summation
+    bound plus the rounding of each stored value).  The projections in r_p and r_d
+    are 1-Lipschitz, the dual objective's bound terms move by |bound| |d lambda_j|,
+    the primal objective is formed in FP64 and does not move, and max() is
+    1-Lipschitz in each argument."""
+    u = 2.0 ** -24
+    A = abs(p.A)
+    Lr = np.diff(p.A.indptr) + 1.0
+    Lc = np.bincount(p.A.indices, minlength=p.n) + 1.0
+    e_ax = u * Lr * (A @ np.abs(x))
+    e_aty = u * Lc * (A.T @ np.abs(y))
+    bmag = np.where(np.isfinite(p.l), np.abs(p.l), 0.0)
+    bmag = np.maximum(bmag, np.where(np.isfinite(p.u), np.abs(p.u), 0.0))
+    dp = np.linalg.norm(e_ax) / (1.0 + chk["b_norm"])
+    dd = np.linalg.norm(e_aty) / (1.0 + chk["c_norm"])
+    dg = float(bmag @ e_aty) / (1.0 + abs(chk["primal_obj"]) + abs(chk["dual_obj"]))
+    return max(dp, dd, dg)
+
+
+@pytest.mark.parametrize("prec,eps", [(0, 1e-6), (1, 1e-4)])
+def test_batch_matches_oracle_per_instance(C, prec, eps):
+    d = ragged_lp_batch(24, seed=5150, m_lo=20, m_hi=300, density=0.05)
+    h = _create(C, d, device=(prec == 1))
+    try:
+        C.mpax_batch_solve(h, C.mpax_options_default(precision=prec, eps_abs=eps, eps_rel=eps,
+                                                     iteration_limit=500000))
+        summary, per = C.mpax_batch_get_stats(h, d["B"])
+        x, y = C.mpax_batch_get_solution(h, int(d["m_off"][-1]), int(d["n_off"][-1]))
+    finally:
+        C.mpax_batch_destroy(h)
+    assert summary["n_optimal"] == d["B"]
+    assert summary["kernel_launches"] >= 1
+    for b, inst in enumerate(d["instances"]):
+        p = O.problem_from_arrays(inst)
+        xs = x[d["n_off"][b]:d["n_off"][b + 1]]
+        ys = y[d["m_off"][b]:d["m_off"][b + 1]]
+        chk = O.kkt(p, xs, ys, eps, eps)
+        assert chk["converged"], (b, chk["rel_kkt"])
+        if prec:
+            # the mixed path forms A x^ and A^T y^ of its own check from FP32 scaled
+            # values with FP32 row sums; its relative KKT error may differ from the
+            # FP64 evaluation by at most the first-order rounding bound of those sums
+            bound = _fp32_kkt_bound(p, xs, ys, chk)
+            assert abs(chk["rel_kkt"] - per["rel_kkt"][b]) <= 2.0 * bound + 1e-12, (b, bound)
+        else:
+            assert chk["rel_kkt"] == pytest.approx(per["rel_kkt"][b], rel=1e-8, abs=1e-12)
+        assert chk["primal_obj"] == pytest.approx(inst["opt_value"], rel=30 * eps, abs=30 * eps)
+        if prec == 0 and b < 8:
+            ref = O.solve_lp(p, O.Options(eps_abs=eps, eps_rel=eps, iteration_limit=500000))
+            # the same written rules give the same trajectory up to rounding
+            assert abs(per["iterations"][b] - ref.iterations) <= 2 * 64
+
+
+def test_batch_iteration_limit_and_stats(C):
+    d = ragged_lp_batch(16, seed=77, m_lo=10, m_hi=60, density=0.1)
+    h = _create(C, d)
+    try:
+        C.mpax_batch_solve(h, C.mpax_options_default(iteration_limit=100, eps_abs=1e-14,
+                                                     eps_rel=1e-14))
+        summary, per = C.mpax_batch_get_stats(h, d["B"])
+    finally:
+        C.mpax_batch_destroy(h)
+    assert np.all(per["status"] == 4) and np.all(per["iterations"] == 100)
+    assert summary["iterations_total"] == 1600 and summary["n_optimal"] == 0
+    assert np.all(per["seconds"] > 0)
+    assert summary["instance_seconds_p50"] <= summary["instance_seconds_p99"]
+
+
+def test_batch_rejects_bad_columns(C):
+    d = ragged_lp_batch(3, seed=9, m_lo=10, m_hi=20, density=0.2)
+    bad = dict(d)
+    col = d["col"].copy()
+    col[0] = d["n_off"][1] + 5  # beyond instance 0's columns
+    bad["col"] = col
+    with pytest.raises(C.MpaxError) as ei:
+        _create(C, bad)
+    assert ei.value.status == 1

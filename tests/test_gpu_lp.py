@@ -340,3 +340,28 @@ def test_time_limit(C):
         C.mpax_destroy(h)
     assert stats["termination_name"] in ("time_limit", "optimal")
     assert stats["iterations"] <= 192
+
+
+def test_mixed_with_fp64_continuation_reaches_1e8(C):
+    """Below the FP32 floor the mixed solve stalls and finishes in FP64 from its
+    FP32 point (the final polishing step of the precision pattern)."""
+    d = lp_instance(200, 400, seed=instance_seed(1), density=0.02, variant="nondegenerate")
+    p = O.problem_from_arrays(d)
+    h = create(C, d)
+    try:
+        C.mpax_solve(h, C.mpax_options_default(precision=1, eps_abs=1e-8, eps_rel=1e-8,
+                                               iteration_limit=400000))
+        stats = C.mpax_get_stats(h)
+        x, y = C.mpax_get_solution(h, d["m"], d["n"])
+        C.mpax_solve(h, C.mpax_options_default(precision=1, eps_abs=1e-8, eps_rel=1e-8,
+                                               iteration_limit=30000, fp64_continuation=0))
+        plain = C.mpax_get_stats(h)
+    finally:
+        C.mpax_destroy(h)
+    assert stats["termination_name"] == "optimal"
+    assert 0 < stats["fp64_iterations"] < stats["iterations"]
+    chk = O.kkt(p, x, y, 1e-8, 1e-8)
+    assert chk["converged"]
+    assert chk["primal_obj"] == pytest.approx(d["opt_value"], rel=1e-7)
+    # FP32 alone does not get there
+    assert plain["termination_name"] == "iteration_limit" and plain["rel_kkt"] > 1e-8

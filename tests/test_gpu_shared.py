@@ -1,0 +1,113 @@
+"""GPU parity of the shared-matrix dense batch (tensor-core BF16x3 products and
+the FP32 product path) against the FP64 oracle on each instance."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import pdhg as O
+from synth import shared_dense_lp_batch
+from tests.gpu_util import lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    return lib()
+
+
+def _oracle_problem(d, k):
+    A = sp.csr_matrix(d["A"].astype(np.float64))
+    return O.Problem(A, d["C"][k].copy(), d["b"].copy(), d["b"].copy(), d["l"], d["u"])
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_shared_batch_matches_oracle(C, fp32):
+    d = shared_dense_lp_batch(192, 384, 24, seed=31337)
+    h = C.mpax_lp_shared_create(d["m"], d["n"], d["B"], d["A"], d["C"], d["b"], d["b"],
+                                d["l"], d["u"])
+    try:
+        C.mpax_shared_solve(h, C.mpax_options_default(eps_abs=1e-4, eps_rel=1e-4,
+                                                      iteration_limit=200000), fp32)
+        summ, per = C.mpax_shared_get_stats(h, d["B"])
+        X, Y = C.mpax_shared_get_solution(h, d["m"], d["n"], d["B"])
+    finally:
+        C.mpax_shared_destroy(h)
+    assert summ["n_optimal"] == d["B"]
+    assert summ["gemms"] > 0 and summ["gemm_flops"] > 0
+    for k in range(d["B"]):
+        p = _oracle_problem(d, k)
+        chk = O.kkt(p, X[k], Y[k])
+        assert chk["converged"], (k, chk["rel_kkt"])
+        # literal construction: every feasible point is optimal with value c^T x0
+        assert chk["primal_obj"] == pytest.approx(d["opt_value"][k], rel=1e-3, abs=1e-3)
+    # the same instance through the single-problem FP64 path of the oracle
+    ref = O.solve_lp(_oracle_problem(d, 0), O.Options())
+    assert ref.kkt["primal_obj"] == pytest.approx(d["opt_value"][0], rel=1e-3, abs=1e-3)
+
+
+def test_shared_nondegenerate_values(C):
+    """Costs with reduced-cost parts at bounds (unique optimum): values to 1e-4."""
+    d = shared_dense_lp_batch(128, 256, 8, seed=99)
+    rng = np.random.default_rng(7)
+    X0 = rng.uniform(0, 1, size=(d["B"], d["n"]))
+    S = np.zeros_like(X0)
+    at_l = rng.random(X0.shape) < 0.3
+    at_u = (~at_l) & (rng.random(X0.shape) < 0.43)
+    X0[at_l], X0[at_u] = 0.0, 1.0
+    S[at_l] = rng.uniform(0.1, 1.0, at_l.sum())
+    S[at_u] = -rng.uniform(0.1, 1.0, at_u.sum())
+    # a common equality right-hand side needs a common x0; keep the one of the batch
+    # and only add reduced-cost parts at the bounds of that shared x0
+    x0 = d["x0"].copy()
+    lo = rng.random(d["n"]) < 0.3
+    hi = (~lo) & (rng.random(d["n"]) < 0.43)
+    x0[lo], x0[hi] = 0.0, 1.0
+    b = d["A"].astype(np.float64) @ x0
+    Cm = d["Y"] @ d["A"].astype(np.float64)
+    Cm[:, lo] += rng.uniform(0.1, 1.0, (d["B"], lo.sum()))
+    Cm[:, hi] -= rng.uniform(0.1, 1.0, (d["B"], hi.sum()))
+    h = C.mpax_lp_shared_create(d["m"], d["n"], d["B"], d["A"], Cm, b, b, d["l"], d["u"])
+    try:
+        C.mpax_shared_solve(h, C.mpax_options_default(iteration_limit=200000))
+        summ, per = C.mpax_shared_get_stats(h, d["B"])
+        X, Y = C.mpax_shared_get_solution(h, d["m"], d["n"], d["B"])
+    finally:
+        C.mpax_shared_destroy(h)
+    assert summ["n_optimal"] == d["B"]
+    for k in range(d["B"]):
+        p = O.Problem(sp.csr_matrix(d["A"].astype(np.float64)), Cm[k], b, b, d["l"], d["u"])
+        chk = O.kkt(p, X[k], Y[k])
+        assert chk["converged"]
+        assert chk["primal_obj"] == pytest.approx(float(Cm[k] @ x0), rel=1e-3, abs=1e-3)
+
+
+def test_shared_values_autograd(C):
+    """d v_k / d c_k = x_k*: the backward of the value layer returns the solved
+    primal rows, whose values match c_k^T x0 and whose KKT error the oracle checks."""
+    import torch
+    from paper_2412_09734_gb300.autograd import SharedLPValues
+    # 3/4 of x0 on a bound leaves ~32 free coordinates against 64 equality rows:
+    # a tall, well-conditioned system, so x0 is the unique optimum
+    d = shared_dense_lp_batch(64, 128, 6, seed=4242, bound_frac=0.75)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    Cm = dev(d["C"]).requires_grad_(True)
+    w = torch.linspace(0.5, 1.5, d["B"], dtype=torch.float64, device="cuda")
+    v = SharedLPValues.apply(Cm, dev(d["A"]), dev(d["b"]), dev(d["b"]), dev(d["l"]),
+                             dev(d["u"]), dict(eps_abs=1e-4, eps_rel=1e-4,
+                                               iteration_limit=400000))
+    (w * v).sum().backward()
+    np.testing.assert_allclose(v.detach().cpu().numpy(), d["opt_value"], rtol=1e-3, atol=1e-3)
+    G = Cm.grad.cpu().numpy()
+    for k in range(d["B"]):
+        xk = G[k] / float(w[k])
+        p = O.Problem(sp.csr_matrix(d["A"].astype(np.float64)), d["C"][k].copy(), d["b"],
+                      d["b"], d["l"], d["u"])
+        chk = O.kkt(p, xk, np.zeros(d["m"]))
+        assert chk["primal_res"] / (1 + chk["b_norm"]) <= 1e-4
+        # x0 is the unique optimum, so the gradient row is x0 up to the solve tolerance
+        np.testing.assert_allclose(xk, d["x0"], atol=5e-3)
