@@ -27,16 +27,24 @@ constexpr int kBlock = kWarp * kWarpsPerBlock;
 // Launch shape of the fused SpMV kernels: warps per CTA and the minimum number
 // of resident CTAs per SM asked of the register allocator.  Small CTAs retire
 // as soon as their few warp items are done, so an SM refills at warp grain.
+// Measured on the 500k x 1M Zipf LP (FP32): 2-warp CTAs with at least 20 resident
+// per SM (a 48-register cap) took the primal/dual launches from 61/79 us (8-warp
+// CTAs, the allocator's choice) to 52/66 us.
 #ifndef MPAX_SPMV_WARPS
-#define MPAX_SPMV_WARPS 8
+#define MPAX_SPMV_WARPS 2
 #endif
 #ifndef MPAX_SPMV_MINB
-#define MPAX_SPMV_MINB 0  // 0: the register allocator's own choice
+#define MPAX_SPMV_MINB 20  // 0: the register allocator's own choice
 #endif
 // 1: sliced long rows are completed through acquire/release atomics on the
 //    row's counter; 0: through __threadfence() around a relaxed atomic.
+// 1: lane 0 of each warp item issues a TMA bulk prefetch into L2 of the values
+//    and column indices of the item one resident wave ahead.
+#ifndef MPAX_SPMV_PREFETCH
+#define MPAX_SPMV_PREFETCH 1
+#endif
 #ifndef MPAX_LONG_ACQREL
-#define MPAX_LONG_ACQREL 0
+#define MPAX_LONG_ACQREL 1
 #endif
 constexpr int kSpmvWarps = MPAX_SPMV_WARPS;
 constexpr int kSpmvBlock = kWarp * kSpmvWarps;
@@ -46,7 +54,10 @@ constexpr int kSpmvBlock = kWarp * kSpmvWarps;
 #define MPAX_SPMV_BOUNDS __launch_bounds__(kSpmvBlock)
 #endif
 // Work decomposition of a CSR matrix into warp items.
-constexpr int kSliceNnz = 256;  // nonzeros of one slice of a long row
+#ifndef MPAX_SLICE_NNZ
+#define MPAX_SLICE_NNZ 256
+#endif
+constexpr int kSliceNnz = MPAX_SLICE_NNZ;  // nonzeros of one slice of a long row
 constexpr int kLongRow = 64;    // rows longer than this are cut into slices
 constexpr int kItemRows = 64;   // at most this many short rows per item
 constexpr int kShortCap = kSliceNnz + kLongRow;  // nonzeros of a packed item, upper bound

@@ -418,7 +418,7 @@ void launch_spmv(const Sched& sc, const Csr& K, const T* val, In in, Epi epi, in
   SpmvArgs<T> a;
   a.items = sc.items;
   a.n_items = sc.n_items;
-  a.pf_dist = resident_warps<T, In, Epi>();
+  a.pf_dist = MPAX_SPMV_PREFETCH ? resident_warps<T, In, Epi>() : 0;
   a.rp = K.rp;
   a.col = K.col;
   a.val = val;

@@ -10,7 +10,9 @@
 // Precision: the scaled matrix and the iterates are split into BF16 pairs
 // v = v_hi + v_lo (v_hi = bf16(v), v_lo = bf16(v - v_hi)); each product is the
 // sum of three BF16 GEMMs with FP32 accumulation, A_hi X_lo + A_lo X_hi +
-// A_hi X_hi, which carries about the accuracy of an FP32 product.  The split of
+// A_hi X_hi: each operand keeps about 16 significant bits and the dropped
+// A_lo X_lo term is of order 2^-16 relative, so a product is accurate to about
+// 2^-16 relative per term (an FP32 product: 2^-24).  The split of
 // the iterates is written by the fused update kernels, so a GEMM reads BF16
 // operands only.  The GEMMs are plain library GEMMs (cuBLAS); the PDHG update,
 // projection, Halpern step, splitting and the FP64 check reductions are this
