@@ -54,6 +54,21 @@ implements the same written rules.  The readings are:
   * Algorithm 1 writes A(2 x^{n,k+1} - x^{n,k}) in its dual line; eq. (3)
     uses the new PDHG primal point, which is what is done here: A(2 x^ - x).
   * rAPDHG schedules: beta_k = theta_k = 2/(k+2), k the inner counter.
+  * Infeasibility detection (LP; Sec. 3 names it, the option table gives
+    eps_primal_infeasible = eps_dual_infeasible = 1e-8): at every check the
+    move of the cycle since its anchor, dx = D_c (x^ - x_anchor) and
+    dy = D_r (y^ - y_anchor), is tested as a certificate.
+      Primal infeasible (a Farkas ray): y = dy projected onto the recession
+      cone of Y (y_i >= 0 where uc_i = +inf, y_i <= 0 where lc_i = -inf),
+      lam = -A^T y, lh = proj_Lambda(lam); the ray's dual objective
+      o = sum lc_i y_i^+ - uc_i y_i^- + sum l_j lh_j^+ - u_j lh_j^- (finite
+      terms) must be positive and ||lam - lh|| <= eps_primal_infeasible * o.
+      Dual infeasible (an unbounded primal ray): x = dx with
+      ||A x - proj_R(A x)||^2 + ||x - proj_X(x)||^2 <= (eps_dual_infeasible c^T x)^2
+      and c^T x < 0, where R and X are the recession cones of [lc, uc] and
+      [l, u] (0 where both bounds are finite, R+ / R- where only the lower /
+      upper one is, R where neither).
+    The certificate is returned as Result.certificate.
 """
 from __future__ import annotations
 
@@ -159,6 +174,8 @@ class Options:
     step_safety: float = 0.998
     power_max_iter: int = 100
     power_tol: float = 1e-4
+    eps_primal_infeasible: float = 1e-8
+    eps_dual_infeasible: float = 1e-8
 
 
 # -----------------------------------------------------------------------------
@@ -383,6 +400,53 @@ class Result:
     Dr: np.ndarray
     Dc: np.ndarray
     history: list = field(default_factory=list)
+    certificate: np.ndarray | None = None
+
+
+# -----------------------------------------------------------------------------
+# Infeasibility certificates (the reading in the module docstring)
+# -----------------------------------------------------------------------------
+
+def _recession(v, lo_finite, hi_finite):
+    """Projection onto the recession cone of an interval with the given finite ends."""
+    return np.where(lo_finite & hi_finite, 0.0,
+                    np.where(lo_finite, np.maximum(v, 0.0),
+                             np.where(hi_finite, np.minimum(v, 0.0), v)))
+
+
+def primal_ray_test(p: Problem, dy):
+    """(violation, objective) of the dual ray dy as a certificate of primal infeasibility."""
+    flc, fuc = np.isfinite(p.lc), np.isfinite(p.uc)
+    y = np.where(~fuc, np.maximum(dy, 0.0), dy)
+    y = np.where(~flc, np.minimum(y, 0.0), y)
+    lam = -(p.A.T @ y)
+    fl, fu = np.isfinite(p.l), np.isfinite(p.u)
+    lh = np.where(fl & fu, lam, np.where(fl, np.maximum(lam, 0.0),
+                                         np.where(fu, np.minimum(lam, 0.0), 0.0)))
+    obj = (float(np.where(flc, p.lc, 0.0) @ np.maximum(y, 0.0))
+           - float(np.where(fuc, p.uc, 0.0) @ np.maximum(-y, 0.0))
+           + float(np.where(fl, p.l, 0.0) @ np.maximum(lh, 0.0))
+           - float(np.where(fu, p.u, 0.0) @ np.maximum(-lh, 0.0)))
+    return float(np.linalg.norm(lam - lh)), obj, y
+
+
+def dual_ray_test(p: Problem, dx):
+    """(violation, c^T dx) of the primal ray dx as a certificate of dual infeasibility."""
+    ax = p.A @ dx
+    vr = ax - _recession(ax, np.isfinite(p.lc), np.isfinite(p.uc))
+    vx = dx - _recession(dx, np.isfinite(p.l), np.isfinite(p.u))
+    return math.sqrt(float(vr @ vr) + float(vx @ vx)), float(p.c @ dx)
+
+
+def infeasibility(p: Problem, dx, dy, opts: Options):
+    """'primal_infeasible' / 'dual_infeasible' with its certificate, or (None, None)."""
+    vp, op, yray = primal_ray_test(p, dy)
+    if op > 0.0 and vp <= opts.eps_primal_infeasible * op:
+        return "primal_infeasible", yray
+    vd, cd = dual_ray_test(p, dx)
+    if cd < 0.0 and vd <= opts.eps_dual_infeasible * (-cd):
+        return "dual_infeasible", dx
+    return None, None
 
 
 def prepare(p: Problem, opts: Options):
@@ -446,6 +510,10 @@ def solve_lp(p: Problem, opts: Options = Options(), x_init=None, y_init=None,
                 status = "optimal" if info["converged"] else "iteration_limit"
                 return Result(Dc * x_hat, Dr * y_hat, status, total, restarts, info, omega,
                               eta, nA, nQ, Dr, Dc, hist)
+            status, cert = infeasibility(p, Dc * (x_hat - xa), Dr * (y_hat - ya), opts)
+            if status is not None:
+                return Result(Dc * x_hat, Dr * y_hat, status, total, restarts, info, omega,
+                              eta, nA, nQ, Dr, Dc, hist, cert)
             r = math.sqrt(omega * float(np.sum((x_hat - x) ** 2))
                           + float(np.sum((y_hat - y) ** 2)) / omega)
             if _restart_decision(r, r_anchor, r_prev, k + 1, total, opts):
