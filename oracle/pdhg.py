@@ -23,8 +23,14 @@ implements the same written rules.  The readings are:
     Scaled data: A~ = D_r A D_c, c~ = D_c c, Q~ = D_c Q D_c, [l~, u~] = [l, u]/D_c,
     [lc~, uc~] = D_r [lc, uc]; x = D_c x~, y = D_r y~.
   * Step sizes: eta = 0.998 / ||A~||_2 with ||A~||_2 from power iteration on
-    A~^T A~ started at the all-ones vector, stopped when the estimate changes
-    by at most 1e-4 relatively, or after 100 rounds.  LP: tau = eta/omega,
+    A~^T A~ started at a fixed pseudo-random vector of entries in [-1, 1]
+    (SplitMix64 of the index, see power_start).  The estimates rise towards the norm
+    with geometrically shrinking increments d_t (ratio q); the iteration stops
+    when d_t and the extrapolated remainder d_t q / (1 - q) are both at most
+    1e-4 of the estimate (or after 1000 rounds) and returns the estimate plus
+    the remainder.  (Stopping on the last change alone left the estimate up to
+    2% low on matrices whose two top singular values are close, and a step with
+    tau sigma ||A~||^2 > 1 diverges.)  LP: tau = eta/omega,
     sigma = eta*omega, fixed inside a restart cycle.  QP: sigma = eta*omega,
     tau = 0.998 / (||Q~||_2 + sigma ||A~||_2^2).
   * Primal weight: omega_0 = ||c~|| / ||b~|| when both exceed 1e-10, else 1,
@@ -172,7 +178,7 @@ class Options:
     restart_artificial: float = 0.36
     primal_weight_smoothing: float = 0.5
     step_safety: float = 0.998
-    power_max_iter: int = 100
+    power_max_iter: int = 1000
     power_tol: float = 1e-4
     eps_primal_infeasible: float = 1e-8
     eps_dual_infeasible: float = 1e-8
@@ -235,14 +241,56 @@ def scale_problem(p: Problem, Dr, Dc) -> Problem:
 # Operator norms by power iteration
 # -----------------------------------------------------------------------------
 
-def power_norm_A(A: sp.csr_matrix, max_iter: int = 100, tol: float = 1e-4):
-    """Estimate ||A||_2 = sqrt(lambda_max(A^T A)); start at the all-ones
-    vector; nu_t = sqrt(||A^T A v_t||) with ||v_t|| = 1."""
+_M64 = (1 << 64) - 1
+POWER_SEED = 0x6D706178  # counter base of the power iteration's start vector
+
+
+def _splitmix64(x: int) -> int:
+    """SplitMix64 (Steele, Lea and Flood, 2014) of the 64-bit counter x."""
+    z = (x + 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def power_start(n: int) -> np.ndarray:
+    """Start vector of the power iterations: v_j = 2 u_j - 1 with u_j the top 53
+    bits of SplitMix64(POWER_SEED + j) over 2^53, normalised.  A vector with
+    entries of both signs and no structure has a component along every singular
+    vector; the all-ones vector can be nearly orthogonal to the top one, and the
+    iteration then settles on the second singular value first."""
+    v = np.array([2.0 * ((_splitmix64(POWER_SEED + j) >> 11) * 2.0 ** -53) - 1.0
+                  for j in range(n)])
+    return v / np.linalg.norm(v)
+
+
+def _power_stop(nu, nu_prev, d_prev, tol):
+    """Stopping rule of the power iterations: the estimates nu_t rise towards the
+    norm with increments d_t = nu_t - nu_{t-1} that shrink geometrically (ratio
+    q = d_t / d_{t-1}) once the top singular vector dominates, so the distance
+    still to go is about d_t q / (1 - q).  Stop when both the last increment and
+    that remainder are at most tol * nu_t; the estimate returned is
+    nu_t + remainder.  Returns (stop, estimate, d_t)."""
+    d = nu - nu_prev
+    if d <= 0.0:                      # no rise left (rounding): converged
+        return True, nu, d
+    q = d / d_prev if d_prev > 0.0 else 1.0
+    if q >= 1.0:                      # not yet in the geometric regime
+        return False, nu, d
+    rem = d * q / (1.0 - q)
+    if d <= tol * nu and rem <= tol * nu:
+        return True, nu + rem, d
+    return False, nu, d
+
+
+def power_norm_A(A: sp.csr_matrix, max_iter: int = 1000, tol: float = 1e-4):
+    """Estimate ||A||_2 = sqrt(lambda_max(A^T A)); start at power_start(n);
+    nu_t = sqrt(||A^T A v_t||) with ||v_t|| = 1; stop by _power_stop."""
     n = A.shape[1]
     if n == 0 or A.nnz == 0:
         return 0.0, 0
-    v = np.ones(n) / math.sqrt(n)
-    nu_prev = None
+    v = power_start(n)
+    nu_prev, d_prev = None, 0.0
     for t in range(1, max_iter + 1):
         w = A @ v
         g = A.T @ w
@@ -251,26 +299,31 @@ def power_norm_A(A: sp.csr_matrix, max_iter: int = 100, tol: float = 1e-4):
             return 0.0, t
         nu = math.sqrt(nrm)
         v = g / nrm
-        if nu_prev is not None and abs(nu - nu_prev) <= tol * nu:
-            return nu, t
+        if nu_prev is not None:
+            stop, est, d_prev = _power_stop(nu, nu_prev, d_prev, tol)
+            if stop:
+                return est, t
         nu_prev = nu
     return nu, max_iter
 
 
-def power_norm_Q(Q, n: int, max_iter: int = 100, tol: float = 1e-4):
-    """Estimate ||Q||_2 for symmetric PSD Q: nu_t = ||Q v_t||, ||v_t|| = 1."""
+def power_norm_Q(Q, n: int, max_iter: int = 1000, tol: float = 1e-4):
+    """Estimate ||Q||_2 for symmetric PSD Q: start at power_start(n);
+    nu_t = ||Q v_t||, ||v_t|| = 1; stop by _power_stop."""
     if Q is None or n == 0:
         return 0.0, 0
-    v = np.ones(n) / math.sqrt(n)
-    nu_prev = None
+    v = power_start(n)
+    nu_prev, d_prev = None, 0.0
     for t in range(1, max_iter + 1):
         g = Q.matvec(v)
         nu = float(np.linalg.norm(g))
         if nu == 0.0:
             return 0.0, t
         v = g / nu
-        if nu_prev is not None and abs(nu - nu_prev) <= tol * nu:
-            return nu, t
+        if nu_prev is not None:
+            stop, est, d_prev = _power_stop(nu, nu_prev, d_prev, tol)
+            if stop:
+                return est, t
         nu_prev = nu
     return nu, max_iter
 

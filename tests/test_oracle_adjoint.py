@@ -21,7 +21,7 @@ def test_lp_value_gradient_matches_finite_differences():
     # a non-degenerate vertex: 10 equality rows + 6 tight inequality rows + 24
     # variables at a bound = n = 40 active constraints, strictly complementary,
     # so both the primal and the dual optimum are unique
-    d = lp_instance(20, 40, seed=instance_seed(401), density=0.3, variant="nondegenerate",
+    d = lp_instance(20, 40, seed=instance_seed(404), density=0.3, variant="nondegenerate",
                     tight_frac=0.6)
     p = O.problem_from_arrays(d)
     r = O.solve_lp(p, O.Options(eps_abs=1e-11, eps_rel=1e-11, iteration_limit=10**6))
