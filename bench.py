@@ -451,6 +451,7 @@ def run_batch(args):
                          p99_s=summ["instance_seconds_p99"],
                          iterations_mean=summ["iterations_total"] / d["B"],
                          rel_kkt_max=summ["rel_kkt_max"], clocks=clk,
+                         fp64_instances=summ["fp64_instances"],
                          gpu_launches=summ["kernel_launches"])
     nnz = int(d["row_ptr"][-1])
     line = {"metric": f"ragged batch LP solves/s to rel KKT 1e-4 ({d['B']} instances)",
@@ -517,6 +518,7 @@ def run_shared(args):
                          tensor_tflops_over_solve=flops / (ms / 1e3) / 1e12,
                          obj_rel_err_max=float(np.max(np.abs(per["primal_obj"] - d["opt_value"])
                                                       / (1 + np.abs(d["opt_value"])))),
+                         switched_to_fp32_instances=summ["fp64_instances"],
                          clocks=clk, gpu_launches=summ["kernel_launches"])
     pk, src = bf16_peak()
     a = out["bf16x3"]["tensor_tflops_over_solve"]

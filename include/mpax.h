@@ -60,8 +60,8 @@ typedef enum mpax_precision { MPAX_PREC_FP64 = 0, MPAX_PREC_MIXED = 1 } mpax_pre
 typedef enum mpax_termination {
   MPAX_TERM_UNSOLVED = 0,
   MPAX_TERM_OPTIMAL = 1,
-  MPAX_TERM_PRIMAL_INFEASIBLE = 2, /* reserved: infeasibility detection not built */
-  MPAX_TERM_DUAL_INFEASIBLE = 3,   /* reserved */
+  MPAX_TERM_PRIMAL_INFEASIBLE = 2, /* LP: a Farkas dual ray was found (see below) */
+  MPAX_TERM_DUAL_INFEASIBLE = 3,   /* LP: an unbounded primal ray was found */
   MPAX_TERM_ITERATION_LIMIT = 4,
   MPAX_TERM_TIME_LIMIT = 5,
   MPAX_TERM_NUMERICAL_ERROR = 6
@@ -78,8 +78,20 @@ typedef struct mpax_options {
   int32_t feasibility_polishing; /* must be 0: not built */
   double eps_abs;             /* 1e-4 */
   double eps_rel;             /* 1e-4 */
-  double eps_primal_infeasible; /* 1e-8, reserved */
-  double eps_dual_infeasible;   /* 1e-8, reserved */
+  double eps_primal_infeasible; /* 1e-8.  LP infeasibility detection (Sec. 3): at each
+                                   check the move since the restart cycle's anchor,
+                                   (dx, dy), is tested.  Primal infeasible: y = dy on
+                                   the recession cone of Y, lam = -A^T y, with
+                                   ||lam - proj_Lambda(lam)|| <= eps * o and o > 0,
+                                   o = sum lc y^+ - uc y^- + l lh^+ - u lh^- (finite
+                                   terms, lh = proj_Lambda(lam)).  <= 0: off.  QPs are
+                                   not tested. */
+  double eps_dual_infeasible;   /* 1e-8.  Dual infeasible (unbounded LP): dx with
+                                   ||(A dx, dx) - proj onto the recession cones of
+                                   ([lc,uc], [l,u])|| <= eps * (-c^T dx), c^T dx < 0.
+                                   <= 0: off.  In MIXED precision the FP32 rays cannot
+                                   meet 1e-8; the stalled run continues in FP64 (see
+                                   fp64_continuation), where the test is met. */
   double eps_feas_polish;       /* 1e-6, reserved */
   int64_t iteration_limit;      /* INT64_MAX */
   double time_limit;            /* seconds, +inf */
@@ -94,15 +106,22 @@ typedef struct mpax_options {
   double restart_artificial;  /* 0.36 */
   double primal_weight_smoothing; /* 0.5 */
   double step_safety;         /* 0.998: eta = step_safety / ||A~||_2 */
-  int32_t power_max_iter;     /* 100 */
-  double power_tol;           /* 1e-4 */
+  int32_t power_max_iter;     /* 1000 */
+  double power_tol;           /* 1e-4.  Power iteration for ||A~||_2 (and ||Q~||_2)
+                                 from a fixed pseudo-random start vector (entries
+                                 2u-1, u from SplitMix64 of the index); it stops
+                                 when the last rise d of the estimate and the
+                                 extrapolated remainder d q / (1 - q) (q: ratio of
+                                 successive rises) are both <= power_tol times the
+                                 estimate, which is then raised by the remainder */
   int32_t use_graphs;         /* 1: replay each check block as one CUDA graph */
   int32_t profile_kernels;    /* 0: 1 = time every fused SpMV launch with CUDA events
                                  (no graphs; for measurement only) */
   int32_t fp64_continuation;  /* 1: a MIXED solve whose relative KKT error stops
-                                 improving (no 10% gain over stall_checks checks)
-                                 continues in FP64 from its FP32 point */
-  int32_t stall_checks;       /* 8 */
+                                 improving (no 10% gain over max(stall_checks,
+                                 checks so far / 4) checks) continues in FP64 from
+                                 its FP32 point */
+  int32_t stall_checks;       /* 8: the shortest stall window, in checks */
 } mpax_options;
 
 typedef struct mpax_stats {
@@ -269,6 +288,10 @@ typedef struct mpax_batch_stats {
   double instance_seconds_max;
   double solve_seconds;           /* whole mpax_batch_solve, host wall clock */
   int64_t kernel_launches;
+  int32_t fp64_instances;         /* ragged batch, MIXED with fp64_continuation: instances
+                                     whose FP32 run stalled and were continued in FP64;
+                                     shared batch: instances still running when the
+                                     products switched from BF16x3 to FP32 */
 } mpax_batch_stats;
 
 mpax_status mpax_lp_batch_create(int32_t B, const int64_t* m_off, const int64_t* n_off,
@@ -279,7 +302,10 @@ mpax_status mpax_lp_batch_create(int32_t B, const int64_t* m_off, const int64_t*
 /* Options as mpax_solve (reflection_gamma must be 1).  The batch runs as one
  * persistent launch; time_limit is measured on the device clock from the start
  * of that launch and is capped at 600 s, so the launch always ends (instances
- * still running then finish with MPAX_TERM_TIME_LIMIT).  Each instance needs m_b + n_b <= 51,200 (FP32) or 25,600 (FP64) for its
+ * still running then finish with MPAX_TERM_TIME_LIMIT).  In MIXED precision with
+ * fp64_continuation, instances whose FP32 KKT error stops improving (the rule of
+ * mpax_options.fp64_continuation, per instance) are continued from their FP32
+ * point in a second, FP64 launch over those instances only.  Each instance needs m_b + n_b <= 51,200 (FP32) or 25,600 (FP64) for its
  * shared-memory vectors; larger instances return MPAX_ERR_UNSUPPORTED. */
 mpax_status mpax_batch_solve(mpax_batch* batch, const mpax_options* opts);
 /* Returned points (x^, y^) of every instance, packed like the inputs. */
@@ -309,7 +335,11 @@ mpax_status mpax_lp_shared_create(int32_t m, int32_t n, int32_t B, const float* 
                                   const double* l, const double* u, mpax_mem_kind kind,
                                   void* cuda_stream, mpax_shared** out);
 /* Options as mpax_solve (reflection_gamma must be 1); time_limit is checked on
- * the host clock at each KKT check. */
+ * the host clock at each KKT check.  With BF16x3 products and fp64_continuation,
+ * once an unfinished instance's KKT error stops improving (the rule of
+ * mpax_options.fp64_continuation, per instance) the rest of the solve forms its
+ * products in FP32; mpax_shared_get_stats then reports the instances still
+ * running at that point in fp64_instances. */
 mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* opts, int32_t fp32_products);
 /* X: B x n (row k = x of instance k), Y: B x m, unscaled; either may be NULL. */
 mpax_status mpax_shared_get_solution(const mpax_shared* sh, double* X, double* Y,

@@ -186,7 +186,8 @@ void destroy_problem(mpax_problem* pb) {
   free_schedule(P.schedFt);
   double* ds[] = {P.val, P.c,     P.lc,    P.uc,    P.l,   P.u,      P.D,      P.fval,
                   P.Dr,  P.Dc,    P.invDr, P.invDc, P.val_s, P.fval_s, P.D_s,  P.rowred,
-                  P.colred, P.red, P.red_out, P.qdiag, pb->dx, pb->dy, pb->dxa, pb->dya, pb->d6};
+                  P.colred, P.rowred2, P.colred2, P.red, P.red_out, P.qdiag, pb->dx, pb->dy,
+                  pb->dxa, pb->dya, pb->d6};
   for (double* d : ds)
     if (d) cudaFree(d);
   int* is[] = {P.permT, P.permF, P.tmp_rows, P.tmp_scan};
@@ -253,6 +254,8 @@ mpax_status create_common(int32_t m, int32_t n, int64_t nnz, const int64_t* row_
   if (!e) e = dmalloc(&P.val_s, nnz);
   if (!e) e = dmalloc(&P.rowred, m);
   if (!e) e = dmalloc(&P.colred, n);
+  if (!e) e = dmalloc(&P.rowred2, m);
+  if (!e) e = dmalloc(&P.colred2, n);
   if (!e) e = dmalloc(&P.tmp_rows, big);
   if (!e) e = dmalloc(&P.tmp_scan, scan_tmp_ints(big));
   if (!e) e = dmalloc(&P.red, kRedBlocks * 8);
@@ -457,7 +460,7 @@ void mpax_options_default(mpax_options* o) {
   o->restart_artificial = 0.36;
   o->primal_weight_smoothing = 0.5;
   o->step_safety = 0.998;
-  o->power_max_iter = 100;
+  o->power_max_iter = 1000;
   o->power_tol = 1e-4;
   o->use_graphs = 1;
   o->profile_kernels = 0;

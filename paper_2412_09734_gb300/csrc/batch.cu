@@ -28,6 +28,12 @@ namespace mpax {
 constexpr int kBatchThreads = 512;
 constexpr double kBatchMaxSeconds = 600.0;
 constexpr int kLPR = 8;  // lanes cooperating on one row
+// Rows each 8-lane group carries per step of a half-step (their memory round
+// trips overlap); 2 doubles the work in flight at the price of register spills.
+#ifndef MPAX_BATCH_ROWS
+#define MPAX_BATCH_ROWS 2
+#endif
+constexpr int kBR = MPAX_BATCH_ROWS;
 
 template <typename T>
 struct BatchArgs {
@@ -54,6 +60,10 @@ struct BatchArgs {
   long long iter_limit;
   long long time_limit_ns;  // from the start of the launch, on the device clock
   int check_every, power_max_iter;
+  const int* todo;  // instances of this launch (nullptr: all B, in order)
+  int n_todo;       // work items of this launch
+  int warm;         // 1: start from the returned points (xout, yout) instead of zero
+  int stall_limit;  // > 0: end an instance whose KKT error stops improving (FP32 floor)
 };
 
 __device__ __forceinline__ double bsum(double v, double* sh) {
@@ -97,10 +107,16 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
   const int grp = threadIdx.x / kLPR, gl = threadIdx.x % kLPR;
   const int G = blockDim.x / kLPR;
 
-  // ---- power iteration for ||A~_b||_2, from the all-ones vector -------------
-  for (int j = threadIdx.x; j < nb; j += blockDim.x) xs[j] = (T)(1.0 / sqrt((double)nb));
+  // ---- power iteration for ||A~_b||_2 from the common start vector ----------
+  double ss0 = 0.0;
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const double r = power_start_raw(j);
+    ss0 += r * r;
+  }
+  const double inv0 = 1.0 / sqrt(fmax(bsum(ss0, sh), 1e-300));
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) xs[j] = (T)(power_start_raw(j) * inv0);
   __syncthreads();
-  double nA = 0.0, nu_prev = 0.0;
+  double nA = 0.0, nu_prev = 0.0, d_prev = 0.0;
   const bool has_rows = mb > 0 && a.rp[m0 + mb] > a.rp[m0];
   for (int t = 1; has_rows && t <= a.power_max_iter; ++t) {
     for (int i0 = 0; i0 < mb; i0 += G) {
@@ -135,7 +151,11 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
     for (int j = threadIdx.x; j < nb; j += blockDim.x) xs[j] = (T)((double)a.gbuf[n0 + j] / nrm);
     __syncthreads();
     nA = nu;
-    if (t > 1 && fabs(nu - nu_prev) <= a.power_tol * nu) break;
+    double est = nu;
+    if (t > 1 && power_stop(nu, nu_prev, &d_prev, a.power_tol, &est)) {
+      nA = est;
+      break;
+    }
     nu_prev = nu;
   }
 
@@ -158,16 +178,19 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
   const double eta = nA > 0.0 ? a.step_safety / nA : 1.0;
   double tau = eta / omega, sigma = eta * omega;
 
-  // ---- start at zero: anchor, reflected point, duals ----------------------
+  // ---- start at zero, or (warm) at the returned point of an earlier launch,
+  // taken back into the scaled space: anchor, reflected point, duals ---------
   for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-    a.xa[n0 + j] = (T)0;
-    a.w[n0 + j] = (T)0;
-    a.xhat[n0 + j] = (T)0;
+    const T v = a.warm ? (T)(a.xout[n0 + j] / a.Dc[n0 + j]) : (T)0;
+    a.xa[n0 + j] = v;
+    a.w[n0 + j] = v;
+    a.xhat[n0 + j] = v;
   }
   for (int i = threadIdx.x; i < mb; i += blockDim.x) {
-    ys[i] = (T)0;
-    a.ya[m0 + i] = (T)0;
-    a.yhat[m0 + i] = (T)0;
+    const T v = a.warm ? (T)(a.yout[m0 + i] / a.Dr[m0 + i]) : (T)0;
+    ys[i] = v;
+    a.ya[m0 + i] = v;
+    a.yhat[m0 + i] = v;
   }
   __syncthreads();
 
@@ -175,6 +198,8 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
   double r_anchor = 0.0, r_prev = 0.0, rel = INFINITY, pobj = 0.0;
   bool have_anchor = false;
   int term = 0;
+  long long checks = 0, stall_count = 0;
+  double best_rel = INFINITY;
   while (true) {
     const int len = (int)min((long long)a.check_every, a.iter_limit - total);
     double P0 = 0, P1 = 0, D0 = 0, D1 = 0;
@@ -183,51 +208,109 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
       const bool chk = (it == len - 1);
       const T rb = (T)(1.0 / (double)(k + 1));  // rebuild weight of x^{n,k}
       const T hb = (T)(1.0 / (double)(k + 2));  // Halpern weight of the anchor
-      // primal half-step over the rows of A^T (eq. 3, first line)
-      for (int j0 = 0; j0 < nb; j0 += G) {
-      const int j = j0 + grp;
-      const bool in_j = j < nb;
-        T s = 0;
-        for (int p = in_j ? a.rpt[n0 + j] + gl : 0; in_j && p < a.rpt[n0 + j + 1]; p += kLPR)
-          s += a.valt[p] * ys[a.colt[p] - m0];
-        s = group_sum(s);
-        if (gl == 0 && in_j) {
-          const int g = n0 + j;
-          const T x0 = a.xa[g], wv = a.w[g];
-          const T x = (k == 0) ? x0 : wv + rb * (x0 - wv);
-          const T xh = clampv<T>(x - tt * (a.c[g] - s), a.l[g], a.u[g]);
-          const T wn = (T)2 * xh - x;
-          a.w[g] = wn;
-          xs[j] = wn;
-          if (chk) {
-            a.xhat[g] = xh;
-            const double d0 = (double)xh - (double)x, d1 = (double)xh - (double)x0;
-            P0 += d0 * d0;
-            P1 += d1 * d1;
+      // primal half-step over the rows of A^T (eq. 3, first line).  Each 8-lane
+      // group takes kBR rows per step (j, j + G, ...) and issues the row pointers,
+      // the epilogue operands and both rows' products before reducing, so every
+      // dependent round trip to memory is shared by kBR rows.
+      for (int j0 = 0; j0 < nb; j0 += kBR * G) {
+        int jr[kBR], pp[kBR], pe[kBR];
+        T sr[kBR], x0r[kBR], wr[kBR], cr[kBR], lr[kBR], ur[kBR];
+#pragma unroll
+        for (int r = 0; r < kBR; ++r) {
+          jr[r] = j0 + r * G + grp;
+          const bool in = jr[r] < nb;
+          pp[r] = in ? a.rpt[n0 + jr[r]] + gl : 0;
+          pe[r] = in ? a.rpt[n0 + jr[r] + 1] : 0;
+          sr[r] = 0;
+          if (gl == 0 && in) {
+            const int g = n0 + jr[r];
+            x0r[r] = a.xa[g];
+            wr[r] = a.w[g];
+            cr[r] = a.c[g];
+            lr[r] = a.l[g];
+            ur[r] = a.u[g];
+          }
+        }
+        for (bool more = true; more;) {
+          more = false;
+#pragma unroll
+          for (int r = 0; r < kBR; ++r)
+            if (pp[r] < pe[r]) {
+              sr[r] += a.valt[pp[r]] * ys[a.colt[pp[r]] - m0];
+              pp[r] += kLPR;
+              more |= pp[r] < pe[r];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kBR; ++r) sr[r] = group_sum(sr[r]);
+        if (gl == 0) {
+#pragma unroll
+          for (int r = 0; r < kBR; ++r) {
+            if (jr[r] >= nb) continue;
+            const int g = n0 + jr[r];
+            const T x0 = x0r[r], wv = wr[r];
+            const T x = (k == 0) ? x0 : wv + rb * (x0 - wv);
+            const T xh = clampv<T>(x - tt * (cr[r] - sr[r]), lr[r], ur[r]);
+            const T wn = (T)2 * xh - x;
+            a.w[g] = wn;
+            xs[jr[r]] = wn;
+            if (chk) {
+              a.xhat[g] = xh;
+              const double d0 = (double)xh - (double)x, d1 = (double)xh - (double)x0;
+              P0 += d0 * d0;
+              P1 += d1 * d1;
+            }
           }
         }
       }
       __syncthreads();
-      // dual half-step over the rows of A (eq. 3, second line) and Halpern (eq. 4)
-      for (int i0 = 0; i0 < mb; i0 += G) {
-      const int i = i0 + grp;
-      const bool in_i = i < mb;
-        T s = 0;
-        for (int p = in_i ? a.rp[m0 + i] + gl : 0; in_i && p < a.rp[m0 + i + 1]; p += kLPR)
-          s += a.val[p] * xs[a.col[p] - n0];
-        s = group_sum(s);
-        if (gl == 0 && in_i) {
-          const int g = m0 + i;
-          const T y0 = ys[i], y0a = a.ya[g];
-          const T v = y0 * iss - s;
-          const T yh = ss * (v - clampv<T>(v, -a.uc[g], -a.lc[g]));
-          const T z = (T)2 * yh - y0;
-          ys[i] = z + hb * (y0a - z);
-          if (chk) {
-            a.yhat[g] = yh;
-            const double d0 = (double)yh - (double)y0, d1 = (double)yh - (double)y0a;
-            D0 += d0 * d0;
-            D1 += d1 * d1;
+      // dual half-step over the rows of A (eq. 3, second line) and Halpern (eq. 4),
+      // kBR rows per group and step as above
+      for (int i0 = 0; i0 < mb; i0 += kBR * G) {
+        int ir[kBR], pp[kBR], pe[kBR];
+        T sr[kBR], yar[kBR], lcr[kBR], ucr[kBR];
+#pragma unroll
+        for (int r = 0; r < kBR; ++r) {
+          ir[r] = i0 + r * G + grp;
+          const bool in = ir[r] < mb;
+          pp[r] = in ? a.rp[m0 + ir[r]] + gl : 0;
+          pe[r] = in ? a.rp[m0 + ir[r] + 1] : 0;
+          sr[r] = 0;
+          if (gl == 0 && in) {
+            const int g = m0 + ir[r];
+            yar[r] = a.ya[g];
+            lcr[r] = a.lc[g];
+            ucr[r] = a.uc[g];
+          }
+        }
+        for (bool more = true; more;) {
+          more = false;
+#pragma unroll
+          for (int r = 0; r < kBR; ++r)
+            if (pp[r] < pe[r]) {
+              sr[r] += a.val[pp[r]] * xs[a.col[pp[r]] - n0];
+              pp[r] += kLPR;
+              more |= pp[r] < pe[r];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kBR; ++r) sr[r] = group_sum(sr[r]);
+        if (gl == 0) {
+#pragma unroll
+          for (int r = 0; r < kBR; ++r) {
+            if (ir[r] >= mb) continue;
+            const int g = m0 + ir[r];
+            const T y0 = ys[ir[r]], y0a = yar[r];
+            const T v = y0 * iss - sr[r];
+            const T yh = ss * (v - clampv<T>(v, -ucr[r], -lcr[r]));
+            const T z = (T)2 * yh - y0;
+            ys[ir[r]] = z + hb * (y0a - z);
+            if (chk) {
+              a.yhat[g] = yh;
+              const double d0 = (double)yh - (double)y0, d1 = (double)yh - (double)y0a;
+              D0 += d0 * d0;
+              D1 += d1 * d1;
+            }
           }
         }
       }
@@ -304,6 +387,22 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
     __syncthreads();
     if (!term && s_late) term = MPAX_TERM_TIME_LIMIT;
     __syncthreads();
+    // the FP32 floor: no 10% improvement of the KKT error over stall_limit
+    // checks.  Unlike the single-problem rule the window does not grow: a batch
+    // instance is small and latency-bound, FP64 costs it about twice per
+    // iteration, and an FP32 run that keeps finding slightly lower minima while
+    // it drifts would otherwise run on.  Every quantity here is uniform over the
+    // block.
+    ++checks;
+    if (!term && a.stall_limit > 0) {
+      const long long window = a.stall_limit;
+      if (rel < 0.9 * best_rel) {
+        best_rel = rel;
+        stall_count = 0;
+      } else if (++stall_count >= window) {
+        term = kTermStalled;
+      }
+    }
     if (term) break;
     // restart rule and primal weight (the same rule as the single-problem path)
     const double r = sqrt(omega * P0 + D0 / omega);
@@ -342,18 +441,19 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
   for (int i = threadIdx.x; i < mb; i += blockDim.x)
     a.yout[m0 + i] = a.Dr[m0 + i] * (double)a.yhat[m0 + i];
   if (threadIdx.x == 0) {
+    // a warm launch continues an instance: its counts and time add to the earlier ones
     a.status[b] = term;
-    a.iters[b] = total;
-    a.restarts[b] = restarts;
+    a.iters[b] = (a.warm ? a.iters[b] : 0) + total;
+    a.restarts[b] = (a.warm ? a.restarts[b] : 0) + restarts;
     a.relkkt[b] = rel;
     a.pobj[b] = pobj;
-    a.secs[b] = (double)(gtimer() - t_start) * 1e-9;
+    a.secs[b] = (a.warm ? a.secs[b] : 0.0) + (double)(gtimer() - t_start) * 1e-9;
   }
   __syncthreads();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBatchThreads) batch_lp_kernel(BatchArgs<T> a) {
+__global__ void __launch_bounds__(kBatchThreads, 2) batch_lp_kernel(BatchArgs<T> a) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ double sh[32];
   __shared__ int s_inst;
@@ -363,10 +463,10 @@ __global__ void __launch_bounds__(kBatchThreads) batch_lp_kernel(BatchArgs<T> a)
   while (true) {
     if (threadIdx.x == 0) s_inst = atomicAdd(a.next, 1);
     __syncthreads();
-    const int b = s_inst;
+    const int w = s_inst;
     __syncthreads();
-    if (b >= a.B) return;
-    solve_instance<T>(a, b, ys, xs, sh, t_launch);
+    if (w >= a.n_todo) return;
+    solve_instance<T>(a, a.todo ? a.todo[w] : w, ys, xs, sh, t_launch);
   }
 }
 
@@ -414,6 +514,8 @@ struct mpax_batch {
   bool solved = false;
   double solve_seconds = 0.0;
   long long launches = 0;
+  int* todo = nullptr;     // device list of instances continued in FP64
+  int fp64_instances = 0;  // instances of the last solve continued in FP64
 };
 
 namespace mpax {
@@ -432,7 +534,8 @@ mpax_status bfail(mpax_status s, const std::string& m) {
 }
 
 template <typename T>
-mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches) {
+mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches,
+                      const int* todo, int n_todo, int warm, int stall_limit) {
   ProblemData& P = *problem_data(bt->prob);
   cudaStream_t s = P.s;
   const int m = P.m, n = P.n, nnz = P.nnz;
@@ -528,7 +631,11 @@ mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_lp_kernel<T>, kBatchThreads, smem);
-  const int grid = std::min(bt->B, std::max(1, occ) * sms);
+  a.todo = todo;
+  a.n_todo = n_todo;
+  a.warm = warm;
+  a.stall_limit = stall_limit;
+  const int grid = std::min(n_todo, std::max(1, occ) * sms);
   cudaMemsetAsync(bt->next, 0, sizeof(int), s);
   batch_lp_kernel<T><<<grid, kBatchThreads, smem, s>>>(a);
   *launches += 1;
@@ -665,9 +772,32 @@ mpax_status mpax_batch_solve(mpax_batch* bt, const mpax_options* o) {
   if (!e) e = compute_scaling(P, o->ruiz_iters, o->pock_chambolle != 0);
   launches += 6 + 5 * o->ruiz_iters + 8;
   if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
-  mpax_status st = o->precision == MPAX_PREC_FP64 ? run_batch<double>(bt, o, &launches)
-                                                  : run_batch<float>(bt, o, &launches);
+  const bool cont = o->precision == MPAX_PREC_MIXED && o->fp64_continuation;
+  mpax_status st =
+      o->precision == MPAX_PREC_FP64
+          ? run_batch<double>(bt, o, &launches, nullptr, bt->B, 0, 0)
+          : run_batch<float>(bt, o, &launches, nullptr, bt->B, 0, cont ? o->stall_checks : 0);
   if (st) return st;
+  if (cont) {
+    // FP64 continuation of the instances that stalled in FP32, warm-started
+    // from their returned points, in one more persistent launch
+    std::vector<int> hs(bt->B), todo;
+    e = cudaMemcpyAsync(hs.data(), bt->status, sizeof(int) * bt->B, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+    for (int b = 0; b < bt->B; ++b)
+      if (hs[b] == kTermStalled) todo.push_back(b);
+    bt->fp64_instances = (int)todo.size();
+    if (!todo.empty()) {
+      if (!bt->todo && (e = cudaMalloc(&bt->todo, sizeof(int) * bt->B)))
+        return bfail(MPAX_ERR_OUT_OF_MEMORY, "batch continuation list");
+      e = cudaMemcpyAsync(bt->todo, todo.data(), sizeof(int) * todo.size(),
+                          cudaMemcpyHostToDevice, s);
+      if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+      st = run_batch<double>(bt, o, &launches, bt->todo, (int)todo.size(), 1, 0);
+      if (st) return st;
+    }
+  }
   e = cudaStreamSynchronize(s);
   if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
   problem_order_user_after(bt->prob);
@@ -727,6 +857,7 @@ mpax_status mpax_batch_get_stats(const mpax_batch* bt, mpax_batch_stats* stats, 
   stats->instance_seconds_max = sorted.back();
   stats->solve_seconds = bt->solve_seconds;
   stats->kernel_launches = bt->launches;
+  stats->fp64_instances = bt->fp64_instances;
   for (int b = 0; b < B; ++b) {
     if (status) status[b] = hs[b];
     if (iterations) iterations[b] = hi[b];
@@ -741,7 +872,7 @@ void mpax_batch_destroy(mpax_batch* bt) {
   if (!bt) return;
   if (bt->prob) mpax_destroy(bt->prob);
   void* bufs[] = {bt->m_off, bt->n_off, bt->next, bt->status, bt->iters, bt->restarts,
-                  bt->relkkt, bt->pobj, bt->secs, bt->xout, bt->yout, bt->work};
+                  bt->relkkt, bt->pobj, bt->secs, bt->xout, bt->yout, bt->work, bt->todo};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete bt;

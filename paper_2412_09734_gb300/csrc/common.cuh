@@ -64,7 +64,7 @@ constexpr int kShortCap = kSliceNnz + kLongRow;  // nonzeros of a packed item, u
 constexpr int kMaxCheckEvery = 1024;
 
 // Number of FP64 partial-sum quantities kept per work item.
-constexpr int kPartQ = 6;
+constexpr int kPartQ = 10;
 
 // Work item encoding (int4):
 //   packed short rows:   {r0, r1, base, end}        rows [r0, r1), nonzeros [base, end),
@@ -97,9 +97,11 @@ struct DevState {
   double primal_res, dual_res, pobj, dobj, gap, rel_kkt;
   double last_restart_metric;
   double pw_scale, pw_nu;  // power iteration: 1/||g|| of the last round, estimate
+  double pw_d;             // power iteration: last increment of the estimate
   long long total, k_base, restarts, checks, iter_limit;
   int pw_done, pw_iters, stall_limit, stall_count;
   double best_rel;
+  double eps_pi, eps_di;  // infeasibility tolerances (LP; <= 0 turns a test off)
   int done, restart_flag, termination, have_anchor;
   int check_every, is_qp, nan_seen, pad;
   // Halpern / averaging coefficient table for the current block:
@@ -107,6 +109,47 @@ struct DevState {
   double coef_a[kMaxCheckEvery + 2];
   double coef_b[kMaxCheckEvery + 2];
 };
+
+// ---- power iteration: start vector and stopping rule ---------------------------
+// Start vector: v_j = 2 u_j - 1, u_j the top 53 bits of SplitMix64(kPowerSeed + j)
+// (Steele, Lea and Flood, 2014) over 2^53, normalised.  Entries of both signs
+// and no structure give a component along every singular vector (the all-ones
+// vector can be nearly orthogonal to the top one, and the iteration then
+// settles on the second singular value first).
+constexpr unsigned long long kPowerSeed = 0x6D706178ull;
+
+__host__ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ double power_start_raw(long long j) {
+  const unsigned long long z = splitmix64(kPowerSeed + (unsigned long long)j);
+  return 2.0 * ((double)(z >> 11) * 1.1102230246251565e-16) - 1.0;  // (z >> 11) / 2^53
+}
+
+// Stopping rule: the estimates rise towards the norm with increments d that
+// shrink geometrically (ratio q = d / d_prev), so about d q / (1 - q) is still
+// to go.  Stop when d and that remainder are both <= tol * nu; the estimate is
+// then nu + remainder.  d_prev (0 before the second estimate) is updated.
+__host__ __device__ __forceinline__ bool power_stop(double nu, double nu_prev, double* d_prev,
+                                                    double tol, double* est) {
+  const double d = nu - nu_prev;
+  const double dp = *d_prev;
+  *d_prev = d;
+  *est = nu;
+  if (d <= 0.0) return true;
+  const double q = dp > 0.0 ? d / dp : 1.0;
+  if (q >= 1.0) return false;
+  const double rem = d * q / (1.0 - q);
+  if (d <= tol * nu && rem <= tol * nu) {
+    *est = nu + rem;
+    return true;
+  }
+  return false;
+}
 
 // Termination recorded when a mixed-precision run stops improving and the
 // solve continues in FP64 (internal; never reported to callers).

@@ -335,6 +335,93 @@ struct EpiKktCol {
   }
 };
 
+// ---- infeasibility rays (LP) ----------------------------------------------------
+// The candidate rays of a check are the moves since the cycle's anchor, in the
+// scaled space: rx~ = x^ - x_anchor, and ry~ = y^ - y_anchor projected onto the
+// recession cone of Y (k_ray_prep).  Unscaled: dx = Dc rx~, dy = Dr ry~.
+//
+// Rows of A, s = (A~ rx~)_i:  (A dx)_i = s / Dr_i.
+// partials: [0] ||A dx - proj_R(A dx)||^2 (R: recession cone of [lc_i, uc_i]),
+//           [1] sum lc_i dy_i^+ - uc_i dy_i^- (finite terms): the Farkas ray's row
+//               objective
+template <typename T>
+struct EpiRayRow {
+  static constexpr int NQ = 2;
+  struct Pre {
+    double idr, dr, lc, uc;
+    T ry;
+  };
+  const int* skipf;
+  const double* invDr;
+  const double* Dr;
+  const double* lc;
+  const double* uc;
+  const T* ry;
+  int check;
+  __device__ __forceinline__ bool skip() const { return skipf && *skipf != 0; }
+  __device__ __forceinline__ void load() {}
+  __device__ __forceinline__ void pre(int i, Pre& p) const {
+    p.idr = invDr[i];
+    p.dr = Dr[i];
+    p.lc = lc[i];
+    p.uc = uc[i];
+    p.ry = ry[i];
+  }
+  __device__ __forceinline__ void row(int i, T s, const Pre& p, double* acc) {
+    const double ax = (double)s * p.idr;
+    const bool lf = isfinite(p.lc), uf = isfinite(p.uc);
+    const double pr = (lf && uf) ? 0.0 : lf ? fmax(ax, 0.0) : uf ? fmin(ax, 0.0) : ax;
+    acc[0] += (ax - pr) * (ax - pr);
+    const double y = p.dr * (double)p.ry;
+    double term = 0.0;
+    if (y > 0.0 && lf) term = p.lc * y;
+    if (y < 0.0 && uf) term = p.uc * y;
+    acc[1] += term;
+  }
+};
+
+// Rows of A^T, t = (A~^T ry~)_j:  lam_j = -(A^T dy)_j = -t / Dc_j.
+// partials: [0] ||lam - proj_Lambda(lam)||^2, [1] sum l_j lh_j^+ - u_j lh_j^- (the
+//           Farkas ray's column objective, lh = proj_Lambda(lam)), [2] c^T dx,
+//           [3] ||dx - proj_X(dx)||^2 (X: recession cone of [l_j, u_j])
+template <typename T>
+struct EpiRayCol {
+  static constexpr int NQ = 4;
+  struct Pre {
+    double idc, dc, c, l, u;
+    T rx;
+  };
+  const int* skipf;
+  const double* invDc;
+  const double* Dc;
+  const double* c;
+  const double* l;
+  const double* u;
+  const T* rx;
+  int check;
+  __device__ __forceinline__ bool skip() const { return skipf && *skipf != 0; }
+  __device__ __forceinline__ void load() {}
+  __device__ __forceinline__ void pre(int j, Pre& p) const {
+    p.idc = invDc[j];
+    p.dc = Dc[j];
+    p.c = c[j];
+    p.l = l[j];
+    p.u = u[j];
+    p.rx = rx[j];
+  }
+  __device__ __forceinline__ void row(int j, T t, const Pre& p, double* acc) {
+    const double lam = -(double)t * p.idc;
+    const bool lf = isfinite(p.l), uf = isfinite(p.u);
+    const double lh = (lf && uf) ? lam : lf ? fmax(lam, 0.0) : uf ? fmin(lam, 0.0) : 0.0;
+    acc[0] += (lam - lh) * (lam - lh);
+    acc[1] += (lf ? p.l * fmax(lh, 0.0) : 0.0) + (uf ? p.u * fmin(lh, 0.0) : 0.0);
+    const double dx = p.dc * (double)p.rx;
+    acc[2] += p.c * dx;
+    const double px = (lf && uf) ? 0.0 : lf ? fmax(dx, 0.0) : uf ? fmin(dx, 0.0) : dx;
+    acc[3] += (dx - px) * (dx - px);
+  }
+};
+
 // ---- plain products (power iteration, Q~ v) ----------------------------------
 // out_r = s * s_scale + diag_r * din_r * d_scale; partial [0] sum out^2
 template <typename T>

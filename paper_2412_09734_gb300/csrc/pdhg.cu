@@ -115,6 +115,7 @@ __device__ void set_step_sizes(DevState* st) {
 
 struct InitParams {
   double eps_abs, eps_rel, r_suff, r_nec, r_art, pw_smooth, step_safety, gamma;
+  double eps_pi, eps_di;
   long long iter_limit;
   int check_every, is_qp, stall_limit;
 };
@@ -153,14 +154,36 @@ __global__ void k_init_state(DevState* st, InitParams p, const double* red) {
     st->best_rel = INFINITY;
     st->stall_count = 0;
     st->stall_limit = p.stall_limit;
+    st->eps_pi = p.eps_pi;
+    st->eps_di = p.eps_di;
   }
   __syncthreads();
   fill_table(st, p.check_every);
 }
 
+// Candidate rays of an LP check (scaled space): rx = x^ - x_anchor, and
+// ry = y^ - y_anchor projected onto the recession cone of Y (ry_i >= 0 where
+// uc_i = +inf, ry_i <= 0 where lc_i = -inf).
+template <typename T>
+__global__ void k_ray_prep(const T* __restrict__ xhat, const T* __restrict__ xa, int n,
+                           const T* __restrict__ yhat, const T* __restrict__ ya,
+                           const double* __restrict__ lc, const double* __restrict__ uc, int m,
+                           const int* skip, T* __restrict__ rx, T* __restrict__ ry) {
+  if (skip && *skip) return;
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) rx[j] = xhat[j] - xa[j];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    T d = yhat[i] - ya[i];
+    if (!isfinite(uc[i]) && d < (T)0) d = (T)0;
+    if (!isfinite(lc[i]) && d > (T)0) d = (T)0;
+    ry[i] = d;
+  }
+}
+
 __global__ void k_power_start(DevState* st) {
   st->pw_scale = 1.0;
   st->pw_nu = 0.0;
+  st->pw_d = 0.0;
   st->pw_done = 0;
   st->pw_iters = 0;
 }
@@ -168,6 +191,30 @@ __global__ void k_power_start(DevState* st) {
 // One power-iteration round done: sum of squares of g in part[0..n).
 // mode 0 (A~^T A~): nu = sqrt(||g||); mode 1 (Q~): nu = ||g||.  v_next = g/||g||
 // through pw_scale.  Writes the estimate to norm_A or norm_Q.
+// The normalised start vector of the power iterations (power_start_raw).
+template <typename T>
+__global__ void k_power_vec(T* __restrict__ v, int n, double inv_norm) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride)
+    v[j] = (T)(power_start_raw(j) * inv_norm);
+}
+
+// ||raw start vector||_2 for n entries (host, once per size).
+double power_start_norm(int n) {
+  thread_local int cached_n = -1;
+  thread_local double cached = 1.0;
+  if (n != cached_n) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double r = power_start_raw(j);
+      s += r * r;
+    }
+    cached = s > 0.0 ? std::sqrt(s) : 1.0;
+    cached_n = n;
+  }
+  return cached;
+}
+
 __global__ void k_power_finalize(const double* __restrict__ part, int n, DevState* st, int t,
                                  double tol, int mode) {
   __shared__ double sh[32];
@@ -185,7 +232,11 @@ __global__ void k_power_finalize(const double* __restrict__ part, int n, DevStat
       const double prev = st->pw_nu;
       st->pw_scale = 1.0 / nrm;
       st->pw_nu = nu;
-      if (t > 1 && fabs(nu - prev) <= tol * nu) st->pw_done = 1;
+      double est = nu;
+      if (t > 1 && power_stop(nu, prev, &st->pw_d, tol, &est)) {
+        st->pw_nu = est;
+        st->pw_done = 1;
+      }
     }
     st->pw_iters = t;
     if (mode == 0) st->norm_A = st->pw_nu;
@@ -202,6 +253,10 @@ __device__ double sum_slot(const double* part, int q, int n, double* sh) {
 // First level of the check reductions: block b sums the fixed chunk b of every
 // partial-sum slot (A^T slots 0..qt-1, then A slots 0..qa-1) into out[q][b].
 constexpr int kChunks = 128;
+// Check quantities reduced per check: 10 partial slots of the A^T schedule
+// (0-1 restart metric, 2-5 KKT columns, 6-9 ray columns) then 6 of the A
+// schedule (0-1 restart metric, 2-3 KKT rows, 4-5 ray rows).
+constexpr int kCheckQt = 10, kCheckQa = 6, kCheckQ = kCheckQt + kCheckQa;
 __global__ void k_part_reduce(const double* __restrict__ partAt, int nAt, int qt,
                               const double* __restrict__ partA, int nA, int qa,
                               const int* skip, double* __restrict__ out) {
@@ -226,10 +281,10 @@ __global__ void k_finalize_check(const double* __restrict__ partAt, int nAt,
                                  const double* __restrict__ partA, int nA, DevState* st,
                                  HostStatus* hs, int len, int next_len) {
   __shared__ double sh[32];
-  __shared__ double vals[10];
+  __shared__ double vals[kCheckQ];
   if (st->done) return;
   // partAt / partA hold the kChunks first-level sums of every slot (k_part_reduce)
-  for (int q = 0; q < 10; ++q) {
+  for (int q = 0; q < kCheckQ; ++q) {
     const double v = sum_slot(partAt, q, kChunks, sh);
     if (threadIdx.x == 0) vals[q] = v;
   }
@@ -239,7 +294,9 @@ __global__ void k_finalize_check(const double* __restrict__ partAt, int nAt,
   __syncthreads();
   if (threadIdx.x == 0) {
     const double P0 = vals[0], P1 = vals[1], C0 = vals[2], C1 = vals[3], C2 = vals[4],
-                 C3 = vals[5], D0 = vals[6], D1 = vals[7], K0 = vals[8], K1 = vals[9];
+                 C3 = vals[5], D0 = vals[10], D1 = vals[11], K0 = vals[12], K1 = vals[13];
+    const double RC0 = vals[6], RC1 = vals[7], RC2 = vals[8], RC3 = vals[9], RR0 = vals[14],
+                 RR1 = vals[15];
     st->total += len;
     st->checks += 1;
     const double nrp = sqrt(K0), nrd = sqrt(C0);
@@ -263,12 +320,27 @@ __global__ void k_finalize_check(const double* __restrict__ partAt, int nAt,
       term = MPAX_TERM_NUMERICAL_ERROR;
     else if (conv) term = MPAX_TERM_OPTIMAL;
     else if (st->total >= st->iter_limit) term = MPAX_TERM_ITERATION_LIMIT;
+    if (!term && !st->is_qp) {
+      // infeasibility certificates from the cycle's move (the oracle's reading):
+      // a Farkas ray with positive objective and reduced costs in their cone, or
+      // a recession ray of the primal with negative cost
+      const double obj = RR1 + RC1;
+      if (st->eps_pi > 0.0 && obj > 0.0 && sqrt(RC0) <= st->eps_pi * obj)
+        term = MPAX_TERM_PRIMAL_INFEASIBLE;
+      else if (st->eps_di > 0.0 && RC2 < 0.0 && sqrt(RR0 + RC3) <= st->eps_di * (-RC2))
+        term = MPAX_TERM_DUAL_INFEASIBLE;
+    }
     if (!term && st->stall_limit > 0) {
-      // the precision floor: no 10% improvement of the KKT error for stall_limit checks
+      // the precision floor: no 10% improvement of the KKT error over a window of
+      // max(stall_limit, checks / 4) checks.  The window grows with the solve, so a
+      // slow but steady decrease (a few per cent per check) is not taken for a
+      // floor, while a plateau costs at most a quarter more iterations.
+      const long long window =
+          st->stall_limit > st->checks / 4 ? (long long)st->stall_limit : st->checks / 4;
       if (rel < 0.9 * st->best_rel) {
         st->best_rel = rel;
         st->stall_count = 0;
-      } else if (++st->stall_count >= st->stall_limit) {
+      } else if (++st->stall_count >= window) {
         term = kTermStalled;
       }
     }
@@ -365,13 +437,14 @@ __global__ void k_kkt_finalize(const double* __restrict__ partAt, int nAt,
                                double* out) {
   __shared__ double sh[32];
   __shared__ double vals[6];
-  // partAt holds the chunk sums of the A^T slots 0..5 then the A slots 0..3
+  // partAt holds the chunk sums of the A^T slots 0..kCheckQt-1 then the A slots
+  // (KKT columns in A^T slots 2..5, KKT rows in A slots 2..3)
   for (int q = 0; q < 4; ++q) {
     const double v = sum_slot(partAt, 2 + q, nAt, sh);
     if (threadIdx.x == 0) vals[q] = v;
   }
   for (int q = 0; q < 2; ++q) {
-    const double v = sum_slot(partAt, 8 + q, nAt, sh);
+    const double v = sum_slot(partAt, kCheckQt + 2 + q, nAt, sh);
     if (threadIdx.x == 0) vals[4 + q] = v;
   }
   (void)partA;
@@ -460,6 +533,8 @@ class Engine final : public EngineBase {
     xa_ = dalloc<T>(n, e);
     xhat_ = dalloc<T>(n, e);
     xprev_ = dalloc<T>(n, e);
+    rayx_ = dalloc<T>(n, e);
+    rayy_ = dalloc<T>(m, e);
     pv_ = dalloc<T>(n, e);
     pg_ = dalloc<T>(n, e);
     y_ = dalloc<T>(m, e);
@@ -492,7 +567,7 @@ class Engine final : public EngineBase {
     void* bufs[] = {valA_, valAt_, c_,    l_,    u_,    lc_,   uc_,    xbar_, wbuf_,
                     xa_,   xhat_,  xprev_, pv_,  pg_,   y_,    ya_,    yhat_, yprev_,
                     pw_,   x_,     xavg_, xref_, xanc_, yavg_, yanc_,  Ds_,   fval_,
-                    ftval_, uvec_, uvec2_, st_};
+                    ftval_, uvec_, uvec2_, rayx_, rayy_, st_};
     for (void* b : bufs)
       if (b) cudaFree(b);
     if (hs_) cudaFreeHost(hs_);
@@ -523,7 +598,7 @@ class Engine final : public EngineBase {
     cudaStream_t s = P.s;
     const int n = P.n;
     k_power_start<<<1, 1, 0, s>>>(st_);
-    k_fill<T><<<grid1(n), 256, 0, s>>>(pv_, n, (T)(1.0 / std::sqrt((double)std::max(n, 1))));
+    k_power_vec<T><<<grid1(n), 256, 0, s>>>(pv_, n, 1.0 / power_start_norm(n));
     *launches += 2;
     T* v = pv_;
     T* g = pg_;
@@ -586,6 +661,8 @@ class Engine final : public EngineBase {
     ip.check_every = o.check_every;
     ip.is_qp = P.is_qp ? 1 : 0;
     ip.stall_limit = (o.precision == MPAX_PREC_MIXED && o.fp64_continuation) ? o.stall_checks : 0;
+    ip.eps_pi = o.eps_primal_infeasible;
+    ip.eps_di = o.eps_dual_infeasible;
     k_init_state<<<1, 256, 0, P.s>>>(st_, ip, P.red_out);
     *launches += 1;
     gamma_one_ = (o.reflection_gamma == 1.0);
@@ -650,8 +727,10 @@ class Engine final : public EngineBase {
     use_xsrc_ = false;
     if (plain) return;
     kkt_launch(&st_->done, prof);
-    k_part_reduce<<<kChunks, 256, 0, s>>>(P.schedAt.part, P.schedAt.n_items, 6, P.schedA.part,
-                                          P.schedA.n_items, 4, &st_->done, P.red);
+    if (!qp) ray_launch(&st_->done);
+    k_part_reduce<<<kChunks, 256, 0, s>>>(P.schedAt.part, P.schedAt.n_items, kCheckQt,
+                                          P.schedA.part, P.schedA.n_items, kCheckQa,
+                                          &st_->done, P.red);
     k_finalize_check<<<1, 512, 0, s>>>(P.red, kChunks, nullptr, 0, st_, hs_dev_, len, block_);
     launches_ += 1;
     if (!qp) {
@@ -665,6 +744,20 @@ class Engine final : public EngineBase {
   }
 
   // KKT SpMVs at (x^, y^) (LP) or (xavg, yavg) (QP), partial slots 2..
+  // Infeasibility rays of an LP check: the anchor moves (k_ray_prep), then A~ rx
+  // and A~^T ry with the ray epilogues into partial slots 4-5 (A) and 6-9 (A^T).
+  void ray_launch(const int* skip) {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    k_ray_prep<T><<<grid1(std::max(P.n, P.m)), 256, 0, s>>>(xhat_, xa_, P.n, yhat_, ya_, P.lc,
+                                                             P.uc, P.m, skip, rayx_, rayy_);
+    EpiRayRow<T> er{skip, P.invDr, P.Dr, P.lc, P.uc, rayy_, 1};
+    launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{rayx_}, er, 4, s);
+    EpiRayCol<T> ec{skip, P.invDc, P.Dc, P.c, P.l, P.u, rayx_, 1};
+    launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{rayy_}, ec, 6, s);
+    launches_ += 3;
+  }
+
   void kkt_launch(const int* skip, bool prof) {
     ProblemData& P = *P_;
     cudaStream_t s = P.s;
@@ -929,8 +1022,8 @@ class Engine final : public EngineBase {
     if (P.schedA.part) cudaMemsetAsync(P.schedA.part, 0, sizeof(double) * kPartQ * std::max(P.schedA.n_items, 1), s);
     if (P.schedAt.part) cudaMemsetAsync(P.schedAt.part, 0, sizeof(double) * kPartQ * std::max(P.schedAt.n_items, 1), s);
     kkt_launch(nullptr, false);
-    k_part_reduce<<<kChunks, 256, 0, s>>>(P.schedAt.part, P.schedAt.n_items, 6, P.schedA.part,
-                                          P.schedA.n_items, 4, nullptr, P.red);
+    k_part_reduce<<<kChunks, 256, 0, s>>>(P.schedAt.part, P.schedAt.n_items, kCheckQt,
+                                          P.schedA.part, P.schedA.n_items, 4, nullptr, P.red);
     k_kkt_finalize<<<1, 256, 0, s>>>(P.red, kChunks, nullptr, 0, st_, out6);
     return cudaGetLastError();
   }
@@ -946,6 +1039,7 @@ class Engine final : public EngineBase {
   T *valA_ = nullptr, *valAt_ = nullptr;
   T *c_ = nullptr, *l_ = nullptr, *u_ = nullptr, *lc_ = nullptr, *uc_ = nullptr;
   T *xbar_ = nullptr, *wbuf_ = nullptr, *xa_ = nullptr, *xhat_ = nullptr, *xprev_ = nullptr;
+  T *rayx_ = nullptr, *rayy_ = nullptr;  // infeasibility rays of an LP check
   T *pv_ = nullptr, *pg_ = nullptr, *pw_ = nullptr;
   T *y_ = nullptr, *ya_ = nullptr, *yhat_ = nullptr, *yprev_ = nullptr;
   T *x_ = nullptr, *xavg_ = nullptr, *xref_ = nullptr, *xanc_ = nullptr;

@@ -29,6 +29,43 @@ __global__ void row_absreduce(const int* __restrict__ rp, const double* __restri
   }
 }
 
+// One pass over the rows of A for a scaling round.  With the previous round's
+// factors (dr, dc non-null) the values are first rescaled in place,
+// v <- (v * dr_i) * dc_j; then |v| is reduced to its row norm (maximum, or sum
+// when SUM, in a fixed-order warp tree) and, for the maximum, to its column
+// maximum through an integer atomicMax on the bit patterns: non-negative
+// doubles order like their bit patterns, so the result is exact and does not
+// depend on the order of arrival.  colmax must start at +0.0 (all bits zero).
+template <bool SUM>
+__global__ void scale_pass(const int* __restrict__ rp, const int* __restrict__ col,
+                           double* __restrict__ val, int rows, const double* __restrict__ dr,
+                           const double* __restrict__ dc, double* __restrict__ rownorm,
+                           unsigned long long* __restrict__ colmax) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += nw) {
+    const double ri = dr ? dr[i] : 1.0;
+    double acc = 0.0;
+    for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+      double v = val[p];
+      const int j = col[p];
+      if (dr) {
+        v = (v * ri) * dc[j];
+        val[p] = v;
+      }
+      const double a = fabs(v);
+      acc = SUM ? acc + a : fmax(acc, a);
+      if (colmax) atomicMax(colmax + j, (unsigned long long)__double_as_longlong(a));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double t = __shfl_xor_sync(0xffffffffu, acc, o);
+      acc = SUM ? acc + t : fmax(acc, t);
+    }
+    if (lane == 0) rownorm[i] = acc;
+  }
+}
+
 // d_i = 1/sqrt(norm_i) (1 for an empty row/column); D_i *= d_i.  d overwrites norm.
 // With qdiag (QP columns) the current scaled diagonal D_i^2 qdiag_i joins the
 // norm first: max with it (Ruiz, SUM = false) or added to it (Pock-Chambolle).
@@ -89,9 +126,12 @@ __global__ void scale_diag(const double* __restrict__ D, const double* __restric
 }
 
 static int grid_for(int k) { return std::max(1, (k + 255) / 256); }
+// One warp per row (up to 2^21 warps, then grid-stride): every row's dependent
+// load chain (row pointer, values and columns, the gathered factor) is in flight
+// at once instead of walking rows one after another.
 static int warp_grid(int rows) {
-  const int warps = std::max(1, std::min(rows, 152 * 64));
-  return (warps * 32 + 255) / 256;
+  const int warps = std::max(1, std::min(rows, 1 << 21));
+  return (warps + 7) / 8;
 }
 
 cudaError_t compute_scaling(ProblemData& P, int ruiz_iters, bool pock_chambolle) {
@@ -106,28 +146,35 @@ cudaError_t compute_scaling(ProblemData& P, int ruiz_iters, bool pock_chambolle)
     q_diagonal<<<grid_for(n), 256, 0, s>>>(P.F.rp, P.fval, P.D, n, P.qdiag);
     qd = P.qdiag;
   }
+  // Round t's norms are taken in the pass that applies round t-1's factors, so a
+  // round costs one pass over A: (rowred, colred) hold the factors of the last
+  // finished round, (rowred2, colred2) receive the next round's norms.
+  double *fr = P.rowred, *fc = P.colred, *nr = P.rowred2, *nc = P.colred2;
+  bool pending = false;  // factors in (fr, fc) not yet applied to val_s
   for (int t = 0; (have || qd) && t < ruiz_iters; ++t) {
-    if (have) {
-      row_absreduce<false><<<warp_grid(m), 256, 0, s>>>(P.A.rp, P.val_s, nullptr, m, P.rowred);
-      row_absreduce<false><<<warp_grid(n), 256, 0, s>>>(P.At.rp, P.val_s, P.permT, n, P.colred);
-    } else {
-      cudaMemsetAsync(P.colred, 0, sizeof(double) * n, s);
-    }
-    if (have) factor_update<false><<<grid_for(m), 256, 0, s>>>(P.rowred, m, P.Dr, nullptr);
-    factor_update<false><<<grid_for(n), 256, 0, s>>>(P.colred, n, P.Dc, qd);
+    cudaMemsetAsync(nc, 0, sizeof(double) * n, s);
     if (have)
-      apply_scale<<<warp_grid(m), 256, 0, s>>>(P.A.rp, P.A.col, P.val_s, P.val_s, m, P.rowred,
-                                                P.colred);
+      scale_pass<false><<<warp_grid(m), 256, 0, s>>>(
+          P.A.rp, P.A.col, P.val_s, m, pending ? fr : nullptr, pending ? fc : nullptr, nr,
+          reinterpret_cast<unsigned long long*>(nc));
+    std::swap(fr, nr);
+    std::swap(fc, nc);
+    if (have) factor_update<false><<<grid_for(m), 256, 0, s>>>(fr, m, P.Dr, nullptr);
+    factor_update<false><<<grid_for(n), 256, 0, s>>>(fc, n, P.Dc, qd);
+    pending = have;
   }
   if ((have || qd) && pock_chambolle) {
     if (have) {
-      row_absreduce<true><<<warp_grid(m), 256, 0, s>>>(P.A.rp, P.val_s, nullptr, m, P.rowred);
-      row_absreduce<true><<<warp_grid(n), 256, 0, s>>>(P.At.rp, P.val_s, P.permT, n, P.colred);
-      factor_update<true><<<grid_for(m), 256, 0, s>>>(P.rowred, m, P.Dr, nullptr);
+      // apply the last Ruiz factors while summing rows; columns through A^T
+      scale_pass<true><<<warp_grid(m), 256, 0, s>>>(P.A.rp, P.A.col, P.val_s, m,
+                                                    pending ? fr : nullptr,
+                                                    pending ? fc : nullptr, nr, nullptr);
+      row_absreduce<true><<<warp_grid(n), 256, 0, s>>>(P.At.rp, P.val_s, P.permT, n, nc);
+      factor_update<true><<<grid_for(m), 256, 0, s>>>(nr, m, P.Dr, nullptr);
     } else {
-      cudaMemsetAsync(P.colred, 0, sizeof(double) * n, s);
+      cudaMemsetAsync(nc, 0, sizeof(double) * n, s);
     }
-    factor_update<true><<<grid_for(n), 256, 0, s>>>(P.colred, n, P.Dc, qd);
+    factor_update<true><<<grid_for(n), 256, 0, s>>>(nc, n, P.Dc, qd);
   }
   // the scaled matrix from the original values and the accumulated factors
   if (have)

@@ -40,6 +40,8 @@ struct ProblemData {
   double* qdiag = nullptr;    // diag(Q) = D + row sums of F^2 (QP)
   double* rowred = nullptr;   // m work
   double* colred = nullptr;   // n work
+  double* rowred2 = nullptr;  // m work (the next Ruiz round's norms)
+  double* colred2 = nullptr;  // n work
 
   // scratch
   int* tmp_rows = nullptr;    // max(m, n, r) + 2 ints

@@ -49,8 +49,8 @@ mpax_status sfail(mpax_status s, const std::string& m) {
 // ---- per-instance state --------------------------------------------------------
 struct Inst {
   double tau, sigma, omega, r_anchor, r_prev, rel, pobj, dobj, c_norm, best_rel;
-  long long k, total, restarts, done_at;
-  int done, status, restart, have_anchor;
+  long long k, total, restarts, done_at, checks, stall_count;
+  int done, status, restart, have_anchor, stalled;
 };
 
 // ---- dense scaling (row-major m x n): row/column infinity- and 1-norms ----------
@@ -275,7 +275,7 @@ __global__ void k_fixed_point_cols(const float* __restrict__ xhat, const float* 
 struct CheckParams {
   double eps_abs, eps_rel, r_suff, r_nec, r_art, pw_smooth, eta, b_norm;
   long long iter_limit, now_ns, time_limit_ns;
-  int B, check_no;
+  int B, check_no, stall_limit;
 };
 
 __global__ void k_check_finalize(Inst* inst, const double* part, CheckParams p) {
@@ -308,6 +308,19 @@ __global__ void k_check_finalize(Inst* inst, const double* part, CheckParams p) 
     I.status = term;
     I.done_at = p.now_ns;
     return;
+  }
+  // the BF16x3 floor (the single-problem rule): no 10% improvement of the KKT
+  // error over max(stall_limit, checks / 4) checks marks the instance stalled;
+  // the host then continues the batch with FP32 products
+  I.checks += 1;
+  if (p.stall_limit > 0 && !I.stalled) {
+    const long long window = p.stall_limit > I.checks / 4 ? (long long)p.stall_limit : I.checks / 4;
+    if (rel < 0.9 * I.best_rel) {
+      I.best_rel = rel;
+      I.stall_count = 0;
+    } else if (++I.stall_count >= window) {
+      I.stalled = 1;
+    }
   }
   const double r = sqrt(I.omega * P0 + D0 / I.omega);
   const bool restart = !I.have_anchor || r <= p.r_suff * I.r_anchor ||
@@ -488,6 +501,8 @@ struct mpax_shared {
   double solve_seconds = 0.0, norm_A = 0.0;
   long long launches = 0, gemms = 0;
   double gemm_flops = 0.0;
+  long long switch_iter = -1;  // last solve: iteration of the switch to FP32 products
+  int switch_active = 0;       // last solve: instances still running at the switch
   std::vector<Inst> h_inst;
 };
 
@@ -668,10 +683,14 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
   {
     float* v = sh->T;    // n (first column of T as scratch)
     float* wv = sh->S;   // m
-    std::vector<float> ones(n, (float)(1.0 / std::sqrt((double)n)));
-    cudaMemcpyAsync(v, ones.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    std::vector<float> v0(n);  // the common start vector (power_start_raw), normalised
+    double ss = 0.0;
+    for (int j = 0; j < n; ++j) ss += power_start_raw(j) * power_start_raw(j);
+    const double inv = 1.0 / std::sqrt(ss > 0.0 ? ss : 1.0);
+    for (int j = 0; j < n; ++j) v0[j] = (float)(power_start_raw(j) * inv);
+    cudaMemcpyAsync(v, v0.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s);
     const float one = 1.0f, zero = 0.0f;
-    double prev = 0.0, nu = 0.0;
+    double prev = 0.0, nu = 0.0, d_prev = 0.0;
     for (int t = 1; t <= o->power_max_iter; ++t) {
       cublasSgemv(sh->blas, CUBLAS_OP_T, n, m, &one, sh->As, n, v, 1, &zero, wv, 1);
       cublasSgemv(sh->blas, CUBLAS_OP_N, n, m, &one, sh->As, n, wv, 1, &zero, v, 1);
@@ -683,7 +702,11 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
       L += 4;
       if (nrm == 0.0) break;
       nu = std::sqrt(nrm);
-      if (t > 1 && std::fabs(nu - prev) <= o->power_tol * nu) break;
+      double est = nu;
+      if (t > 1 && power_stop(nu, prev, &d_prev, o->power_tol, &est)) {
+        nu = est;
+        break;
+      }
       prev = nu;
     }
     sh->norm_A = nu;
@@ -706,7 +729,9 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
   cudaMemsetAsync(sh->y_hi, 0, sizeof(__nv_bfloat16) * mB, s);
   cudaMemsetAsync(sh->y_lo, 0, sizeof(__nv_bfloat16) * mB, s);
   L += 4;
-  const bool bf = !fp32_products;
+  bool bf = !fp32_products;
+  long long switch_iter = -1;  // iteration at which BF16x3 gave way to FP32 products
+  int switch_active = 0;
   Vecs V{m, n, B, sh->ct, sh->lf, sh->uf, sh->lcf, sh->ucf, sh->w, sh->xa, sh->xhat, sh->T,
          sh->y, sh->ya, sh->yhat, sh->S, sh->xh_hi, sh->xh_lo, sh->y_hi, sh->y_lo, sh->part,
          sh->inst};
@@ -758,7 +783,7 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
                    o->iteration_limit,
                    (long long)std::chrono::duration_cast<std::chrono::nanoseconds>(
                        std::chrono::steady_clock::now() - t0).count(),
-                   tl_ns, B, check_no};
+                   tl_ns, B, check_no, (bf && o->fp64_continuation) ? o->stall_checks : 0};
     k_check_finalize<<<(B + 255) / 256, 256, 0, s>>>(sh->inst, sh->part, cp);
     // the BF16 splits of the iterates are rebuilt (restart copies x^, y^ into them)
     k_split<<<g1(nB), 256, 0, s>>>(sh->w, sh->xh_hi, sh->xh_lo, nB);
@@ -767,9 +792,19 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
     L += 8;
     cudaMemcpyAsync(hi.data(), sh->inst, sizeof(Inst) * B, cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
-    int active = 0;
-    for (const Inst& I : hi) active += !I.done;
+    int active = 0, stalled = 0;
+    for (const Inst& I : hi) {
+      active += !I.done;
+      stalled += !I.done && I.stalled;
+    }
     if (!active) break;
+    if (bf && stalled) {
+      // an instance reached the BF16x3 floor: the rest of the solve forms its
+      // products in FP32 (the iterates are FP32 throughout, so nothing converts)
+      bf = false;
+      switch_iter = done_iters;
+      switch_active = active;
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (!result && e) result = sfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
@@ -782,6 +817,8 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
   cudaEventDestroy(ev);
   sh->h_inst = hi;
   sh->launches = L;
+  sh->switch_iter = switch_iter;
+  sh->switch_active = switch_active;
   sh->solved = !result;
   sh->solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return result;
@@ -832,6 +869,7 @@ mpax_status mpax_shared_get_stats(const mpax_shared* sh, mpax_batch_stats* stats
   stats->instance_seconds_max = so.back();
   stats->solve_seconds = sh->solve_seconds;
   stats->kernel_launches = sh->launches;
+  stats->fp64_instances = sh->switch_active;
   if (gemm_info) {
     gemm_info[0] = (double)sh->gemms;
     gemm_info[1] = sh->gemm_flops;

@@ -91,7 +91,7 @@ class BatchStats(ctypes.Structure):
         ("restarts_total", ctypes.c_int64), ("rel_kkt_max", ctypes.c_double),
         ("instance_seconds_p50", ctypes.c_double), ("instance_seconds_p99", ctypes.c_double),
         ("instance_seconds_max", ctypes.c_double), ("solve_seconds", ctypes.c_double),
-        ("kernel_launches", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64), ("fp64_instances", ctypes.c_int32),
     ]
 
     def as_dict(self):

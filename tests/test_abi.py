@@ -54,7 +54,8 @@ def test_struct_layout_matches_header(C, tmp_path):
     """Field offsets of the ctypes mirrors equal the C compiler's for mpax.h."""
     import subprocess
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mpax.h"', 'int main(void){']
-    for cname, cls in (("mpax_options", C.Options), ("mpax_stats", C.Stats)):
+    for cname, cls in (("mpax_options", C.Options), ("mpax_stats", C.Stats),
+                       ("mpax_batch_stats", C.BatchStats)):
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for f, _ in cls._fields_:
             lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
@@ -69,7 +70,8 @@ def test_struct_layout_matches_header(C, tmp_path):
     for line in out.splitlines():
         a, b, v = line.split()
         got[(a, b)] = int(v)
-    for cname, cls in (("mpax_options", C.Options), ("mpax_stats", C.Stats)):
+    for cname, cls in (("mpax_options", C.Options), ("mpax_stats", C.Stats),
+                       ("mpax_batch_stats", C.BatchStats)):
         assert got[(cname, "size")] == ctypes.sizeof(cls)
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)

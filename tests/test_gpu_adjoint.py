@@ -22,7 +22,7 @@ def C():
 
 
 def _lp_case():
-    return lp_instance(20, 40, seed=instance_seed(401), density=0.3, variant="nondegenerate",
+    return lp_instance(20, 40, seed=instance_seed(404), density=0.3, variant="nondegenerate",
                        tight_frac=0.6)
 
 

@@ -109,3 +109,30 @@ def test_batch_rejects_bad_columns(C):
     with pytest.raises(C.MpaxError) as ei:
         _create(C, bad)
     assert ei.value.status == 1
+
+
+def test_batch_mixed_continues_stalled_instances_in_fp64(C):
+    """64 instances of the bench recipe (m ~ U{50..2000}, 1% density).  With a
+    one-check stall window many FP32 runs count as stalled and are continued in
+    FP64 from their FP32 points; every instance must still meet 1e-4 in the
+    oracle's evaluation.  Without continuation no instance is handed over."""
+    d = ragged_lp_batch(64)
+    out = {}
+    for cont in (1, 0):
+        h = _create(C, d, device=True)
+        try:
+            C.mpax_batch_solve(h, C.mpax_options_default(precision=1, fp64_continuation=cont,
+                                                         stall_checks=1, iteration_limit=20000))
+            summary, per = C.mpax_batch_get_stats(h, d["B"])
+            x, y = C.mpax_batch_get_solution(h, int(d["m_off"][-1]), int(d["n_off"][-1]))
+        finally:
+            C.mpax_batch_destroy(h)
+        out[cont] = (summary, per, x, y)
+    summary, per, x, y = out[1]
+    assert summary["n_optimal"] == d["B"]
+    assert summary["fp64_instances"] >= 1
+    for b, inst in enumerate(d["instances"]):
+        p = O.problem_from_arrays(inst)
+        chk = O.kkt(p, x[d["n_off"][b]:d["n_off"][b + 1]], y[d["m_off"][b]:d["m_off"][b + 1]])
+        assert chk["converged"], (b, chk["rel_kkt"])
+    assert out[0][0]["fp64_instances"] == 0
