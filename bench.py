@@ -316,6 +316,26 @@ def run_ours(args):
                  "iterations_per_solve": it64 / args.fp64_steps,
                  "rel_kkt": max(kkt64), "steps": args.fp64_steps}
 
+    # FP64 continuation: a tolerance below the FP32 floor, mixed + continuation
+    # against the plain FP64 path (one solve each, after one untimed solve)
+    cont = {}
+    for name, prec in (("mixed_continuation", C.MPAX_PREC_MIXED), ("fp64", C.MPAX_PREC_FP64)):
+        o7 = C.mpax_options_default(precision=prec, eps_abs=1e-7, eps_rel=1e-7,
+                                    iteration_limit=400000)
+        C.mpax_solve(h, o7)
+        barrier()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record()
+        C.mpax_solve(h, o7)
+        c1.record()
+        barrier()
+        s7 = C.mpax_get_stats(h)
+        cont[name] = {"time_s": allmax(c0.elapsed_time(c1)) / 1e3, "iterations": s7["iterations"],
+                      "fp64_iterations": s7["fp64_iterations"], "rel_kkt": s7["rel_kkt"],
+                      "termination": s7["termination_name"]}
+    cont["speedup"] = cont["fp64"]["time_s"] / cont["mixed_continuation"]["time_s"]
+
     # end to end through the C ABI with host buffers: H2D of the problem, solve,
     # D2H of the solution inside the timed region
     h2d = sum(int(np.asarray(d[k]).nbytes) for k in keys)
@@ -380,6 +400,7 @@ def run_ours(args):
             "iterations_per_solve": iters / args.steps, "rel_kkt": max(kkt),
             "fp64_path": fp64_path,
             "speedup_vs_fp64_time_to_tol": (ms64 / args.fp64_steps) / (ms_max / args.steps),
+            "time_to_1e-7": cont,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches}
     if rank == 0:

@@ -24,7 +24,9 @@ implements the same written rules.  The readings are:
     [lc~, uc~] = D_r [lc, uc]; x = D_c x~, y = D_r y~.
   * Step sizes: eta = 0.998 / ||A~||_2 with ||A~||_2 from power iteration on
     A~^T A~ started at a fixed pseudo-random vector of entries in [-1, 1]
-    (SplitMix64 of the index, see power_start).  The estimates rise towards the norm
+    (SplitMix64 of the index, see power_start).  After the Pock-Chambolle round
+    ||A~||_2 <= 1 (Schur's test), and the iteration stops, using 1, once its
+    extrapolated estimate is within 1e-3 of that bound.  The estimates rise towards the norm
     with geometrically shrinking increments d_t (ratio q); the iteration stops
     when d_t and the extrapolated remainder d_t q / (1 - q) are both at most
     1e-4 of the estimate (or after 1000 rounds) and returns the estimate plus
@@ -264,28 +266,36 @@ def power_start(n: int) -> np.ndarray:
     return v / np.linalg.norm(v)
 
 
-def _power_stop(nu, nu_prev, d_prev, tol):
+def _power_stop(nu, nu_prev, d_prev, tol, cap=math.inf):
     """Stopping rule of the power iterations: the estimates nu_t rise towards the
     norm with increments d_t = nu_t - nu_{t-1} that shrink geometrically (ratio
     q = d_t / d_{t-1}) once the top singular vector dominates, so the distance
     still to go is about d_t q / (1 - q).  Stop when both the last increment and
-    that remainder are at most tol * nu_t; the estimate returned is
-    nu_t + remainder.  Returns (stop, estimate, d_t)."""
+    that remainder are at most tol * nu_t; the estimate is nu_t + remainder.
+    With a certified upper bound `cap` on the norm, stop as soon as the
+    extrapolated estimate is within 10 tol of the cap, and use the cap, once the
+    increments are small (d_t <= 100 tol nu_t: before that the ratio q is not yet
+    settled and the extrapolation overshoots); an estimate never exceeds the
+    cap.  Returns (stop, estimate, d_t)."""
     d = nu - nu_prev
     if d <= 0.0:                      # no rise left (rounding): converged
-        return True, nu, d
+        return True, min(nu, cap), d
     q = d / d_prev if d_prev > 0.0 else 1.0
     if q >= 1.0:                      # not yet in the geometric regime
         return False, nu, d
     rem = d * q / (1.0 - q)
+    if d <= 100.0 * tol * nu and nu + rem >= (1.0 - 10.0 * tol) * cap:
+        return True, cap, d
     if d <= tol * nu and rem <= tol * nu:
-        return True, nu + rem, d
+        return True, min(nu + rem, cap), d
     return False, nu, d
 
 
-def power_norm_A(A: sp.csr_matrix, max_iter: int = 1000, tol: float = 1e-4):
+def power_norm_A(A: sp.csr_matrix, max_iter: int = 1000, tol: float = 1e-4,
+                 cap: float = math.inf):
     """Estimate ||A||_2 = sqrt(lambda_max(A^T A)); start at power_start(n);
-    nu_t = sqrt(||A^T A v_t||) with ||v_t|| = 1; stop by _power_stop."""
+    nu_t = sqrt(||A^T A v_t||) with ||v_t|| = 1; stop by _power_stop with the
+    certified bound `cap` (min(cap, last estimate) after max_iter rounds)."""
     n = A.shape[1]
     if n == 0 or A.nnz == 0:
         return 0.0, 0
@@ -300,11 +310,11 @@ def power_norm_A(A: sp.csr_matrix, max_iter: int = 1000, tol: float = 1e-4):
         nu = math.sqrt(nrm)
         v = g / nrm
         if nu_prev is not None:
-            stop, est, d_prev = _power_stop(nu, nu_prev, d_prev, tol)
+            stop, est, d_prev = _power_stop(nu, nu_prev, d_prev, tol, cap)
             if stop:
                 return est, t
         nu_prev = nu
-    return nu, max_iter
+    return (cap if math.isfinite(cap) else nu), max_iter
 
 
 def power_norm_Q(Q, n: int, max_iter: int = 1000, tol: float = 1e-4):
@@ -507,7 +517,12 @@ def prepare(p: Problem, opts: Options):
     qd = None if p.Q is None else p.Q.diagonal()
     Dr, Dc = scaling_factors(p.A, opts.ruiz_iters, opts.pock_chambolle, qd)
     ps = scale_problem(p, Dr, Dc)
-    nA, _ = power_norm_A(ps.A, opts.power_max_iter, opts.power_tol)
+    # after the Pock-Chambolle round (alpha = 1) A~_ij = K_ij / sqrt(r_i c_j) with
+    # r, c the row and column 1-norms of the Ruiz-scaled K (c_j also holding Q's
+    # scaled diagonal), and Schur's test with weights sqrt(r_i), sqrt(c_j) gives
+    # ||A~||_2 <= 1
+    cap = 1.0 if opts.pock_chambolle else math.inf
+    nA, _ = power_norm_A(ps.A, opts.power_max_iter, opts.power_tol, cap)
     nQ, _ = power_norm_Q(ps.Q, ps.n, opts.power_max_iter, opts.power_tol)
     eta = opts.step_safety / nA if nA > 0 else 1.0
     omega = initial_primal_weight(ps.c, bound_vector(ps.lc, ps.uc))

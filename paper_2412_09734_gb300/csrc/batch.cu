@@ -63,6 +63,7 @@ struct BatchArgs {
   const int* todo;  // instances of this launch (nullptr: all B, in order)
   int n_todo;       // work items of this launch
   int warm;         // 1: start from the returned points (xout, yout) instead of zero
+  double power_cap; // certified bound on ||A~_b||_2 (1 after Pock-Chambolle, else inf)
   int stall_limit;  // > 0: end an instance whose KKT error stops improving (FP32 floor)
 };
 
@@ -152,10 +153,11 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
     __syncthreads();
     nA = nu;
     double est = nu;
-    if (t > 1 && power_stop(nu, nu_prev, &d_prev, a.power_tol, &est)) {
+    if (t > 1 && power_stop(nu, nu_prev, &d_prev, a.power_tol, a.power_cap, &est)) {
       nA = est;
       break;
     }
+    if (t == a.power_max_iter && isfinite(a.power_cap)) nA = a.power_cap;
     nu_prev = nu;
   }
 
@@ -621,6 +623,7 @@ mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches
   a.time_limit_ns = (long long)(std::min(o->time_limit, kBatchMaxSeconds) * 1e9);
   a.check_every = o->check_every;
   a.power_max_iter = o->power_max_iter;
+  a.power_cap = o->pock_chambolle ? 1.0 : INFINITY;
   const size_t smem = sizeof(T) * ((size_t)a.smem_m + (size_t)bt->max_n);
   if (smem > 200 * 1024)
     return bfail(MPAX_ERR_UNSUPPORTED,

@@ -133,19 +133,30 @@ __host__ __device__ __forceinline__ double power_start_raw(long long j) {
 // Stopping rule: the estimates rise towards the norm with increments d that
 // shrink geometrically (ratio q = d / d_prev), so about d q / (1 - q) is still
 // to go.  Stop when d and that remainder are both <= tol * nu; the estimate is
-// then nu + remainder.  d_prev (0 before the second estimate) is updated.
+// then nu + remainder.  With a certified upper bound `cap` on the norm (1 after
+// the Pock-Chambolle round, by Schur's test), stop as soon as the increments are
+// small (d <= 100 tol nu) and the extrapolated estimate is within 10 tol of the
+// cap, and use the cap; an estimate never exceeds the cap.  d_prev (0 before
+// the second estimate) is updated.
 __host__ __device__ __forceinline__ bool power_stop(double nu, double nu_prev, double* d_prev,
-                                                    double tol, double* est) {
+                                                    double tol, double cap, double* est) {
   const double d = nu - nu_prev;
   const double dp = *d_prev;
   *d_prev = d;
   *est = nu;
-  if (d <= 0.0) return true;
+  if (d <= 0.0) {
+    *est = nu < cap ? nu : cap;
+    return true;
+  }
   const double q = dp > 0.0 ? d / dp : 1.0;
   if (q >= 1.0) return false;
   const double rem = d * q / (1.0 - q);
+  if (d <= 100.0 * tol * nu && nu + rem >= (1.0 - 10.0 * tol) * cap) {
+    *est = cap;
+    return true;
+  }
   if (d <= tol * nu && rem <= tol * nu) {
-    *est = nu + rem;
+    *est = nu + rem < cap ? nu + rem : cap;
     return true;
   }
   return false;

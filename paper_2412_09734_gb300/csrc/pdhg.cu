@@ -216,7 +216,7 @@ double power_start_norm(int n) {
 }
 
 __global__ void k_power_finalize(const double* __restrict__ part, int n, DevState* st, int t,
-                                 double tol, int mode) {
+                                 double tol, int mode, double cap, int max_iter) {
   __shared__ double sh[32];
   if (st->pw_done) return;
   double v = 0;
@@ -233,9 +233,11 @@ __global__ void k_power_finalize(const double* __restrict__ part, int n, DevStat
       st->pw_scale = 1.0 / nrm;
       st->pw_nu = nu;
       double est = nu;
-      if (t > 1 && power_stop(nu, prev, &st->pw_d, tol, &est)) {
+      if (t > 1 && power_stop(nu, prev, &st->pw_d, tol, cap, &est)) {
         st->pw_nu = est;
         st->pw_done = 1;
+      } else if (t >= max_iter && isfinite(cap)) {
+        st->pw_nu = cap;  // out of rounds: the certified bound
       }
     }
     st->pw_iters = t;
@@ -612,7 +614,8 @@ class Engine final : public EngineBase {
         launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{pw_}, e2, 0, s);
         k_part_reduce<<<kChunks, 256, 0, s>>>(P.schedAt.part, P.schedAt.n_items, 1, nullptr, 0,
                                               0, skip, P.red);
-        k_power_finalize<<<1, 256, 0, s>>>(P.red, kChunks, st_, t, o.power_tol, 0);
+        k_power_finalize<<<1, 256, 0, s>>>(P.red, kChunks, st_, t, o.power_tol, 0,
+                                           o.pock_chambolle ? 1.0 : INFINITY, o.power_max_iter);
       } else {
         e1.out = uvec_;
         launch_spmv<T>(P.schedFt, P.Ft, ftval_, InPlain<T>{v}, e1, 0, s);
@@ -622,7 +625,8 @@ class Engine final : public EngineBase {
         launch_spmv<T>(P.schedF, P.F, fval_, InPlain<T>{uvec_}, e2, 0, s);
         k_part_reduce<<<kChunks, 256, 0, s>>>(P.schedF.part, P.schedF.n_items, 1, nullptr, 0,
                                               0, skip, P.red);
-        k_power_finalize<<<1, 256, 0, s>>>(P.red, kChunks, st_, t, o.power_tol, 1);
+        k_power_finalize<<<1, 256, 0, s>>>(P.red, kChunks, st_, t, o.power_tol, 1, INFINITY,
+                                           o.power_max_iter);
       }
       *launches += 4;
       std::swap(v, g);

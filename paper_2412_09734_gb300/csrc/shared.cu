@@ -703,10 +703,12 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
       if (nrm == 0.0) break;
       nu = std::sqrt(nrm);
       double est = nu;
-      if (t > 1 && power_stop(nu, prev, &d_prev, o->power_tol, &est)) {
+      const double cap = o->pock_chambolle ? 1.0 : INFINITY;
+      if (t > 1 && power_stop(nu, prev, &d_prev, o->power_tol, cap, &est)) {
         nu = est;
         break;
       }
+      if (t == o->power_max_iter && std::isfinite(cap)) nu = cap;
       prev = nu;
     }
     sh->norm_A = nu;
