@@ -77,6 +77,7 @@ implements the same written rules.  The readings are:
       [l, u] (0 where both bounds are finite, R+ / R- where only the lower /
       upper one is, R where neither).
     The certificate is returned as Result.certificate.
+  * Feasibility polishing (Sec. 3.3; off by default): see polish_lp.
 """
 from __future__ import annotations
 
@@ -503,12 +504,14 @@ def dual_ray_test(p: Problem, dx):
 
 def infeasibility(p: Problem, dx, dy, opts: Options):
     """'primal_infeasible' / 'dual_infeasible' with its certificate, or (None, None)."""
-    vp, op, yray = primal_ray_test(p, dy)
-    if op > 0.0 and vp <= opts.eps_primal_infeasible * op:
-        return "primal_infeasible", yray
-    vd, cd = dual_ray_test(p, dx)
-    if cd < 0.0 and vd <= opts.eps_dual_infeasible * (-cd):
-        return "dual_infeasible", dx
+    if opts.eps_primal_infeasible > 0.0:
+        vp, op, yray = primal_ray_test(p, dy)
+        if op > 0.0 and vp <= opts.eps_primal_infeasible * op:
+            return "primal_infeasible", yray
+    if opts.eps_dual_infeasible > 0.0:
+        vd, cd = dual_ray_test(p, dx)
+        if cd < 0.0 and vd <= opts.eps_dual_infeasible * (-cd):
+            return "dual_infeasible", dx
     return None, None
 
 
@@ -554,8 +557,10 @@ def _update_weight(omega, dx, dy, opts: Options):
 
 
 def solve_lp(p: Problem, opts: Options = Options(), x_init=None, y_init=None,
-             keep_history=False) -> Result:
-    """r^2HPDHG (Algorithm 1) on the scaled LP."""
+             keep_history=False, feasibility=None) -> Result:
+    """r^2HPDHG (Algorithm 1) on the scaled LP.  feasibility = "primal" / "dual"
+    ends the run on that residual alone (||r_p|| <= eps_abs + eps_rel ||b||, or
+    ||r_d|| <= eps_abs + eps_rel ||c||): the polishing runs."""
     ps, Dr, Dc, nA, nQ, eta, omega = prepare(p, opts)
     x = np.zeros(p.n) if x_init is None else np.asarray(x_init, dtype=np.float64) / Dc
     y = np.zeros(p.m) if y_init is None else np.asarray(y_init, dtype=np.float64) / Dr
@@ -574,8 +579,13 @@ def solve_lp(p: Problem, opts: Options = Options(), x_init=None, y_init=None,
             info = kkt(p, Dc * x_hat, Dr * y_hat, opts.eps_abs, opts.eps_rel)
             if keep_history:
                 hist.append((total, info["rel_kkt"]))
-            if info["converged"] or total >= opts.iteration_limit:
-                status = "optimal" if info["converged"] else "iteration_limit"
+            done = info["converged"]
+            if feasibility == "primal":
+                done = info["primal_res"] <= opts.eps_abs + opts.eps_rel * info["b_norm"]
+            elif feasibility == "dual":
+                done = info["dual_res"] <= opts.eps_abs + opts.eps_rel * info["c_norm"]
+            if done or total >= opts.iteration_limit:
+                status = "optimal" if done else "iteration_limit"
                 return Result(Dc * x_hat, Dr * y_hat, status, total, restarts, info, omega,
                               eta, nA, nQ, Dr, Dc, hist)
             status, cert = infeasibility(p, Dc * (x_hat - xa), Dr * (y_hat - ya), opts)
@@ -600,6 +610,25 @@ def solve_lp(p: Problem, opts: Options = Options(), x_init=None, y_init=None,
         g = opts.reflection_gamma
         x, y = halpern(x_hat, x, xa, k, g), halpern(y_hat, y, ya, k, g)
         k += 1
+
+
+def polish_lp(p: Problem, x, y, opts: Options = Options(), eps_feas_polish: float = 1e-6):
+    """Feasibility polishing (Sec. 3.3: the feasibility-only problem, objective
+    set to zero, solved by the same method from the current point).  Reading:
+    primal phase -- min 0 s.t. the same constraints, from (x, 0), until
+    ||r_p|| <= eps (1 + ||b||); dual phase -- the LP with every finite bound set
+    to zero (the cones of Y and Lambda unchanged), from (0, y), until
+    ||r_d|| <= eps (1 + ||c||).  Infeasibility tests are off in both.  Returns
+    (x_polished, y_polished, primal Result, dual Result)."""
+    import dataclasses
+    o = dataclasses.replace(opts, eps_abs=eps_feas_polish, eps_rel=eps_feas_polish,
+                            eps_primal_infeasible=0.0, eps_dual_infeasible=0.0)
+    pp = Problem(p.A, np.zeros(p.n), p.lc, p.uc, p.l, p.u)
+    rp = solve_lp(pp, o, x_init=x, y_init=np.zeros(p.m), feasibility="primal")
+    z = lambda v: np.where(np.isfinite(v), 0.0, v)  # noqa: E731
+    pd = Problem(p.A, p.c, z(p.lc), z(p.uc), z(p.l), z(p.u))
+    rd = solve_lp(pd, o, x_init=np.zeros(p.n), y_init=y, feasibility="dual")
+    return rp.x, rd.y, rp, rd
 
 
 def solve_qp(p: Problem, opts: Options = Options(), x_init=None, y_init=None,
