@@ -75,7 +75,8 @@ typedef struct mpax_options {
   int32_t verbose;            /* 0: print a line every display_frequency checks */
   int32_t display_frequency;  /* 10 */
   int32_t warm_start;         /* informational: x0/y0 of mpax_solve are used when non-NULL */
-  int32_t feasibility_polishing; /* must be 0: not built */
+  int32_t feasibility_polishing; /* 0; 1: polish an OPTIMAL LP solve (eps_feas_polish);
+                                    ignored for QPs */
   double eps_abs;             /* 1e-4 */
   double eps_rel;             /* 1e-4 */
   double eps_primal_infeasible; /* 1e-8.  LP infeasibility detection (Sec. 3): at each
@@ -92,7 +93,14 @@ typedef struct mpax_options {
                                    <= 0: off.  In MIXED precision the FP32 rays cannot
                                    meet 1e-8; the stalled run continues in FP64 (see
                                    fp64_continuation), where the test is met. */
-  double eps_feas_polish;       /* 1e-6, reserved */
+  double eps_feas_polish;       /* 1e-6.  With feasibility_polishing = 1, an LP solve
+                                   that ends OPTIMAL is polished (Sec. 3.3) in FP64:
+                                   the zero-objective problem from (x^, 0) until
+                                   ||r_p|| <= eps (1 + ||b||), then the problem with
+                                   every finite bound at zero from (0, y^) until
+                                   ||r_d|| <= eps (1 + ||c||).  mpax_get_solution then
+                                   returns that pair and mpax_stats its KKT values
+                                   (optimality may relax: the gap is not re-tested). */
   int64_t iteration_limit;      /* INT64_MAX */
   double time_limit;            /* seconds, +inf */
 
@@ -142,6 +150,7 @@ typedef struct mpax_stats {
   double profile_ms[4];
   int64_t profile_launches[4];
   int64_t fp64_iterations;           /* iterations of the FP64 continuation (MIXED) */
+  int64_t polish_iterations;         /* iterations of the two feasibility-polishing runs */
 } mpax_stats;
 
 typedef struct mpax_problem mpax_problem;

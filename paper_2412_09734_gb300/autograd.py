@@ -7,6 +7,9 @@ LPValue: v = min c^T x  s.t.  lc <= A x <= uc, l <= x <= u, differentiable in
          (c, lc, uc) through the envelope theorem (dv/dc = x*, ...).
 SharedLPValues: v_k = min c_k^T x  s.t.  lc <= A x <= uc, l <= x <= u for the B rows
          c_k of C with one dense A shared by the batch; dv_k/dc_k = x_k*.
+SPOPlusLoss: the SPO+ surrogate loss of predicted costs c^_k against true costs c_k
+         over the same shared feasible set, with subgradient 2 (x*(c_k) - x~_k),
+         x~_k = argmin (2 c^_k - c_k)^T x: one batched solve per forward.
 """
 from __future__ import annotations
 
@@ -101,3 +104,36 @@ class SharedLPValues(torch.autograd.Function):
     def backward(ctx, gv):
         (X,) = ctx.saved_tensors
         return (gv[:, None] * X).to(gv.dtype), None, None, None, None, None, None, None
+
+
+class SPOPlusLoss(torch.autograd.Function):
+    """forward(C_hat, C_true, X_true, Z_true, A, lc, uc, l, u, options, fp32_products)
+    -> (B,) losses  l_k = -min (2 c^_k - c_k)^T x + 2 c^_k^T x*_k - z*_k.
+
+    X_true (B, n) and Z_true (B,) are the optima of the true costs (for example
+    from SharedLPValues); only C_hat is differentiable."""
+
+    @staticmethod
+    def forward(ctx, C_hat, C_true, X_true, Z_true, A, lc, uc, l, u, options,
+                fp32_products=False):
+        B, n = C_hat.shape
+        m = A.shape[0]
+        Q = (2.0 * C_hat.detach() - C_true.detach()).to(torch.float64).contiguous()
+        h = C.mpax_lp_shared_create(m, n, B, A.detach(), Q, _f64(lc), _f64(uc), _f64(l),
+                                    _f64(u))
+        try:
+            C.mpax_shared_solve(h, C.mpax_options_default(**(options or {})), fp32_products)
+            _, per = C.mpax_shared_get_stats(h, B)
+            Xt, _ = C.mpax_shared_get_solution(h, m, n, B, device=C_hat)
+        finally:
+            C.mpax_shared_destroy(h)
+        Xs = X_true.detach().to(torch.float64)
+        v = torch.as_tensor(per["primal_obj"], dtype=torch.float64, device=C_hat.device)
+        loss = -v + 2.0 * (C_hat.detach().to(torch.float64) * Xs).sum(1) - Z_true.to(torch.float64)
+        ctx.save_for_backward(Xs - Xt)
+        return loss.to(C_hat.dtype)
+
+    @staticmethod
+    def backward(ctx, gl):
+        (D,) = ctx.saved_tensors
+        return ((2.0 * gl.to(torch.float64)[:, None] * D).to(gl.dtype),) + (None,) * 10

@@ -155,6 +155,9 @@ struct mpax_problem {
   double* dya = nullptr;
   double* d6 = nullptr;  // 8 doubles
   cudaEvent_t ev = nullptr;
+  double* dxp = nullptr;  // polished x (n), allocated on the first polishing
+  double* dyp = nullptr;  // polished y (m)
+  bool polished = false;  // the last solve returned the polished pair
 };
 
 namespace {
@@ -187,7 +190,7 @@ void destroy_problem(mpax_problem* pb) {
   double* ds[] = {P.val, P.c,     P.lc,    P.uc,    P.l,   P.u,      P.D,      P.fval,
                   P.Dr,  P.Dc,    P.invDr, P.invDc, P.val_s, P.fval_s, P.D_s,  P.rowred,
                   P.colred, P.rowred2, P.colred2, P.red, P.red_out, P.qdiag, pb->dx, pb->dy,
-                  pb->dxa, pb->dya, pb->d6};
+                  pb->dxa, pb->dya, pb->d6, pb->dxp, pb->dyp};
   for (double* d : ds)
     if (d) cudaFree(d);
   int* is[] = {P.permT, P.permF, P.tmp_rows, P.tmp_scan};
@@ -351,8 +354,8 @@ mpax_status check_options(const mpax_options* o) {
   if (!(o->step_safety > 0.0 && o->step_safety < 1.0))
     return fail(MPAX_ERR_INVALID_ARGUMENT, "step_safety must be in (0, 1)");
   if (o->power_max_iter < 1) return fail(MPAX_ERR_INVALID_ARGUMENT, "power_max_iter must be >= 1");
-  if (o->feasibility_polishing)
-    return fail(MPAX_ERR_UNSUPPORTED, "feasibility polishing is not built");
+  if (o->feasibility_polishing && !(o->eps_feas_polish > 0.0))
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "eps_feas_polish must be > 0");
   if (!(o->time_limit >= 0)) return fail(MPAX_ERR_INVALID_ARGUMENT, "time_limit must be >= 0");
   if (o->fp64_continuation && o->stall_checks < 1)
     return fail(MPAX_ERR_INVALID_ARGUMENT, "stall_checks must be >= 1");
@@ -564,6 +567,41 @@ mpax_status mpax_solve(mpax_problem* pb, const mpax_options* opts, const double*
     }
     info = info64;
   }
+  pb->polished = false;
+  long long polish_iters = 0;
+  if (opts->feasibility_polishing && !P.is_qp && info.termination == MPAX_TERM_OPTIMAL) {
+    // Feasibility polishing (Sec. 3.3), in FP64: the zero-objective problem from
+    // (x^, 0) until the primal residual meets eps_feas_polish, then the problem
+    // with every finite bound at zero from (0, y^) until the dual residual does.
+    if (!pb->dxp) TRY_CUDA(cudaMalloc(&pb->dxp, sizeof(double) * std::max(P.n, 1)), "alloc");
+    if (!pb->dyp) TRY_CUDA(cudaMalloc(&pb->dyp, sizeof(double) * std::max(P.m, 1)), "alloc");
+    TRY_CUDA(eng->get_solution(pb->dxa, pb->dya), "point to polish");
+    mpax_options op = *opts;
+    op.precision = MPAX_PREC_FP64;
+    op.eps_abs = op.eps_rel = opts->eps_feas_polish;
+    op.eps_primal_infeasible = op.eps_dual_infeasible = 0.0;
+    op.fp64_continuation = 0;
+    st = do_prepare(pb, &op, &launches);
+    if (st) return st;
+    eng = pb->eng[pb->cur];
+    for (int phase = 1; phase <= 2; ++phase) {
+      if (phase == 2) TRY_CUDA(eng->load_values(), "reload");
+      TRY_CUDA(eng->set_feasibility(phase), "polishing data");
+      TRY_CUDA(eng->init_state(op, &launches), "polishing state");
+      TRY_CUDA(eng->init_iterate(phase == 1 ? pb->dxa : nullptr, phase == 2 ? pb->dya : nullptr),
+               "polishing start");
+      RunInfo ip;
+      e = eng->run(op, &ip);
+      if (e) return cuda_fail(e, "feasibility polishing");
+      polish_iters += ip.iterations;
+      info.launches += ip.launches;
+      TRY_CUDA(eng->get_solution(phase == 1 ? pb->dxp : pb->dx, phase == 1 ? pb->dy : pb->dyp),
+               "polished point");
+    }
+    TRY_CUDA(eng->load_values(), "restore");
+    TRY_CUDA(eng->kkt_at(pb->dxp, pb->dyp, pb->d6), "polished kkt");
+    pb->polished = true;
+  }
   DevState h;
   TRY_CUDA(eng->read_state(&h), "read state");
   TRY_CUDA(order_user_after(pb), "stream order");
@@ -592,6 +630,18 @@ mpax_status mpax_solve(mpax_problem* pb, const mpax_options* opts, const double*
     S.profile_launches[i] = info.profile_launches[i];
   }
   S.fp64_iterations = fp64_iters;
+  S.polish_iterations = polish_iters;
+  if (pb->polished) {
+    double k6[6];
+    TRY_CUDA(cudaMemcpyAsync(k6, pb->d6, sizeof(k6), cudaMemcpyDeviceToHost, P.s), "kkt");
+    TRY_CUDA(cudaStreamSynchronize(P.s), "kkt");
+    S.primal_res = k6[0];
+    S.dual_res = k6[1];
+    S.primal_obj = k6[2];
+    S.dual_obj = k6[3];
+    S.gap = k6[4];
+    S.rel_kkt = k6[5];
+  }
   pb->solved = true;
   pb->last_opts = *opts;
   if (info.termination == MPAX_TERM_NUMERICAL_ERROR)
@@ -606,9 +656,16 @@ mpax_status mpax_get_solution(const mpax_problem* cpb, double* x, double* y,
   if (!pb->solved) return fail(MPAX_ERR_NOT_SOLVED, "call mpax_solve first");
   const ProblemData& P = pb->P;
   EngineBase* eng = pb->eng[pb->cur];
-  TRY_CUDA(eng->get_solution(pb->dx, pb->dy), "get solution");
-  if (x) TRY_CUDA(copy_out(x, pb->dx, sizeof(double) * P.n, kind, P.s), "copy x");
-  if (y) TRY_CUDA(copy_out(y, pb->dy, sizeof(double) * P.m, kind, P.s), "copy y");
+  const double* sx = pb->dx;
+  const double* sy = pb->dy;
+  if (pb->polished) {
+    sx = pb->dxp;
+    sy = pb->dyp;
+  } else {
+    TRY_CUDA(eng->get_solution(pb->dx, pb->dy), "get solution");
+  }
+  if (x) TRY_CUDA(copy_out(x, sx, sizeof(double) * P.n, kind, P.s), "copy x");
+  if (y) TRY_CUDA(copy_out(y, sy, sizeof(double) * P.m, kind, P.s), "copy y");
   TRY_CUDA(cudaStreamSynchronize(P.s), "get solution");
   return MPAX_OK;
 }

@@ -102,6 +102,7 @@ struct DevState {
   int pw_done, pw_iters, stall_limit, stall_count;
   double best_rel;
   double eps_pi, eps_di;  // infeasibility tolerances (LP; <= 0 turns a test off)
+  int feas_mode, pad2;    // 0: KKT test; 1 / 2: primal / dual residual alone (polishing)
   int done, restart_flag, termination, have_anchor;
   int check_every, is_qp, nan_seen, pad;
   // Halpern / averaging coefficient table for the current block:

@@ -36,6 +36,10 @@ class EngineBase {
   virtual cudaError_t get_solution(double* x, double* y) = 0;  // unscaled
   virtual cudaError_t kkt_at(const double* x, const double* y, double* out6) = 0;  // unscaled
   virtual cudaError_t read_state(DevState* h) = 0;
+  // Feasibility polishing (LP): 1 = objective set to zero, the run ends on the
+  // primal residual; 2 = every finite bound set to zero, the run ends on the
+  // dual residual; 0 = the problem as loaded.  Call init_state afterwards.
+  virtual cudaError_t set_feasibility(int mode) = 0;
 };
 
 EngineBase* make_engine(ProblemData* P, int precision, cudaError_t* err);

@@ -117,7 +117,7 @@ struct InitParams {
   double eps_abs, eps_rel, r_suff, r_nec, r_art, pw_smooth, step_safety, gamma;
   double eps_pi, eps_di;
   long long iter_limit;
-  int check_every, is_qp, stall_limit;
+  int check_every, is_qp, stall_limit, feas_mode;
 };
 
 // red: [0] ||c~||, [1] ||b~||, [2] ||c||, [3] ||b||  (norm_A, norm_Q already in st)
@@ -135,7 +135,10 @@ __global__ void k_init_state(DevState* st, InitParams p, const double* red) {
     st->check_every = p.check_every;
     st->is_qp = p.is_qp;
     const double nc = red[0], nb = red[1];
-    st->omega = (nc > 1e-10 && nb > 1e-10) ? nc / nb : 1.0;
+    // a polishing run has a zero objective (mode 1) or zero bounds (mode 2): the
+    // initial primal weight is then 1, as the zero norm gives
+    st->omega = (nc > 1e-10 && nb > 1e-10 && p.feas_mode == 0) ? nc / nb : 1.0;
+    st->feas_mode = p.feas_mode;
     st->c_norm = red[2];
     st->b_norm = red[3];
     st->eta = st->norm_A > 0.0 ? p.step_safety / st->norm_A : 1.0;
@@ -191,6 +194,16 @@ __global__ void k_power_start(DevState* st) {
 // One power-iteration round done: sum of squares of g in part[0..n).
 // mode 0 (A~^T A~): nu = sqrt(||g||); mode 1 (Q~): nu = ||g||.  v_next = g/||g||
 // through pw_scale.  Writes the estimate to norm_A or norm_Q.
+// Every finite bound of the pair (lo, hi) set to zero (the dual polishing problem).
+template <typename T>
+__global__ void k_zero_finite(T* __restrict__ lo, T* __restrict__ hi, int k) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+    if (isfinite(lo[i])) lo[i] = (T)0;
+    if (isfinite(hi[i])) hi[i] = (T)0;
+  }
+}
+
 // The normalised start vector of the power iterations (power_start_raw).
 template <typename T>
 __global__ void k_power_vec(T* __restrict__ v, int n, double inv_norm) {
@@ -315,8 +328,10 @@ __global__ void k_finalize_check(const double* __restrict__ partAt, int nAt,
     st->gap = gap;
     st->rel_kkt = rel;
     const double ea = st->eps_abs, er = st->eps_rel;
-    const bool conv = nrp <= ea + er * bn && nrd <= ea + er * cn &&
-                      gap <= ea + er * (fabs(pobj) + fabs(dobj));
+    const bool conv = st->feas_mode == 1   ? nrp <= ea + er * bn
+                      : st->feas_mode == 2 ? nrd <= ea + er * cn
+                                           : nrp <= ea + er * bn && nrd <= ea + er * cn &&
+                                                 gap <= ea + er * (fabs(pobj) + fabs(dobj));
     int term = 0;
     if (!isfinite(rel) || !isfinite(P0) || !isfinite(D0) || !isfinite(P1) || !isfinite(D1))
       term = MPAX_TERM_NUMERICAL_ERROR;
@@ -575,10 +590,24 @@ class Engine final : public EngineBase {
     if (hs_) cudaFreeHost(hs_);
   }
 
+  cudaError_t set_feasibility(int mode) override {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    feas_mode_ = mode;
+    if (mode == 1 && P.n) return cudaMemsetAsync(c_, 0, sizeof(T) * P.n, s);
+    if (mode == 2) {
+      if (P.n) k_zero_finite<T><<<grid1(P.n), 256, 0, s>>>(l_, u_, P.n);
+      if (P.m) k_zero_finite<T><<<grid1(P.m), 256, 0, s>>>(lc_, uc_, P.m);
+      return cudaGetLastError();
+    }
+    return cudaSuccess;
+  }
+
   cudaError_t load_values() override {
     ProblemData& P = *P_;
     cudaStream_t s = P.s;
     cudaError_t e;
+    feas_mode_ = 0;
     if ((e = cast_vec<T>(P.val_s, valA_, P.nnz, s))) return e;
     if ((e = gather_cast<T>(P.val_s, P.permT, valAt_, P.nnz, s))) return e;
     if ((e = scale_cast<T>(P.c, P.Dc, false, c_, P.n, s))) return e;
@@ -667,6 +696,7 @@ class Engine final : public EngineBase {
     ip.stall_limit = (o.precision == MPAX_PREC_MIXED && o.fp64_continuation) ? o.stall_checks : 0;
     ip.eps_pi = o.eps_primal_infeasible;
     ip.eps_di = o.eps_dual_infeasible;
+    ip.feas_mode = feas_mode_;
     k_init_state<<<1, 256, 0, P.s>>>(st_, ip, P.red_out);
     *launches += 1;
     gamma_one_ = (o.reflection_gamma == 1.0);
@@ -1044,6 +1074,7 @@ class Engine final : public EngineBase {
   T *c_ = nullptr, *l_ = nullptr, *u_ = nullptr, *lc_ = nullptr, *uc_ = nullptr;
   T *xbar_ = nullptr, *wbuf_ = nullptr, *xa_ = nullptr, *xhat_ = nullptr, *xprev_ = nullptr;
   T *rayx_ = nullptr, *rayy_ = nullptr;  // infeasibility rays of an LP check
+  int feas_mode_ = 0;                     // polishing mode of the loaded data
   T *pv_ = nullptr, *pg_ = nullptr, *pw_ = nullptr;
   T *y_ = nullptr, *ya_ = nullptr, *yhat_ = nullptr, *yprev_ = nullptr;
   T *x_ = nullptr, *xavg_ = nullptr, *xref_ = nullptr, *xanc_ = nullptr;

@@ -72,7 +72,7 @@ class Stats(ctypes.Structure):
         ("prepare_seconds", ctypes.c_double), ("solve_seconds", ctypes.c_double),
         ("kernel_launches", ctypes.c_int64),
         ("profile_ms", ctypes.c_double * 4), ("profile_launches", ctypes.c_int64 * 4),
-        ("fp64_iterations", ctypes.c_int64),
+        ("fp64_iterations", ctypes.c_int64), ("polish_iterations", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -12,5 +12,6 @@ from .generators import (  # noqa: F401
     qp_instance,
     ragged_lp_batch,
     shared_dense_lp_batch,
+    knapsack_lp,
     random_state,
 )

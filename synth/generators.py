@@ -301,3 +301,22 @@ def random_state(n: int, m: int, *, seed: int, lo=None, hi=None) -> dict:
     return dict(x=vec(n, xl, xh), y=rng.standard_normal(m), x_anchor=vec(n, xl, xh),
                 y_anchor=rng.standard_normal(m), xbar=vec(n, xl, xh),
                 ybar=rng.standard_normal(m))
+
+
+# ----------------------------------------------------------------------------
+# Dense multi-dimensional knapsack relaxation (one instance)
+# ----------------------------------------------------------------------------
+
+def knapsack_lp(d: int, m: int, *, seed: int = MASTER_SEED, frac: float = 0.25) -> dict:
+    """LP relaxation of a d-dimensional knapsack over m items:
+        min -v^T x  s.t.  W x <= b,  0 <= x <= 1,
+    W ~ U[0, 1] dense (d x m, FP32, row-major), item values v ~ U[0, 1], and
+    capacities b = frac * W 1 (each dimension holds a fraction of all items).
+    The objective is the negated value, so the LP is a maximisation of value as
+    the knapsack relaxation intends."""
+    rng = _rng(seed)
+    W = rng.random((d, m), dtype=np.float32)
+    v = rng.random(m)
+    b = frac * W.astype(np.float64).sum(axis=1)
+    return dict(kind="knapsack", d=d, m_items=m, A=W, c=-v, lc=np.full(d, -np.inf), uc=b,
+                l=np.zeros(m), u=np.ones(m))

@@ -118,3 +118,64 @@ def test_shared_values_autograd(C):
         assert chk["primal_res"] / (1 + chk["b_norm"]) <= 1e-4
         # x0 is the unique optimum, so the gradient row is x0 up to the solve tolerance
         np.testing.assert_allclose(xk, d["x0"], atol=5e-3)
+
+
+def test_spo_plus_loss_matches_oracle(C):
+    """SPO+ over a shared feasible set: the batched losses equal the oracle's, and
+    the returned gradient rows are subgradients of the oracle's loss (convexity
+    inequality along random directions)."""
+    import torch
+    from oracle import spo
+    from paper_2412_09734_gb300.autograd import SharedLPValues, SPOPlusLoss
+    d = shared_dense_lp_batch(64, 128, 4, seed=777, bound_frac=0.75)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    opts = dict(eps_abs=1e-6, eps_rel=1e-6, iteration_limit=400000)
+    A, b, l, u = dev(d["A"]), dev(d["b"]), dev(d["l"]), dev(d["u"])
+    Ct = dev(d["C"])
+    with torch.no_grad():
+        zt = SharedLPValues.apply(Ct, A, b, b, l, u, opts, True)
+    # the true optimum is x0 (unique, reduced costs at the bounds)
+    Xt = torch.from_numpy(np.tile(d["x0"], (d["B"], 1))).cuda()
+    rng = np.random.default_rng(11)
+    Ch = dev(d["C"] + rng.normal(0, 0.5, d["C"].shape)).requires_grad_(True)
+    loss = SPOPlusLoss.apply(Ch, Ct, Xt, zt, A, b, b, l, u, opts, True)
+    loss.sum().backward()
+    G = Ch.grad.cpu().numpy()
+    Lg = loss.detach().cpu().numpy()
+    Ah = sp.csr_matrix(d["A"].astype(np.float64))
+    oo = O.Options(eps_abs=1e-8, eps_rel=1e-8, iteration_limit=10**6)
+    for k in range(d["B"]):
+        p = O.Problem(Ah, d["C"][k].copy(), d["b"], d["b"], d["l"], d["u"])
+        ch = Ch.detach().cpu().numpy()[k]
+        lo, go, _ = spo.spo_plus(p, ch, d["x0"], float(zt[k]), oo)
+        assert Lg[k] == pytest.approx(lo, rel=1e-3, abs=1e-3)
+        for _ in range(3):
+            delta = rng.normal(0, 0.1, d["n"])
+            l2 = spo.spo_plus(p, ch + delta, d["x0"], float(zt[k]), oo)[0]
+            assert l2 >= lo + G[k] @ delta - 1e-3 * (1 + abs(lo))
+
+
+def test_dense_single_knapsack_matches_highs(C):
+    """One dense LP (the knapsack relaxation, B = 1, FP32 products: with one cost
+    vector the products are matrix-vector products) against HiGHS's optimum and
+    the oracle's KKT evaluation."""
+    from scipy.optimize import linprog
+    from synth import knapsack_lp
+    d = knapsack_lp(40, 2000, seed=2024)
+    h = C.mpax_lp_shared_create(d["d"], d["m_items"], 1, d["A"], d["c"][None, :], d["lc"],
+                                d["uc"], d["l"], d["u"])
+    try:
+        C.mpax_shared_solve(h, C.mpax_options_default(eps_abs=1e-6, eps_rel=1e-6,
+                                                      iteration_limit=400000), True)
+        summ, per = C.mpax_shared_get_stats(h, 1)
+        X, Y = C.mpax_shared_get_solution(h, d["d"], d["m_items"], 1)
+    finally:
+        C.mpax_shared_destroy(h)
+    assert summ["n_optimal"] == 1
+    A = d["A"].astype(np.float64)
+    p = O.Problem(sp.csr_matrix(A), d["c"], d["lc"], d["uc"], d["l"], d["u"])
+    chk = O.kkt(p, X[0], Y[0], 1e-6, 1e-6)
+    assert chk["converged"], chk["rel_kkt"]
+    res = linprog(d["c"], A_ub=A, b_ub=d["uc"], bounds=(0, 1), method="highs")
+    assert res.status == 0
+    assert chk["primal_obj"] == pytest.approx(res.fun, rel=1e-5)
