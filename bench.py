@@ -317,12 +317,12 @@ def run_ours(args):
                  "rel_kkt": max(kkt64), "steps": args.fp64_steps}
 
     # FP64 continuation: a tolerance below the FP32 floor, mixed + continuation
-    # against the plain FP64 path (one solve each, after one untimed solve)
+    # against the plain FP64 path (one solve each; both engines are warm from
+    # the solves above, and a solve takes seconds)
     cont = {}
     for name, prec in (("mixed_continuation", C.MPAX_PREC_MIXED), ("fp64", C.MPAX_PREC_FP64)):
         o7 = C.mpax_options_default(precision=prec, eps_abs=1e-7, eps_rel=1e-7,
                                     iteration_limit=400000)
-        C.mpax_solve(h, o7)
         barrier()
         c0 = torch.cuda.Event(enable_timing=True)
         c1 = torch.cuda.Event(enable_timing=True)
