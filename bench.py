@@ -238,6 +238,24 @@ def run_reference(args):
 # our arm
 # -----------------------------------------------------------------------------
 
+def rank_reduce(v, op, dist=None, device="cpu"):
+    """Max or sum of a scalar over the ranks of the replica job (the value itself
+    on one rank): the slowest rank's time and the whole job's work."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_value(work_per_rank, seconds_per_rank, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: the work of every rank over
+    the slowest rank's time."""
+    return (rank_reduce(work_per_rank, "sum", dist, device)
+            / rank_reduce(seconds_per_rank, "max", dist, device))
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -256,18 +274,10 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def allmax(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_reduce(v, "max", dist, "cuda")
 
     def allsum(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return rank_reduce(v, "sum", dist, "cuda")
 
     from paper_2412_09734_gb300 import mpax as C
 
