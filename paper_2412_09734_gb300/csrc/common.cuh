@@ -43,6 +43,13 @@ constexpr int kBlock = kWarp * kWarpsPerBlock;
 #ifndef MPAX_SPMV_PREFETCH
 #define MPAX_SPMV_PREFETCH 1
 #endif
+// 1: the fused SpMVs are launched with programmatic stream serialization and
+//    overlap their matrix loads with the previous launch's tail.  Measured on the
+//    500k x 1M LP it does not pay (time to 1e-4 0.311 s against 0.299 s; the
+//    primal launch 58 against 52 us: early CTAs hold SM slots while they wait).
+#ifndef MPAX_SPMV_PDL
+#define MPAX_SPMV_PDL 0
+#endif
 #ifndef MPAX_LONG_ACQREL
 #define MPAX_LONG_ACQREL 1
 #endif

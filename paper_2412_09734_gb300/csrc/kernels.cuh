@@ -74,6 +74,21 @@ __device__ __forceinline__ void item_range(const int4& it, int& p0, int& p1) {
   }
 }
 
+// Programmatic dependent launch (sm_90+ griddepcontrol).  launch_dependents lets
+// the next kernel of the stream start its CTAs once every CTA of this grid has
+// issued it or exited; wait returns when the previous grid has completed and its
+// memory operations are visible.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() {
+#if MPAX_SPMV_PDL
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void pdl_wait() {
+#if MPAX_SPMV_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
 // TMA bulk prefetch of [p, p + bytes) into L2 (16-byte aligned, rounded out;
 // arrays carry at least 16 bytes of padding past their end).
 __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
@@ -90,14 +105,11 @@ __global__ void MPAX_SPMV_BOUNDS spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int item = blockIdx.x * kSpmvWarps + wib;
+  // The next launch may start its CTAs as this grid drains (programmatic
+  // dependent launch); it reads only the constant matrix arrays before its wait.
+  pdl_launch_dependents();
   if (item >= a.n_items) return;
   const int4 it = a.items[item];
-  if (epi.skip()) return;
-  in.load();
-  epi.load();
-  double acc[Epi::NQ];
-#pragma unroll
-  for (int q = 0; q < Epi::NQ; ++q) acc[q] = 0.0;
   const bool do_pf = (lane == 0) && a.pf_dist > 0 && item + a.pf_dist < a.n_items;
 
   if (it.x >= 0) {
@@ -108,9 +120,6 @@ __global__ void MPAX_SPMV_BOUNDS spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
     const int sa = ha ? ra : r0, sb = hb ? rb : r0;  // always-valid rows
     const int pa0 = a.rp[sa], pa1 = a.rp[sa + 1];
     const int pb0 = a.rp[sb], pb1 = a.rp[sb + 1];
-    typename Epi::Pre pra, prb;
-    epi.pre(sa, pra);
-    epi.pre(sb, prb);
     T v[kShortLoads];
     int c[kShortLoads];
 #pragma unroll
@@ -123,6 +132,17 @@ __global__ void MPAX_SPMV_BOUNDS spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
     }
     int4 ft;
     if (do_pf) ft = a.items[item + a.pf_dist];
+    // everything below reads or writes state of the previous launches
+    pdl_wait();
+    if (epi.skip()) return;
+    in.load();
+    epi.load();
+    double acc[Epi::NQ];
+#pragma unroll
+    for (int q = 0; q < Epi::NQ; ++q) acc[q] = 0.0;
+    typename Epi::Pre pra, prb;
+    epi.pre(sa, pra);
+    epi.pre(sb, prb);
     T* buf = sbuf[wib];
 #pragma unroll
     for (int u = 0; u < kShortLoads; ++u) {
@@ -160,8 +180,6 @@ __global__ void MPAX_SPMV_BOUNDS spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
   const int r = -(it.x + 1), p0 = it.y, p1 = it.z;
   const int si = it.w >> 16, S = it.w & 0xffff;
   const int first = item - si;
-  typename Epi::Pre pr;
-  epi.pre(r, pr);
   T v[kSliceLoads];
   int c[kSliceLoads];
 #pragma unroll
@@ -174,6 +192,15 @@ __global__ void MPAX_SPMV_BOUNDS spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
   }
   int4 ft;
   if (do_pf) ft = a.items[item + a.pf_dist];
+  pdl_wait();
+  if (epi.skip()) return;
+  in.load();
+  epi.load();
+  double acc[Epi::NQ];
+#pragma unroll
+  for (int q = 0; q < Epi::NQ; ++q) acc[q] = 0.0;
+  typename Epi::Pre pr;
+  epi.pre(r, pr);
   T s = 0;
 #pragma unroll
   for (int u = 0; u < kSliceLoads; ++u) {

@@ -517,7 +517,21 @@ void launch_spmv(const Sched& sc, const Csr& K, const T* val, In in, Epi epi, in
   a.part = sc.part;
   a.q0 = q0;
   const int grid = (sc.n_items + kSpmvWarps - 1) / kSpmvWarps;
+#if MPAX_SPMV_PDL
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kSpmvBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, spmv_fused<T, In, Epi>, a, in, epi);
+#else
   spmv_fused<T, In, Epi><<<grid, kSpmvBlock, 0, s>>>(a, in, epi);
+#endif
 }
 
 template <typename T>
