@@ -136,3 +136,55 @@ def test_batch_mixed_continues_stalled_instances_in_fp64(C):
         chk = O.kkt(p, x[d["n_off"][b]:d["n_off"][b + 1]], y[d["m_off"][b]:d["m_off"][b + 1]])
         assert chk["converged"], (b, chk["rel_kkt"])
     assert out[0][0]["fp64_instances"] == 0
+
+
+def _mixed_bounds_instance(m, n, density, rng):
+    """Feasible, bounded LP with every bound type: equality, >=, <= and free rows
+    (some rows empty); boxed, lower-only, upper-only and free columns.  x0 lies
+    inside the column bounds, the row bounds hold at x0, and c = A_eq^T y0, so
+    c^T x = y0^T b_eq on the whole feasible set."""
+    from synth import csr_random
+    rp, col, val = csr_random(m, n, rng, density=density)
+    kc = rng.integers(0, 4, size=n)
+    l = np.where((kc == 0) | (kc == 1), -1.0, -np.inf)
+    u = np.where((kc == 0) | (kc == 2), 2.0, np.inf)
+    x0 = rng.uniform(-0.5, 1.5, size=n)
+    ax = np.bincount(np.repeat(np.arange(m), np.diff(rp)), weights=val * x0[col], minlength=m)
+    kr = rng.integers(0, 4, size=m)
+    lc = np.where(kr == 0, ax, np.where(kr == 1, ax - rng.uniform(0, 1, m), -np.inf))
+    uc = np.where(kr == 0, ax, np.where(kr == 2, ax + rng.uniform(0, 1, m), np.inf))
+    y0 = np.where(kr == 0, rng.standard_normal(m), 0.0)
+    c = np.bincount(col, weights=val * y0[np.repeat(np.arange(m), np.diff(rp))], minlength=n)
+    return dict(m=m, n=n, nnz=int(rp[-1]), row_ptr=rp, col=col, val=val, c=c, lc=lc, uc=uc,
+                l=l, u=u, opt_value=float(c @ x0))
+
+
+def test_batch_with_every_bound_type(C):
+    rng = np.random.default_rng(2027)
+    insts = [_mixed_bounds_instance(int(rng.integers(30, 200)), int(rng.integers(40, 300)),
+                                    0.05, rng) for _ in range(12)]
+    B = len(insts)
+    m_off = np.concatenate([[0], np.cumsum([d["m"] for d in insts])]).astype(np.int64)
+    n_off = np.concatenate([[0], np.cumsum([d["n"] for d in insts])]).astype(np.int64)
+    nz_off = np.concatenate([[0], np.cumsum([d["nnz"] for d in insts])])
+    d = dict(B=B, m_off=m_off, n_off=n_off,
+             row_ptr=np.concatenate([[0]] + [x["row_ptr"][1:] + nz_off[i]
+                                             for i, x in enumerate(insts)]).astype(np.int64),
+             **{k: np.concatenate([x[k] for x in insts]) for k in ("col", "val", "c", "lc",
+                                                                  "uc", "l", "u")})
+    for prec, eps in ((0, 1e-6), (1, 1e-4)):
+        h = _create(C, d, device=(prec == 1))
+        try:
+            C.mpax_batch_solve(h, C.mpax_options_default(precision=prec, eps_abs=eps,
+                                                         eps_rel=eps, iteration_limit=200000))
+            summary, per = C.mpax_batch_get_stats(h, B)
+            x, y = C.mpax_batch_get_solution(h, int(m_off[-1]), int(n_off[-1]))
+        finally:
+            C.mpax_batch_destroy(h)
+        assert summary["n_optimal"] == B
+        for b, inst in enumerate(insts):
+            p = O.problem_from_arrays(inst)
+            chk = O.kkt(p, x[n_off[b]:n_off[b + 1]], y[m_off[b]:m_off[b + 1]], eps, eps)
+            assert chk["converged"], (prec, b, chk["rel_kkt"])
+            assert chk["primal_obj"] == pytest.approx(inst["opt_value"], rel=30 * eps,
+                                                      abs=30 * eps)
