@@ -34,6 +34,11 @@ constexpr int kLPR = 8;  // lanes cooperating on one row
 #define MPAX_BATCH_ROWS 2
 #endif
 constexpr int kBR = MPAX_BATCH_ROWS;
+// 1: stage each instance's row pointers in shared memory when two CTAs per SM
+//    still fit (<= 100 KB of shared memory per CTA).
+#ifndef MPAX_BATCH_SMEM_RP
+#define MPAX_BATCH_SMEM_RP 1
+#endif
 
 template <typename T>
 struct BatchArgs {
@@ -56,6 +61,8 @@ struct BatchArgs {
   double *relkkt, *pobj, *secs;
   int* next;
   int smem_m;  // elements of y held in shared memory (>= max m_b)
+  int smem_n;  // elements of the primal vector held in shared memory (>= max n_b)
+  int rp_smem; // 1: the instance's row pointers are staged in shared memory
   double eps_abs, eps_rel, r_suff, r_nec, r_art, pw_smooth, step_safety, power_tol;
   long long iter_limit;
   long long time_limit_ns;  // from the start of the launch, on the device clock
@@ -99,7 +106,7 @@ __device__ __forceinline__ unsigned long long gtimer() {
 }
 
 template <typename T>
-__device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, double* sh,
+__device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, int* srp, double* sh,
                                unsigned long long t_launch) {
   const unsigned long long t_start = gtimer();
   __shared__ int s_late;
@@ -107,6 +114,19 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
   const int n0 = (int)a.n_off[b], nb = (int)(a.n_off[b + 1] - a.n_off[b]);
   const int grp = threadIdx.x / kLPR, gl = threadIdx.x % kLPR;
   const int G = blockDim.x / kLPR;
+  // Row pointers of A_b and A_b^T: staged in shared memory when they fit (one
+  // global round trip less in every step of a half-step), else read in place.
+  const int* rpl = a.rp + m0;
+  const int* rptl = a.rpt + n0;
+  if (a.rp_smem) {
+    int* sa = srp;
+    int* st = srp + (mb + 1);
+    for (int i = threadIdx.x; i <= mb; i += blockDim.x) sa[i] = a.rp[m0 + i];
+    for (int j = threadIdx.x; j <= nb; j += blockDim.x) st[j] = a.rpt[n0 + j];
+    __syncthreads();
+    rpl = sa;
+    rptl = st;
+  }
 
   // ---- power iteration for ||A~_b||_2 from the common start vector ----------
   double ss0 = 0.0;
@@ -118,13 +138,13 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
   for (int j = threadIdx.x; j < nb; j += blockDim.x) xs[j] = (T)(power_start_raw(j) * inv0);
   __syncthreads();
   double nA = 0.0, nu_prev = 0.0, d_prev = 0.0;
-  const bool has_rows = mb > 0 && a.rp[m0 + mb] > a.rp[m0];
+  const bool has_rows = mb > 0 && rpl[mb] > rpl[0];
   for (int t = 1; has_rows && t <= a.power_max_iter; ++t) {
     for (int i0 = 0; i0 < mb; i0 += G) {
       const int i = i0 + grp;
       const bool in_i = i < mb;
       T s = 0;
-      for (int p = in_i ? a.rp[m0 + i] + gl : 0; in_i && p < a.rp[m0 + i + 1]; p += kLPR)
+      for (int p = in_i ? rpl[i] + gl : 0; in_i && p < rpl[i + 1]; p += kLPR)
         s += a.val[p] * xs[a.col[p] - n0];
       s = group_sum(s);
       if (gl == 0 && in_i) ys[i] = s;
@@ -135,7 +155,7 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
       const int j = j0 + grp;
       const bool in_j = j < nb;
       T s = 0;
-      for (int p = in_j ? a.rpt[n0 + j] + gl : 0; in_j && p < a.rpt[n0 + j + 1]; p += kLPR)
+      for (int p = in_j ? rptl[j] + gl : 0; in_j && p < rptl[j + 1]; p += kLPR)
         s += a.valt[p] * ys[a.colt[p] - m0];
       s = group_sum(s);
       if (gl == 0 && in_j) {
@@ -221,8 +241,8 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
         for (int r = 0; r < kBR; ++r) {
           jr[r] = j0 + r * G + grp;
           const bool in = jr[r] < nb;
-          pp[r] = in ? a.rpt[n0 + jr[r]] + gl : 0;
-          pe[r] = in ? a.rpt[n0 + jr[r] + 1] : 0;
+          pp[r] = in ? rptl[jr[r]] + gl : 0;
+          pe[r] = in ? rptl[jr[r] + 1] : 0;
           sr[r] = 0;
           if (gl == 0 && in) {
             const int g = n0 + jr[r];
@@ -275,8 +295,8 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
         for (int r = 0; r < kBR; ++r) {
           ir[r] = i0 + r * G + grp;
           const bool in = ir[r] < mb;
-          pp[r] = in ? a.rp[m0 + ir[r]] + gl : 0;
-          pe[r] = in ? a.rp[m0 + ir[r] + 1] : 0;
+          pp[r] = in ? rpl[ir[r]] + gl : 0;
+          pe[r] = in ? rpl[ir[r] + 1] : 0;
           sr[r] = 0;
           if (gl == 0 && in) {
             const int g = m0 + ir[r];
@@ -328,7 +348,7 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
       const int i = i0 + grp;
       const bool in_i = i < mb;
       T s = 0;
-      for (int p = in_i ? a.rp[m0 + i] + gl : 0; in_i && p < a.rp[m0 + i + 1]; p += kLPR)
+      for (int p = in_i ? rpl[i] + gl : 0; in_i && p < rpl[i + 1]; p += kLPR)
         s += a.val[p] * xs[a.col[p] - n0];
       s = group_sum(s);
       if (gl == 0 && in_i) {
@@ -346,7 +366,7 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, doubl
       const int j = j0 + grp;
       const bool in_j = j < nb;
       T s = 0;
-      for (int p = in_j ? a.rpt[n0 + j] + gl : 0; in_j && p < a.rpt[n0 + j + 1]; p += kLPR)
+      for (int p = in_j ? rptl[j] + gl : 0; in_j && p < rptl[j + 1]; p += kLPR)
         s += a.valt[p] * a.yhat[a.colt[p]];
       s = group_sum(s);
       if (gl == 0 && in_j) {
@@ -461,6 +481,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_lp_kernel(BatchArgs<T>
   __shared__ int s_inst;
   T* ys = reinterpret_cast<T*>(sm);
   T* xs = ys + a.smem_m;
+  int* srp = reinterpret_cast<int*>(xs + a.smem_n);  // rp_smem only
   const unsigned long long t_launch = gtimer();  // used by thread 0 only
   while (true) {
     if (threadIdx.x == 0) s_inst = atomicAdd(a.next, 1);
@@ -468,7 +489,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_lp_kernel(BatchArgs<T>
     const int w = s_inst;
     __syncthreads();
     if (w >= a.n_todo) return;
-    solve_instance<T>(a, a.todo ? a.todo[w] : w, ys, xs, sh, t_launch);
+    solve_instance<T>(a, a.todo ? a.todo[w] : w, ys, xs, srp, sh, t_launch);
   }
 }
 
@@ -609,6 +630,7 @@ mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches
   a.secs = bt->secs;
   a.next = bt->next;
   a.smem_m = (bt->max_m + 3) / 4 * 4;
+  a.smem_n = (bt->max_n + 3) / 4 * 4;
   a.eps_abs = o->eps_abs;
   a.eps_rel = o->eps_rel;
   a.r_suff = o->restart_sufficient;
@@ -624,10 +646,13 @@ mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches
   a.check_every = o->check_every;
   a.power_max_iter = o->power_max_iter;
   a.power_cap = o->pock_chambolle ? 1.0 : INFINITY;
-  const size_t smem = sizeof(T) * ((size_t)a.smem_m + (size_t)bt->max_n);
+  size_t smem = sizeof(T) * ((size_t)a.smem_m + (size_t)a.smem_n);
   if (smem > 200 * 1024)
     return bfail(MPAX_ERR_UNSUPPORTED,
                  "batch instances too large for one CTA's shared memory (max_m + max_n)");
+  const size_t rp_bytes = sizeof(int) * ((size_t)bt->max_m + (size_t)bt->max_n + 2);
+  a.rp_smem = (MPAX_BATCH_SMEM_RP && smem + rp_bytes <= 100 * 1024) ? 1 : 0;
+  if (a.rp_smem) smem += rp_bytes;
   cudaFuncSetAttribute(batch_lp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   int occ = 0, dev = 0, sms = 0;
