@@ -34,6 +34,13 @@ constexpr int kLPR = 8;  // lanes cooperating on one row
 #define MPAX_BATCH_ROWS 2
 #endif
 constexpr int kBR = MPAX_BATCH_ROWS;
+// Values and columns each lane loads per row before using any (see rows_dot).
+// Measured on 1024 instances of the bench recipe: 1 (0.369 s per batch, mixed)
+// beats 2 (0.370 s) and 4 (0.405 s): at 64 registers deeper batches spill.
+#ifndef MPAX_BATCH_UNROLL
+#define MPAX_BATCH_UNROLL 1
+#endif
+constexpr int kBU = MPAX_BATCH_UNROLL;
 // 1: stage each instance's row pointers in shared memory when two CTAs per SM
 //    still fit (<= 100 KB of shared memory per CTA).
 #ifndef MPAX_BATCH_SMEM_RP
@@ -103,6 +110,40 @@ __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Dot products of kBR rows (one per slot r, lane offset already in pp[r]) with
+// the shared-memory vector vec (columns offset by off): each pass issues up to
+// kBU values and columns per row and lane before any of them is used, so a row
+// of up to kBU * kLPR nonzeros costs one memory round trip.
+template <typename T>
+__device__ __forceinline__ void rows_dot(const int* pp, const int* pe, const T* __restrict__ val,
+                                         const int* __restrict__ col, const T* vec, int off,
+                                         T* sr) {
+  for (int base = 0;; base += kBU * kLPR) {
+    T v[kBR][kBU];
+    int c[kBR][kBU];
+    bool any = false;
+#pragma unroll
+    for (int r = 0; r < kBR; ++r)
+#pragma unroll
+      for (int u = 0; u < kBU; ++u) {
+        const int p = pp[r] + base + u * kLPR;
+        if (p < pe[r]) {
+          v[r][u] = val[p];
+          c[r][u] = col[p];
+          any = true;
+        }
+      }
+    if (!any) break;
+#pragma unroll
+    for (int r = 0; r < kBR; ++r)
+#pragma unroll
+      for (int u = 0; u < kBU; ++u) {
+        const int p = pp[r] + base + u * kLPR;
+        if (p < pe[r]) sr[r] += v[r][u] * vec[c[r][u] - off];
+      }
+  }
 }
 
 template <typename T>
@@ -253,16 +294,7 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, int* 
             ur[r] = a.u[g];
           }
         }
-        for (bool more = true; more;) {
-          more = false;
-#pragma unroll
-          for (int r = 0; r < kBR; ++r)
-            if (pp[r] < pe[r]) {
-              sr[r] += a.valt[pp[r]] * ys[a.colt[pp[r]] - m0];
-              pp[r] += kLPR;
-              more |= pp[r] < pe[r];
-            }
-        }
+        rows_dot<T>(pp, pe, a.valt, a.colt, ys, m0, sr);
 #pragma unroll
         for (int r = 0; r < kBR; ++r) sr[r] = group_sum(sr[r]);
         if (gl == 0) {
@@ -305,16 +337,7 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, int* 
             ucr[r] = a.uc[g];
           }
         }
-        for (bool more = true; more;) {
-          more = false;
-#pragma unroll
-          for (int r = 0; r < kBR; ++r)
-            if (pp[r] < pe[r]) {
-              sr[r] += a.val[pp[r]] * xs[a.col[pp[r]] - n0];
-              pp[r] += kLPR;
-              more |= pp[r] < pe[r];
-            }
-        }
+        rows_dot<T>(pp, pe, a.val, a.col, xs, n0, sr);
 #pragma unroll
         for (int r = 0; r < kBR; ++r) sr[r] = group_sum(sr[r]);
         if (gl == 0) {
