@@ -114,7 +114,9 @@ typedef struct mpax_options {
   double restart_artificial;  /* 0.36 */
   double primal_weight_smoothing; /* 0.5 */
   double step_safety;         /* 0.998: eta = step_safety / ||A~||_2 */
-  int32_t power_max_iter;     /* 1000 */
+  int32_t power_max_iter;     /* 1000.  0 (LPs, with pock_chambolle): no power
+                                 iteration; ||A~||_2 := 1, the bound that the
+                                 Pock-Chambolle round guarantees (Schur's test) */
   double power_tol;           /* 1e-4.  Power iteration for ||A~||_2 (and ||Q~||_2)
                                  from a fixed pseudo-random start vector (entries
                                  2u-1, u from SplitMix64 of the index); it stops

@@ -26,7 +26,9 @@ implements the same written rules.  The readings are:
     A~^T A~ started at a fixed pseudo-random vector of entries in [-1, 1]
     (SplitMix64 of the index, see power_start).  After the Pock-Chambolle round
     ||A~||_2 <= 1 (Schur's test), and the iteration stops, using 1, once its
-    extrapolated estimate is within 1e-3 of that bound.  The estimates rise towards the norm
+    extrapolated estimate is within 1e-3 of that bound; power_max_iter = 0
+    takes that bound without any power round (on small instances the rounds
+    cost as much as the solve).  The estimates rise towards the norm
     with geometrically shrinking increments d_t (ratio q); the iteration stops
     when d_t and the extrapolated remainder d_t q / (1 - q) are both at most
     1e-4 of the estimate (or after 1000 rounds) and returns the estimate plus
@@ -300,6 +302,10 @@ def power_norm_A(A: sp.csr_matrix, max_iter: int = 1000, tol: float = 1e-4,
     n = A.shape[1]
     if n == 0 or A.nnz == 0:
         return 0.0, 0
+    if max_iter == 0:                 # no power iteration: the certified bound itself
+        if not math.isfinite(cap):
+            raise ValueError("power_max_iter = 0 needs a certified bound on ||A~||_2")
+        return cap, 0
     v = power_start(n)
     nu_prev, d_prev = None, 0.0
     for t in range(1, max_iter + 1):

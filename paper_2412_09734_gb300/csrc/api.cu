@@ -353,7 +353,10 @@ mpax_status check_options(const mpax_options* o) {
   if (o->ruiz_iters < 0) return fail(MPAX_ERR_INVALID_ARGUMENT, "ruiz_iters must be >= 0");
   if (!(o->step_safety > 0.0 && o->step_safety < 1.0))
     return fail(MPAX_ERR_INVALID_ARGUMENT, "step_safety must be in (0, 1)");
-  if (o->power_max_iter < 1) return fail(MPAX_ERR_INVALID_ARGUMENT, "power_max_iter must be >= 1");
+  if (o->power_max_iter < 0) return fail(MPAX_ERR_INVALID_ARGUMENT, "power_max_iter must be >= 0");
+  if (o->power_max_iter == 0 && !o->pock_chambolle)
+    return fail(MPAX_ERR_INVALID_ARGUMENT,
+                "power_max_iter = 0 takes the bound ||A~||_2 <= 1 of the Pock-Chambolle round");
   if (o->feasibility_polishing && !(o->eps_feas_polish > 0.0))
     return fail(MPAX_ERR_INVALID_ARGUMENT, "eps_feas_polish must be > 0");
   if (!(o->time_limit >= 0)) return fail(MPAX_ERR_INVALID_ARGUMENT, "time_limit must be >= 0");
@@ -365,6 +368,8 @@ mpax_status check_options(const mpax_options* o) {
 mpax_status do_prepare(mpax_problem* pb, const mpax_options* o, long long* launches) {
   ProblemData& P = pb->P;
   cudaStream_t s = P.s;
+  if (P.is_qp && o->power_max_iter == 0)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "power_max_iter = 0 is for LPs (||Q~|| has no bound)");
   // structure: transpose(s) and work-item schedules
   TRY_CUDA(transpose_csr(P.A, P.At, P.permT, P.tmp_rows, P.tmp_scan, s), "transpose");
   *launches += 6;

@@ -180,6 +180,7 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, int* 
   __syncthreads();
   double nA = 0.0, nu_prev = 0.0, d_prev = 0.0;
   const bool has_rows = mb > 0 && rpl[mb] > rpl[0];
+  if (has_rows && a.power_max_iter == 0) nA = a.power_cap;  // the certified bound
   for (int t = 1; has_rows && t <= a.power_max_iter; ++t) {
     for (int i0 = 0; i0 < mb; i0 += G) {
       const int i = i0 + grp;
@@ -809,7 +810,8 @@ mpax_status mpax_batch_solve(mpax_batch* bt, const mpax_options* o) {
   if (o->reflection_gamma != 1.0)
     return bfail(MPAX_ERR_UNSUPPORTED, "the batch path implements reflection_gamma = 1");
   if (o->check_every < 1 || o->iteration_limit < 1 || o->ruiz_iters < 0 ||
-      !(o->step_safety > 0 && o->step_safety < 1) || o->power_max_iter < 1 ||
+      !(o->step_safety > 0 && o->step_safety < 1) || o->power_max_iter < 0 ||
+      (o->power_max_iter == 0 && !o->pock_chambolle) ||
       !(o->time_limit >= 0))
     return bfail(MPAX_ERR_INVALID_ARGUMENT, "invalid options");
   if (o->precision != MPAX_PREC_FP64 && o->precision != MPAX_PREC_MIXED)

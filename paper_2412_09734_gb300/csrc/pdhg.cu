@@ -204,6 +204,14 @@ __global__ void k_zero_finite(T* __restrict__ lo, T* __restrict__ hi, int k) {
   }
 }
 
+// ||A~||_2 := 1, the bound of the Pock-Chambolle round (power_max_iter = 0).
+__global__ void k_power_bound(DevState* st, int mode) {
+  st->pw_nu = 1.0;
+  st->pw_done = 1;
+  st->pw_iters = 0;
+  if (mode == 0) st->norm_A = 1.0;
+}
+
 // The normalised start vector of the power iterations (power_start_raw).
 template <typename T>
 __global__ void k_power_vec(T* __restrict__ v, int n, double inv_norm) {
@@ -643,8 +651,14 @@ class Engine final : public EngineBase {
     cudaStream_t s = P.s;
     const int n = P.n;
     k_power_start<<<1, 1, 0, s>>>(st_);
+    *launches += 1;
+    if (o.power_max_iter == 0) {  // the certified bound of the Pock-Chambolle round
+      k_power_bound<<<1, 1, 0, s>>>(st_, mode);
+      *launches += 1;
+      return cudaGetLastError();
+    }
     k_power_vec<T><<<grid1(n), 256, 0, s>>>(pv_, n, 1.0 / power_start_norm(n));
-    *launches += 2;
+    *launches += 1;
     T* v = pv_;
     T* g = pg_;
     const int* skip = &st_->pw_done;

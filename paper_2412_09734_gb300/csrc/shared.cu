@@ -634,7 +634,8 @@ mpax_status mpax_lp_shared_create(int32_t m, int32_t n, int32_t B, const float* 
 mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp32_products) {
   if (!sh || !o) return sfail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
   if (o->reflection_gamma != 1.0 || o->check_every < 1 || o->iteration_limit < 1 ||
-      !(o->time_limit >= 0))
+      !(o->time_limit >= 0) || o->power_max_iter < 0 ||
+      (o->power_max_iter == 0 && !o->pock_chambolle))
     return sfail(MPAX_ERR_INVALID_ARGUMENT, "invalid options (reflection_gamma must be 1)");
   const auto t0 = std::chrono::steady_clock::now();
   const int m = sh->m, n = sh->n, B = sh->B;
@@ -711,6 +712,7 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
       if (t == o->power_max_iter && std::isfinite(cap)) nu = cap;
       prev = nu;
     }
+    if (o->power_max_iter == 0) nu = 1.0;  // the bound of the Pock-Chambolle round
     sh->norm_A = nu;
   }
   const double eta = sh->norm_A > 0 ? o->step_safety / sh->norm_A : 1.0;

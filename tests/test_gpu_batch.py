@@ -51,13 +51,15 @@ def _fp32_kkt_bound(p, x, y, chk):
     return max(dp, dd, dg)
 
 
-@pytest.mark.parametrize("prec,eps", [(0, 1e-6), (1, 1e-4)])
-def test_batch_matches_oracle_per_instance(C, prec, eps):
+@pytest.mark.parametrize("prec,eps,pmax", [(0, 1e-6, 1000), (1, 1e-4, 1000), (0, 1e-6, 0),
+                                           (1, 1e-4, 0)])
+def test_batch_matches_oracle_per_instance(C, prec, eps, pmax):
     d = ragged_lp_batch(24, seed=5150, m_lo=20, m_hi=300, density=0.05)
     h = _create(C, d, device=(prec == 1))
     try:
         C.mpax_batch_solve(h, C.mpax_options_default(precision=prec, eps_abs=eps, eps_rel=eps,
-                                                     iteration_limit=500000))
+                                                     iteration_limit=500000,
+                                                     power_max_iter=pmax))
         summary, per = C.mpax_batch_get_stats(h, d["B"])
         x, y = C.mpax_batch_get_solution(h, int(d["m_off"][-1]), int(d["n_off"][-1]))
     finally:
@@ -80,7 +82,8 @@ def test_batch_matches_oracle_per_instance(C, prec, eps):
             assert chk["rel_kkt"] == pytest.approx(per["rel_kkt"][b], rel=1e-8, abs=1e-12)
         assert chk["primal_obj"] == pytest.approx(inst["opt_value"], rel=30 * eps, abs=30 * eps)
         if prec == 0 and b < 8:
-            ref = O.solve_lp(p, O.Options(eps_abs=eps, eps_rel=eps, iteration_limit=500000))
+            ref = O.solve_lp(p, O.Options(eps_abs=eps, eps_rel=eps, iteration_limit=500000,
+                                          power_max_iter=pmax))
             # the same written rules give the same trajectory up to rounding
             assert abs(per["iterations"][b] - ref.iterations) <= 2 * 64
 

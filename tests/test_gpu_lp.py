@@ -365,3 +365,25 @@ def test_mixed_with_fp64_continuation_reaches_1e8(C):
     assert chk["primal_obj"] == pytest.approx(d["opt_value"], rel=1e-7)
     # FP32 alone does not get there
     assert plain["termination_name"] == "iteration_limit" and plain["rel_kkt"] > 1e-8
+
+
+def test_certified_norm_bound_without_power_iteration(C):
+    """power_max_iter = 0 takes ||A~||_2 := 1 (the Pock-Chambolle bound): the FP64
+    solve follows the oracle's run with the same rule."""
+    d = lp_instance(200, 400, seed=instance_seed(77), density=0.02, variant="nondegenerate")
+    p = O.problem_from_arrays(d)
+    ref = O.solve_lp(p, O.Options(eps_abs=1e-8, eps_rel=1e-8, power_max_iter=0))
+    h = create(C, d)
+    try:
+        C.mpax_solve(h, C.mpax_options_default(precision=0, eps_abs=1e-8, eps_rel=1e-8,
+                                               power_max_iter=0))
+        s = C.mpax_get_stats(h)
+        x, y = C.mpax_get_solution(h, d["m"], d["n"])
+        with pytest.raises(Exception):
+            C.mpax_solve(h, C.mpax_options_default(power_max_iter=0, pock_chambolle=0))
+    finally:
+        C.mpax_destroy(h)
+    assert s["norm_A"] == 1.0
+    assert s["termination_name"] == "optimal"
+    assert abs(s["iterations"] - ref.iterations) <= 2 * 64
+    assert O.kkt(p, x, y, 1e-8, 1e-8)["converged"]
