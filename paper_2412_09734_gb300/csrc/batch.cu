@@ -27,11 +27,20 @@ namespace mpax {
 
 constexpr int kBatchThreads = 512;
 constexpr double kBatchMaxSeconds = 600.0;
-constexpr int kLPR = 8;  // lanes cooperating on one row
-// Rows each 8-lane group carries per step of a half-step (their memory round
-// trips overlap); 2 doubles the work in flight at the price of register spills.
+// Lanes cooperating on one row of an instance (a power of two <= 32).  Rows of
+// the batch recipe hold ~1-40 nonzeros: measured on 4096 instances, 2 lanes per
+// row (0.325 s per batch mixed, 0.450 s FP64) beat 8 (0.490 / 0.956 s) and 1
+// (0.521 / 0.597 s) -- with 8 lanes a row's shuffle reduction and its one-lane
+// epilogue cost more than its two or three loads per lane.
+#ifndef MPAX_BATCH_LPR
+#define MPAX_BATCH_LPR 2
+#endif
+constexpr int kLPR = MPAX_BATCH_LPR;
+// Rows each lane group carries per step of a half-step (their memory round
+// trips overlap).  With 2-lane groups a step already covers 256 rows, and 1 row
+// per group measured best (0.325 against 0.329 s per 4096-instance batch).
 #ifndef MPAX_BATCH_ROWS
-#define MPAX_BATCH_ROWS 2
+#define MPAX_BATCH_ROWS 1
 #endif
 constexpr int kBR = MPAX_BATCH_ROWS;
 // Values and columns each lane loads per row before using any (see rows_dot).
@@ -272,7 +281,7 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, int* 
       const bool chk = (it == len - 1);
       const T rb = (T)(1.0 / (double)(k + 1));  // rebuild weight of x^{n,k}
       const T hb = (T)(1.0 / (double)(k + 2));  // Halpern weight of the anchor
-      // primal half-step over the rows of A^T (eq. 3, first line).  Each 8-lane
+      // primal half-step over the rows of A^T (eq. 3, first line).  Each kLPR-lane
       // group takes kBR rows per step (j, j + G, ...) and issues the row pointers,
       // the epilogue operands and both rows' products before reducing, so every
       // dependent round trip to memory is shared by kBR rows.
