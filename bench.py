@@ -683,8 +683,18 @@ def run_knapsack(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     summ, per = C.mpax_shared_get_stats(h, 1)
-    C.mpax_shared_destroy(h)
     its = int(per["iterations"][0])
+    # the paper's protocol for this instance (Table 2): a fixed 10,000 iterations
+    o10k = C.mpax_options_default(iteration_limit=10000, eps_abs=1e-14, eps_rel=1e-14)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e2.record()
+    C.mpax_shared_solve(h, o10k, True)
+    e3.record()
+    torch.cuda.synchronize()
+    s10k = e2.elapsed_time(e3) / 1e3
+    C.mpax_shared_destroy(h)
     # two matrix-vector products per iteration and two per check, each reading A (FP32)
     products = 2 * its + 2 * (its // 64 + 1)
     a_bytes = 4.0 * dd * mm
@@ -704,6 +714,10 @@ def run_knapsack(args):
                                  "solve time (vector traffic and the other kernels "
                                  "included in the time): a lower bound on the GEMV rate",
                          "peak_source": src + ", of measured"},
+            "time_10k_iterations_s": s10k,
+            "paper_context": {"time_10k_iterations_s": 2.49, "hardware": "NVIDIA H200 SXM",
+                              "precision": "FP32", "source": "Table 2",
+                              "ratio_this_over_paper": s10k / 2.49},
             "clocks": clk, "gpu_launches": summ["kernel_launches"]}
     print(json.dumps(line), flush=True)
     return 0
