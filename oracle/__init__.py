@@ -11,4 +11,7 @@ Modules
   brute  -- brute-force checkers that pin the converged answers: LP vertex
             enumeration and QP active-set enumeration on tiny instances.
   adjoint -- LP optimal-value gradients and the QP active-set implicit adjoint.
+  unrolled -- gradients of a QP solve by differentiating through its rAPDHG
+            steps along the path it took (reverse sweep over the taped path).
+  spo    -- the SPO+ surrogate loss and its subgradient.
 """

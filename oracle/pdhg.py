@@ -638,8 +638,11 @@ def polish_lp(p: Problem, x, y, opts: Options = Options(), eps_feas_polish: floa
 
 
 def solve_qp(p: Problem, opts: Options = Options(), x_init=None, y_init=None,
-             keep_history=False) -> Result:
-    """rAPDHG (Algorithm 2) on the scaled QP."""
+             keep_history=False, tape=None) -> Result:
+    """rAPDHG (Algorithm 2) on the scaled QP.  With a list `tape`, every step
+    appends ("step", k, tau, sigma, x, y, xavg, yavg) -- its inner counter,
+    step sizes and the scaled state it starts from -- and every restart appends
+    ("restart",); oracle.unrolled differentiates along that record."""
     ps, Dr, Dc, nA, nQ, eta, omega = prepare(p, opts)
     x = np.zeros(p.n) if x_init is None else np.asarray(x_init, dtype=np.float64) / Dc
     y = np.zeros(p.m) if y_init is None else np.asarray(y_init, dtype=np.float64) / Dr
@@ -653,6 +656,8 @@ def solve_qp(p: Problem, opts: Options = Options(), x_init=None, y_init=None,
     r_prev = None
     hist = []
     while True:
+        if tape is not None:
+            tape.append(("step", k, tau, sigma, x.copy(), y.copy(), xavg.copy(), yavg.copy()))
         x, y, xavg, yavg, _ = apdhg_step_qp(ps, x, y, xavg, yavg, k, tau, sigma)
         total += 1
         k += 1
@@ -676,6 +681,8 @@ def solve_qp(p: Problem, opts: Options = Options(), x_init=None, y_init=None,
                 restarts += 1
                 r_anchor = r
                 r_prev = r
+                if tape is not None:
+                    tape.append(("restart",))
                 continue
             r_prev = r
 
