@@ -637,6 +637,33 @@ def run_qp(args):
         out[name] = dict(steps_per_s=1e3 / ms, ms_per_step=ms, iterations=float(np.mean(its)),
                          backward_s=float(np.mean(bw)), adjoint_rel_residual=max(res),
                          clocks=clk, gpu_launches=launches)
+    # the paper's own QP gradient: differentiation through the FP64 iterations
+    # (tape of the path, replay and reverse sweep), against the implicit adjoint
+    h = C.mpax_qp_create_diag_lowrank(
+        m, n, dev["row_ptr"], dev["col"], dev["val"], dev["c"], dev["lc"], dev["uc"], dev["l"],
+        dev["u"], dev["D"], d["f_cols"], dev["f_row_ptr"], dev["f_col"], dev["f_val"])
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        C.mpax_solve(h, C.mpax_options_default(precision=C.MPAX_PREC_FP64, record_tape=1))
+        t1 = time.perf_counter()
+        s = C.mpax_get_stats(h)
+        x, _ = C.mpax_get_solution(h, m, n, device=xt)
+        t2 = time.perf_counter()
+        G = C.mpax_qp_unrolled_grad(h, x - xt, m, n)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        back_launches = C.mpax_get_stats(h)["kernel_launches"]
+        dc, _, _, _ = C.mpax_qp_adjoint(h, x - xt, m, n, tol=1e-8)
+        rel = float(torch.linalg.norm(G["c"] - dc) / torch.linalg.norm(dc))
+    finally:
+        C.mpax_destroy(h)
+    blocks = -(-s["iterations"] // 64)
+    out["unrolled_fp64"] = dict(forward_s=t1 - t0, backward_s=t3 - t2,
+                                iterations=s["iterations"], restarts=s["restarts"],
+                                tape_bytes=blocks * (64 + 8 * 2 * (n + m)),
+                                backward_launches=back_launches,
+                                dc_rel_diff_vs_implicit_adjoint=rel)
     line = {"metric": "differentiable QP forward (rel KKT 1e-4) + backward steps/s",
             "value": out["mixed"]["steps_per_s"], "unit": "steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["mixed"]["ms_per_step"],
@@ -644,7 +671,7 @@ def run_qp(args):
             "data": "synthetic",
             "config": {"workload": f"QP n={n} m={m}, Q = diag(U[0.1,1]) + F F^T (F n x 32, 1%), "
                                    f"A 0.01% N(0,1), box [-1,1], b = A x0; loss 1/2||x*-x_t||^2"},
-            "mixed": out["mixed"], "fp64": out["fp64"],
+            "mixed": out["mixed"], "fp64": out["fp64"], "unrolled_fp64": out["unrolled_fp64"],
             "speedup_vs_fp64": out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"],
             "clocks": out["mixed"]["clocks"], "gpu_launches": out["mixed"]["gpu_launches"]}
     print(json.dumps(line), flush=True)

@@ -132,6 +132,12 @@ typedef struct mpax_options {
                                  checks so far / 4) checks) continues in FP64 from
                                  its FP32 point */
   int32_t stall_checks;       /* 8: the shortest stall window, in checks */
+  int32_t record_tape;        /* 0.  1 (QP, FP64 precision): keep one record per check
+                                 block -- step sizes, counters, restart flag and the
+                                 block's start state (x, xavg, y, yavg), i.e.
+                                 2(n + m) values -- for mpax_qp_unrolled_grad.  The
+                                 records stay in device memory until the next
+                                 mpax_solve or mpax_destroy. */
 } mpax_options;
 
 typedef struct mpax_stats {
@@ -275,6 +281,21 @@ mpax_status mpax_lp_value_grad(mpax_problem* prob, double* dc, double* dlc, doub
 mpax_status mpax_qp_adjoint(mpax_problem* prob, const double* g, double* dc, double* db,
                             double* dD, double tol, int32_t max_iter, mpax_mem_kind kind,
                             double* info);
+
+/* Gradients of a QP solve by differentiating through its iterations (Sec. 3.4:
+ * the paper differentiates QPs by unrolling Algorithm 2).  The last mpax_solve
+ * of `prob` must have run with record_tape = 1 and precision FP64.  For the
+ * loss L = gx . x + gy . y at its returned point (x, y), the derivative is
+ * taken along the path that solve took: its restarts, step sizes (primal
+ * weight), scaling and stopping point held fixed, each projection with
+ * derivative 1 strictly inside its interval and 0 at or beyond a bound (and 1
+ * in the bound it returned).  Outputs, all nullable: dc, dl, du, dD (n),
+ * dlc, duc (m); an equality row's dL/db is dlc + duc.  gy is nullable (zero).
+ * Cost: every block of the path is replayed once and run backwards, about two
+ * forward solves.  MPAX_ERR_NOT_SOLVED without a taped solve. */
+mpax_status mpax_qp_unrolled_grad(mpax_problem* prob, const double* gx, const double* gy,
+                                  double* dc, double* dlc, double* duc, double* dl,
+                                  double* du, double* dD, mpax_mem_kind kind);
 
 /* ---- Ragged batch of independent LPs ---------------------------------------- */
 

@@ -3,6 +3,9 @@ adjoint run in the library's kernels).
 
 QPLayer: x* = argmin 1/2 x^T (diag(D) + F F^T) x + c^T x  s.t.  A x = b, l <= x <= u,
          differentiable in (c, b, D) through the implicit adjoint on the active set.
+QPUnrolledLayer: the same solution map differentiated through the solver's
+         iterations (the paper's QP gradients): the solve records its path and the
+         backward runs the path in reverse.
 LPValue: v = min c^T x  s.t.  lc <= A x <= uc, l <= x <= u, differentiable in
          (c, lc, uc) through the envelope theorem (dv/dc = x*, ...).
 SharedLPValues: v_k = min c_k^T x  s.t.  lc <= A x <= uc, l <= x <= u for the B rows
@@ -52,6 +55,41 @@ class QPLayer(torch.autograd.Function):
             C.mpax_destroy(ctx.h)
             ctx.h = None
         return dc.to(gx.dtype), db.to(gx.dtype), dD.to(gx.dtype), None, None
+
+
+class QPUnrolledLayer(torch.autograd.Function):
+    """forward(c, b, D, data, options) -> x*, as QPLayer, in FP64 with the path
+    recorded (record_tape); backward: gradients of the returned point along that
+    path (restarts, step sizes and stopping point held fixed), which tend to
+    QPLayer's as the solve converges.  Costs about two forward solves."""
+
+    @staticmethod
+    def forward(ctx, c, b, D, data, options):
+        d = data
+        opts = dict(options or {})
+        opts.update(record_tape=1, precision=C.MPAX_PREC_FP64)
+        h = C.mpax_qp_create_diag_lowrank(
+            d["m"], d["n"], d["row_ptr"], d["col"], d["val"], _f64(c), _f64(b), _f64(b),
+            d["l"], d["u"], _f64(D), d["r"], d["f_row_ptr"], d["f_col"], d["f_val"])
+        try:
+            C.mpax_solve(h, C.mpax_options_default(**opts))
+            x, _ = C.mpax_get_solution(h, d["m"], d["n"], device=c)
+        except Exception:
+            C.mpax_destroy(h)
+            raise
+        ctx.h = h
+        ctx.m, ctx.n = d["m"], d["n"]
+        return x.to(c.dtype)
+
+    @staticmethod
+    def backward(ctx, gx):
+        try:
+            g = C.mpax_qp_unrolled_grad(ctx.h, _f64(gx), ctx.m, ctx.n)
+        finally:
+            C.mpax_destroy(ctx.h)
+            ctx.h = None
+        db = g["lc"] + g["uc"]
+        return g["c"].to(gx.dtype), db.to(gx.dtype), g["D"].to(gx.dtype), None, None
 
 
 class LPValue(torch.autograd.Function):

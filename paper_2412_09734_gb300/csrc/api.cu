@@ -362,6 +362,8 @@ mpax_status check_options(const mpax_options* o) {
   if (!(o->time_limit >= 0)) return fail(MPAX_ERR_INVALID_ARGUMENT, "time_limit must be >= 0");
   if (o->fp64_continuation && o->stall_checks < 1)
     return fail(MPAX_ERR_INVALID_ARGUMENT, "stall_checks must be >= 1");
+  if (o->record_tape && o->precision != MPAX_PREC_FP64)
+    return fail(MPAX_ERR_UNSUPPORTED, "record_tape needs precision FP64");
   return MPAX_OK;
 }
 
@@ -474,6 +476,7 @@ void mpax_options_default(mpax_options* o) {
   o->profile_kernels = 0;
   o->fp64_continuation = 1;
   o->stall_checks = 8;
+  o->record_tape = 0;
 }
 
 mpax_status mpax_lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
@@ -516,6 +519,8 @@ mpax_status mpax_solve(mpax_problem* pb, const mpax_options* opts, const double*
   if (kind != MPAX_MEM_HOST && kind != MPAX_MEM_DEVICE)
     return fail(MPAX_ERR_INVALID_ARGUMENT, "bad memory kind");
   ProblemData& P = pb->P;
+  if (opts->record_tape && !P.is_qp)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "record_tape is for QPs");
   const double t0 = now_s();
   TRY_CUDA(order_after_user(pb), "stream order");
   long long launches = 0;
@@ -672,6 +677,61 @@ mpax_status mpax_get_solution(const mpax_problem* cpb, double* x, double* y,
   if (x) TRY_CUDA(copy_out(x, sx, sizeof(double) * P.n, kind, P.s), "copy x");
   if (y) TRY_CUDA(copy_out(y, sy, sizeof(double) * P.m, kind, P.s), "copy y");
   TRY_CUDA(cudaStreamSynchronize(P.s), "get solution");
+  return MPAX_OK;
+}
+
+mpax_status mpax_qp_unrolled_grad(mpax_problem* pb, const double* gx, const double* gy,
+                                  double* dc, double* dlc, double* duc, double* dl,
+                                  double* du, double* dD, mpax_mem_kind kind) {
+  if (!pb || !gx) return fail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  if (kind != MPAX_MEM_HOST && kind != MPAX_MEM_DEVICE)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "bad memory kind");
+  ProblemData& P = pb->P;
+  if (!P.is_qp) return fail(MPAX_ERR_INVALID_ARGUMENT, "mpax_qp_unrolled_grad needs a QP");
+  if (!pb->solved || !pb->last_opts.record_tape || pb->cur != MPAX_PREC_FP64)
+    return fail(MPAX_ERR_NOT_SOLVED, "solve with record_tape = 1 (FP64) first");
+  const int n = P.n, m = P.m;
+  cudaStream_t s = P.s;
+  TRY_CUDA(order_after_user(pb), "stream order");
+  // device buffers: the loss gradients in, the six gradients out
+  double* buf = nullptr;
+  const size_t N = (size_t)n, M = (size_t)m;
+  TRY_CUDA(cudaMalloc(&buf, sizeof(double) * (6 * N + 4 * M + 8)), "unrolled buffers");
+  double* dgx = buf;
+  double* dgy = dgx + N;
+  double* ogc = dgy + M;
+  double* ogl = ogc + N;
+  double* ogu = ogl + N;
+  double* ogD = ogu + N;
+  double* oglc = ogD + N;
+  double* oguc = oglc + M;
+  const cudaMemcpyKind kin =
+      kind == MPAX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind kout =
+      kind == MPAX_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  cudaError_t e = cudaMemcpyAsync(dgx, gx, sizeof(double) * N, kin, s);
+  if (!e && gy && m) e = cudaMemcpyAsync(dgy, gy, sizeof(double) * M, kin, s);
+  long long launches = 0;
+  if (!e)
+    e = pb->eng[pb->cur]->unrolled_backward(dgx, gy ? dgy : nullptr, ogc, oglc, oguc, ogl, ogu,
+                                            ogD, &launches);
+  if (e == cudaErrorNotReady) {
+    cudaFree(buf);
+    cudaGetLastError();
+    return fail(MPAX_ERR_NOT_SOLVED, "no tape: solve with record_tape = 1 (FP64) first");
+  }
+  struct {
+    double* dst;
+    const double* src;
+    size_t k;
+  } outs[] = {{dc, ogc, N}, {dl, ogl, N}, {du, ogu, N}, {dD, ogD, N}, {dlc, oglc, M}, {duc, oguc, M}};
+  for (auto& o : outs)
+    if (!e && o.dst && o.k) e = cudaMemcpyAsync(o.dst, o.src, sizeof(double) * o.k, kout, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  cudaFree(buf);
+  if (e) return cuda_fail(e, "unrolled gradient");
+  TRY_CUDA(order_user_after(pb), "stream order");
+  pb->stats.kernel_launches = launches;
   return MPAX_OK;
 }
 

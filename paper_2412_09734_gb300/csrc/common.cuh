@@ -106,10 +106,12 @@ struct DevState {
   double pw_scale, pw_nu;  // power iteration: 1/||g|| of the last round, estimate
   double pw_d;             // power iteration: last increment of the estimate
   long long total, k_base, restarts, checks, iter_limit;
+  long long tape_cursor;  // unrolled differentiation: the record the backward pass is on
   int pw_done, pw_iters, stall_limit, stall_count;
   double best_rel;
   double eps_pi, eps_di;  // infeasibility tolerances (LP; <= 0 turns a test off)
-  int feas_mode, pad2;    // 0: KKT test; 1 / 2: primal / dual residual alone (polishing)
+  int feas_mode;          // 0: KKT test; 1 / 2: primal / dual residual alone (polishing)
+  int tape_err;           // a taped block found no record to write
   int done, restart_flag, termination, have_anchor;
   int check_every, is_qp, nan_seen, pad;
   // Halpern / averaging coefficient table for the current block:
@@ -196,6 +198,13 @@ __device__ __forceinline__ T clampv(T v, T lo, T hi) {
 template <>
 __device__ __forceinline__ float clampv<float>(float v, float lo, float hi) {
   return fminf(fmaxf(v, lo), hi);
+}
+
+// Which value clampv(v, lo, hi) returned: 0 v itself (lo < v < hi), 1 lo, 2 hi.
+template <typename T>
+__device__ __forceinline__ unsigned char clamp_code(T v, T lo, T hi) {
+  if (v > lo && v < hi) return 0;
+  return (v > lo) ? 2 : 1;
 }
 
 template <typename T>

@@ -40,6 +40,13 @@ class EngineBase {
   // primal residual; 2 = every finite bound set to zero, the run ends on the
   // dual residual; 0 = the problem as loaded.  Call init_state afterwards.
   virtual cudaError_t set_feasibility(int mode) = 0;
+  // Unrolled differentiation (QP, FP64) of the last run, which had
+  // record_tape set: gradients of gx . x + gy . y at its returned point along
+  // its path.  Device vectors; gy nullable; gc, gl, gu, gD have n entries,
+  // glc, guc m.  cudaErrorNotReady: no tape.
+  virtual cudaError_t unrolled_backward(const double* gx, const double* gy, double* gc,
+                                        double* glc, double* guc, double* gl, double* gu,
+                                        double* gD, long long* launches) = 0;
 };
 
 EngineBase* make_engine(ProblemData* P, int precision, cudaError_t* err);

@@ -139,7 +139,9 @@ struct EpiDualLP {
 //   x+ = proj_[l,u](x - tau (q + c - t))            (eq. 6)
 //   xref = 2 x+ - x;  xavg+ = xavg + theta (x+ - xavg)
 // check partials: [1] sum (xavg+ - x_anchor)^2
-template <typename T>
+// TAPE (replay of a block for the reverse sweep): also writes x_md and the
+// clamp code of the projection (0 inside, 1 at l, 2 at u).
+template <typename T, bool TAPE = false>
 struct EpiPrimalQP {
   static constexpr int NQ = 2;
   struct Pre {
@@ -161,6 +163,8 @@ struct EpiPrimalQP {
   const T* uvec;
   T* xprev;
   int it, record, check;
+  T* tape_xmd;
+  unsigned char* tape_code;
   T tau, beta;
   __device__ __forceinline__ bool skip() const { return st->done != 0; }
   __device__ __forceinline__ void load() {
@@ -182,7 +186,12 @@ struct EpiPrimalQP {
     const T xmd = p.xa + beta * (p.x - p.xa);
     T q = p.d * xmd;
     for (int k = p.f0; k < p.f1; ++k) q += fval[k] * uvec[fcol[k]];
-    const T xn = clampv<T>(p.x - tau * (q + p.c - t), p.l, p.u);
+    const T vx = p.x - tau * (q + p.c - t);
+    const T xn = clampv<T>(vx, p.l, p.u);
+    if constexpr (TAPE) {
+      tape_xmd[j] = xmd;
+      tape_code[j] = clamp_code<T>(vx, p.l, p.u);
+    }
     xref[j] = (T)2 * xn - p.x;
     x[j] = xn;
     const T xan = p.xa + beta * (xn - p.xa);
@@ -197,7 +206,8 @@ struct EpiPrimalQP {
 
 // Dual step over the rows of A, s = (A xref)_i (eq. 5 second line), then the
 // weighted average.  check partials: [1] sum (yavg+ - y_anchor)^2
-template <typename T>
+// TAPE: also writes the clamp code of proj_[-uc,-lc] (0 inside, 1 at -uc, 2 at -lc).
+template <typename T, bool TAPE = false>
 struct EpiDualQP {
   static constexpr int NQ = 2;
   struct Pre {
@@ -210,6 +220,7 @@ struct EpiDualQP {
   const T* lc;
   const T* uc;
   int it, check;
+  unsigned char* tape_code;
   T sigma, inv_sigma, theta;
   __device__ __forceinline__ bool skip() const { return st->done != 0; }
   __device__ __forceinline__ void load() {
@@ -227,6 +238,7 @@ struct EpiDualQP {
   __device__ __forceinline__ void row(int i, T s, const Pre& p, double* acc) {
     const T v = p.y * inv_sigma - s;
     const T yn = sigma * (v - clampv<T>(v, -p.uc, -p.lc));
+    if constexpr (TAPE) tape_code[i] = clamp_code<T>(v, -p.uc, -p.lc);
     y[i] = yn;
     const T yan = p.ya + theta * (yn - p.ya);
     yavg[i] = yan;

@@ -14,9 +14,12 @@
 #include <map>
 #include <vector>
 
+#include <type_traits>
+
 #include "engine.cuh"
 #include "epilogues.cuh"
 #include "kernels.cuh"
+#include "unrolled.cuh"
 
 namespace mpax {
 
@@ -85,6 +88,26 @@ __device__ void fill_table(DevState* st, int len) {
     }
   }
 }
+
+// Unrolled differentiation, backward: open the previous tape record
+// (tape_cursor - 1): its step sizes and averaging table, iteration on.
+__global__ void k_tape_open(DevState* st, char* const* tab) {
+  __shared__ int len;
+  if (threadIdx.x == 0) {
+    const long long slot = --st->tape_cursor;
+    const TapeHead* h = reinterpret_cast<const TapeHead*>(tab[slot]);
+    st->tau = h->tau;
+    st->sigma = h->sigma;
+    st->inv_sigma = 1.0 / h->sigma;
+    st->k_base = h->k_base;
+    st->done = 0;
+    len = h->len;
+  }
+  __syncthreads();
+  fill_table(st, len);
+}
+
+__global__ void k_set_cursor(DevState* st, long long v) { st->tape_cursor = v; }
 
 __global__ void k_set_table(DevState* st, long long k_base, int len) {
   if (threadIdx.x == 0) st->k_base = k_base;
@@ -610,6 +633,9 @@ class Engine final : public EngineBase {
     for (void* b : bufs)
       if (b) cudaFree(b);
     if (hs_) cudaFreeHost(hs_);
+    tape_free();
+    if (tape_tab_) cudaFree(tape_tab_);
+    if (tape_tab_h_) cudaFreeHost(tape_tab_h_);
   }
 
   cudaError_t set_feasibility(int mode) override {
@@ -752,6 +778,11 @@ class Engine final : public EngineBase {
     ProblemData& P = *P_;
     cudaStream_t s = P.s;
     const bool qp = P.is_qp;
+    if (tape_on_ && !plain) {
+      k_tape_save<T><<<grid1(std::max(P.n, P.m)), 256, 0, s>>>(
+          st_, tape_tab_, kTapeSlots, P.n, P.m, x_, xavg_, y_, yavg_, len);
+      launches_ += 1;
+    }
     for (int it = 0; it < len; ++it) {
       const bool last = (it == len - 1) && !plain;
       const int rec = (record_all || last) ? 1 : 0;
@@ -879,7 +910,8 @@ class Engine final : public EngineBase {
       graph_launches_.clear();
       graph_gen_ = sched_generation;
     }
-    const long long key = (long long)len + 4096LL * block_ + (gamma_one_ ? (1LL << 40) : 0);
+    const long long key = (long long)len + 4096LL * block_ + (gamma_one_ ? (1LL << 40) : 0) +
+                          (tape_on_ ? (1LL << 41) : 0);
     auto itg = graphs_.find(key);
     if (itg != graphs_.end()) {
       *out = itg->second;
@@ -917,6 +949,14 @@ class Engine final : public EngineBase {
     const bool prof = o.profile_kernels != 0;
     const bool graphs = o.use_graphs != 0 && !prof;
     const long long limit = o.iteration_limit;
+    tape_on_ = o.record_tape != 0 && P.is_qp;
+    tape_valid_ = false;
+    tape_slots_ = 0;
+    if (tape_on_) {
+      if ((e = tape_init())) return e;
+    } else {
+      tape_free();
+    }
     const auto t0 = std::chrono::steady_clock::now();
     cudaEvent_t ev[2];
     cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
@@ -926,6 +966,7 @@ class Engine final : public EngineBase {
     bool stop = false;
     for (long long b = 0; !stop; ++b) {
       const int len = (int)std::min<long long>(block_, limit - launched);
+      if (tape_on_ && (e = tape_ensure(b))) break;
       if (graphs) {
         cudaGraphExec_t ge;
         if ((e = block_graph(len, &ge))) break;
@@ -971,6 +1012,12 @@ class Engine final : public EngineBase {
     if ((e = cudaStreamSynchronize(s))) return e;
     DevState h;
     if ((e = read_state(&h))) return e;
+    if (tape_on_) {
+      tape_on_ = false;
+      if (h.tape_err) return cudaErrorMemoryAllocation;
+      tape_slots_ = h.checks;
+      tape_valid_ = true;
+    }
     info->termination = h.termination;
     if (!h.done && info->time_limit_hit) info->termination = MPAX_TERM_TIME_LIMIT;
     info->iterations = h.total;
@@ -978,6 +1025,172 @@ class Engine final : public EngineBase {
     info->checks = h.checks;
     info->launches = launches_;
     return cudaSuccess;
+  }
+
+  // ---- tape of a QP solve and the unrolled reverse sweep -----------------------
+  cudaError_t tape_init() {
+    ProblemData& P = *P_;
+    cudaError_t e;
+    const size_t bytes = sizeof(TapeHead) + sizeof(T) * (2 * (size_t)P.n + 2 * (size_t)P.m);
+    const size_t rec = (bytes + 255) / 256 * 256;
+    if (rec != tape_rec_bytes_) tape_free();
+    tape_rec_bytes_ = rec;
+    if (!tape_tab_) {
+      if ((e = cudaMalloc(&tape_tab_, sizeof(char*) * kTapeSlots))) return e;
+      if ((e = cudaMemsetAsync(tape_tab_, 0, sizeof(char*) * kTapeSlots, P.s))) return e;
+      if ((e = cudaHostAlloc(&tape_tab_h_, sizeof(char*) * kTapeSlots, cudaHostAllocDefault)))
+        return e;
+    }
+    return cudaSuccess;
+  }
+
+  // Records for blocks 0..slot exist (chunks of kTapeChunk records).
+  cudaError_t tape_ensure(long long slot) {
+    const long long have = (long long)tape_chunks_.size() * kTapeChunk;
+    if (slot < have) return cudaSuccess;
+    if (slot >= kTapeSlots) return cudaErrorMemoryAllocation;
+    char* chunk = nullptr;
+    cudaError_t e = cudaMalloc(&chunk, tape_rec_bytes_ * kTapeChunk);
+    if (e) return e;
+    tape_chunks_.push_back(chunk);
+    for (int k = 0; k < kTapeChunk; ++k) tape_tab_h_[have + k] = chunk + k * tape_rec_bytes_;
+    return cudaMemcpyAsync(tape_tab_ + have, tape_tab_h_ + have, sizeof(char*) * kTapeChunk,
+                           cudaMemcpyHostToDevice, P_->s);
+  }
+
+  void tape_free() {
+    if (tape_chunks_.empty()) return;
+    cudaStreamSynchronize(P_->s);
+    for (char* c : tape_chunks_) cudaFree(c);
+    tape_chunks_.clear();
+    if (tape_tab_) cudaMemsetAsync(tape_tab_, 0, sizeof(char*) * kTapeSlots, P_->s);
+    tape_valid_ = false;
+    tape_slots_ = 0;
+  }
+
+  // One block of the taped path again from its restored start state, with the
+  // forward kernels recording x_md and the clamp codes of every step.
+  void replay_block(int len, T* xmd, unsigned char* cx, unsigned char* cy) {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    const size_t n = P.n, m = P.m;
+    for (int it = 0; it < len; ++it) {
+      if (P.f_nnz > 0) {
+        EpiStore<T> eu{&st_->done, uvec_, nullptr, nullptr, nullptr, nullptr, 0};
+        launch_spmv<T>(P.schedFt, P.Ft, ftval_, InMomentum<T>{x_, xavg_, st_, it}, eu, 0, s);
+        launches_ += 1;
+      }
+      EpiPrimalQP<T, true> ep{st_, x_,    xavg_,  xref_,  xanc_, c_,     l_,  u_,
+                              Ds_, P.F.rp, P.F.col, fval_, uvec_, xprev_, it, 0,
+                              0,   xmd + it * n, cx + it * n};
+      launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{y_}, ep, 0, s);
+      EpiDualQP<T, true> ed{st_, y_, yavg_, yanc_, lc_, uc_, it, 0, cy + it * m};
+      launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{xref_}, ed, 0, s);
+      launches_ += 2;
+    }
+  }
+
+  cudaError_t unrolled_backward(const double* gx, const double* gy, double* gc, double* glc,
+                                double* guc, double* gl, double* gu, double* gD,
+                                long long* launches) override {
+    if constexpr (!std::is_same<T, double>::value) {
+      return cudaErrorNotSupported;
+    } else {
+      ProblemData& P = *P_;
+      cudaStream_t s = P.s;
+      const int n = P.n, m = P.m;
+      if (!tape_valid_ || tape_slots_ <= 0) return cudaErrorNotReady;
+      cudaError_t e;
+      std::vector<TapeHead> H((size_t)tape_slots_);
+      for (long long b = 0; b < tape_slots_; ++b)
+        if ((e = cudaMemcpyAsync(&H[b], tape_tab_h_[b], sizeof(TapeHead), cudaMemcpyDeviceToHost,
+                                 s)))
+          return e;
+      if ((e = cudaStreamSynchronize(s))) return e;
+      int lmax = 1;
+      for (const TapeHead& h : H) lmax = std::max(lmax, h.len);
+      // scratch: adjoints, the replayed block's x_md and codes, the saved state
+      e = cudaSuccess;
+      double* ax = dalloc<double>(n, &e);
+      double* axa = dalloc<double>(n, &e);
+      double* uu = dalloc<double>(n, &e);
+      double* ay = dalloc<double>(m, &e);
+      double* aya = dalloc<double>(m, &e);
+      double* ws = dalloc<double>(m, &e);
+      double* tq = dalloc<double>(std::max(P.r, 1), &e);
+      T* xmd = dalloc<T>((size_t)lmax * n, &e);
+      unsigned char* cx = dalloc<unsigned char>((size_t)lmax * n, &e);
+      unsigned char* cy = dalloc<unsigned char>((size_t)lmax * m, &e);
+      T* sv = dalloc<T>(2 * (size_t)n + 2 * (size_t)m, &e);
+      DevState* sts = dalloc<DevState>(1, &e);
+      void* bufs[] = {ax, axa, uu, ay, aya, ws, tq, xmd, cx, cy, sv, sts};
+      auto release = [&]() {
+        cudaStreamSynchronize(s);
+        for (void* b : bufs)
+          if (b) cudaFree(b);
+      };
+      if (e) {
+        release();
+        return e;
+      }
+      const long long l0 = launches_;
+      // the returned point and the state survive the sweep
+      cudaMemcpyAsync(sts, st_, sizeof(DevState), cudaMemcpyDeviceToDevice, s);
+      const size_t nn = n, mm = m;
+      cudaMemcpyAsync(sv, x_, sizeof(T) * nn, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(sv + nn, xavg_, sizeof(T) * nn, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(sv + 2 * nn, y_, sizeof(T) * mm, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(sv + 2 * nn + mm, yavg_, sizeof(T) * mm, cudaMemcpyDeviceToDevice, s);
+      for (double* g : {gc, gl, gu, gD}) cudaMemsetAsync(g, 0, sizeof(double) * nn, s);
+      for (double* g : {glc, guc})
+        if (m) cudaMemsetAsync(g, 0, sizeof(double) * mm, s);
+      const int gN = grid1(std::max(n, m));
+      k_rev_seed<<<gN, 256, 0, s>>>(gx, gy, P.Dc, P.Dr, n, m, ax, axa, ay, aya);
+      k_set_cursor<<<1, 1, 0, s>>>(st_, tape_slots_);
+      launches_ += 2;
+      for (long long b = tape_slots_ - 1; b >= 0; --b) {
+        const int L = H[b].len;
+        k_tape_open<<<1, 256, 0, s>>>(st_, tape_tab_);
+        k_tape_restore<T><<<gN, 256, 0, s>>>(st_, tape_tab_, n, m, x_, xavg_, y_, yavg_, ax,
+                                             axa, ay, aya);
+        launches_ += 2;
+        replay_block(L, xmd, cx, cy);
+        if (m) {
+          k_rev_r1<<<grid1(m), 256, 0, s>>>(st_, L - 1, m, cy + (size_t)(L - 1) * mm, ay, aya,
+                                            ws, glc, guc);
+          launches_ += 1;
+        }
+        for (int it = L - 1; it >= 0; --it) {
+          EpiRevPrimal<T> ep{st_, ax, axa, uu, gc, gl, gu, gD, cx + (size_t)it * nn, Ds_,
+                             P.F.rp, P.F.col, fval_, tq,
+                             it < L - 1 ? xmd + (size_t)(it + 1) * nn : nullptr, it, 0};
+          launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{ws}, ep, 0, s);
+          if (P.f_nnz > 0) {
+            EpiStore<T> eu{nullptr, tq, nullptr, nullptr, nullptr, nullptr, 0};
+            launch_spmv<T>(P.schedFt, P.Ft, ftval_, InPlain<T>{uu}, eu, 0, s);
+            launches_ += 1;
+          }
+          EpiRevDual<T> ed{st_, ay, aya, ws, glc, guc,
+                           it > 0 ? cy + (size_t)(it - 1) * mm : nullptr, it, 0};
+          launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{uu}, ed, 0, s);
+          launches_ += 2;
+        }
+        k_rev_r4<T><<<grid1(n), 256, 0, s>>>(st_, 0, n, Ds_, P.F.rp, P.F.col, fval_, tq, uu, xmd,
+                                             ax, axa, gD);
+        launches_ += 1;
+      }
+      k_rev_unscale<<<gN, 256, 0, s>>>(P.Dc, P.Dr, n, m, gc, gl, gu, gD, glc, guc);
+      cudaMemcpyAsync(x_, sv, sizeof(T) * nn, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(xavg_, sv + nn, sizeof(T) * nn, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(y_, sv + 2 * nn, sizeof(T) * mm, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(yavg_, sv + 2 * nn + mm, sizeof(T) * mm, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(st_, sts, sizeof(DevState), cudaMemcpyDeviceToDevice, s);
+      launches_ += 1;
+      *launches += launches_ - l0;
+      e = cudaGetLastError();
+      release();
+      return e;
+    }
   }
 
   // ---- lower-level access -----------------------------------------------------
@@ -1123,6 +1336,15 @@ class Engine final : public EngineBase {
   std::vector<cudaEvent_t> prof_ev_;
   std::vector<int> prof_cls_;
   size_t prof_used_ = 0;
+  // tape of a QP solve: one record per check block (TapeHead + x, xavg, y, yavg)
+  static constexpr long long kTapeSlots = 1LL << 20;
+  static constexpr int kTapeChunk = 16;
+  bool tape_on_ = false, tape_valid_ = false;
+  long long tape_slots_ = 0;
+  size_t tape_rec_bytes_ = 0;
+  char** tape_tab_ = nullptr;    // device: record of block b
+  char** tape_tab_h_ = nullptr;  // pinned host mirror
+  std::vector<char*> tape_chunks_;
 };
 
 EngineBase* make_engine(ProblemData* P, int precision, cudaError_t* err) {

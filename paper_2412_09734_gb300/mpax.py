@@ -21,6 +21,10 @@ MPAX_MEM_HOST = 0
 MPAX_MEM_DEVICE = 1
 MPAX_PREC_FP64 = 0
 MPAX_PREC_MIXED = 1
+MPAX_ERR_INVALID_ARGUMENT = 1
+MPAX_ERR_NOT_SOLVED = 4
+MPAX_ERR_UNSUPPORTED = 7
+MPAX_TERM_OPTIMAL = 1
 TERMINATION = {0: "unsolved", 1: "optimal", 2: "primal_infeasible", 3: "dual_infeasible",
                4: "iteration_limit", 5: "time_limit", 6: "numerical_error"}
 
@@ -28,7 +32,8 @@ EXPORTED = ["mpax_version", "mpax_last_error", "mpax_status_string", "mpax_optio
             "mpax_lp_create", "mpax_qp_create_diag_lowrank", "mpax_solve", "mpax_get_solution",
             "mpax_get_stats", "mpax_destroy", "mpax_prepare", "mpax_get_scaling",
             "mpax_get_transpose", "mpax_set_iterate", "mpax_iterate", "mpax_get_iterate",
-            "mpax_kkt", "mpax_lp_value_grad", "mpax_qp_adjoint", "mpax_lp_batch_create", "mpax_batch_solve", "mpax_batch_get_solution",
+            "mpax_kkt", "mpax_lp_value_grad", "mpax_qp_adjoint", "mpax_qp_unrolled_grad",
+            "mpax_lp_batch_create", "mpax_batch_solve", "mpax_batch_get_solution",
             "mpax_batch_get_stats", "mpax_batch_destroy", "mpax_lp_shared_create", "mpax_shared_solve",
             "mpax_shared_get_solution", "mpax_shared_get_stats", "mpax_shared_destroy",
             "mpax_lp_kkt_noalloc"]
@@ -56,6 +61,7 @@ class Options(ctypes.Structure):
         ("power_max_iter", ctypes.c_int32), ("power_tol", ctypes.c_double),
         ("use_graphs", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
         ("fp64_continuation", ctypes.c_int32), ("stall_checks", ctypes.c_int32),
+        ("record_tape", ctypes.c_int32),
     ]
 
 
@@ -130,6 +136,7 @@ _sig = {
     "mpax_lp_kkt_noalloc": ([_I32, _I32, _I64] + [_P] * 15, _INT),
     "mpax_lp_value_grad": ([_P, _P, _P, _P, _P, _P, _INT], _INT),
     "mpax_qp_adjoint": ([_P, _P, _P, _P, _P, _D, _I32, _INT, _P], _INT),
+    "mpax_qp_unrolled_grad": ([_P] * 9 + [_INT], _INT),
     "mpax_lp_batch_create": ([_I32] + [_P] * 10 + [_INT, _P, ctypes.POINTER(_P)], _INT),
     "mpax_batch_solve": ([_P, ctypes.POINTER(Options)], _INT),
     "mpax_batch_get_solution": ([_P, _P, _P, _INT], _INT),
@@ -435,6 +442,23 @@ def mpax_qp_adjoint(h, g, m, n, tol=1e-10, max_iter=10000):
     _check(_lib.mpax_qp_adjoint(h, gp, _ptr_out(dc), _ptr_out(db), _ptr_out(dD), float(tol),
                                 int(max_iter), kind, info.ctypes.data))
     return dc, db, dD, dict(iterations=int(info[0]), rel_residual=float(info[1]))
+
+
+def mpax_qp_unrolled_grad(h, gx, m, n, gy=None):
+    """Gradients of L = gx . x + gy . y along the path of the last solve, which
+    ran with record_tape = 1: dict(c, lc, uc, l, u, D); CUDA tensors when gx is
+    one, else numpy arrays."""
+    kind = _kind_of(gx)
+    kp = _Keep(kind)
+    gxp = kp.ptr(gx, np.float64)
+    gyp = kp.ptr(gy, np.float64) if gy is not None else None
+    tmpl = gx if kind == MPAX_MEM_DEVICE else None
+    outs = {k: _out(sz, tmpl)[0] for k, sz in (("c", n), ("lc", m), ("uc", m), ("l", n),
+                                               ("u", n), ("D", n))}
+    _check(_lib.mpax_qp_unrolled_grad(h, gxp, gyp, _ptr_out(outs["c"]), _ptr_out(outs["lc"]),
+                                      _ptr_out(outs["uc"]), _ptr_out(outs["l"]),
+                                      _ptr_out(outs["u"]), _ptr_out(outs["D"]), kind))
+    return outs
 
 
 # ---------------------------------------------------------------------------
