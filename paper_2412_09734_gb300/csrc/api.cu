@@ -714,7 +714,7 @@ mpax_status mpax_qp_unrolled_grad(mpax_problem* pb, const double* gx, const doub
   long long launches = 0;
   if (!e)
     e = pb->eng[pb->cur]->unrolled_backward(dgx, gy ? dgy : nullptr, ogc, oglc, oguc, ogl, ogu,
-                                            ogD, &launches);
+                                            ogD, pb->last_opts.use_graphs != 0, &launches);
   if (e == cudaErrorNotReady) {
     cudaFree(buf);
     cudaGetLastError();

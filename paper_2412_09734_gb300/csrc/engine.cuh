@@ -43,10 +43,11 @@ class EngineBase {
   // Unrolled differentiation (QP, FP64) of the last run, which had
   // record_tape set: gradients of gx . x + gy . y at its returned point along
   // its path.  Device vectors; gy nullable; gc, gl, gu, gD have n entries,
-  // glc, guc m.  cudaErrorNotReady: no tape.
+  // glc, guc m.  use_graphs: replay each block's launches as one CUDA graph.
+  // cudaErrorNotReady: no tape.
   virtual cudaError_t unrolled_backward(const double* gx, const double* gy, double* gc,
                                         double* glc, double* guc, double* gl, double* gu,
-                                        double* gD, long long* launches) = 0;
+                                        double* gD, bool use_graphs, long long* launches) = 0;
 };
 
 EngineBase* make_engine(ProblemData* P, int precision, cudaError_t* err);

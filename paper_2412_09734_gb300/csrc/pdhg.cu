@@ -1091,7 +1091,7 @@ class Engine final : public EngineBase {
   }
 
   cudaError_t unrolled_backward(const double* gx, const double* gy, double* gc, double* glc,
-                                double* guc, double* gl, double* gu, double* gD,
+                                double* guc, double* gl, double* gu, double* gD, bool use_graphs,
                                 long long* launches) override {
     if constexpr (!std::is_same<T, double>::value) {
       return cudaErrorNotSupported;
@@ -1148,8 +1148,10 @@ class Engine final : public EngineBase {
       k_rev_seed<<<gN, 256, 0, s>>>(gx, gy, P.Dc, P.Dr, n, m, ax, axa, ay, aya);
       k_set_cursor<<<1, 1, 0, s>>>(st_, tape_slots_);
       launches_ += 2;
-      for (long long b = tape_slots_ - 1; b >= 0; --b) {
-        const int L = H[b].len;
+      // One block backwards: every launch reads its block's scalars from the
+      // device state, so the sequence is captured once per block length as a
+      // CUDA graph and replayed for every block.
+      auto rev_block = [&](int L) {
         k_tape_open<<<1, 256, 0, s>>>(st_, tape_tab_);
         k_tape_restore<T><<<gN, 256, 0, s>>>(st_, tape_tab_, n, m, x_, xavg_, y_, yavg_, ax,
                                              axa, ay, aya);
@@ -1178,6 +1180,36 @@ class Engine final : public EngineBase {
         k_rev_r4<T><<<grid1(n), 256, 0, s>>>(st_, 0, n, Ds_, P.F.rp, P.F.col, fval_, tq, uu, xmd,
                                              ax, axa, gD);
         launches_ += 1;
+      };
+      std::map<int, std::pair<cudaGraphExec_t, long long>> rg;
+      for (long long b = tape_slots_ - 1; b >= 0 && !e; --b) {
+        const int L = H[b].len;
+        if (!use_graphs) {
+          rev_block(L);
+          continue;
+        }
+        auto it = rg.find(L);
+        if (it == rg.end()) {
+          cudaGraph_t g;
+          if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal))) break;
+          const long long before = launches_;
+          rev_block(L);
+          const long long nl = launches_ - before;
+          launches_ = before;
+          if ((e = cudaStreamEndCapture(s, &g))) break;
+          cudaGraphExec_t ge;
+          e = cudaGraphInstantiate(&ge, g, 0);
+          cudaGraphDestroy(g);
+          if (e) break;
+          it = rg.emplace(L, std::make_pair(ge, nl)).first;
+        }
+        if ((e = cudaGraphLaunch(it->second.first, s))) break;
+        launches_ += it->second.second;
+      }
+      for (auto& kv : rg) cudaGraphExecDestroy(kv.second.first);
+      if (e) {
+        release();
+        return e;
       }
       k_rev_unscale<<<gN, 256, 0, s>>>(P.Dc, P.Dr, n, m, gc, gl, gu, gD, glc, guc);
       cudaMemcpyAsync(x_, sv, sizeof(T) * nn, cudaMemcpyDeviceToDevice, s);
