@@ -179,6 +179,15 @@ mpax_status mpax_lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row
                            const double* u, mpax_mem_kind kind, void* cuda_stream,
                            mpax_problem** out);
 
+/* mpax_lp_create with FP32 values and vectors (row_ptr and col_idx as there).
+ * They are widened to FP64 on entry, so the problem is exactly the FP64 problem
+ * with those values; the iteration precision is still chosen by the options. */
+mpax_status mpax_lp_create_f32(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                               const int32_t* col_idx, const float* val, const float* c,
+                               const float* lc, const float* uc, const float* l,
+                               const float* u, mpax_mem_kind kind, void* cuda_stream,
+                               mpax_problem** out);
+
 /* Create a convex QP with Q = diag(D) + F F^T (Sec. 2, eq. 1), D >= 0
  * (n entries), F an n x r CSR matrix (f_row_ptr has n+1 entries).  Other
  * arguments and ownership as mpax_lp_create. */
@@ -188,6 +197,22 @@ mpax_status mpax_qp_create_diag_lowrank(
     const double* u, const double* D, int32_t r, int64_t f_nnz, const int64_t* f_row_ptr,
     const int32_t* f_col_idx, const double* f_val, mpax_mem_kind kind, void* cuda_stream,
     mpax_problem** out);
+
+/* Problem (1) with a general sparse Q (Sec. 2, eq. 1): Q is n x n in CSR
+ * (q_row_ptr n+1 int64 entries, q_col_idx sorted within each row, q_val),
+ * symmetric positive semidefinite with BOTH triangles stored; symmetry and
+ * definiteness are the caller's (not verified).  Q's diagonal joins the
+ * column norms of the scaling, ||Q~||_2 comes from power iteration, and every
+ * Q product of the iteration, the KKT test, the implicit adjoint and the
+ * unrolled gradient is one SpMV with Q~ = D_c Q D_c.  Other arguments,
+ * validation and ownership as mpax_lp_create.  In the differentiation calls the
+ * gradient named dD is that of Q's diagonal. */
+mpax_status mpax_qp_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                           const int32_t* col_idx, const double* val, const double* c,
+                           const double* lc, const double* uc, const double* l,
+                           const double* u, int64_t q_nnz, const int64_t* q_row_ptr,
+                           const int32_t* q_col_idx, const double* q_val, mpax_mem_kind kind,
+                           void* cuda_stream, mpax_problem** out);
 
 /* Solve from (x0, y0) given in the unscaled space (either may be NULL: zeros,
  * the paper's default start, Sec. 3.5).  Runs transpose, scaling, norm
@@ -258,6 +283,11 @@ mpax_status mpax_kkt(mpax_problem* prob, const double* x, const double* y, mpax_
                      double* out);
 
 /* ---- Differentiation of the returned solution ------------------------------ */
+
+/* Reduced costs lam = Q x + c - A^T y (unscaled, n entries) at the point
+ * mpax_get_solution returns: the multipliers of the variable bounds (eq. 1's
+ * dual, Sec. 2). */
+mpax_status mpax_get_reduced_cost(mpax_problem* prob, double* lam, mpax_mem_kind kind);
 
 /* Gradients of an LP's optimal value at the returned point (x, y) of the last
  * mpax_solve, by the envelope theorem (the paper differentiates LPs through

@@ -10,8 +10,8 @@ itself, which the paper does not state, so these are definitions written out:
 * LP value v(c, lc, uc, l, u) = min c^T x: by the envelope theorem its gradient
   at a primal-dual optimum (x*, y*) with reduced costs lam* = c - A^T y* is
       dv/dc = x*,  dv/dlc = y*^+,  dv/duc = -y*^-,  dv/dl = lam*^+,  dv/du = -lam*^-.
-* QP solution x*(c, b, D) for Q = diag(D) + F F^T, equality rows A x = b and
-  box bounds.  On the free set F (variables strictly inside their bounds, plus
+* QP solution x*(c, b, D) for Q = diag(D) + F F^T (or a general sparse Q, D
+  then standing for Q's diagonal), equality rows A x = b and box bounds.  On the free set F (variables strictly inside their bounds, plus
   bound variables whose multiplier is at most delta' in magnitude) and the
   active rows R (equalities and inequality rows with y_i != 0), x* solves
       Q_FF x_F - A_RF^T y_R = -c_F - Q_FB x_B,   A_RF x_F = b_R - A_RB x_B.
@@ -57,9 +57,11 @@ def qp_adjoint(p: Problem, x, y, g, free=None, rows=None):
         free, rows = active_sets(p, x, y)
     Fi = np.flatnonzero(free)
     Ri = np.flatnonzero(rows)
-    Qd = p.Q.D
-    Ff = p.Q.F[Fi]
-    QFF = sp.diags(Qd[Fi]) + Ff @ Ff.T
+    if hasattr(p.Q, "D"):
+        Ff = p.Q.F[Fi]
+        QFF = sp.diags(p.Q.D[Fi]) + Ff @ Ff.T
+    else:  # a general sparse Q; dD is then the gradient of Q's diagonal
+        QFF = p.Q.Q[Fi][:, Fi]
     ARF = p.A[Ri][:, Fi]
     K = sp.bmat([[QFF, ARF.T], [ARF, None]], format="csc")
     rhs = np.concatenate([g[Fi], np.zeros(len(Ri))])

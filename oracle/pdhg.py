@@ -164,6 +164,9 @@ def problem_from_arrays(d: dict) -> Problem:
     if "D" in d:
         F = sp.csr_matrix((d["f_val"], d["f_col"], d["f_row_ptr"]), shape=(d["n"], d["f_cols"]))
         Q = DiagLowRankQ(d["D"], F)
+    elif "q_row_ptr" in d:
+        Q = SparseQ(sp.csr_matrix((d["q_val"], d["q_col"], d["q_row_ptr"]),
+                                  shape=(d["n"], d["n"])))
     return Problem(A, np.array(d["c"], dtype=np.float64), np.array(d["lc"], dtype=np.float64),
                    np.array(d["uc"], dtype=np.float64), np.array(d["l"], dtype=np.float64),
                    np.array(d["u"], dtype=np.float64), Q)

@@ -107,8 +107,8 @@ def replay(ps: Problem, sched, x0=None, y0=None):
 
 def unrolled_gradient(p: Problem, res, tape, gx, gy=None):
     """Gradients of L = gx . x + gy . y at the returned point (x, y) of a taped
-    solve, along its path: dict(c, lc, uc, l, u, D) (D only for a
-    diagonal-plus-low-rank Q), all for the unscaled data."""
+    solve, along its path: dict(c, lc, uc, l, u, D) (D: the diagonal of
+    diag(D) + F F^T, or of a general sparse Q), all for the unscaled data."""
     Dr, Dc = res.Dr, res.Dc
     ps = scale_problem(p, Dr, Dc)
     n, m = p.n, p.m
@@ -161,7 +161,7 @@ def unrolled_gradient(p: Problem, res, tape, gx, gy=None):
         g_ya = (1.0 - b) * g_ya
         g_x, g_y = new_gx, new_gy
     out = dict(c=Dc * G["c"], l=G["l"] / Dc, u=G["u"] / Dc, lc=Dr * G["lc"], uc=Dr * G["uc"])
-    if p.Q is not None and hasattr(p.Q, "D"):
+    if p.Q is not None:  # D of diag(D) + F F^T, or the diagonal of a general Q
         out["D"] = Dc * Dc * G["D"]
     return out
 

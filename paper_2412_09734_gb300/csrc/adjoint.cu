@@ -210,6 +210,9 @@ cudaError_t lambda_unscaled(ProblemData& P, const double* x, const double* y, do
                                        nullptr, nullptr, tmpr, 0);
     k_rows<<<wgrid(P.n), 256, 0, s>>>(P.F.rp, P.F.col, P.fval, nullptr, P.n, tmpr, P.D, x,
                                        nullptr, lam, 0);
+    if (P.q_general)  // + Q x for a general sparse Q (D = 0, F empty)
+      k_rows<<<wgrid(P.n), 256, 0, s>>>(P.Q.rp, P.Q.col, P.qval, nullptr, P.n, x, nullptr,
+                                         nullptr, nullptr, lam, 1);
     qx = lam;
   }
   k_lam_finish<<<g1(P.n), 256, 0, s>>>(tmpn, P.c, qx, P.n, lam);
@@ -219,6 +222,29 @@ cudaError_t lambda_unscaled(ProblemData& P, const double* x, const double* y, do
 }  // namespace
 
 extern "C" {
+
+mpax_status mpax_get_reduced_cost(mpax_problem* prob, double* lam, mpax_mem_kind kind) {
+  if (!prob || !lam) return afail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  ProblemData& P = *problem_data(prob);
+  const int n = P.n, m = P.m;
+  cudaStream_t s = P.s;
+  DBuf B;
+  cudaError_t e = cudaSuccess;
+  double* x = B.get<double>(n, &e);
+  double* y = B.get<double>(m, &e);
+  double* out = B.get<double>(n, &e);
+  double* tmp = B.get<double>(n, &e);
+  double* tmpr = B.get<double>(std::max(P.r, 1), &e);
+  if (e) return afail(MPAX_ERR_OUT_OF_MEMORY, "reduced-cost buffers");
+  mpax_status st = mpax_get_solution(prob, x, y, MPAX_MEM_DEVICE);
+  if (st) return st;
+  if ((e = lambda_unscaled(P, x, y, out, tmp, tmpr, s))) return afail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  const cudaMemcpyKind k = kind == MPAX_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (n) e = cudaMemcpyAsync(lam, out, sizeof(double) * n, k, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return afail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  return MPAX_OK;
+}
 
 mpax_status mpax_lp_value_grad(mpax_problem* prob, double* dc, double* dlc, double* duc,
                                double* dl, double* du, mpax_mem_kind kind) {
@@ -305,6 +331,9 @@ mpax_status mpax_qp_adjoint(mpax_problem* prob, const double* g, double* dc, dou
                                        nullptr, nullptr, tmpr, 0);
     k_rows<<<wgrid(n), 256, 0, s>>>(P.F.rp, P.F.col, P.fval_s, nullptr, n, tmpr, P.D_s, in,
                                      nullptr, out, 0);
+    if (P.q_general)
+      k_rows<<<wgrid(n), 256, 0, s>>>(P.Q.rp, P.Q.col, P.qval_s, nullptr, n, in, nullptr,
+                                       nullptr, nullptr, out, 1);
     k_rows<<<wgrid(n), 256, 0, s>>>(P.At.rp, P.At.col, As_t, nullptr, n, in + n, nullptr,
                                      nullptr, freem, out, 1);
     // bottom: mask_R A~ in_top

@@ -77,6 +77,13 @@ __global__ void k_check_csr(const int* __restrict__ rp, const int* __restrict__ 
   }
 }
 
+// FP32 inputs widened to FP64 (mpax_lp_create_f32)
+__global__ void k_widen(const float* __restrict__ a, double* __restrict__ b, size_t k) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < k;
+       i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
 __global__ void k_check_vecs(const double* c, const double* l, const double* u, int n,
                              const double* lc, const double* uc, int m, const double* D,
                              int* flags) {
@@ -183,10 +190,14 @@ void destroy_problem(mpax_problem* pb) {
   free_csr(P.At);
   free_csr(P.F);
   free_csr(P.Ft);
+  free_csr(P.Q);
   free_schedule(P.schedA);
   free_schedule(P.schedAt);
   free_schedule(P.schedF);
   free_schedule(P.schedFt);
+  free_schedule(P.schedQ);
+  if (P.qval) cudaFree(P.qval);
+  if (P.qval_s) cudaFree(P.qval_s);
   double* ds[] = {P.val, P.c,     P.lc,    P.uc,    P.l,   P.u,      P.D,      P.fval,
                   P.Dr,  P.Dc,    P.invDr, P.invDc, P.val_s, P.fval_s, P.D_s,  P.rowred,
                   P.colred, P.rowred2, P.colred2, P.red, P.red_out, P.qdiag, pb->dx, pb->dy,
@@ -209,20 +220,26 @@ mpax_status create_common(int32_t m, int32_t n, int64_t nnz, const int64_t* row_
                           const double* u, const double* D, int32_t r, int64_t f_nnz,
                           const int64_t* f_row_ptr, const int32_t* f_col_idx,
                           const double* f_val, bool is_qp, mpax_mem_kind kind,
-                          void* cuda_stream, mpax_problem** out) {
+                          void* cuda_stream, mpax_problem** out, int64_t q_nnz = 0,
+                          const int64_t* q_row_ptr = nullptr, const int32_t* q_col_idx = nullptr,
+                          const double* q_val = nullptr) {
   if (!out) return fail(MPAX_ERR_INVALID_ARGUMENT, "out must not be NULL");
   *out = nullptr;
-  if (m < 0 || n < 0 || nnz < 0 || r < 0 || f_nnz < 0)
+  const bool q_general = q_row_ptr != nullptr;
+  if (m < 0 || n < 0 || nnz < 0 || r < 0 || f_nnz < 0 || q_nnz < 0)
     return fail(MPAX_ERR_INVALID_ARGUMENT, "sizes must be non-negative");
-  if (nnz >= (1LL << 31) || f_nnz >= (1LL << 31))
+  if (nnz >= (1LL << 31) || f_nnz >= (1LL << 31) || q_nnz >= (1LL << 31))
     return fail(MPAX_ERR_UNSUPPORTED, "nnz must be < 2^31");
+  if (q_general && (bad_ptr(q_col_idx, q_nnz) || bad_ptr(q_val, q_nnz)))
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "a required Q array pointer is NULL");
   if (kind != MPAX_MEM_HOST && kind != MPAX_MEM_DEVICE)
     return fail(MPAX_ERR_INVALID_ARGUMENT, "kind must be MPAX_MEM_HOST or MPAX_MEM_DEVICE");
   if (bad_ptr(row_ptr, 1) || bad_ptr(col_idx, nnz) || bad_ptr(val, nnz) || bad_ptr(c, n) ||
       bad_ptr(l, n) || bad_ptr(u, n) || bad_ptr(lc, m) || bad_ptr(uc, m))
     return fail(MPAX_ERR_INVALID_ARGUMENT, "a required array pointer is NULL");
-  if (is_qp && (bad_ptr(D, n) || bad_ptr(f_row_ptr, 1) || bad_ptr(f_col_idx, f_nnz) ||
-                bad_ptr(f_val, f_nnz)))
+  if (is_qp && !q_general &&
+      (bad_ptr(D, n) || bad_ptr(f_row_ptr, 1) || bad_ptr(f_col_idx, f_nnz) ||
+       bad_ptr(f_val, f_nnz)))
     return fail(MPAX_ERR_INVALID_ARGUMENT, "a required QP array pointer is NULL");
   if (is_qp && r == 0 && f_nnz > 0)
     return fail(MPAX_ERR_INVALID_ARGUMENT, "F has entries but r = 0");
@@ -235,6 +252,7 @@ mpax_status create_common(int32_t m, int32_t n, int64_t nnz, const int64_t* row_
   P.is_qp = is_qp;
   P.r = r;
   P.f_nnz = (int)f_nnz;
+  P.q_general = q_general;
   pb->user = (cudaStream_t)cuda_stream;
   mpax_options_default(&pb->last_opts);
   std::memset(&pb->stats, 0, sizeof(pb->stats));
@@ -283,6 +301,15 @@ mpax_status create_common(int32_t m, int32_t n, int64_t nnz, const int64_t* row_
     if (!e) e = dmalloc(&P.Ft.col, f_nnz + kPad);
     if (!e) e = dmalloc(&P.permF, f_nnz);
   }
+  if (q_general) {
+    if (!e) e = dmalloc(&P.Q.rp, n + 1);
+    if (!e) e = dmalloc(&P.Q.col, q_nnz + kPad);
+    if (!e) e = dmalloc(&P.qval, q_nnz);
+    if (!e) e = dmalloc(&P.qval_s, q_nnz);
+  }
+  P.Q.rows = n;
+  P.Q.cols = n;
+  P.Q.nnz = (int)q_nnz;
   P.A.rows = m;
   P.A.cols = n;
   P.A.nnz = (int)nnz;
@@ -305,7 +332,7 @@ mpax_status create_common(int32_t m, int32_t n, int64_t nnz, const int64_t* row_
   if (!e) e = copy_in(P.u, u, sizeof(double) * n, kind, s);
   if (!e) e = copy_in(P.lc, lc, sizeof(double) * m, kind, s);
   if (!e) e = copy_in(P.uc, uc, sizeof(double) * m, kind, s);
-  if (is_qp) {
+  if (is_qp && !q_general) {
     if (!e) e = copy_in(P.D, D, sizeof(double) * n, kind, s);
     if (!e) e = cudaStreamSynchronize(s);  // rp64 reused below
     if (!e) e = copy_in(rp64, f_row_ptr, sizeof(int64_t) * (n + 1), kind, s);
@@ -314,9 +341,22 @@ mpax_status create_common(int32_t m, int32_t n, int64_t nnz, const int64_t* row_
     if (!e) e = copy_in(P.F.col, f_col_idx, sizeof(int32_t) * f_nnz, kind, s);
     if (!e) e = copy_in(P.fval, f_val, sizeof(double) * f_nnz, kind, s);
   }
+  if (q_general) {
+    // D = 0 and an empty F: the diagonal-plus-low-rank terms vanish
+    if (!e) e = cudaMemsetAsync(P.D, 0, sizeof(double) * std::max(n, 1), s);
+    if (!e) e = cudaMemsetAsync(P.F.rp, 0, sizeof(int) * (n + 1), s);
+    if (!e) e = cudaStreamSynchronize(s);  // rp64 reused below
+    if (!e) e = copy_in(rp64, q_row_ptr, sizeof(int64_t) * (n + 1), kind, s);
+    if (!e)
+      k_rowptr64_to_32<<<(n + 256) / 256, 256, 0, s>>>(rp64, P.Q.rp, n, q_nnz, flags);
+    if (!e) e = copy_in(P.Q.col, q_col_idx, sizeof(int32_t) * q_nnz, kind, s);
+    if (!e) e = copy_in(P.qval, q_val, sizeof(double) * q_nnz, kind, s);
+  }
   if (!e && m > 0) k_check_csr<<<(m + 255) / 256, 256, 0, s>>>(P.A.rp, P.A.col, P.val, m, n, flags);
   if (!e && is_qp && n > 0)
     k_check_csr<<<(n + 255) / 256, 256, 0, s>>>(P.F.rp, P.F.col, P.fval, n, r, flags);
+  if (!e && q_general && n > 0)
+    k_check_csr<<<(n + 255) / 256, 256, 0, s>>>(P.Q.rp, P.Q.col, P.qval, n, n, flags);
   if (!e)
     k_check_vecs<<<std::max(1, std::min(4096, (std::max(m, n) + 255) / 256)), 256, 0, s>>>(
         P.c, P.l, P.u, n, P.lc, P.uc, m, is_qp ? P.D : nullptr, flags);
@@ -387,6 +427,10 @@ mpax_status do_prepare(mpax_problem* pb, const mpax_options* o, long long* launc
     TRY_CUDA(build_schedule(P.F, P.schedF, s, P.tmp_rows, P.tmp_scan), "schedule F");
     TRY_CUDA(build_schedule(P.Ft, P.schedFt, s, P.tmp_rows, P.tmp_scan), "schedule F^T");
     *launches += 12;
+  }
+  if (P.q_general) {
+    TRY_CUDA(build_schedule(P.Q, P.schedQ, s, P.tmp_rows, P.tmp_scan), "schedule Q");
+    *launches += 6;
   }
   P.scheduled = true;
   TRY_CUDA(compute_scaling(P, o->ruiz_iters, o->pock_chambolle != 0), "scaling");
@@ -496,6 +540,63 @@ mpax_status mpax_qp_create_diag_lowrank(
     mpax_problem** out) {
   return create_common(m, n, nnz, row_ptr, col_idx, val, c, lc, uc, l, u, D, r, f_nnz,
                        f_row_ptr, f_col_idx, f_val, true, kind, cuda_stream, out);
+}
+
+mpax_status mpax_lp_create_f32(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                               const int32_t* col_idx, const float* val, const float* c,
+                               const float* lc, const float* uc, const float* l,
+                               const float* u, mpax_mem_kind kind, void* cuda_stream,
+                               mpax_problem** out) {
+  if (m < 0 || n < 0 || nnz < 0) return fail(MPAX_ERR_INVALID_ARGUMENT, "sizes must be non-negative");
+  if (kind != MPAX_MEM_HOST && kind != MPAX_MEM_DEVICE)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "kind must be MPAX_MEM_HOST or MPAX_MEM_DEVICE");
+  if (bad_ptr(val, nnz) || bad_ptr(c, n) || bad_ptr(l, n) || bad_ptr(u, n) || bad_ptr(lc, m) ||
+      bad_ptr(uc, m))
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "a required array pointer is NULL");
+  const float* src[6] = {val, c, lc, uc, l, u};
+  const size_t len[6] = {(size_t)nnz, (size_t)n, (size_t)m, (size_t)m, (size_t)n, (size_t)n};
+  if (kind == MPAX_MEM_HOST) {
+    std::vector<double> w[6];
+    for (int q = 0; q < 6; ++q) w[q].assign(src[q], src[q] + len[q]);
+    return create_common(m, n, nnz, row_ptr, col_idx, w[0].data(), w[1].data(), w[2].data(),
+                         w[3].data(), w[4].data(), w[5].data(), nullptr, 0, 0, nullptr, nullptr,
+                         nullptr, false, kind, cuda_stream, out);
+  }
+  // device inputs: widen into temporaries on the caller's stream, then copy in
+  double* buf = nullptr;
+  const size_t tot = len[0] + len[1] + len[2] + len[3] + len[4] + len[5];
+  TRY_CUDA(cudaMalloc(&buf, sizeof(double) * std::max<size_t>(tot, 1)), "f32 widening");
+  double* dst[6];
+  size_t off = 0;
+  for (int q = 0; q < 6; ++q) {
+    dst[q] = buf + off;
+    off += len[q];
+    if (len[q])
+      k_widen<<<(int)std::min<size_t>(4096, (len[q] + 255) / 256), 256, 0,
+                (cudaStream_t)cuda_stream>>>(src[q], dst[q], len[q]);
+  }
+  cudaError_t e = cudaGetLastError();
+  mpax_status st = MPAX_ERR_CUDA;
+  if (!e)
+    st = create_common(m, n, nnz, row_ptr, col_idx, dst[0], dst[1], dst[2], dst[3], dst[4],
+                       dst[5], nullptr, 0, 0, nullptr, nullptr, nullptr, false, kind,
+                       cuda_stream, out);
+  cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  cudaFree(buf);
+  if (e) return cuda_fail(e, "f32 widening");
+  return st;
+}
+
+mpax_status mpax_qp_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                           const int32_t* col_idx, const double* val, const double* c,
+                           const double* lc, const double* uc, const double* l,
+                           const double* u, int64_t q_nnz, const int64_t* q_row_ptr,
+                           const int32_t* q_col_idx, const double* q_val, mpax_mem_kind kind,
+                           void* cuda_stream, mpax_problem** out) {
+  if (!q_row_ptr) return fail(MPAX_ERR_INVALID_ARGUMENT, "q_row_ptr must not be NULL");
+  return create_common(m, n, nnz, row_ptr, col_idx, val, c, lc, uc, l, u, nullptr, 1, 0,
+                       nullptr, nullptr, nullptr, true, kind, cuda_stream, out, q_nnz,
+                       q_row_ptr, q_col_idx, q_val);
 }
 
 mpax_status mpax_prepare(mpax_problem* pb, const mpax_options* opts) {

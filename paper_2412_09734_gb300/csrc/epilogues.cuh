@@ -165,6 +165,7 @@ struct EpiPrimalQP {
   int it, record, check;
   T* tape_xmd;
   unsigned char* tape_code;
+  const T* qadd;  // general sparse Q: (Q~ x_md)_j from the SpMV launched before
   T tau, beta;
   __device__ __forceinline__ bool skip() const { return st->done != 0; }
   __device__ __forceinline__ void load() {
@@ -186,6 +187,7 @@ struct EpiPrimalQP {
     const T xmd = p.xa + beta * (p.x - p.xa);
     T q = p.d * xmd;
     for (int k = p.f0; k < p.f1; ++k) q += fval[k] * uvec[fcol[k]];
+    if (qadd) q += qadd[j];
     const T vx = p.x - tau * (q + p.c - t);
     const T xn = clampv<T>(vx, p.l, p.u);
     if constexpr (TAPE) {
@@ -312,6 +314,7 @@ struct EpiKktCol {
   const double* fval;
   const T* uvec;
   int check;
+  const T* qadd;  // general sparse Q: (Q~ x~)_j
   __device__ __forceinline__ bool skip() const { return skipf && *skipf != 0; }
   __device__ __forceinline__ void load() {}
   __device__ __forceinline__ void pre(int j, Pre& p) const {
@@ -330,6 +333,7 @@ struct EpiKktCol {
     if (is_qp) {
       double q = Ds[j] * xs;
       for (int k = frp[j]; k < frp[j + 1]; ++k) q += fval[k] * (double)uvec[fcol[k]];
+      if (qadd) q += (double)qadd[j];
       qx = q * p.idc;
     }
     const double lam = qx + p.c - aty;

@@ -616,6 +616,11 @@ class Engine final : public EngineBase {
       ftval_ = dalloc<T>((size_t)P->f_nnz + kPad, e);
       uvec_ = dalloc<T>(P->r, e);
       uvec2_ = dalloc<T>(P->r, e);
+      if (P->q_general) {
+        qv_ = dalloc<T>((size_t)P->Q.nnz + kPad, e);
+        qvec_ = dalloc<T>(n, e);
+        qvec2_ = dalloc<T>(n, e);
+      }
     }
     st_ = dalloc<DevState>(1, e);
     if (*e == cudaSuccess) *e = cudaHostAlloc(&hs_, sizeof(HostStatus), cudaHostAllocMapped);
@@ -629,7 +634,7 @@ class Engine final : public EngineBase {
     void* bufs[] = {valA_, valAt_, c_,    l_,    u_,    lc_,   uc_,    xbar_, wbuf_,
                     xa_,   xhat_,  xprev_, pv_,  pg_,   y_,    ya_,    yhat_, yprev_,
                     pw_,   x_,     xavg_, xref_, xanc_, yavg_, yanc_,  Ds_,   fval_,
-                    ftval_, uvec_, uvec2_, rayx_, rayy_, st_};
+                    ftval_, uvec_, uvec2_, rayx_, rayy_, qv_, qvec_, qvec2_, st_};
     for (void* b : bufs)
       if (b) cudaFree(b);
     if (hs_) cudaFreeHost(hs_);
@@ -667,6 +672,7 @@ class Engine final : public EngineBase {
       if ((e = cast_vec<T>(P.D_s, Ds_, P.n, s))) return e;
       if ((e = cast_vec<T>(P.fval_s, fval_, P.f_nnz, s))) return e;
       if ((e = gather_cast<T>(P.fval_s, P.permF, ftval_, P.f_nnz, s))) return e;
+      if (P.q_general && (e = cast_vec<T>(P.qval_s, qv_, P.Q.nnz, s))) return e;
     }
     return cudaGetLastError();
   }
@@ -699,6 +705,14 @@ class Engine final : public EngineBase {
                                               0, skip, P.red);
         k_power_finalize<<<1, 256, 0, s>>>(P.red, kChunks, st_, t, o.power_tol, 0,
                                            o.pock_chambolle ? 1.0 : INFINITY, o.power_max_iter);
+      } else if (P.q_general) {
+        // g = Q~ (v pw_scale), sum of squares for the norm
+        EpiStore<T> eq{skip, g, &st_->pw_scale, nullptr, nullptr, nullptr, 1};
+        launch_spmv<T>(P.schedQ, P.Q, qv_, InPlain<T>{v}, eq, 0, s);
+        k_part_reduce<<<kChunks, 256, 0, s>>>(P.schedQ.part, P.schedQ.n_items, 1, nullptr, 0,
+                                              0, skip, P.red);
+        k_power_finalize<<<1, 256, 0, s>>>(P.red, kChunks, st_, t, o.power_tol, 1, INFINITY,
+                                           o.power_max_iter);
       } else {
         e1.out = uvec_;
         launch_spmv<T>(P.schedFt, P.Ft, ftval_, InPlain<T>{v}, e1, 0, s);
@@ -805,8 +819,14 @@ class Engine final : public EngineBase {
           launch_spmv<T>(P.schedFt, P.Ft, ftval_, InMomentum<T>{x_, xavg_, st_, it}, eu, 0, s);
           launches_ += 1;
         }
+        if (P.q_general) {
+          EpiStore<T> eq{&st_->done, qvec_, nullptr, nullptr, nullptr, nullptr, 0};
+          launch_spmv<T>(P.schedQ, P.Q, qv_, InMomentum<T>{x_, xavg_, st_, it}, eq, 0, s);
+          launches_ += 1;
+        }
         EpiPrimalQP<T> ep{st_, x_,  xavg_,    xref_,    xanc_,  c_,     l_,    u_,
-                          Ds_, P.F.rp, P.F.col, fval_, uvec_, xprev_, it,    rec, chk};
+                          Ds_, P.F.rp, P.F.col, fval_, uvec_, xprev_, it,    rec, chk,
+                          nullptr, nullptr, P.q_general ? qvec_ : nullptr};
         prof_begin(prof, 0);
         launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{y_}, ep, 0, s);
         prof_end(prof, 0);
@@ -866,8 +886,14 @@ class Engine final : public EngineBase {
     prof_begin(prof, 2);
     launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{xv}, er, 2, s);
     prof_end(prof, 2);
+    if (qp && P.q_general) {
+      EpiStore<T> eq{skip, qvec2_, nullptr, nullptr, nullptr, nullptr, 0};
+      launch_spmv<T>(P.schedQ, P.Q, qv_, InPlain<T>{xv}, eq, 0, s);
+      launches_ += 1;
+    }
     EpiKktCol<T> ec{skip, P.invDc, P.Dc, P.c, P.l, P.u, xv, qp ? 1 : 0, P.D_s,
-                    P.F.rp, P.F.col, P.fval_s, uvec2_, 1};
+                    P.F.rp, P.F.col, P.fval_s, uvec2_, 1,
+                    (qp && P.q_general) ? qvec2_ : nullptr};
     prof_begin(prof, 3);
     launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{yv}, ec, 2, s);
     prof_end(prof, 3);
@@ -1080,9 +1106,14 @@ class Engine final : public EngineBase {
         launch_spmv<T>(P.schedFt, P.Ft, ftval_, InMomentum<T>{x_, xavg_, st_, it}, eu, 0, s);
         launches_ += 1;
       }
+      if (P.q_general) {
+        EpiStore<T> eq{&st_->done, qvec_, nullptr, nullptr, nullptr, nullptr, 0};
+        launch_spmv<T>(P.schedQ, P.Q, qv_, InMomentum<T>{x_, xavg_, st_, it}, eq, 0, s);
+        launches_ += 1;
+      }
       EpiPrimalQP<T, true> ep{st_, x_,    xavg_,  xref_,  xanc_, c_,     l_,  u_,
                               Ds_, P.F.rp, P.F.col, fval_, uvec_, xprev_, it, 0,
-                              0,   xmd + it * n, cx + it * n};
+                              0,   xmd + it * n, cx + it * n, P.q_general ? qvec_ : nullptr};
       launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{y_}, ep, 0, s);
       EpiDualQP<T, true> ed{st_, y_, yavg_, yanc_, lc_, uc_, it, 0, cy + it * m};
       launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{xref_}, ed, 0, s);
@@ -1118,12 +1149,13 @@ class Engine final : public EngineBase {
       double* aya = dalloc<double>(m, &e);
       double* ws = dalloc<double>(m, &e);
       double* tq = dalloc<double>(std::max(P.r, 1), &e);
+      double* qu = P.q_general ? dalloc<double>(n, &e) : nullptr;
       T* xmd = dalloc<T>((size_t)lmax * n, &e);
       unsigned char* cx = dalloc<unsigned char>((size_t)lmax * n, &e);
       unsigned char* cy = dalloc<unsigned char>((size_t)lmax * m, &e);
       T* sv = dalloc<T>(2 * (size_t)n + 2 * (size_t)m, &e);
       DevState* sts = dalloc<DevState>(1, &e);
-      void* bufs[] = {ax, axa, uu, ay, aya, ws, tq, xmd, cx, cy, sv, sts};
+      void* bufs[] = {ax, axa, uu, ay, aya, ws, tq, qu, xmd, cx, cy, sv, sts};
       auto release = [&]() {
         cudaStreamSynchronize(s);
         for (void* b : bufs)
@@ -1165,11 +1197,16 @@ class Engine final : public EngineBase {
         for (int it = L - 1; it >= 0; --it) {
           EpiRevPrimal<T> ep{st_, ax, axa, uu, gc, gl, gu, gD, cx + (size_t)it * nn, Ds_,
                              P.F.rp, P.F.col, fval_, tq,
-                             it < L - 1 ? xmd + (size_t)(it + 1) * nn : nullptr, it, 0};
+                             it < L - 1 ? xmd + (size_t)(it + 1) * nn : nullptr, it, 0, qu};
           launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{ws}, ep, 0, s);
           if (P.f_nnz > 0) {
             EpiStore<T> eu{nullptr, tq, nullptr, nullptr, nullptr, nullptr, 0};
             launch_spmv<T>(P.schedFt, P.Ft, ftval_, InPlain<T>{uu}, eu, 0, s);
+            launches_ += 1;
+          }
+          if (P.q_general) {
+            EpiStore<T> eq{nullptr, qu, nullptr, nullptr, nullptr, nullptr, 0};
+            launch_spmv<T>(P.schedQ, P.Q, qv_, InPlain<T>{uu}, eq, 0, s);
             launches_ += 1;
           }
           EpiRevDual<T> ed{st_, ay, aya, ws, glc, guc,
@@ -1178,7 +1215,7 @@ class Engine final : public EngineBase {
           launches_ += 2;
         }
         k_rev_r4<T><<<grid1(n), 256, 0, s>>>(st_, 0, n, Ds_, P.F.rp, P.F.col, fval_, tq, uu, xmd,
-                                             ax, axa, gD);
+                                             qu, ax, axa, gD);
         launches_ += 1;
       };
       std::map<int, std::pair<cudaGraphExec_t, long long>> rg;
@@ -1353,6 +1390,7 @@ class Engine final : public EngineBase {
   T *x_ = nullptr, *xavg_ = nullptr, *xref_ = nullptr, *xanc_ = nullptr;
   T *yavg_ = nullptr, *yanc_ = nullptr;
   T *Ds_ = nullptr, *fval_ = nullptr, *ftval_ = nullptr, *uvec_ = nullptr, *uvec2_ = nullptr;
+  T *qv_ = nullptr, *qvec_ = nullptr, *qvec2_ = nullptr;  // general sparse Q
   DevState* st_ = nullptr;
   HostStatus* hs_ = nullptr;
   HostStatus* hs_dev_ = nullptr;

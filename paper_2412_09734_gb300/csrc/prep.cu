@@ -108,6 +108,17 @@ __global__ void q_diagonal(const int* __restrict__ frp, const double* __restrict
   out[j] = s;
 }
 
+// diag(Q)_j += Q_jj for a general sparse Q (entries of row j in column j)
+__global__ void q_diagonal_add(const int* __restrict__ qrp, const int* __restrict__ qcol,
+                               const double* __restrict__ qval, int n, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int p = qrp[j]; p < qrp[j + 1]; ++p)
+    if (qcol[p] == j) s += qval[p];
+  out[j] += s;
+}
+
 __global__ void fill_ones(double* a, int k) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < k) a[i] = 1.0;
@@ -144,6 +155,8 @@ cudaError_t compute_scaling(ProblemData& P, int ruiz_iters, bool pock_chambolle)
   const double* qd = nullptr;
   if (P.is_qp && n) {
     q_diagonal<<<grid_for(n), 256, 0, s>>>(P.F.rp, P.fval, P.D, n, P.qdiag);
+    if (P.q_general)
+      q_diagonal_add<<<grid_for(n), 256, 0, s>>>(P.Q.rp, P.Q.col, P.qval, n, P.qdiag);
     qd = P.qdiag;
   }
   // Round t's norms are taken in the pass that applies round t-1's factors, so a
@@ -186,6 +199,9 @@ cudaError_t compute_scaling(ProblemData& P, int ruiz_iters, bool pock_chambolle)
     if (P.f_nnz)
       apply_scale<<<warp_grid(n), 256, 0, s>>>(P.F.rp, P.F.col, P.fval, P.fval_s, n, P.Dc,
                                                 nullptr);  // F~ = diag(Dc) F
+    if (P.q_general && P.Q.nnz)  // Q~ = diag(Dc) Q diag(Dc)
+      apply_scale<<<warp_grid(n), 256, 0, s>>>(P.Q.rp, P.Q.col, P.qval, P.qval_s, n, P.Dc,
+                                                P.Dc);
   }
   return cudaGetLastError();
 }

@@ -23,13 +23,21 @@ struct ProblemData {
   Csr Ft;                     // r x n (device transpose of F)
   int* permF = nullptr;
 
+  // QP with a general sparse Q (mpax_qp_create): Q is n x n CSR, symmetric with
+  // both triangles stored; D = 0 and F is an empty n x 1 matrix, so the
+  // diagonal-plus-low-rank terms vanish and every Q product is a SpMV with Q.
+  bool q_general = false;
+  Csr Q;
+  double* qval = nullptr;     // original values
+  double* qval_s = nullptr;   // scaled: Dc_i Q_ij Dc_j
+
   // device transpose of A
   Csr At;
   int* permT = nullptr;
   bool transposed = false;
 
   // schedules
-  Sched schedA, schedAt, schedF, schedFt;
+  Sched schedA, schedAt, schedF, schedFt, schedQ;
   bool scheduled = false;
 
   // scaling: A~ = diag(Dr) A diag(Dc)

@@ -504,6 +504,12 @@ struct mpax_shared {
   long long switch_iter = -1;  // last solve: iteration of the switch to FP32 products
   int switch_active = 0;       // last solve: instances still running at the switch
   std::vector<Inst> h_inst;
+  // B = 1: partial sums of the A^T y product over gemv_chunks row chunks and of
+  // the A w product over gemv_nchunks column chunks
+  float* gpart = nullptr;
+  float* gpart_n = nullptr;
+  int gemv_chunks = 1, gemv_nchunks = 1;
+  long long gemv_launches = 0;
 };
 
 namespace {
@@ -516,13 +522,146 @@ void free_shared(mpax_shared* sh) {
                   sh->ct,  sh->lf,   sh->uf,    sh->lcf,   sh->ucf,  sh->w,    sh->xa,
                   sh->xhat, sh->T,   sh->xprev, sh->y,     sh->ya,   sh->yhat, sh->S,
                   sh->yprev, sh->xh_hi, sh->xh_lo, sh->y_hi, sh->y_lo, sh->part, sh->cn,
-                  sh->cns, sh->inst, sh->Xout, sh->Yout};
+                  sh->cns, sh->inst, sh->Xout, sh->Yout, sh->gpart, sh->gpart_n};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (sh->blas) cublasDestroy(sh->blas);
   if (sh->s) cudaStreamDestroy(sh->s);
   delete sh;
 }
+
+}  // namespace
+
+// Template kernels sit in a named namespace: the host stubs generated for a
+// template kernel name its enclosing unnamed namespace, which is ambiguous in
+// this file (mpax's and the global one).
+namespace mpax_gemv {
+
+// ---- single instance (B = 1, FP32 products): the two matrix-vector products --------
+// With one cost vector each product reads A once and is bound by HBM.  Both are
+// plain FP32 sums in a fixed order (no atomics), so results do not depend on the
+// schedule.  V = 4: float4 loads (n % 4 == 0 and 16-byte aligned rows), else 1.
+constexpr int kGemvThreads = 256;
+
+// part[s][j] = sum_{i in chunk s} A_ij y_i: block (bx, s) covers V * 256 columns
+// from bx * V * 256 and the rows [s * rows_per, (s + 1) * rows_per), four rows
+// in flight per thread.
+template <int V>
+__global__ void __launch_bounds__(kGemvThreads) k_gemv_t_part(const float* __restrict__ A, int m,
+                                                              int n, const float* __restrict__ y,
+                                                              int rows_per,
+                                                              float* __restrict__ part) {
+  const int j0 = (blockIdx.x * kGemvThreads + threadIdx.x) * V;
+  if (j0 >= n) return;
+  const int r0 = blockIdx.y * rows_per, r1 = min(m, r0 + rows_per);
+  float acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = 0.0f;
+  int i = r0;
+  for (; i + 4 <= r1; i += 4) {
+    float a[4][V];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float* row = A + (size_t)(i + k) * n + j0;
+      if constexpr (V == 4) {
+        const float4 q = __ldcs(reinterpret_cast<const float4*>(row));
+        a[k][0] = q.x;
+        a[k][1] = q.y;
+        a[k][2] = q.z;
+        a[k][3] = q.w;
+      } else {
+        a[k][0] = __ldcs(row);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float yk = __ldg(y + i + k);
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = fmaf(a[k][v], yk, acc[v]);
+    }
+  }
+  for (; i < r1; ++i) {
+    const float yk = __ldg(y + i);
+    const float* row = A + (size_t)i * n + j0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = fmaf(__ldcs(row + v), yk, acc[v]);
+  }
+  float* out = part + (size_t)blockIdx.y * n + j0;
+#pragma unroll
+  for (int v = 0; v < V; ++v) out[v] = acc[v];
+}
+
+// T_j = sum_s part[s][j], s in order.
+__global__ void k_gemv_t_sum(const float* __restrict__ part, int chunks, int n,
+                             float* __restrict__ T) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    float t = 0.0f;
+    for (int c = 0; c < chunks; ++c) t += part[(size_t)c * n + j];
+    T[j] = t;
+  }
+}
+
+// part[c][i] = sum_{j in column chunk c} A_ij w_j for R rows per block: block
+// (bx, c) covers rows [bx R, bx R + R) and the columns [c cols_per, (c + 1)
+// cols_per) (cols_per a multiple of 4).  Each float4 of w is loaded once and used
+// for the R rows, so every thread keeps R independent loads of A in flight; the
+// R sums are reduced over the block in a fixed order.
+constexpr int kGemvRows = 8;
+template <int V>
+__global__ void __launch_bounds__(kGemvThreads) k_gemv_n_part(const float* __restrict__ A, int m,
+                                                              int n, const float* __restrict__ w,
+                                                              int cols_per,
+                                                              float* __restrict__ part) {
+  constexpr int R = kGemvRows;
+  __shared__ float sh[R][kGemvThreads / 32];
+  const int r0 = blockIdx.x * R;
+  const int j0 = blockIdx.y * cols_per, j1 = min(n, j0 + cols_per);
+  float acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0.0f;
+  const float* rows[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) rows[r] = A + (size_t)min(r0 + r, m - 1) * n;  // valid row
+  if constexpr (V == 4) {
+    for (int q = j0 / 4 + threadIdx.x; q < j1 / 4; q += kGemvThreads) {
+      const float4 wv = __ldg(reinterpret_cast<const float4*>(w) + q);
+      float4 a[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) a[r] = __ldcs(reinterpret_cast<const float4*>(rows[r]) + q);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        acc[r] = fmaf(a[r].x, wv.x, fmaf(a[r].y, wv.y, fmaf(a[r].z, wv.z, fmaf(a[r].w, wv.w, acc[r]))));
+    }
+  } else {
+    for (int j = j0 + threadIdx.x; j < j1; j += kGemvThreads) {
+      const float wv = __ldg(w + j);
+      float a[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) a[r] = __ldcs(rows[r] + j);
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = fmaf(a[r], wv, acc[r]);
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const float t = mpax::warp_sum(acc[r]);
+    if (lane == 0) sh[r][wid] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < R && r0 + threadIdx.x < m) {
+    float t = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kGemvThreads / 32; ++k) t += sh[threadIdx.x][k];
+    part[(size_t)blockIdx.y * m + r0 + threadIdx.x] = t;
+  }
+}
+
+}  // namespace mpax_gemv
+
+namespace {
+
+using namespace mpax_gemv;
 
 // C (rows x B, col-major) = op(M) V, M the stored column-major n x m matrix
 // (A row-major).  trans = 1: C = M^T V (= A V, rows = m, K = n); trans = 0:
@@ -535,6 +674,29 @@ cublasStatus_t product(mpax_shared* sh, int trans, const __nv_bfloat16* vhi,
   const cublasOperation_t op = trans ? CUBLAS_OP_T : CUBLAS_OP_N;
   const float one = 1.0f, zero = 0.0f;
   cublasStatus_t st;
+  if (!bf16x3 && B == 1) {
+    const bool v4 = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(Mf) & 15) == 0) &&
+                    ((reinterpret_cast<uintptr_t>(vf) & 15) == 0);
+    if (trans) {
+      const dim3 grid((m + kGemvRows - 1) / kGemvRows, sh->gemv_nchunks);
+      const int cols_per = ((n + sh->gemv_nchunks - 1) / sh->gemv_nchunks + 3) / 4 * 4;
+      if (v4) k_gemv_n_part<4><<<grid, kGemvThreads, 0, sh->s>>>(Mf, m, n, vf, cols_per, sh->gpart_n);
+      else k_gemv_n_part<1><<<grid, kGemvThreads, 0, sh->s>>>(Mf, m, n, vf, cols_per, sh->gpart_n);
+      k_gemv_t_sum<<<g1(m), 256, 0, sh->s>>>(sh->gpart_n, sh->gemv_nchunks, m, C);
+      sh->gemv_launches += 2;
+    } else {
+      const int V = v4 ? 4 : 1;
+      const dim3 grid((n + V * kGemvThreads - 1) / (V * kGemvThreads), sh->gemv_chunks);
+      const int rows_per = (m + sh->gemv_chunks - 1) / sh->gemv_chunks;
+      if (v4) k_gemv_t_part<4><<<grid, kGemvThreads, 0, sh->s>>>(Mf, m, n, vf, rows_per, sh->gpart);
+      else k_gemv_t_part<1><<<grid, kGemvThreads, 0, sh->s>>>(Mf, m, n, vf, rows_per, sh->gpart);
+      k_gemv_t_sum<<<g1(n), 256, 0, sh->s>>>(sh->gpart, sh->gemv_chunks, n, C);
+      sh->gemv_launches += 2;
+    }
+    sh->gemms += 1;
+    sh->gemm_flops += 2.0 * rows * (double)K;
+    return cudaGetLastError() == cudaSuccess ? CUBLAS_STATUS_SUCCESS : CUBLAS_STATUS_EXECUTION_FAILED;
+  }
   if (!bf16x3) {
     st = cublasSgemm(sh->blas, op, CUBLAS_OP_N, rows, B, K, &one, Mf, n, vf, K, &zero, C, rows);
     sh->gemms += 1;
@@ -609,6 +771,18 @@ mpax_status mpax_lp_shared_create(int32_t m, int32_t n, int32_t B, const float* 
   al(&sh->inst, B);
   al(&sh->Xout, nB);
   al(&sh->Yout, mB);
+  if (B == 1) {
+    // row chunks of the A^T y product: about four blocks per SM in all
+    const long long tiles = (n + 4LL * kGemvThreads - 1) / (4LL * kGemvThreads);
+    const long long want = (4LL * 152 + tiles - 1) / tiles;
+    sh->gemv_chunks = (int)std::max(1LL, std::min(want, std::max(1LL, (long long)m / 16)));
+    al(&sh->gpart, (size_t)sh->gemv_chunks * n);
+    // column chunks of the A w product (multiples of 1024 columns)
+    const long long groups = (m + kGemvRows - 1) / kGemvRows;
+    const long long want_n = (4LL * 152 + groups - 1) / groups;
+    sh->gemv_nchunks = (int)std::max(1LL, std::min(want_n, (n + 1023LL) / 1024));
+    al(&sh->gpart_n, (size_t)sh->gemv_nchunks * m);
+  }
   const cudaMemcpyKind k = kind == MPAX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   if (!e) e = cudaMemcpy(sh->A0, A, sizeof(float) * mn, k);
   if (!e) e = cudaMemcpy(sh->C0, C, sizeof(double) * nB, k);
@@ -648,6 +822,7 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
   long long L = 0;
   sh->gemms = 0;
   sh->gemm_flops = 0.0;
+  sh->gemv_launches = 0;
   // ---- scaling of the shared matrix (Ruiz, Pock-Chambolle) ----------------------
   auto fill1 = [&](double* p, int cnt) {
     std::vector<double> ones(cnt, 1.0);
@@ -820,7 +995,7 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
   cudaStreamWaitEvent(sh->user, ev, 0);
   cudaEventDestroy(ev);
   sh->h_inst = hi;
-  sh->launches = L;
+  sh->launches = L + sh->gemv_launches;
   sh->switch_iter = switch_iter;
   sh->switch_active = switch_active;
   sh->solved = !result;

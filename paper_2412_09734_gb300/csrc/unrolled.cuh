@@ -25,8 +25,8 @@
 //   R2 (rows of A^T)  t = (A^T ws)_j;  tx = ax + b axa + 2 t;  u = tx inside
 //                     the box, else 0, and gl / gu += tx at l / u;
 //                     gc += -tau u;  ax <- u - t
-//   R3                tq = F^T u
-//   R4 (rows of F)    gq = -tau u;  gxmd = D gq - tau (F tq)_j;  gD += gq x_md;
+//   R3                tq = F^T u  (general sparse Q: qu = Q~ u)
+//   R4 (rows of F)    gq = -tau u;  gxmd = D gq - tau (F tq + qu)_j;  gD += gq x_md;
 //                     ax += b gxmd;  axa <- (1 - b)(axa + gxmd)
 //   R5 (rows of A)    ay += tau (A u)_i
 // Inside a block, R4 of step t runs in the epilogue of R2 of step t-1 and R1
@@ -137,11 +137,11 @@ __global__ void k_rev_r4(const DevState* st, int it, int n, const T* __restrict_
                          const int* __restrict__ frp, const int* __restrict__ fcol,
                          const T* __restrict__ fval, const double* __restrict__ tq,
                          const double* __restrict__ u, const T* __restrict__ xmd,
-                         double* __restrict__ ax, double* __restrict__ axa,
-                         double* __restrict__ gD) {
+                         const double* __restrict__ qu, double* __restrict__ ax,
+                         double* __restrict__ axa, double* __restrict__ gD) {
   const double b = st->coef_a[it], tau = st->tau;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    double fq = 0.0;
+    double fq = qu ? qu[j] : 0.0;
     for (int k = frp[j]; k < frp[j + 1]; ++k) fq += (double)fval[k] * tq[fcol[k]];
     const double gq = -tau * u[j];
     const double gxmd = (double)Ds[j] * gq - tau * fq;
@@ -177,6 +177,7 @@ struct EpiRevPrimal {
   const double* tq;     // F^T u of step it + 1
   const T* xmd_next;    // x_md of step it + 1; nullptr: no R4 here
   int it, check;
+  const double* qu;     // general sparse Q: Q~ u of step it + 1 (else nullptr)
   double tau, b, b1;
   __device__ __forceinline__ bool skip() const { return false; }
   __device__ __forceinline__ void load() {
@@ -201,6 +202,7 @@ struct EpiRevPrimal {
     if (xmd_next) {
       double fq = 0.0;
       for (int k = p.f0; k < p.f1; ++k) fq += (double)fval[k] * tq[fcol[k]];
+      if (qu) fq += qu[j];
       const double gq = -tau * p.u1;
       const double gxmd = p.d * gq - tau * fq;
       gD[j] += gq * p.x1;

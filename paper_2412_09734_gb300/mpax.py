@@ -29,7 +29,9 @@ TERMINATION = {0: "unsolved", 1: "optimal", 2: "primal_infeasible", 3: "dual_inf
                4: "iteration_limit", 5: "time_limit", 6: "numerical_error"}
 
 EXPORTED = ["mpax_version", "mpax_last_error", "mpax_status_string", "mpax_options_default",
-            "mpax_lp_create", "mpax_qp_create_diag_lowrank", "mpax_solve", "mpax_get_solution",
+            "mpax_lp_create", "mpax_lp_create_f32", "mpax_qp_create_diag_lowrank",
+            "mpax_qp_create", "mpax_get_reduced_cost", "mpax_solve",
+            "mpax_get_solution",
             "mpax_get_stats", "mpax_destroy", "mpax_prepare", "mpax_get_scaling",
             "mpax_get_transpose", "mpax_set_iterate", "mpax_iterate", "mpax_get_iterate",
             "mpax_kkt", "mpax_lp_value_grad", "mpax_qp_adjoint", "mpax_qp_unrolled_grad",
@@ -122,6 +124,11 @@ _sig = {
                                                                        _INT, _P,
                                                                        ctypes.POINTER(_P)],
                                     _INT),
+    "mpax_lp_create_f32": ([_I32, _I32, _I64] + [_P] * 8 + [_INT, _P, ctypes.POINTER(_P)],
+                           _INT),
+    "mpax_get_reduced_cost": ([_P, _P, _INT], _INT),
+    "mpax_qp_create": ([_I32, _I32, _I64] + [_P] * 8 + [_I64, _P, _P, _P, _INT, _P,
+                                                          ctypes.POINTER(_P)], _INT),
     "mpax_solve": ([_P, ctypes.POINTER(Options), _P, _P, _INT], _INT),
     "mpax_get_solution": ([_P, _P, _P, _INT], _INT),
     "mpax_get_stats": ([_P, ctypes.POINTER(Stats)], _INT),
@@ -190,7 +197,7 @@ class _Keep:
             return None
         if _is_torch(a):
             import torch
-            tdt = {np.float64: torch.float64, np.int64: torch.int64,
+            tdt = {np.float64: torch.float64, np.float32: torch.float32, np.int64: torch.int64,
                    np.int32: torch.int32}[dtype]
             if self.kind == MPAX_MEM_DEVICE and not a.is_cuda:
                 raise ValueError("mixed host/device arguments")
@@ -266,6 +273,43 @@ def mpax_qp_create_diag_lowrank(m, n, row_ptr, col_idx, val, c, lc, uc, l, u, D,
         k.ptr(l, np.float64), k.ptr(u, np.float64), k.ptr(D, np.float64), r, f_nnz,
         k.ptr(f_row_ptr, np.int64), k.ptr(f_col_idx, np.int32), k.ptr(f_val, np.float64),
         kind, _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def mpax_lp_create_f32(m, n, row_ptr, col_idx, val, c, lc, uc, l, u, stream=None):
+    """mpax_lp_create with FP32 values and vectors (widened to FP64 on entry)."""
+    kind = _kind_of(row_ptr, val)
+    k = _Keep(kind)
+    nnz = int(len(val)) if not _is_torch(val) else int(val.numel())
+    h = _P()
+    _check(_lib.mpax_lp_create_f32(
+        m, n, nnz, k.ptr(row_ptr, np.int64), k.ptr(col_idx, np.int32), k.ptr(val, np.float32),
+        k.ptr(c, np.float32), k.ptr(lc, np.float32), k.ptr(uc, np.float32),
+        k.ptr(l, np.float32), k.ptr(u, np.float32), kind, _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def mpax_get_reduced_cost(h, n, device=None):
+    """lam = Q x + c - A^T y at the returned point (unscaled)."""
+    lam, kind = _out(n, device)
+    _check(_lib.mpax_get_reduced_cost(h, _ptr_out(lam), kind))
+    return lam
+
+
+def mpax_qp_create(m, n, row_ptr, col_idx, val, c, lc, uc, l, u, q_row_ptr, q_col_idx, q_val,
+                   stream=None):
+    """QP with a general sparse symmetric PSD Q (CSR, both triangles stored)."""
+    kind = _kind_of(row_ptr, val)
+    k = _Keep(kind)
+    nnz = int(len(val)) if not _is_torch(val) else int(val.numel())
+    q_nnz = int(len(q_val)) if not _is_torch(q_val) else int(q_val.numel())
+    h = _P()
+    _check(_lib.mpax_qp_create(
+        m, n, nnz, k.ptr(row_ptr, np.int64), k.ptr(col_idx, np.int32), k.ptr(val, np.float64),
+        k.ptr(c, np.float64), k.ptr(lc, np.float64), k.ptr(uc, np.float64),
+        k.ptr(l, np.float64), k.ptr(u, np.float64), q_nnz, k.ptr(q_row_ptr, np.int64),
+        k.ptr(q_col_idx, np.int32), k.ptr(q_val, np.float64), kind, _stream(stream),
+        ctypes.byref(h)))
     return h
 
 

@@ -10,6 +10,7 @@ from .generators import (  # noqa: F401
     csr_random,
     lp_instance,
     qp_instance,
+    qp_sparse_q_instance,
     ragged_lp_batch,
     shared_dense_lp_batch,
     knapsack_lp,

@@ -222,6 +222,29 @@ def qp_instance(n: int, m: int, *, seed: int, a_density: float = 1e-4, f_cols: i
                 x0=x0, x_target=x_target)
 
 
+def qp_sparse_q_instance(n: int, m: int, *, seed: int, a_density: float = 1e-4,
+                         b_density: float = 2e-4, lo: float = -1.0, hi: float = 1.0,
+                         min_row: int = 0) -> dict:
+    """Convex QP with a general sparse Q = B B^T + diag(U[0.1, 1]) (B n x n with
+    N(0, 1) entries at `b_density`), stored as CSR with both triangles and sorted
+    columns; A, the box, b = A x0 and c ~ N(0, 1) as in qp_instance."""
+    import scipy.sparse as sp
+    rng = _rng(seed)
+    row_ptr, col, val = csr_random(m, n, rng, density=a_density, min_row=min_row)
+    b_ptr, b_col, b_val = csr_random(n, n, rng, density=b_density)
+    Bm = sp.csr_matrix((b_val, b_col, b_ptr), shape=(n, n))
+    Q = sp.csr_matrix(Bm @ Bm.T + sp.diags(rng.uniform(0.1, 1.0, size=n)))
+    Q.sort_indices()
+    x0 = rng.uniform(lo, hi, size=n)
+    b = _matvec(row_ptr, col, val, x0)
+    c = rng.standard_normal(n)
+    x_target = rng.uniform(lo, hi, size=n)
+    return dict(kind="qp", m=m, n=n, nnz=int(row_ptr[-1]), row_ptr=row_ptr, col=col, val=val,
+                c=c, lc=b.copy(), uc=b.copy(), l=np.full(n, lo), u=np.full(n, hi),
+                q_row_ptr=Q.indptr.astype(np.int64), q_col=Q.indices.astype(np.int32),
+                q_val=Q.data.astype(np.float64), x0=x0, x_target=x_target)
+
+
 # ----------------------------------------------------------------------------
 # Ragged batch of independent LPs (packed CSR)
 # ----------------------------------------------------------------------------

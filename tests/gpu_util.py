@@ -16,6 +16,9 @@ def create(C, d, device=False):
         import torch
         conv = (lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda())
     args = [conv(d[k]) for k in ("row_ptr", "col", "val", "c", "lc", "uc", "l", "u")]
+    if "q_row_ptr" in d:
+        return C.mpax_qp_create(d["m"], d["n"], *args, conv(d["q_row_ptr"]), conv(d["q_col"]),
+                                conv(d["q_val"]))
     if "D" in d:
         return C.mpax_qp_create_diag_lowrank(d["m"], d["n"], *args, conv(d["D"]), d["f_cols"],
                                              conv(d["f_row_ptr"]), conv(d["f_col"]),

@@ -47,10 +47,15 @@ def test_lp_value_gradient_matches_oracle(C):
         assert np.max(np.abs(g[k] - gr[k])) <= 1e-6 * (1 + np.max(np.abs(gr[k]))), k
 
 
-@pytest.mark.parametrize("case,eps,tol", [("small", 1e-11, 1e-5), ("4k", 1e-8, 1e-3)])
+@pytest.mark.parametrize("case,eps,tol", [("small", 1e-11, 1e-5), ("4k", 1e-8, 1e-3),
+                                          ("sparse_q", 1e-11, 1e-5)])
 def test_qp_adjoint_matches_oracle(C, case, eps, tol):
     if case == "small":
         d = _qp_small()
+    elif case == "sparse_q":
+        from synth import qp_sparse_q_instance
+        d = qp_sparse_q_instance(50, 25, seed=instance_seed(204), a_density=0.04,
+                                 b_density=0.04, min_row=2)
     else:
         d = qp_instance(4000, 2000, seed=instance_seed(201), a_density=5e-3, f_cols=32,
                         f_density=0.01)

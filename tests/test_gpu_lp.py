@@ -387,3 +387,29 @@ def test_certified_norm_bound_without_power_iteration(C):
     assert s["termination_name"] == "optimal"
     assert abs(s["iterations"] - ref.iterations) <= 2 * 64
     assert O.kkt(p, x, y, 1e-8, 1e-8)["converged"]
+
+
+def test_f32_create_and_reduced_costs(C):
+    """mpax_lp_create_f32 on FP32-representable data solves exactly the problem of
+    the FP64 create (bitwise equal results), and the reduced costs are
+    c - A^T y at the returned point (oracle arithmetic)."""
+    d = lp_instance(200, 400, seed=instance_seed(11), density=0.02)
+    f = {k: np.asarray(d[k], dtype=np.float32) for k in ("val", "c", "lc", "uc", "l", "u")}
+    d64 = dict(d, **{k: v.astype(np.float64) for k, v in f.items()})
+    opts = C.mpax_options_default(eps_abs=1e-6, eps_rel=1e-6, iteration_limit=100000)
+    h1 = create(C, d64)
+    h2 = C.mpax_lp_create_f32(d["m"], d["n"], d["row_ptr"], d["col"], f["val"], f["c"], f["lc"],
+                              f["uc"], f["l"], f["u"])
+    try:
+        C.mpax_solve(h1, opts)
+        C.mpax_solve(h2, opts)
+        x1, y1 = C.mpax_get_solution(h1, d["m"], d["n"])
+        x2, y2 = C.mpax_get_solution(h2, d["m"], d["n"])
+        lam = C.mpax_get_reduced_cost(h1, d["n"])
+    finally:
+        C.mpax_destroy(h1)
+        C.mpax_destroy(h2)
+    assert np.array_equal(x1, x2) and np.array_equal(y1, y2)
+    p = O.problem_from_arrays(d64)
+    ref = p.c - p.A.T @ y1
+    assert rel_inf(lam, ref) <= 1e-12

@@ -1,10 +1,11 @@
 """GPU parity of the QP path (rAPDHG, Algorithm 2) against the FP64 oracle.
-Q = diag(D) + F F^T with F sparse n x r, as in the differentiable-QP workload."""
+Q = diag(D) + F F^T with F sparse n x r, as in the differentiable-QP workload, and
+a general sparse Q (mpax_qp_create)."""
 import numpy as np
 import pytest
 
 from oracle import pdhg as O
-from synth import instance_seed, qp_instance, random_state
+from synth import instance_seed, qp_instance, qp_sparse_q_instance, random_state
 from tests.gpu_util import create, lib, rel_inf
 
 pytestmark = pytest.mark.gpu
@@ -26,6 +27,11 @@ CASES = {
     # the n = 50 finite-difference copy: densities raised so each row has >= 2 entries
     "qp_50_25": lambda: qp_instance(50, 25, seed=instance_seed(202), a_density=0.04,
                                     f_cols=32, f_density=0.04, min_row=2),
+    # general sparse Q = B B^T + diag (about 5 entries per row at 20k)
+    "qpq_20k_10k": lambda: qp_sparse_q_instance(20000, 10000, seed=instance_seed(203),
+                                                a_density=1e-3, b_density=1e-4),
+    "qpq_50_25": lambda: qp_sparse_q_instance(50, 25, seed=instance_seed(204), a_density=0.04,
+                                              b_density=0.04, min_row=2),
 }
 
 
@@ -86,7 +92,8 @@ def test_qp_norms_and_kkt_match_oracle(C, case):
 
 
 @pytest.mark.parametrize("case,prec,eps", [("qp_50_25", 0, 1e-8), ("qp_20k_10k", 0, 1e-6),
-                                           ("qp_20k_10k", 1, 1e-4)])
+                                           ("qp_20k_10k", 1, 1e-4), ("qpq_50_25", 0, 1e-8),
+                                           ("qpq_20k_10k", 0, 1e-6), ("qpq_20k_10k", 1, 1e-4)])
 def test_qp_solve_matches_oracle(C, case, prec, eps):
     d = CASES[case]()
     p = O.problem_from_arrays(d)
@@ -98,9 +105,11 @@ def test_qp_solve_matches_oracle(C, case, prec, eps):
                                                iteration_limit=500000))
         stats = C.mpax_get_stats(h)
         x, y = C.mpax_get_solution(h, d["m"], d["n"])
+        lam = C.mpax_get_reduced_cost(h, d["n"])
     finally:
         C.mpax_destroy(h)
     assert stats["termination_name"] == "optimal"
+    assert rel_inf(lam, p.qx(x) + p.c - p.A.T @ y) <= 1e-12
     chk = O.kkt(p, x, y, eps, eps)
     assert chk["converged"]
     # strictly convex: the solution is unique; distance bounded by the tolerance

@@ -27,13 +27,17 @@ def _case(name):
         # equality, lower- and upper-bounded rows, all active
         p, d = _mixed_rows_problem()
         return dict(d, lc=p.lc, uc=p.uc), 400, 16
+    if name == "sparse_q":
+        from synth import qp_sparse_q_instance
+        return qp_sparse_q_instance(2000, 1000, seed=instance_seed(205), a_density=5e-3,
+                                    b_density=1e-3), 320, 32
     # 4000 variables: several SpMV tiles, long and short rows, a ragged tail
     d = qp_instance(4000, 2000, seed=instance_seed(201), a_density=5e-3, f_cols=32,
                     f_density=0.01)
     return d, 640, 64
 
 
-@pytest.mark.parametrize("name", ["small", "4k"])
+@pytest.mark.parametrize("name", ["small", "4k", "sparse_q"])
 def test_unrolled_gradient_matches_oracle(C, name):
     d, iters, every = _case(name)
     p = O.problem_from_arrays(d)

@@ -104,3 +104,39 @@ def test_qp_adjoint_matches_finite_differences():
             D[j] += s
             return O.Problem(p.A, p.c, p.lc, p.uc, p.l, p.u, O.DiagLowRankQ(D, p.Q.F))
         assert fd(mk) == pytest.approx(dD[j], rel=1e-4, abs=1e-6)
+
+
+def test_sparse_q_adjoint_matches_finite_differences():
+    """A general sparse Q: dL/dc and the gradient of Q's diagonal against central
+    differences of converged oracle solves."""
+    import scipy.sparse as sp
+    from synth import qp_sparse_q_instance
+    d = qp_sparse_q_instance(50, 25, seed=instance_seed(204), a_density=0.04, b_density=0.04,
+                             min_row=2)
+    p = O.problem_from_arrays(d)
+    xt = d["x_target"]
+    opts = O.Options(eps_abs=1e-11, eps_rel=1e-11, iteration_limit=10**6)
+    r = O.solve_qp(p, opts)
+    free, rows = AD.active_sets(p, r.x, r.y, 1e-7, 1e-7)
+    lam = p.qx(r.x) + p.c - p.A.T @ r.y
+    assert np.all(np.abs(lam[~free]) > 1e-6)
+    dc, db, dD = AD.qp_adjoint(p, r.x, r.y, r.x - xt, free, rows)
+    h = 1e-6
+    rng = np.random.default_rng(3)
+
+    def fd(make):
+        return (_qp_loss(make(+h), xt, opts) - _qp_loss(make(-h), xt, opts)) / (2 * h)
+
+    for j in rng.choice(p.n, 4, replace=False):
+        def mk(s, j=j):
+            c = p.c.copy()
+            c[j] += s
+            return O.Problem(p.A, c, p.lc, p.uc, p.l, p.u, p.Q)
+        assert fd(mk) == pytest.approx(dc[j], rel=1e-4, abs=1e-6)
+    for j in rng.choice(np.flatnonzero(free), 3, replace=False):
+        def mk(s, j=j):
+            e = np.zeros(p.n)
+            e[j] = s
+            return O.Problem(p.A, p.c, p.lc, p.uc, p.l, p.u,
+                             O.SparseQ(p.Q.Q + sp.diags(e)))
+        assert fd(mk) == pytest.approx(dD[j], rel=1e-4, abs=1e-6)

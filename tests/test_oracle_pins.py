@@ -270,6 +270,29 @@ def test_qp_matches_active_set_enumeration(seed, n, m):
     assert r.kkt["primal_obj"] == pytest.approx(val, rel=1e-8, abs=1e-8)
 
 
+def _sparse_psd_q(n, seed):
+    """Q = B B^T + diag(U[0.1, 1]) with B n x n at 30% density: sparse, symmetric,
+    positive definite, with off-diagonal entries of both signs."""
+    rng = np.random.default_rng(seed)
+    B = sp.random(n, n, density=0.3, random_state=rng, data_rvs=rng.standard_normal)
+    return sp.csr_matrix(B @ B.T + sp.diags(rng.uniform(0.1, 1.0, n)))
+
+
+@pytest.mark.parametrize("seed,n,m", [(83, 6, 2), (84, 8, 3)])
+def test_sparse_q_qp_matches_active_set_enumeration(seed, n, m):
+    """A general sparse Q (SparseQ): its diagonal joins the scaling, its norm the
+    step sizes and its product the iteration and the KKT test."""
+    d = qp_instance(n, m, seed=instance_seed(seed), a_density=0.6, f_cols=3, f_density=0.5,
+                    min_row=2)
+    p0 = O.problem_from_arrays(d)
+    p = O.Problem(p0.A, p0.c, p0.lc, p0.uc, p0.l, p0.u, O.SparseQ(_sparse_psd_q(n, seed)))
+    r = O.solve_qp(p, O.Options(eps_abs=1e-10, eps_rel=1e-10, iteration_limit=2000000))
+    assert r.status == "optimal"
+    x, y, val = brute.qp_active_set_enumeration(p.Q.dense(), p.c, p.A.toarray(), p.lc, p.l, p.u)
+    np.testing.assert_allclose(r.x, x, rtol=0, atol=1e-6)
+    assert r.kkt["primal_obj"] == pytest.approx(val, rel=1e-8, abs=1e-8)
+
+
 def test_box_qp_diagonal_closed_form():
     rng = np.random.default_rng(9)
     n = 30

@@ -140,3 +140,34 @@ def test_one_step_closed_form():
     np.testing.assert_allclose(G["c"][inside], -tau * res.Dc[inside] ** 2 * gx[inside],
                                rtol=1e-14, atol=0)
     assert np.all(G["c"][~inside] == 0)
+
+
+def test_sparse_q_unrolled_gradient_matches_path_differences():
+    """A general sparse Q: dL/dc and the gradient of Q's diagonal along the path."""
+    import scipy.sparse as sp
+    from synth import qp_sparse_q_instance
+    d = qp_sparse_q_instance(50, 25, seed=instance_seed(204), a_density=0.04, b_density=0.04,
+                             min_row=2)
+    p = O.problem_from_arrays(d)
+    res, tape = U.taped_solve(p, O.Options(eps_abs=1e-14, eps_rel=1e-14, iteration_limit=300,
+                                           check_every=16))
+    rng = np.random.default_rng(12)
+    gx = rng.standard_normal(p.n)
+    G = U.unrolled_gradient(p, res, tape, gx)
+    sched = U.schedule(tape)
+    gy = np.zeros(p.m)
+    h = 1e-7
+
+    def fd(make):
+        return (_path_loss(make(+h), res, sched, gx, gy)
+                - _path_loss(make(-h), res, sched, gx, gy)) / (2 * h)
+
+    for j in rng.choice(p.n, 4, replace=False):
+        e = np.eye(p.n)[j]
+        assert fd(lambda s, e=e: O.Problem(p.A, p.c + s * e, p.lc, p.uc, p.l, p.u, p.Q)) == \
+            pytest.approx(G["c"][j], rel=1e-5, abs=1e-6)
+    for j in rng.choice(p.n, 4, replace=False):
+        e = np.eye(p.n)[j]
+        mk = lambda s, e=e: O.Problem(p.A, p.c, p.lc, p.uc, p.l, p.u,  # noqa: E731
+                                      O.SparseQ(p.Q.Q + sp.diags(s * e)))
+        assert fd(mk) == pytest.approx(G["D"][j], rel=1e-5, abs=1e-6)
