@@ -149,17 +149,25 @@ struct Vecs {
 
 // primal: T = A~^T Y; x = w + (anchor - w)/(k+1); x^ = proj(x - tau (c~ - T));
 // w <- 2 x^ - x (also split to BF16 for the next product)
-__global__ void k_primal(Vecs v, int check) {
+// tpart (B = 1 only): T is the sum of the GEMV's tchunks partials, in order.
+__global__ void k_primal(Vecs v, int check, const float* __restrict__ tpart, int tchunks) {
   const size_t total = (size_t)v.n * v.B;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(e / v.n), j = (int)(e % v.n);
     const Inst& I = v.inst[k];
     if (I.done) continue;
+    float t;
+    if (tpart) {
+      t = 0.0f;
+      for (int c = 0; c < tchunks; ++c) t += tpart[(size_t)c * v.n + j];
+    } else {
+      t = v.T[e];
+    }
     const float rb = (float)(1.0 / (double)(I.k + 1));
     const float x0 = v.xa[e], wv = v.w[e];
     const float x = (I.k == 0) ? x0 : wv + rb * (x0 - wv);
-    const float xh = fminf(fmaxf(x - (float)I.tau * (v.ct[e] - v.T[e]), v.l[j]), v.u[j]);
+    const float xh = fminf(fmaxf(x - (float)I.tau * (v.ct[e] - t), v.l[j]), v.u[j]);
     const float wn = 2.0f * xh - x;
     v.w[e] = wn;
     split_store(wn, v.xh_hi, v.xh_lo, e);
@@ -169,17 +177,25 @@ __global__ void k_primal(Vecs v, int check) {
 
 // dual: S = A~ xbar; y^ = sigma (v - proj_[-uc,-lc](v)), v = y/sigma - S;
 // y <- z + (anchor - z)/(k+2), z = 2 y^ - y (also split)
-__global__ void k_dual(Vecs v, int check) {
+// spart (B = 1 only): S is the sum of the GEMV's schunks partials, in order.
+__global__ void k_dual(Vecs v, int check, const float* __restrict__ spart, int schunks) {
   const size_t total = (size_t)v.m * v.B;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(e / v.m), i = (int)(e % v.m);
     const Inst& I = v.inst[k];
     if (I.done) continue;
+    float sv;
+    if (spart) {
+      sv = 0.0f;
+      for (int c = 0; c < schunks; ++c) sv += spart[(size_t)c * v.m + i];
+    } else {
+      sv = v.S[e];
+    }
     const float sg = (float)I.sigma, isg = (float)(1.0 / I.sigma);
     const float hb = (float)(1.0 / (double)(I.k + 2));
     const float y0 = v.y[e];
-    const float vv = y0 * isg - v.S[e];
+    const float vv = y0 * isg - sv;
     const float yh = sg * (vv - fminf(fmaxf(vv, -v.uc[i]), -v.lc[i]));
     const float z = 2.0f * yh - y0;
     const float yn = z + hb * (v.ya[e] - z);
@@ -663,6 +679,29 @@ namespace {
 
 using namespace mpax_gemv;
 
+// B = 1, FP32 products: the partial-sum kernel of one product, trans = 1: A v
+// into gpart_n (column chunks), trans = 0: A^T v into gpart (row chunks).
+void gemv_part(mpax_shared* sh, int trans, const float* vf, const float* Mf) {
+  const int m = sh->m, n = sh->n;
+  const bool v4 = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(Mf) & 15) == 0) &&
+                  ((reinterpret_cast<uintptr_t>(vf) & 15) == 0);
+  if (trans) {
+    const dim3 grid((m + kGemvRows - 1) / kGemvRows, sh->gemv_nchunks);
+    const int cols_per = ((n + sh->gemv_nchunks - 1) / sh->gemv_nchunks + 3) / 4 * 4;
+    if (v4) k_gemv_n_part<4><<<grid, kGemvThreads, 0, sh->s>>>(Mf, m, n, vf, cols_per, sh->gpart_n);
+    else k_gemv_n_part<1><<<grid, kGemvThreads, 0, sh->s>>>(Mf, m, n, vf, cols_per, sh->gpart_n);
+  } else {
+    const int V = v4 ? 4 : 1;
+    const dim3 grid((n + V * kGemvThreads - 1) / (V * kGemvThreads), sh->gemv_chunks);
+    const int rows_per = (m + sh->gemv_chunks - 1) / sh->gemv_chunks;
+    if (v4) k_gemv_t_part<4><<<grid, kGemvThreads, 0, sh->s>>>(Mf, m, n, vf, rows_per, sh->gpart);
+    else k_gemv_t_part<1><<<grid, kGemvThreads, 0, sh->s>>>(Mf, m, n, vf, rows_per, sh->gpart);
+  }
+  sh->gemv_launches += 1;
+  sh->gemms += 1;
+  sh->gemm_flops += 2.0 * m * (double)n;
+}
+
 // C (rows x B, col-major) = op(M) V, M the stored column-major n x m matrix
 // (A row-major).  trans = 1: C = M^T V (= A V, rows = m, K = n); trans = 0:
 // C = M V (= A^T V, rows = n, K = m).  BF16x3 or FP32.
@@ -675,26 +714,10 @@ cublasStatus_t product(mpax_shared* sh, int trans, const __nv_bfloat16* vhi,
   const float one = 1.0f, zero = 0.0f;
   cublasStatus_t st;
   if (!bf16x3 && B == 1) {
-    const bool v4 = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(Mf) & 15) == 0) &&
-                    ((reinterpret_cast<uintptr_t>(vf) & 15) == 0);
-    if (trans) {
-      const dim3 grid((m + kGemvRows - 1) / kGemvRows, sh->gemv_nchunks);
-      const int cols_per = ((n + sh->gemv_nchunks - 1) / sh->gemv_nchunks + 3) / 4 * 4;
-      if (v4) k_gemv_n_part<4><<<grid, kGemvThreads, 0, sh->s>>>(Mf, m, n, vf, cols_per, sh->gpart_n);
-      else k_gemv_n_part<1><<<grid, kGemvThreads, 0, sh->s>>>(Mf, m, n, vf, cols_per, sh->gpart_n);
-      k_gemv_t_sum<<<g1(m), 256, 0, sh->s>>>(sh->gpart_n, sh->gemv_nchunks, m, C);
-      sh->gemv_launches += 2;
-    } else {
-      const int V = v4 ? 4 : 1;
-      const dim3 grid((n + V * kGemvThreads - 1) / (V * kGemvThreads), sh->gemv_chunks);
-      const int rows_per = (m + sh->gemv_chunks - 1) / sh->gemv_chunks;
-      if (v4) k_gemv_t_part<4><<<grid, kGemvThreads, 0, sh->s>>>(Mf, m, n, vf, rows_per, sh->gpart);
-      else k_gemv_t_part<1><<<grid, kGemvThreads, 0, sh->s>>>(Mf, m, n, vf, rows_per, sh->gpart);
-      k_gemv_t_sum<<<g1(n), 256, 0, sh->s>>>(sh->gpart, sh->gemv_chunks, n, C);
-      sh->gemv_launches += 2;
-    }
-    sh->gemms += 1;
-    sh->gemm_flops += 2.0 * rows * (double)K;
+    gemv_part(sh, trans, vf, Mf);
+    if (trans) k_gemv_t_sum<<<g1(m), 256, 0, sh->s>>>(sh->gpart_n, sh->gemv_nchunks, m, C);
+    else k_gemv_t_sum<<<g1(n), 256, 0, sh->s>>>(sh->gpart, sh->gemv_chunks, n, C);
+    sh->gemv_launches += 1;
     return cudaGetLastError() == cudaSuccess ? CUBLAS_STATUS_SUCCESS : CUBLAS_STATUS_EXECUTION_FAILED;
   }
   if (!bf16x3) {
@@ -931,17 +954,27 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
         k_copy_f<<<g1(mB), 256, 0, s>>>(sh->y, sh->yprev, mB);
         L += 2;
       }
+      if (B == 1 && !bf) {
+        // one instance, FP32: GEMV partials, summed inside the update kernels
+        gemv_part(sh, 0, sh->y, sh->As);
+        k_primal<<<g1(nB), 256, 0, s>>>(V, chk, sh->gpart, sh->gemv_chunks);
+        gemv_part(sh, 1, sh->w, sh->As);
+        k_dual<<<g1(mB), 256, 0, s>>>(V, chk, sh->gpart_n, sh->gemv_nchunks);
+        k_advance<<<(B + 255) / 256, 256, 0, s>>>(sh->inst, B);
+        L += 3;
+        continue;
+      }
       if (product(sh, 0, sh->y_hi, sh->y_lo, sh->y, sh->T, bf, sh->As)) {
         result = sfail(MPAX_ERR_CUDA, "cuBLAS product failed");
         break;
       }
-      k_primal<<<g1(nB), 256, 0, s>>>(V, chk);
+      k_primal<<<g1(nB), 256, 0, s>>>(V, chk, nullptr, 0);
       // the dual product reads the reflected point w (FP32) or its BF16 split
       if (product(sh, 1, sh->xh_hi, sh->xh_lo, sh->w, sh->S, bf, sh->As)) {
         result = sfail(MPAX_ERR_CUDA, "cuBLAS product failed");
         break;
       }
-      k_dual<<<g1(mB), 256, 0, s>>>(V, chk);
+      k_dual<<<g1(mB), 256, 0, s>>>(V, chk, nullptr, 0);
       k_advance<<<(B + 255) / 256, 256, 0, s>>>(sh->inst, B);
       L += 3;
     }

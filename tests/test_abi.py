@@ -99,3 +99,39 @@ def test_invalid_sizes_rejected_before_device_work(C):
 def test_status_strings(C):
     for s in range(8):
         assert C._lib.mpax_status_string(s).decode() != "unknown status"
+
+
+def test_new_entry_points_check_arguments_before_device_work(C):
+    """mpax_qp_create, mpax_lp_create_f32, mpax_qp_unrolled_grad and
+    mpax_get_reduced_cost reject bad arguments on the host."""
+    h = ctypes.c_void_p()
+    rp = np.array([0, 1, 2], dtype=np.int64)
+    # general sparse Q without its row pointer
+    st = C._lib.mpax_qp_create(2, 3, 0, rp.ctypes.data, None, None, None, None, None, None,
+                               None, 0, None, None, None, 0, None, ctypes.byref(h))
+    assert st == C.MPAX_ERR_INVALID_ARGUMENT and "q_row_ptr" in C.mpax_last_error()
+    # Q with entries but no column indices
+    st = C._lib.mpax_qp_create(2, 3, 0, rp.ctypes.data, None, None, None, None, None, None,
+                               None, 4, rp.ctypes.data, None, None, 0, None, ctypes.byref(h))
+    assert st == C.MPAX_ERR_INVALID_ARGUMENT
+    # Q with 2^31 entries
+    st = C._lib.mpax_qp_create(2, 3, 0, rp.ctypes.data, None, None, None, None, None, None,
+                               None, 1 << 31, rp.ctypes.data, None, None, 0, None, ctypes.byref(h))
+    assert st == C.MPAX_ERR_UNSUPPORTED
+    # FP32 create: negative sizes, bad memory kind, NULL vectors
+    st = C._lib.mpax_lp_create_f32(-1, 3, 0, None, None, None, None, None, None, None, None,
+                                   0, None, ctypes.byref(h))
+    assert st == C.MPAX_ERR_INVALID_ARGUMENT
+    st = C._lib.mpax_lp_create_f32(2, 3, 0, rp.ctypes.data, None, None, None, None, None, None,
+                                   None, 7, None, ctypes.byref(h))
+    assert st == C.MPAX_ERR_INVALID_ARGUMENT and "kind" in C.mpax_last_error()
+    st = C._lib.mpax_lp_create_f32(2, 3, 0, rp.ctypes.data, None, None, None, None, None, None,
+                                   None, 0, None, ctypes.byref(h))
+    assert st == C.MPAX_ERR_INVALID_ARGUMENT and "NULL" in C.mpax_last_error()
+    # differentiation and getters on a NULL problem
+    g = np.zeros(3)
+    assert C._lib.mpax_qp_unrolled_grad(None, g.ctypes.data, None, None, None, None, None,
+                                        None, None, 0) == C.MPAX_ERR_INVALID_ARGUMENT
+    assert C._lib.mpax_get_reduced_cost(None, g.ctypes.data, 0) == C.MPAX_ERR_INVALID_ARGUMENT
+    # record_tape is an FP64 option: the default leaves it off
+    assert C.mpax_options_default().record_tape == 0
