@@ -653,7 +653,7 @@ def run_qp(args):
         G = C.mpax_qp_unrolled_grad(h, x - xt, m, n)
         torch.cuda.synchronize()
         t3 = time.perf_counter()
-        back_launches = C.mpax_get_stats(h)["kernel_launches"]
+        back_launches = C.mpax_get_stats(h)["backward_launches"]
         dc, _, _, _ = C.mpax_qp_adjoint(h, x - xt, m, n, tol=1e-8)
         rel = float(torch.linalg.norm(G["c"] - dc) / torch.linalg.norm(dc))
     finally:

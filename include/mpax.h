@@ -159,6 +159,7 @@ typedef struct mpax_stats {
   int64_t profile_launches[4];
   int64_t fp64_iterations;           /* iterations of the FP64 continuation (MIXED) */
   int64_t polish_iterations;         /* iterations of the two feasibility-polishing runs */
+  int64_t backward_launches;         /* library kernels of the last mpax_qp_unrolled_grad */
 } mpax_stats;
 
 typedef struct mpax_problem mpax_problem;

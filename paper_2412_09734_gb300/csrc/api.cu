@@ -832,7 +832,7 @@ mpax_status mpax_qp_unrolled_grad(mpax_problem* pb, const double* gx, const doub
   cudaFree(buf);
   if (e) return cuda_fail(e, "unrolled gradient");
   TRY_CUDA(order_user_after(pb), "stream order");
-  pb->stats.kernel_launches = launches;
+  pb->stats.backward_launches = launches;
   return MPAX_OK;
 }
 

@@ -81,6 +81,7 @@ class Stats(ctypes.Structure):
         ("kernel_launches", ctypes.c_int64),
         ("profile_ms", ctypes.c_double * 4), ("profile_launches", ctypes.c_int64 * 4),
         ("fp64_iterations", ctypes.c_int64), ("polish_iterations", ctypes.c_int64),
+        ("backward_launches", ctypes.c_int64),
     ]
 
     def as_dict(self):
