@@ -133,3 +133,38 @@ def test_unrolled_layer_matches_the_adjoint_layer(C):
         grads.append([t.grad.cpu().numpy() for t in (c, b, D)])
     for ga, gu in zip(*grads):
         assert np.linalg.norm(gu - ga) <= 1e-4 * np.linalg.norm(ga)
+
+
+@pytest.mark.parametrize("form", ["diag_lowrank", "sparse_q"])
+def test_box_qp_without_rows(C, form):
+    """m = 0, Q diagonal: x* = clamp(-c / D, l, u) (closed form), and at
+    convergence the unrolled gradient of g . x is -g / D on the free coordinates
+    and 0 on the clamped ones."""
+    n = 3000
+    rng = np.random.default_rng(21)
+    D = rng.uniform(0.1, 1.0, n)
+    c = 2.0 * rng.standard_normal(n)
+    l, u = -np.ones(n), np.ones(n)
+    empty = dict(m=0, n=n, row_ptr=np.zeros(1, dtype=np.int64), col=np.zeros(0, dtype=np.int32),
+                 val=np.zeros(0), c=c, lc=np.zeros(0), uc=np.zeros(0), l=l, u=u)
+    if form == "diag_lowrank":
+        d = dict(empty, D=D, f_cols=1, f_row_ptr=np.zeros(n + 1, dtype=np.int64),
+                 f_col=np.zeros(0, dtype=np.int32), f_val=np.zeros(0))
+    else:
+        d = dict(empty, q_row_ptr=np.arange(n + 1, dtype=np.int64),
+                 q_col=np.arange(n, dtype=np.int32), q_val=D)
+    g = rng.standard_normal(n)
+    h = create(C, d)
+    try:
+        C.mpax_solve(h, C.mpax_options_default(eps_abs=1e-10, eps_rel=1e-10,
+                                               iteration_limit=10**6, record_tape=1))
+        assert C.mpax_get_stats(h)["termination"] == C.MPAX_TERM_OPTIMAL
+        x, _ = C.mpax_get_solution(h, 0, n)
+        G = C.mpax_qp_unrolled_grad(h, g, 0, n)
+    finally:
+        C.mpax_destroy(h)
+    xs = np.clip(-c / D, l, u)
+    np.testing.assert_allclose(x, xs, rtol=0, atol=1e-7)
+    free = np.abs(xs) < 1 - 1e-3
+    np.testing.assert_allclose(G["c"][free], -g[free] / D[free], rtol=1e-6, atol=1e-9)
+    assert np.max(np.abs(G["c"][~free])) <= 1e-9
