@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sparse_lp_500k",
                     choices=list(WORKLOADS) + ["ragged_lp_4096", "shared_dense_512",
-                                               "qp_200k", "knapsack_1000x100000"])
+                                               "qp_200k", "knapsack_1000x100000",
+                                               "next_rows_20k"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-iters", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -750,8 +751,71 @@ def run_knapsack(args):
     return 0
 
 
+def run_next_rows(args):
+    """Infeasibility detection and feasibility polishing on the 20k x 40k Zipf LP
+    (bench recipe at 1/25 of the size).  Value: seconds to certify primal
+    infeasibility of the LP with one contradicting row (row 0 again, with its
+    lower bound above its upper one), mixed precision with FP64 continuation."""
+    import torch
+    torch.cuda.init()
+    from paper_2412_09734_gb300 import mpax as C
+    from synth import instance_seed, lp_instance
+    m, n, nnz = 20_000, 40_000, 400_000
+    d = lp_instance(m, n, seed=instance_seed(9), nnz=nnz, rows="zipf")
+    rp = d["row_ptr"]
+    r0 = slice(int(rp[0]), int(rp[1]))
+    row_ptr = np.append(rp, rp[-1] + (rp[1] - rp[0]))
+    col = np.concatenate([d["col"], d["col"][r0]])
+    val = np.concatenate([d["val"], d["val"][r0]])
+    lc = np.append(d["lc"], d["uc"][0] + 1.0)
+    uc = np.append(d["uc"], np.inf)
+
+    def timed(create, opts):
+        h = create()
+        try:
+            C.mpax_solve(h, opts)  # warm-up (graphs, schedules)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            C.mpax_solve(h, opts)
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0, C.mpax_get_stats(h)
+        finally:
+            C.mpax_destroy(h)
+
+    infeas = {}
+    for prec, name in ((C.MPAX_PREC_MIXED, "mixed"), (C.MPAX_PREC_FP64, "fp64")):
+        sec, st = timed(lambda: C.mpax_lp_create(m + 1, n, row_ptr, col, val, d["c"], lc, uc,
+                                                 d["l"], d["u"]),
+                        C.mpax_options_default(precision=prec, iteration_limit=200000))
+        infeas[name] = dict(seconds=sec, termination=st["termination_name"],
+                            iterations=st["iterations"], fp64_iterations=st["fp64_iterations"])
+    polish = {}
+    for flag in (0, 1):
+        sec, st = timed(lambda: C.mpax_lp_create(m, n, d["row_ptr"], d["col"], d["val"], d["c"],
+                                                 d["lc"], d["uc"], d["l"], d["u"]),
+                        C.mpax_options_default(feasibility_polishing=flag, eps_feas_polish=1e-6,
+                                               iteration_limit=200000))
+        polish["polished" if flag else "plain"] = dict(
+            seconds=sec, termination=st["termination_name"], iterations=st["iterations"],
+            polish_iterations=st["polish_iterations"], primal_res=st["primal_res"],
+            dual_res=st["dual_res"], rel_kkt=st["rel_kkt"])
+    line = {"metric": "seconds to certify primal infeasibility (Zipf LP 20k x 40k plus one "
+                      "contradicting row)",
+            "value": infeas["mixed"]["seconds"], "unit": "s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": 1e3 * infeas["mixed"]["seconds"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"sparse LP m={m} n={n} nnz={nnz} Zipf rows (bench recipe); "
+                                   "infeasible copy: row 0 repeated with lc = uc_0 + 1"},
+            "infeasibility": infeas, "feasibility_polishing": polish}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "next_rows_20k":
+        return run_next_rows(args)
     if args.workload == "ragged_lp_4096":
         return run_batch(args)
     if args.workload == "shared_dense_512":
