@@ -90,9 +90,10 @@ typedef struct mpax_options {
   double eps_dual_infeasible;   /* 1e-8.  Dual infeasible (unbounded LP): dx with
                                    ||(A dx, dx) - proj onto the recession cones of
                                    ([lc,uc], [l,u])|| <= eps * (-c^T dx), c^T dx < 0.
-                                   <= 0: off.  In MIXED precision the FP32 rays cannot
-                                   meet 1e-8; the stalled run continues in FP64 (see
-                                   fp64_continuation), where the test is met. */
+                                   <= 0: off.  In MIXED precision, where the FP32 rays
+                                   cannot meet the tolerance, the stalled run continues
+                                   in FP64 (see fp64_continuation), where the test is
+                                   met. */
   double eps_feas_polish;       /* 1e-6.  With feasibility_polishing = 1, an LP solve
                                    that ends OPTIMAL is polished (Sec. 3.3) in FP64:
                                    the zero-objective problem from (x^, 0) until
