@@ -44,7 +44,7 @@ typedef enum mpax_status {
   MPAX_ERR_NOT_SOLVED = 4,       /* results requested before mpax_solve          */
   MPAX_ERR_DEVICE_TIMEOUT = 5,   /* a bounded device-side wait gave up           */
   MPAX_ERR_NUMERICAL = 6,        /* NaN/Inf appeared in the iterates             */
-  MPAX_ERR_UNSUPPORTED = 7       /* option or input form this build lacks        */
+  MPAX_ERR_UNSUPPORTED = 7       /* option or input form the library does not take */
 } mpax_status;
 
 typedef enum mpax_mem_kind { MPAX_MEM_HOST = 0, MPAX_MEM_DEVICE = 1 } mpax_mem_kind;

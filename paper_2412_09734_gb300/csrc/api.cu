@@ -1,5 +1,5 @@
 // C ABI of the library (include/mpax.h): argument checks, device copies of the
-// problem data, validation on the device, preprocessing and the solve driver.
+// problem data, validation on the device, preprocessing and the solve routine.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
