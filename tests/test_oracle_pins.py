@@ -200,6 +200,21 @@ def test_scaling_preserves_the_optimum():
 
 # ---------------------------------------------------------------- norms
 
+def test_splitmix64_reference_sequence():
+    """The power iteration's start vector uses SplitMix64 (Steele, Lea and Flood,
+    2014): seeded with 0, the generator's first outputs are the published
+    E220A8397B1DCDAF, 6E789E6AA1B965F4, 06C45D188009454F (output k mixes the
+    state k * 0x9E3779B97F4A7C15)."""
+    golden = 0x9E3779B97F4A7C15
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    got = [O._splitmix64((k * golden) & ((1 << 64) - 1)) for k in range(3)]
+    assert got == want
+    # the start vector: unit norm, entries of both signs in balance (2u - 1, u uniform)
+    v = O.power_start(10000)
+    assert np.linalg.norm(v) == pytest.approx(1.0, rel=1e-14)
+    assert 0.48 < float(np.mean(v > 0)) < 0.52
+
+
 def test_power_norm_matches_svd():
     d = lp_instance(80, 120, seed=instance_seed(51), density=0.1)
     A = O.problem_from_arrays(d).A
