@@ -25,6 +25,16 @@ def _f64(t):
     return t.detach().to(torch.float64).contiguous()
 
 
+def _keep_if_needed(ctx, h):
+    """The solved handle, kept for the backward pass when (c, b, D) need a
+    gradient; otherwise (no_grad, constant inputs) freed at once, since no
+    backward will come to free it."""
+    if any(ctx.needs_input_grad[:3]):
+        return h
+    C.mpax_destroy(h)
+    return None
+
+
 class QPLayer(torch.autograd.Function):
     """forward(c, b, D, data, options) -> x*.
 
@@ -43,8 +53,8 @@ class QPLayer(torch.autograd.Function):
         except Exception:
             C.mpax_destroy(h)
             raise
-        ctx.h = h
         ctx.m, ctx.n = d["m"], d["n"]
+        ctx.h = _keep_if_needed(ctx, h)
         return x.to(c.dtype)
 
     @staticmethod
@@ -77,8 +87,8 @@ class QPUnrolledLayer(torch.autograd.Function):
         except Exception:
             C.mpax_destroy(h)
             raise
-        ctx.h = h
         ctx.m, ctx.n = d["m"], d["n"]
+        ctx.h = _keep_if_needed(ctx, h)
         return x.to(c.dtype)
 
     @staticmethod

@@ -135,3 +135,20 @@ def test_new_entry_points_check_arguments_before_device_work(C):
     assert C._lib.mpax_get_reduced_cost(None, g.ctypes.data, 0) == C.MPAX_ERR_INVALID_ARGUMENT
     # record_tape is an FP64 option: the default leaves it off
     assert C.mpax_options_default().record_tape == 0
+
+
+def test_qp_layers_free_their_handle_without_backward(C, monkeypatch):
+    """Host logic of the QP layers: a forward whose inputs need no gradient (no_grad,
+    constants) frees its handle at once, since no backward will free it."""
+    from paper_2412_09734_gb300 import autograd as AG
+    freed = []
+    monkeypatch.setattr(AG.C, "mpax_destroy", lambda h: freed.append(h))
+
+    class Ctx:
+        pass
+
+    ctx = Ctx()
+    ctx.needs_input_grad = (False, False, False, False, False)
+    assert AG._keep_if_needed(ctx, "h1") is None and freed == ["h1"]
+    ctx.needs_input_grad = (False, True, False, False, False)
+    assert AG._keep_if_needed(ctx, "h2") == "h2" and freed == ["h1"]
