@@ -25,12 +25,31 @@ def _f64(t):
     return t.detach().to(torch.float64).contiguous()
 
 
+class _Handle:
+    """Owns a solved library handle for the backward pass and frees it when
+    dropped: after backward, or with the graph (or the context, under no_grad)
+    when no backward comes."""
+
+    def __init__(self, h):
+        self.h = h
+
+    def close(self):
+        h, self.h = self.h, None
+        if h:
+            C.mpax_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover - interpreter shutdown
+            pass
+
+
 def _keep_if_needed(ctx, h):
-    """The solved handle, kept for the backward pass when (c, b, D) need a
-    gradient; otherwise (no_grad, constant inputs) freed at once, since no
-    backward will come to free it."""
+    """The solved handle wrapped for the backward pass when one of (c, b, D)
+    needs a gradient; otherwise freed at once and None."""
     if any(ctx.needs_input_grad[:3]):
-        return h
+        return _Handle(h)
     C.mpax_destroy(h)
     return None
 
@@ -60,10 +79,9 @@ class QPLayer(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gx):
         try:
-            dc, db, dD, _ = C.mpax_qp_adjoint(ctx.h, _f64(gx), ctx.m, ctx.n)
+            dc, db, dD, _ = C.mpax_qp_adjoint(ctx.h.h, _f64(gx), ctx.m, ctx.n)
         finally:
-            C.mpax_destroy(ctx.h)
-            ctx.h = None
+            ctx.h.close()
         return dc.to(gx.dtype), db.to(gx.dtype), dD.to(gx.dtype), None, None
 
 
@@ -94,10 +112,9 @@ class QPUnrolledLayer(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gx):
         try:
-            g = C.mpax_qp_unrolled_grad(ctx.h, _f64(gx), ctx.m, ctx.n)
+            g = C.mpax_qp_unrolled_grad(ctx.h.h, _f64(gx), ctx.m, ctx.n)
         finally:
-            C.mpax_destroy(ctx.h)
-            ctx.h = None
+            ctx.h.close()
         db = g["lc"] + g["uc"]
         return g["c"].to(gx.dtype), db.to(gx.dtype), g["D"].to(gx.dtype), None, None
 

@@ -151,4 +151,59 @@ def test_qp_layers_free_their_handle_without_backward(C, monkeypatch):
     ctx.needs_input_grad = (False, False, False, False, False)
     assert AG._keep_if_needed(ctx, "h1") is None and freed == ["h1"]
     ctx.needs_input_grad = (False, True, False, False, False)
-    assert AG._keep_if_needed(ctx, "h2") == "h2" and freed == ["h1"]
+    k = AG._keep_if_needed(ctx, "h2")
+    assert k.h == "h2" and freed == ["h1"]
+    k.close()  # after backward: freed once
+    k.close()
+    assert freed == ["h1", "h2"]
+    # a kept handle whose backward never comes is freed when dropped
+    k3 = AG._keep_if_needed(ctx, "h3")
+    del k3
+    import gc
+    gc.collect()
+    assert freed == ["h1", "h2", "h3"]
+
+
+def test_qp_layers_release_handles_on_every_path(C, monkeypatch):
+    """With a fake library (no GPU): each QP layer frees its handle exactly once
+    after backward, under no_grad, and when its graph is dropped unused."""
+    import gc
+    import types
+
+    import torch
+
+    from paper_2412_09734_gb300 import autograd as AG
+    log = []
+    f64 = torch.float64
+    fake = types.SimpleNamespace(
+        MPAX_PREC_FP64=0,
+        mpax_qp_create_diag_lowrank=lambda *a, **k: "H",
+        mpax_solve=lambda h, o: None,
+        mpax_options_default=lambda **k: None,
+        mpax_get_solution=lambda h, m, n, device=None: (torch.zeros(n, dtype=f64), None),
+        mpax_destroy=lambda h: log.append(h),
+        mpax_qp_adjoint=lambda h, g, m, n: (torch.ones(n, dtype=f64),) * 3 + ({},),
+        mpax_qp_unrolled_grad=lambda h, g, m, n: {"c": torch.ones(n, dtype=f64),
+                                                  "lc": torch.zeros(m, dtype=f64),
+                                                  "uc": torch.zeros(m, dtype=f64),
+                                                  "D": torch.ones(n, dtype=f64)})
+    monkeypatch.setattr(AG, "C", fake)
+    data = dict(m=2, n=3, row_ptr=None, col=None, val=None, l=None, u=None, f_row_ptr=None,
+                f_col=None, f_val=None, r=1)
+    for layer in (AG.QPLayer, AG.QPUnrolledLayer):
+        c = torch.zeros(3, dtype=f64, requires_grad=True)
+        b = torch.zeros(2, dtype=f64)
+        D = torch.ones(3, dtype=f64)
+        log.clear()
+        layer.apply(c, b, D, data, {}).sum().backward()
+        assert log == ["H"] and c.grad.tolist() == [1.0, 1.0, 1.0]
+        log.clear()
+        with torch.no_grad():
+            layer.apply(c, b, D, data, {})
+        gc.collect()
+        assert log == ["H"]
+        log.clear()
+        x = layer.apply(c, b, D, data, {})
+        del x
+        gc.collect()
+        assert log == ["H"]
