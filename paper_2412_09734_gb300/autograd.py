@@ -13,9 +13,13 @@ SharedLPValues: v_k = min c_k^T x  s.t.  lc <= A x <= uc, l <= x <= u for the B 
 SPOPlusLoss: the SPO+ surrogate loss of predicted costs c^_k against true costs c_k
          over the same shared feasible set, with subgradient 2 (x*(c_k) - x~_k),
          x~_k = argmin (2 c^_k - c_k)^T x: one batched solve per forward.
+SparseLPValues, SPOPlusLossSparse: the same two layers over one SPARSE feasible set
+         (for example the grid shortest-path LP of the paper's Warcraft experiment):
+         the B cost rows are solved as B instances of one ragged-batch launch.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import mpax as C
@@ -202,3 +206,70 @@ class SPOPlusLoss(torch.autograd.Function):
     def backward(ctx, gl):
         (D,) = ctx.saved_tensors
         return ((2.0 * gl.to(torch.float64)[:, None] * D).to(gl.dtype),) + (None,) * 10
+
+
+# ---- one sparse feasible set, B cost vectors: the ragged batch ----------------
+
+def _batch_solve(data, Cm, options):
+    """Solve min c_k^T x over the sparse set `data` (numpy m, n, row_ptr, col,
+    val, lc, uc, l, u) for the B rows c_k of Cm as one ragged batch (B copies of
+    the CSR with local columns).  Returns (X (B, n) like Cm, values (B,) FP64)."""
+    B = int(Cm.shape[0])
+    m, n = int(data["m"]), int(data["n"])
+    rp = np.asarray(data["row_ptr"], dtype=np.int64)
+    nnz = int(rp[-1])
+    m_off = np.arange(B + 1, dtype=np.int64) * m
+    n_off = np.arange(B + 1, dtype=np.int64) * n
+    row_ptr = np.concatenate([[0], (rp[1:][None, :] + nnz * np.arange(B)[:, None]).ravel()])
+    tile = lambda a, t: np.tile(np.asarray(a, dtype=t), B)  # noqa: E731
+    c = Cm.detach().to(torch.float64).cpu().numpy().reshape(-1)
+    h = C.mpax_lp_batch_create(B, m_off, n_off, row_ptr, tile(data["col"], np.int32),
+                               tile(data["val"], np.float64), c, tile(data["lc"], np.float64),
+                               tile(data["uc"], np.float64), tile(data["l"], np.float64),
+                               tile(data["u"], np.float64))
+    try:
+        C.mpax_batch_solve(h, C.mpax_options_default(**(options or {})))
+        x, _ = C.mpax_batch_get_solution(h, B * m, B * n)
+        _, per = C.mpax_batch_get_stats(h, B)
+    finally:
+        C.mpax_batch_destroy(h)
+    X = torch.from_numpy(x.reshape(B, n)).to(device=Cm.device)
+    v = torch.from_numpy(per["primal_obj"].copy()).to(device=Cm.device)
+    return X, v
+
+
+class SparseLPValues(torch.autograd.Function):
+    """forward(C, data, options) -> (B,) optimal values v_k = min c_k^T x over the
+    sparse set `data` (see _batch_solve); dv_k/dc_k = x_k*."""
+
+    @staticmethod
+    def forward(ctx, Cm, data, options):
+        X, v = _batch_solve(data, Cm, options)
+        ctx.save_for_backward(X)
+        return v.to(Cm.dtype)
+
+    @staticmethod
+    def backward(ctx, gv):
+        (X,) = ctx.saved_tensors
+        return (gv[:, None] * X).to(gv.dtype), None, None
+
+
+class SPOPlusLossSparse(torch.autograd.Function):
+    """forward(C_hat, C_true, X_true, Z_true, data, options) -> (B,) SPO+ losses
+    -min (2 c^_k - c_k)^T x + 2 c^_k^T x*_k - z*_k over the sparse set `data`,
+    one ragged-batch solve; subgradient 2 (x*_k - x~_k).  Only C_hat is
+    differentiable."""
+
+    @staticmethod
+    def forward(ctx, C_hat, C_true, X_true, Z_true, data, options):
+        Q = 2.0 * C_hat.detach().to(torch.float64) - C_true.detach().to(torch.float64)
+        Xt, v = _batch_solve(data, Q, options)
+        Xs = X_true.detach().to(torch.float64)
+        loss = -v + 2.0 * (C_hat.detach().to(torch.float64) * Xs).sum(1) - Z_true.to(torch.float64)
+        ctx.save_for_backward(Xs - Xt)
+        return loss.to(C_hat.dtype)
+
+    @staticmethod
+    def backward(ctx, gl):
+        (D,) = ctx.saved_tensors
+        return ((2.0 * gl.to(torch.float64)[:, None] * D).to(gl.dtype),) + (None,) * 5

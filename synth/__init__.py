@@ -14,5 +14,6 @@ from .generators import (  # noqa: F401
     ragged_lp_batch,
     shared_dense_lp_batch,
     knapsack_lp,
+    grid_shortest_path_lp,
     random_state,
 )

@@ -245,6 +245,45 @@ def qp_sparse_q_instance(n: int, m: int, *, seed: int, a_density: float = 1e-4,
                 q_val=Q.data.astype(np.float64), x0=x0, x_target=x_target)
 
 
+def grid_shortest_path_lp(k: int, B: int = 1, *, seed: int = MASTER_SEED,
+                          lo: float = 0.1, hi: float = 1.0) -> dict:
+    """Node-arc shortest-path LP on a k x k grid (the 2-D grid shortest path LP of
+    the paper's Warcraft experiment, Sec. 4): nodes are cells, arcs join each cell
+    to its up to 8 neighbours, flow conservation with supply 1 at the top-left
+    cell (source) and demand 1 at the bottom-right one (sink), 0 <= x <= 1.  B
+    cost vectors: node costs w_b ~ U[lo, hi] per cell, arc (u -> v) costs w_b[v]
+    (the cost of entering v).  Rows: nodes (row v = out-flow minus in-flow);
+    columns: arcs, listed cell by cell."""
+    rng = _rng(seed)
+    V = k * k
+    tails, heads = [], []
+    for r in range(k):
+        for c in range(k):
+            for dr in (-1, 0, 1):
+                for dc in (-1, 0, 1):
+                    rr, cc = r + dr, c + dc
+                    if (dr or dc) and 0 <= rr < k and 0 <= cc < k:
+                        tails.append(r * k + c)
+                        heads.append(rr * k + cc)
+    tails = np.asarray(tails, dtype=np.int64)
+    heads = np.asarray(heads, dtype=np.int64)
+    E = len(tails)
+    # CSR by node: +1 on the arcs leaving it, -1 on the arcs entering it
+    rows = np.concatenate([tails, heads])
+    cols = np.concatenate([np.arange(E), np.arange(E)])
+    vals = np.concatenate([np.ones(E), -np.ones(E)])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    row_ptr = np.zeros(V + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=V), out=row_ptr[1:])
+    b = np.zeros(V)
+    b[0], b[V - 1] = 1.0, -1.0
+    W = rng.uniform(lo, hi, size=(B, V))
+    return dict(kind="lp", m=V, n=E, nnz=2 * E, row_ptr=row_ptr, col=cols.astype(np.int32),
+                val=vals, lc=b.copy(), uc=b.copy(), l=np.zeros(E), u=np.ones(E),
+                C=W[:, heads], W=W, tails=tails, heads=heads, k=k, B=B)
+
+
 # ----------------------------------------------------------------------------
 # Ragged batch of independent LPs (packed CSR)
 # ----------------------------------------------------------------------------

@@ -147,11 +147,12 @@ def test_spo_plus_loss_matches_oracle(C):
     for k in range(d["B"]):
         p = O.Problem(Ah, d["C"][k].copy(), d["b"], d["b"], d["l"], d["u"])
         ch = Ch.detach().cpu().numpy()[k]
-        lo, go, _ = spo.spo_plus(p, ch, d["x0"], float(zt[k]), oo)
+        # the oracle side takes the closed-form optimum c_k^T x0 of the construction
+        lo, go, _ = spo.spo_plus(p, ch, d["x0"], float(d["opt_value"][k]), oo)
         assert Lg[k] == pytest.approx(lo, rel=1e-3, abs=1e-3)
         for _ in range(3):
             delta = rng.normal(0, 0.1, d["n"])
-            l2 = spo.spo_plus(p, ch + delta, d["x0"], float(zt[k]), oo)[0]
+            l2 = spo.spo_plus(p, ch + delta, d["x0"], float(d["opt_value"][k]), oo)[0]
             assert l2 >= lo + G[k] @ delta - 1e-3 * (1 + abs(lo))
 
 

@@ -64,3 +64,24 @@ def test_subgradient_matches_central_differences():
         e[j] = h
         fd = (highs_loss(c_hat + e) - highs_loss(c_hat - e)) / (2 * h)
         assert fd == pytest.approx(g[j], abs=1e-5)
+
+
+def test_grid_shortest_path_lp_value_is_the_dijkstra_distance():
+    """The node-arc LP of the grid shortest path (Sec. 4, the Warcraft LP) solved
+    by the oracle has the value of the shortest path found by Dijkstra's
+    algorithm (networkx) on the same arc costs, and an integral solution."""
+    import networkx as nx
+    import scipy.sparse as sp
+    from synth import grid_shortest_path_lp
+    g = grid_shortest_path_lp(8, B=3, seed=instance_seed(31))
+    A = sp.csr_matrix((g["val"], g["col"], g["row_ptr"]), shape=(g["m"], g["n"]))
+    for b in range(g["B"]):
+        p = O.Problem(A, g["C"][b], g["lc"], g["uc"], g["l"], g["u"])
+        r = O.solve_lp(p, O.Options(eps_abs=1e-8, eps_rel=1e-8, iteration_limit=10**6))
+        assert r.status == "optimal"
+        G = nx.DiGraph()
+        G.add_weighted_edges_from(zip(g["tails"].tolist(), g["heads"].tolist(),
+                                      g["C"][b].tolist()))
+        dist = nx.dijkstra_path_length(G, 0, g["m"] - 1)
+        assert r.kkt["primal_obj"] == pytest.approx(dist, rel=1e-6)
+        assert np.max(np.minimum(np.abs(r.x), np.abs(1 - r.x))) < 1e-4

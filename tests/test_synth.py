@@ -79,3 +79,18 @@ def test_batch_generators():
     k = knapsack_lp(10, 200, seed=instance_seed(9))
     np.testing.assert_allclose(k["uc"], 0.25 * k["A"].astype(np.float64).sum(axis=1), rtol=1e-6)
     assert np.all(k["c"] <= 0)  # the value maximisation min -v^T x
+
+
+def test_grid_shortest_path_lp_is_a_node_arc_incidence():
+    from synth import grid_shortest_path_lp
+    g = grid_shortest_path_lp(6, B=2, seed=instance_seed(10))
+    _check_csr(g["row_ptr"], g["col"], g["m"], g["n"])
+    A = sp.csr_matrix((g["val"], g["col"], g["row_ptr"]), shape=(g["m"], g["n"])).toarray()
+    # every arc leaves its tail (+1) and enters its head (-1)
+    assert np.all(A[g["tails"], np.arange(g["n"])] == 1)
+    assert np.all(A[g["heads"], np.arange(g["n"])] == -1)
+    assert np.all(np.abs(A).sum(axis=0) == 2)
+    # 8-neighbour arcs on a 6 x 6 grid: 4 k (k - 1) + 4 (k - 1)^2 directed arcs
+    assert g["n"] == 4 * 6 * 5 + 4 * 25
+    assert g["lc"][0] == 1 and g["lc"][-1] == -1 and g["lc"].sum() == 0
+    assert np.array_equal(g["C"], g["W"][:, g["heads"]])
