@@ -318,3 +318,52 @@ def test_box_qp_diagonal_closed_form():
                   O.DiagLowRankQ(D, sp.csr_matrix((n, 1))))
     r = O.solve_qp(p, O.Options(eps_abs=1e-11, eps_rel=1e-11, iteration_limit=200000))
     np.testing.assert_allclose(r.x, np.clip(-c / D, l, u), rtol=0, atol=1e-8)
+
+
+# ---------------------------------------------------------------- the checkers themselves
+
+@pytest.mark.parametrize("seed", [71, 72, 73])
+def test_vertex_enumeration_agrees_with_highs(seed):
+    """The brute-force LP checker against HiGHS on tiny LPs with equality, one- and
+    two-sided rows and finite boxes (an independent solver pins the checker)."""
+    from scipy.optimize import linprog
+    rng = np.random.default_rng(seed)
+    m, n = 3, 5
+    A = rng.normal(size=(m, n))
+    x0 = rng.uniform(0, 1, n)
+    ax = A @ x0
+    lc = np.array([ax[0], ax[1] - 0.5, -np.inf])
+    uc = np.array([ax[0], np.inf, ax[2] + 0.5])
+    l, u = np.zeros(n), np.full(n, 2.0)
+    c = rng.normal(size=n)
+    best, _ = brute.lp_vertex_enumeration(A, c, lc, uc, l, u)
+    A_ub = np.vstack([-A[1:2], A[2:3]])
+    b_ub = np.array([-lc[1], uc[2]])
+    ref = linprog(c, A_ub=A_ub, b_ub=b_ub, A_eq=A[0:1], b_eq=lc[0:1],
+                  bounds=list(zip(l, u)), method="highs")
+    assert ref.status == 0
+    assert best == pytest.approx(ref.fun, rel=1e-9, abs=1e-9)
+
+
+@pytest.mark.parametrize("seed", [91, 92])
+def test_active_set_enumeration_agrees_with_slsqp(seed):
+    """The brute-force QP checker against SciPy's SLSQP on tiny strictly convex QPs
+    with an equality row and a box."""
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(seed)
+    n = 5
+    B = rng.normal(size=(n, n))
+    Q = B @ B.T + 0.5 * np.eye(n)
+    c = 3.0 * rng.normal(size=n)
+    A = rng.normal(size=(1, n))
+    b = A @ rng.uniform(-0.5, 0.5, n)
+    l, u = -np.ones(n), np.ones(n)
+    x, _, val = brute.qp_active_set_enumeration(Q, c, A, b, l, u)
+    f = lambda z: 0.5 * z @ Q @ z + c @ z  # noqa: E731
+    r = minimize(f, np.zeros(n), jac=lambda z: Q @ z + c, method="SLSQP",
+                 bounds=list(zip(l, u)),
+                 constraints=[dict(type="eq", fun=lambda z: A @ z - b, jac=lambda z: A)],
+                 options=dict(ftol=1e-14, maxiter=1000))
+    assert r.success
+    np.testing.assert_allclose(x, r.x, atol=1e-6)
+    assert val == pytest.approx(f(r.x), rel=1e-9, abs=1e-9)
