@@ -367,3 +367,19 @@ def test_active_set_enumeration_agrees_with_slsqp(seed):
     assert r.success
     np.testing.assert_allclose(x, r.x, atol=1e-6)
     assert val == pytest.approx(f(r.x), rel=1e-9, abs=1e-9)
+
+
+def test_restart_rule_and_primal_weight_update_by_hand():
+    """The restart rule (sufficient 0.2, necessary 0.8 with no progress, artificial
+    0.36 of all iterations) and the smoothed primal-weight update, on hand inputs."""
+    o = O.Options()
+    assert O._restart_decision(1.0, None, None, 1, 64, o)  # the first check always restarts
+    assert O._restart_decision(0.19, 1.0, 0.5, 10, 1000, o)  # sufficient decay
+    assert not O._restart_decision(0.21, 1.0, 0.5, 10, 1000, o)  # progress, not enough
+    assert O._restart_decision(0.7, 1.0, 0.6, 10, 1000, o)  # necessary + no progress
+    assert not O._restart_decision(0.7, 1.0, 0.8, 10, 1000, o)  # still progressing
+    assert O._restart_decision(0.9, 1.0, 0.8, 360, 1000, o)  # artificial: k >= 0.36 t
+    assert not O._restart_decision(0.9, 1.0, 0.8, 359, 1000, o)
+    # omega <- exp(0.5 log(dy/dx) + 0.5 log omega): the geometric mean of dy/dx and omega
+    assert O._update_weight(2.0, 1.0, 8.0, o) == pytest.approx(4.0, rel=1e-15)
+    assert O._update_weight(2.0, 0.0, 8.0, o) == 2.0  # a zero move keeps omega
