@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=4096, help="instances of the ragged batch")
     ap.add_argument("--profile-run", action="store_true",
                     help="only run short solves (128 iterations, mixed then FP64) as an ncu target")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the other workloads the default run adds to its JSON line")
     return ap.parse_args()
 
 
@@ -169,6 +171,44 @@ def peaks():
 # CPU baseline: the oracle as it stands
 # -----------------------------------------------------------------------------
 
+class RowParallel:
+    """A CSR matrix whose products (A @ x and A.T @ y) run as row chunks on a pool
+    of host threads (scipy's sparse product releases the GIL).  Each row's sum is
+    the same sum in the same order as one scipy product, so the oracle's results
+    are unchanged: only the timing leg uses this, to time the oracle on every
+    host core."""
+
+    def __init__(self, A, pool, threads, At=None):
+        import scipy.sparse as sp
+        self.A = sp.csr_matrix(A)
+        self.shape = self.A.shape
+        self.pool, self.threads = pool, threads
+        b = np.linspace(0, self.shape[0], threads + 1).astype(int)
+        self.bounds = list(zip(b[:-1], b[1:]))
+        self.parts = [self.A[lo:hi] for lo, hi in self.bounds]
+        self._At = At
+
+    def __matmul__(self, x):
+        out = np.empty(self.shape[0])
+
+        def f(i):
+            lo, hi = self.bounds[i]
+            out[lo:hi] = self.parts[i] @ x
+
+        list(self.pool.map(f, range(self.threads)))
+        return out
+
+    @property
+    def T(self):
+        if self._At is None:
+            self._At = RowParallel(self.A.T.tocsr(), self.pool, self.threads, self)
+        return self._At
+
+
+def oracle_threads():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
 def oracle_prepare(d):
     """The oracle's preprocessing of the instance (not timed).  Returns
     (problem, prepared tuple, seconds)."""
@@ -179,12 +219,21 @@ def oracle_prepare(d):
     return p, prepared, time.perf_counter() - t0
 
 
-def oracle_sample(d, iters, pre=None):
+def oracle_sample(d, iters, pre=None, threads=1):
     """Time `iters` iterations of the oracle's r^2HPDHG loop (its own step,
     Halpern and KKT functions, KKT checked every 64 iterations) after its
-    preprocessing, which is not timed.  Returns (iters/s, seconds, prep seconds)."""
+    preprocessing, which is not timed.  threads > 1: the sparse products run on
+    that many host threads (RowParallel), the rest of the oracle as it stands.
+    Returns (iters/s, seconds, prep seconds)."""
+    import dataclasses
+    from concurrent.futures import ThreadPoolExecutor
     from oracle import pdhg as O
     p, (ps, Dr, Dc, nA, nQ, eta, omega), prep = pre if pre is not None else oracle_prepare(d)
+    pool = None
+    if threads > 1:
+        pool = ThreadPoolExecutor(threads)
+        p = dataclasses.replace(p, A=RowParallel(p.A, pool, threads))
+        ps = dataclasses.replace(ps, A=RowParallel(ps.A, pool, threads))
     opts = O.Options()
     tau, sigma = O.step_sizes(eta, omega, nA, nQ, opts, False)
     x = np.zeros(p.n)
@@ -197,6 +246,8 @@ def oracle_sample(d, iters, pre=None):
             O.kkt(p, Dc * xh, Dr * yh)
         x, y = O.halpern(xh, x, xa, k, 1.0), O.halpern(yh, y, ya, k, 1.0)
     dt = time.perf_counter() - t0
+    if pool is not None:
+        pool.shutdown()
     return iters / dt, dt, prep
 
 
@@ -367,34 +418,73 @@ def run_ours(args):
     e2e = {"value": allsum(e_iters) / e2e_s, "unit": "iters/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "time_to_1e-4_s": e2e_s / args.steps}
 
-    # dominant fused SpMV: CUDA-event times of every launch in one profiled solve
-    prof = C.mpax_options_default(precision=C.MPAX_PREC_MIXED, profile_kernels=1)
-    C.mpax_solve(h, prof)
-    ps = C.mpax_get_stats(h)
-    names = ["primal", "dual"]
-    tot = ps["profile_ms"][:2]
-    which = names[int(np.argmax(tot))]
-    idx = names.index(which)
-    avg_s = ps["profile_ms"][idx] / max(1, ps["profile_launches"][idx]) / 1e3
-    alg = algorithmic_bytes(m, n, nnz, None, False, which)
+    # the paper's protocol (Table 2): a fixed 10,000 iterations, mixed precision
+    o10k = C.mpax_options_default(precision=C.MPAX_PREC_MIXED, iteration_limit=10000,
+                                  eps_abs=1e-14, eps_rel=1e-14, fp64_continuation=0)
+    C.mpax_solve(h, o10k)
+    barrier()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record()
+    C.mpax_solve(h, o10k)
+    f1.record()
+    barrier()
+    s10k = allmax(f0.elapsed_time(f1)) / 1e3
+    fixed10k = {"iterations": C.mpax_get_stats(h)["iterations"], "time_s": s10k,
+                "iters_per_s": allsum(10000) / s10k,
+                "note": "includes the solve's preparation (transpose, scaling, norms)"}
+
+    # the fused SpMVs: CUDA-event times of every launch in one profiled solve,
+    # mixed precision (the headline kernel) and FP64 (the plain path's)
     pk, pk_src = peaks()
-    achieved = alg / avg_s / 1e9
-    other = names[1 - idx]
-    other_avg = ps["profile_ms"][1 - idx] / max(1, ps["profile_launches"][1 - idx]) / 1e3
-    other_gbs = algorithmic_bytes(m, n, nnz, None, False, other) / other_avg / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
-            "frac": achieved / pk, "traffic": measured_traffic(which, "mixed", args.workload),
-            "kernel": f"spmv_fused<{which}, float>", "peak_source": pk_src + ", of measured",
-            "algorithmic_bytes_per_launch": alg, "avg_launch_us": avg_s * 1e6,
-            "other_spmv": {"kernel": f"spmv_fused<{other}, float>", "achieved": other_gbs,
-                           "frac": other_gbs / pk}}
+    kname = {0: "spmv_fused", 1: "spmv_pipe"}
+    names = ["primal", "dual"]
+    spmv = {}
+    for prec, pname in ((C.MPAX_PREC_MIXED, "mixed"), (C.MPAX_PREC_FP64, "fp64")):
+        prof = C.mpax_options_default(precision=prec, profile_kernels=1, iteration_limit=1024,
+                                      fp64_continuation=0)
+        C.mpax_solve(h, prof)
+        ps = C.mpax_get_stats(h)
+        for idx, which in enumerate(names):
+            avg_s = ps["profile_ms"][idx] / max(1, ps["profile_launches"][idx]) / 1e3
+            alg = algorithmic_bytes(m, n, nnz, None, prec == C.MPAX_PREC_FP64, which)
+            kind = ps["spmv_kernel"][1 if which == "primal" else 0]
+            spmv[f"{pname}/{which}"] = {
+                "kernel": f"{kname.get(kind, kind)}<{which}, "
+                          f"{'double' if pname == 'fp64' else 'float'}>",
+                "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": alg,
+                "achieved": alg / avg_s / 1e9, "frac": alg / avg_s / 1e9 / pk,
+                "launches": ps["profile_launches"][idx],
+                "autotuner_us": {"A": list(ps["spmv_tune_us"][:2]),
+                                 "A^T": list(ps["spmv_tune_us"][2:])}}
+    mixed_ms = {w: spmv[f"mixed/{w}"]["avg_launch_us"] * spmv[f"mixed/{w}"]["launches"]
+                for w in names}
+    which = max(names, key=lambda w: mixed_ms[w])
+    other = names[1 - names.index(which)]
+    dom = spmv[f"mixed/{which}"]
+    roof = {"bound": "hbm", "achieved": dom["achieved"], "peak": pk, "unit": "GB/s",
+            "frac": dom["frac"], "traffic": measured_traffic(which, "mixed", args.workload),
+            "kernel": dom["kernel"], "peak_source": pk_src + ", of measured",
+            "algorithmic_bytes_per_launch": dom["algorithmic_bytes_per_launch"],
+            "avg_launch_us": dom["avg_launch_us"],
+            "other_spmv": {k: spmv[f"mixed/{other}"][k] for k in ("kernel", "achieved", "frac")},
+            "fp64_spmv": {w: {k: spmv[f"fp64/{w}"][k]
+                              for k in ("kernel", "avg_launch_us", "achieved", "frac")}
+                          for w in names},
+            "autotuner_us": dom["autotuner_us"]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        r, dt, prep = oracle_sample(d, args.cpu_iters)
-        cpu = {"value": r, "unit": "iters/s", "cores": 1, "kind": "oracle",
+        pre = oracle_prepare(d)
+        r1, _, prep = oracle_sample(d, args.cpu_iters, pre)
+        nt = oracle_threads()
+        rn, _, _ = oracle_sample(d, args.cpu_iters, pre, threads=nt) if nt > 1 else (r1, 0, 0)
+        cpu = {"value": r1, "unit": "iters/s", "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_iters} r2HPDHG iterations of the FP64 oracle on the same "
-                         f"instance after its untimed preprocessing ({prep:.1f} s)"}
+                         f"instance after its untimed preprocessing ({prep:.1f} s)",
+               "all_cores": {"value": rn, "cores": nt,
+                             "how": "the oracle's sparse products on row chunks over every "
+                                    "host thread (identical results); the rest as it stands"}}
 
     C.mpax_destroy(h)
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
@@ -413,13 +503,78 @@ def run_ours(args):
             "fp64_path": fp64_path,
             "speedup_vs_fp64_time_to_tol": (ms64 / args.fp64_steps) / (ms_max / args.steps),
             "time_to_1e-7": cont,
+            "fixed_10k_iterations": fixed10k,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches}
+    if world == 1 and not args.headline_only:
+        line["workloads"] = run_subworkloads(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def run_small_lp(args):
+    """The small LP (200 x 400, 2% density, FP64 to rel KKT 1e-8): launch- and
+    latency-bound (all its data fits in one SM's shared memory), so the figure
+    is time per solve through the C ABI, with its launch count."""
+    import torch
+    from paper_2412_09734_gb300 import mpax as C
+    from synth import instance_seed, lp_instance
+    d = lp_instance(200, 400, seed=instance_seed(1), density=0.02)
+    keys = ("row_ptr", "col", "val", "c", "lc", "uc", "l", "u")
+    dev = {k: torch.from_numpy(np.ascontiguousarray(d[k])).cuda() for k in keys}
+    h = C.mpax_lp_create(200, 400, *[dev[k] for k in keys])
+    opts = C.mpax_options_default(eps_abs=1e-8, eps_rel=1e-8, iteration_limit=10**7)
+    try:
+        for _ in range(max(1, args.warmup)):
+            C.mpax_solve(h, opts)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        steps = max(1, args.steps)
+        e0.record()
+        for _ in range(steps):
+            C.mpax_solve(h, opts)
+        e1.record()
+        torch.cuda.synchronize()
+        s = C.mpax_get_stats(h)
+    finally:
+        C.mpax_destroy(h)
+    ms = e0.elapsed_time(e1) / steps
+    return {"metric": "time to rel KKT 1e-8, FP64", "value": ms / 1e3, "unit": "s",
+            "higher_is_better": False, "steps": steps,
+            "config": {"workload": "LP m=200 n=400, 2% density, N(0,1), box [0,10], half "
+                                   "equality rows, feasible by construction; FP64, rel KKT 1e-8"},
+            "iterations": s["iterations"], "iters_per_s": s["iterations"] / (ms / 1e3),
+            "rel_kkt": s["rel_kkt"], "kernel_launches_per_solve": s["kernel_launches"],
+            "note": "launch-bound: about 40 KB of data; each 64-iteration block is one CUDA "
+                    "graph of ~134 launches, so the time is set by launch latency, not HBM"}
+
+
+def run_subworkloads(args):
+    """The other workloads of the scope, measured in the default run with short
+    step counts and attached to its JSON line (each keeps its own roofline,
+    clocks and launch count).  Their full-length runs: --workload NAME."""
+    import types
+    out = {}
+    short = types.SimpleNamespace(**vars(args))
+    short.steps, short.warmup, short.fp64_steps = 2, 1, 3
+    plans = [("small_lp_200x400", run_small_lp), ("ragged_lp_4096", run_batch),
+             ("knapsack_1000x100000", run_knapsack), ("qp_200k", run_qp),
+             ("shared_dense_512", run_shared)]
+    for name, fn in plans:
+        t0 = time.perf_counter()
+        try:
+            short.sub = True
+            out[name] = fn(short)
+        except Exception as exc:  # reported, not hidden: the line says what failed
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        out[name]["driver_s"] = time.perf_counter() - t0
+        print(f"[bench] {name}: {out[name].get('value')} {out[name].get('unit')} "
+              f"({out[name]['driver_s']:.0f} s)", file=sys.stderr, flush=True)
+    return out
 
 
 def run_profile_target(args):
@@ -481,7 +636,19 @@ def run_batch(args):
         ms = e0.elapsed_time(e1) / steps
         summ, per = C.mpax_batch_get_stats(h, d["B"])
         C.mpax_batch_destroy(h)
+        # two matrix passes per iteration over each instance's CSR (values + columns)
+        vbytes = 4 if name == "mixed" else 8
+        nnz_b = np.diff(d["nnz_off"]).astype(np.float64)
+        mat_bytes = float(np.sum(per["iterations"] * 2.0 * nnz_b * (vbytes + 4)))
+        pk, pk_src = peaks()
+        ach = mat_bytes / (ms / 1e3) / 1e9
         out[name] = dict(solves_per_s=d["B"] / (ms / 1e3), ms_per_batch=ms,
+                         roofline={"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
+                                   "frac": ach / pk, "traffic": None,
+                                   "note": "matrix bytes of every instance's iterations (2 "
+                                           "passes of values + columns) over the batch time: "
+                                           "a lower bound on the kernel's rate",
+                                   "peak_source": pk_src + ", of measured"},
                          n_optimal=summ["n_optimal"], p50_s=summ["instance_seconds_p50"],
                          p99_s=summ["instance_seconds_p99"],
                          iterations_mean=summ["iterations_total"] / d["B"],
@@ -498,8 +665,7 @@ def run_batch(args):
                                    f"nnz {nnz}, one persistent launch per batch",
                        "step_norm": "power_max_iter = 0: ||A~||_2 := 1 (Pock-Chambolle bound)"},
             "mixed": out["mixed"], "fp64": out["fp64"]}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def bf16_peak():
@@ -524,7 +690,9 @@ def run_shared(args):
     dev = {k: torch.from_numpy(np.ascontiguousarray(d[k])).cuda()
            for k in ("A", "C", "b", "l", "u")}
     out = {}
-    for fp32, name in ((False, "bf16x3"), (True, "fp32")):
+    legs = ((False, "bf16x3"),) if getattr(args, "sub", False) else ((False, "bf16x3"),
+                                                                      (True, "fp32"))
+    for fp32, name in legs:
         h = C.mpax_lp_shared_create(m, n, B, dev["A"], dev["C"], dev["b"], dev["b"], dev["l"],
                                     dev["u"])
         opts = C.mpax_options_default()
@@ -571,11 +739,11 @@ def run_shared(args):
                          "note": "BF16 GEMM flops executed (3 per BF16x3 product) over the whole "
                                  "solve time, so a lower bound on the GEMMs' own rate",
                          "peak_source": src + ", of measured"},
-            "bf16x3": out["bf16x3"], "fp32": out["fp32"],
-            "speedup_vs_fp32_products": out["fp32"]["ms_per_batch"] / out["bf16x3"]["ms_per_batch"],
+            "bf16x3": out["bf16x3"], "fp32": out.get("fp32"),
+            "speedup_vs_fp32_products": (out["fp32"]["ms_per_batch"] / out["bf16x3"]["ms_per_batch"]
+                                         if "fp32" in out else None),
             "clocks": out["bf16x3"]["clocks"], "gpu_launches": out["bf16x3"]["gpu_launches"]}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_qp(args):
@@ -638,33 +806,35 @@ def run_qp(args):
         out[name] = dict(steps_per_s=1e3 / ms, ms_per_step=ms, iterations=float(np.mean(its)),
                          backward_s=float(np.mean(bw)), adjoint_rel_residual=max(res),
                          clocks=clk, gpu_launches=launches)
-    # the paper's own QP gradient: differentiation through the FP64 iterations
-    # (tape of the path, replay and reverse sweep), against the implicit adjoint
-    h = C.mpax_qp_create_diag_lowrank(
-        m, n, dev["row_ptr"], dev["col"], dev["val"], dev["c"], dev["lc"], dev["uc"], dev["l"],
-        dev["u"], dev["D"], d["f_cols"], dev["f_row_ptr"], dev["f_col"], dev["f_val"])
-    try:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        C.mpax_solve(h, C.mpax_options_default(precision=C.MPAX_PREC_FP64, record_tape=1))
-        t1 = time.perf_counter()
-        s = C.mpax_get_stats(h)
-        x, _ = C.mpax_get_solution(h, m, n, device=xt)
-        t2 = time.perf_counter()
-        G = C.mpax_qp_unrolled_grad(h, x - xt, m, n)
-        torch.cuda.synchronize()
-        t3 = time.perf_counter()
-        back_launches = C.mpax_get_stats(h)["backward_launches"]
-        dc, _, _, _ = C.mpax_qp_adjoint(h, x - xt, m, n, tol=1e-8)
-        rel = float(torch.linalg.norm(G["c"] - dc) / torch.linalg.norm(dc))
-    finally:
-        C.mpax_destroy(h)
-    blocks = -(-s["iterations"] // 64)
-    out["unrolled_fp64"] = dict(forward_s=t1 - t0, backward_s=t3 - t2,
-                                iterations=s["iterations"], restarts=s["restarts"],
-                                tape_bytes=blocks * (64 + 8 * 2 * (n + m)),
-                                backward_launches=back_launches,
-                                dc_rel_diff_vs_implicit_adjoint=rel)
+    out["unrolled_fp64"] = None
+    if not getattr(args, "sub", False):
+        # the paper's own QP gradient: differentiation through the FP64 iterations
+        # (tape of the path, replay and reverse sweep), against the implicit adjoint
+        h = C.mpax_qp_create_diag_lowrank(
+            m, n, dev["row_ptr"], dev["col"], dev["val"], dev["c"], dev["lc"], dev["uc"], dev["l"],
+            dev["u"], dev["D"], d["f_cols"], dev["f_row_ptr"], dev["f_col"], dev["f_val"])
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            C.mpax_solve(h, C.mpax_options_default(precision=C.MPAX_PREC_FP64, record_tape=1))
+            t1 = time.perf_counter()
+            s = C.mpax_get_stats(h)
+            x, _ = C.mpax_get_solution(h, m, n, device=xt)
+            t2 = time.perf_counter()
+            G = C.mpax_qp_unrolled_grad(h, x - xt, m, n)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            back_launches = C.mpax_get_stats(h)["backward_launches"]
+            dc, _, _, _ = C.mpax_qp_adjoint(h, x - xt, m, n, tol=1e-8)
+            rel = float(torch.linalg.norm(G["c"] - dc) / torch.linalg.norm(dc))
+        finally:
+            C.mpax_destroy(h)
+        blocks = -(-s["iterations"] // 64)
+        out["unrolled_fp64"] = dict(forward_s=t1 - t0, backward_s=t3 - t2,
+                                    iterations=s["iterations"], restarts=s["restarts"],
+                                    tape_bytes=blocks * (64 + 8 * 2 * (n + m)),
+                                    backward_launches=back_launches,
+                                    dc_rel_diff_vs_implicit_adjoint=rel)
     line = {"metric": "differentiable QP forward (rel KKT 1e-4) + backward steps/s",
             "value": out["mixed"]["steps_per_s"], "unit": "steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["mixed"]["ms_per_step"],
@@ -675,8 +845,7 @@ def run_qp(args):
             "mixed": out["mixed"], "fp64": out["fp64"], "unrolled_fp64": out["unrolled_fp64"],
             "speedup_vs_fp64": out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"],
             "clocks": out["mixed"]["clocks"], "gpu_launches": out["mixed"]["gpu_launches"]}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_knapsack(args):
@@ -747,8 +916,7 @@ def run_knapsack(args):
                               "precision": "FP32", "source": "Table 2",
                               "ratio_this_over_paper": s10k / 2.49},
             "clocks": clk, "gpu_launches": summ["kernel_launches"]}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_next_rows(args):
@@ -808,22 +976,17 @@ def run_next_rows(args):
             "config": {"workload": f"sparse LP m={m} n={n} nnz={nnz} Zipf rows (bench recipe); "
                                    "infeasible copy: row 0 repeated with lc = uc_0 + 1"},
             "infeasibility": infeas, "feasibility_polishing": polish}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def main():
     args = parse()
-    if args.workload == "next_rows_20k":
-        return run_next_rows(args)
-    if args.workload == "ragged_lp_4096":
-        return run_batch(args)
-    if args.workload == "shared_dense_512":
-        return run_shared(args)
-    if args.workload == "qp_200k":
-        return run_qp(args)
-    if args.workload == "knapsack_1000x100000":
-        return run_knapsack(args)
+    single = {"next_rows_20k": run_next_rows, "ragged_lp_4096": run_batch,
+              "shared_dense_512": run_shared, "qp_200k": run_qp,
+              "knapsack_1000x100000": run_knapsack}
+    if args.workload in single:
+        print(json.dumps(single[args.workload](args)), flush=True)
+        return 0
     if args.profile_run:
         return run_profile_target(args)
     if args.impl == "reference":

@@ -139,6 +139,15 @@ typedef struct mpax_options {
                                  2(n + m) values -- for mpax_qp_unrolled_grad.  The
                                  records stay in device memory until the next
                                  mpax_solve or mpax_destroy. */
+  int32_t spmv_kernel;        /* -1: autotuned.  Kernel of the A and A^T products of
+                                 the iteration: 0 one warp per work item, 1 persistent
+                                 warps with TMA-staged matrix rows.  Both compute
+                                 every product and sum in the same order, so results
+                                 are identical bit for bit; -1 times both on the
+                                 problem's own matrices at the first prepare (five
+                                 launches each) and keeps the faster, cached for the
+                                 process by matrix signature (rows, columns, nnz,
+                                 precision, histogram of log2 row lengths) */
 } mpax_options;
 
 typedef struct mpax_stats {
@@ -161,6 +170,10 @@ typedef struct mpax_stats {
   int64_t fp64_iterations;           /* iterations of the FP64 continuation (MIXED) */
   int64_t polish_iterations;         /* iterations of the two feasibility-polishing runs */
   int64_t backward_launches;         /* library kernels of the last mpax_qp_unrolled_grad */
+  int32_t spmv_kernel[2];            /* kernel (mpax_options.spmv_kernel) of A, A^T */
+  double spmv_tune_us[4];            /* autotuner timings of the last prepare that timed:
+                                        A kind 0, A kind 1, A^T kind 0, A^T kind 1
+                                        (microseconds per launch; 0 = not timed) */
 } mpax_stats;
 
 typedef struct mpax_problem mpax_problem;
@@ -232,6 +245,15 @@ mpax_status mpax_get_solution(const mpax_problem* prob, double* x, double* y,
                               mpax_mem_kind kind);
 mpax_status mpax_get_stats(const mpax_problem* prob, mpax_stats* stats);
 
+/* Restarts of the last run (Algorithms 1/2; the restart rule and the primal-weight
+ * update of Sec. 3 as mpax_options states them): *count receives how many there
+ * were; the first min(*count, cap, 256) entries of iters / omega (HOST memory,
+ * either nullable) receive the iteration count at which each restart happened
+ * and the primal weight after its update.  For a MIXED solve continued in FP64
+ * this is the FP64 run's log.  MPAX_ERR_NOT_SOLVED before a solve. */
+mpax_status mpax_get_restart_history(const mpax_problem* prob, int32_t cap, int64_t* iters,
+                                     double* omega, int32_t* count);
+
 /* Free everything the handle owns.  NULL is a no-op. */
 void mpax_destroy(mpax_problem* prob);
 
@@ -279,6 +301,9 @@ mpax_status mpax_get_iterate(const mpax_problem* prob, double* x, double* y, dou
  *       projected lam, terms with an infinite bound dropped;
  *   rel = max(||r_p||/(1+||b||), ||r_d||/(1+||c||), |p-d|/(1+|p|+|d|)),
  *         b_i the finite one of (lc_i, uc_i) (larger magnitude if both).
+ * y must be sign-consistent with the row bounds (y_i <= 0 where lc_i = -inf,
+ * y_i >= 0 where uc_i = +inf), as the solver's points are: the term of an
+ * infinite bound is dropped, so the wrong sign there goes unreported.
  * out[0] ||r_p||, out[1] ||r_d||, out[2] p, out[3] d, out[4] |p-d|,
  * out[5] rel.  Needs mpax_prepare. */
 mpax_status mpax_kkt(mpax_problem* prob, const double* x, const double* y, mpax_mem_kind kind,
@@ -369,8 +394,11 @@ mpax_status mpax_lp_batch_create(int32_t B, const int64_t* m_off, const int64_t*
  * still running then finish with MPAX_TERM_TIME_LIMIT).  In MIXED precision with
  * fp64_continuation, instances whose FP32 KKT error stops improving (the rule of
  * mpax_options.fp64_continuation, per instance) are continued from their FP32
- * point in a second, FP64 launch over those instances only.  Each instance needs m_b + n_b <= 51,200 (FP32) or 25,600 (FP64) for its
- * shared-memory vectors; larger instances return MPAX_ERR_UNSUPPORTED. */
+ * point in a second, FP64 launch over those instances only.  An instance's two
+ * gathered vectors sit in its CTA's shared memory when m_b + n_b <= 51,200
+ * (FP32) or 25,600 (FP64), and in global memory otherwise (same arithmetic,
+ * slower gathers); the shared pool of a launch is sized to the largest instance
+ * of that launch that fits. */
 mpax_status mpax_batch_solve(mpax_batch* batch, const mpax_options* opts);
 /* Returned points (x^, y^) of every instance, packed like the inputs. */
 mpax_status mpax_batch_get_solution(const mpax_batch* batch, double* x, double* y,
@@ -381,6 +409,42 @@ mpax_status mpax_batch_get_stats(const mpax_batch* batch, mpax_batch_stats* stat
                                  int32_t* status, int64_t* iterations, double* rel_kkt,
                                  double* primal_obj, double* seconds);
 void mpax_batch_destroy(mpax_batch* batch);
+
+/* B copies of ONE LP's constraints -- min c_b^T x s.t. lc <= A x <= uc,
+ * l <= x <= u, A m x n in CSR as mpax_lp_create takes it -- as a ragged batch
+ * whose instances differ only in their costs (the batched solving of Sec. 3.2
+ * over a shared sparse feasible set, as in the paper's shortest-path
+ * experiment, Sec. 4).  The B copies are built on the device from one copy of
+ * the set; the costs start at zero (set them with mpax_batch_set_costs).
+ * Errors as mpax_lp_batch_create; B * nnz, B * m, B * n must be < 2^31. */
+mpax_status mpax_lp_batch_create_replicated(int32_t B, int32_t m, int32_t n, int64_t nnz,
+                                            const int64_t* row_ptr, const int32_t* col_idx,
+                                            const double* val, const double* lc,
+                                            const double* uc, const double* l, const double* u,
+                                            mpax_mem_kind kind, void* cuda_stream,
+                                            mpax_batch** out);
+/* Replace every instance's cost vector (packed like the batch's inputs: sum n_b
+ * entries; for a replicated batch row b of a B x n row-major matrix).  The next
+ * solve uses them. */
+mpax_status mpax_batch_set_costs(mpax_batch* batch, const double* c, mpax_mem_kind kind);
+/* Primal objective c_b^T x_b of every instance's returned point (B entries). */
+mpax_status mpax_batch_get_objective(const mpax_batch* batch, double* v, mpax_mem_kind kind);
+/* The SPO+ surrogate loss (Sec. 3.4: the paper trains LP decision models through
+ * surrogate losses; SPO+ is the one of Elmachtoub and Grigas, 2022) of predicted
+ * costs c_hat against true costs c_true, all instances at once:
+ *   loss_b = -min_x (2 c_hat_b - c_true_b)^T x + 2 c_hat_b^T x*_b - z*_b,
+ *   grad_b = 2 (x*_b - x~_b),  x~_b the returned minimiser of the first term,
+ * a subgradient of loss_b in c_hat_b.  x*_b, z*_b (the true costs' optimum and
+ * value) are inputs.  The call writes 2 c_hat - c_true into the batch's costs,
+ * solves with `opts` (as mpax_batch_solve) and forms loss and grad in FP64 on
+ * the device.  c_hat, c_true, x_true, grad: packed like the costs; z_true, loss:
+ * B entries; all in `kind` memory (DEVICE: nothing crosses to the host but the
+ * solve's own control words).  Afterwards the batch holds the solve of
+ * 2 c_hat - c_true (mpax_batch_get_solution gives x~). */
+mpax_status mpax_batch_spo_plus(mpax_batch* batch, const mpax_options* opts,
+                                const double* c_hat, const double* c_true,
+                                const double* x_true, const double* z_true, double* loss,
+                                double* grad, mpax_mem_kind kind);
 
 /* ---- Batch of LPs sharing one dense constraint matrix ----------------------- */
 
@@ -415,6 +479,38 @@ mpax_status mpax_shared_get_stats(const mpax_shared* sh, mpax_batch_stats* stats
                                   int32_t* status, int64_t* iterations, double* rel_kkt,
                                   double* primal_obj, double* seconds, double* gemm_info);
 void mpax_shared_destroy(mpax_shared* sh);
+/* Replace the B cost vectors (B x n, row-major) of a shared-matrix batch; the
+ * matrix, its scaling inputs and the bounds stay. */
+mpax_status mpax_shared_set_costs(mpax_shared* sh, const double* C, mpax_mem_kind kind);
+/* Primal objective c_k^T x_k of every instance's returned point (B entries). */
+mpax_status mpax_shared_get_objective(const mpax_shared* sh, double* v, mpax_mem_kind kind);
+/* SPO+ over the shared feasible set, as mpax_batch_spo_plus (C_hat, C_true,
+ * X_true, grad: B x n row-major; z_true, loss: B), solving with
+ * mpax_shared_solve(opts, fp32_products). */
+mpax_status mpax_shared_spo_plus(mpax_shared* sh, const mpax_options* opts,
+                                 int32_t fp32_products, const double* C_hat,
+                                 const double* C_true, const double* X_true,
+                                 const double* z_true, double* loss, double* grad,
+                                 mpax_mem_kind kind);
+
+/* One product of the shared-matrix batch on its own (Sec. 3.2: with the
+ * iterates of B instances as the columns of a matrix, the two products of an
+ * iteration are dense matrix products):
+ *   D (M x N) = A_op (M x K) . V^T,   V: N x K (row n = the vector of instance n),
+ * A_op = A stored row-major [M][K] (a_mn_major = 0; the dual step's A~ X) or
+ * A^T of an A stored [K][M] (a_mn_major = 1; the primal step's A~^T Y).  Both
+ * FP32 operands are split x = x_hi + x_lo (x_hi = bf16(x), x_lo = bf16(x - x_hi))
+ * and D = A_hi V_lo + A_lo V_hi + A_hi V_hi is formed on the tensor cores
+ * (tcgen05, FP32 accumulation), the kernel the shared batch uses.  Its error
+ * against the exact product is at most (3 * 2^-18 + (3K + 2) * 2^-24) *
+ * sum_k |A_op,mk| |V_nk| per entry.  D is [N][M] (row n = instance n).  All
+ * pointers in `kind` memory; the call allocates its BF16 operand copies and
+ * returns when D is written.  Errors: MPAX_ERR_INVALID_ARGUMENT,
+ * MPAX_ERR_OUT_OF_MEMORY, MPAX_ERR_CUDA, MPAX_ERR_DEVICE_TIMEOUT (a bounded wait
+ * of the kernel gave up). */
+mpax_status mpax_dense_bf16x3(int32_t M, int32_t N, int32_t K, int32_t a_mn_major,
+                              const float* A, const float* V, float* D, mpax_mem_kind kind,
+                              void* cuda_stream);
 
 /* ---- Evaluation without device allocation --------------------------------- */
 
@@ -433,8 +529,13 @@ void mpax_shared_destroy(mpax_shared* sh);
  * (6 doubles of device memory).  The work is queued on `cuda_stream` (NULL =
  * legacy default stream) and the call returns without waiting for it.
  *
+ * y must be sign-consistent with the row bounds (y_i <= 0 where lc_i = -inf,
+ * y_i >= 0 where uc_i = +inf), as every point the solver returns is: the dual
+ * objective drops the term of an infinite bound, so a y of the wrong sign there
+ * would go unreported (mpax_kkt takes the same convention).
+ *
  * Scratch: the per-block partial sums live in one static device array of
- * 2.5 MiB, held by every GPU that loads the library until the process exits.
+ * 3.5 MiB, held by every GPU that loads the library until the process exits.
  * Its size is the limit: m and n must each be at most 16,777,216; larger sizes
  * return MPAX_ERR_UNSUPPORTED with a message.  Every slot read by a call is
  * written earlier in the same call, so nothing needs clearing between calls,

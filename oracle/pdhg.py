@@ -474,6 +474,8 @@ class Result:
     Dc: np.ndarray
     history: list = field(default_factory=list)
     certificate: np.ndarray | None = None
+    # (total iterations, primal weight after the update) at every restart
+    restart_log: list = field(default_factory=list)
 
 
 # -----------------------------------------------------------------------------
@@ -581,6 +583,7 @@ def solve_lp(p: Problem, opts: Options = Options(), x_init=None, y_init=None,
     r_anchor = None
     r_prev = None
     hist = []
+    rlog = []
     while True:
         x_hat, y_hat, _ = pdhg_step_lp(ps, x, y, tau, sigma)
         total += 1
@@ -596,17 +599,18 @@ def solve_lp(p: Problem, opts: Options = Options(), x_init=None, y_init=None,
             if done or total >= opts.iteration_limit:
                 status = "optimal" if done else "iteration_limit"
                 return Result(Dc * x_hat, Dr * y_hat, status, total, restarts, info, omega,
-                              eta, nA, nQ, Dr, Dc, hist)
+                              eta, nA, nQ, Dr, Dc, hist, restart_log=rlog)
             status, cert = infeasibility(p, Dc * (x_hat - xa), Dr * (y_hat - ya), opts)
             if status is not None:
                 return Result(Dc * x_hat, Dr * y_hat, status, total, restarts, info, omega,
-                              eta, nA, nQ, Dr, Dc, hist, cert)
+                              eta, nA, nQ, Dr, Dc, hist, cert, restart_log=rlog)
             r = math.sqrt(omega * float(np.sum((x_hat - x) ** 2))
                           + float(np.sum((y_hat - y) ** 2)) / omega)
             if _restart_decision(r, r_anchor, r_prev, k + 1, total, opts):
                 dx = float(np.linalg.norm(x_hat - xa))
                 dy = float(np.linalg.norm(y_hat - ya))
                 omega = _update_weight(omega, dx, dy, opts)
+                rlog.append((total, omega))
                 tau, sigma = step_sizes(eta, omega, nA, nQ, opts, False)
                 x, y = x_hat, y_hat
                 xa, ya = x_hat.copy(), y_hat.copy()
@@ -658,6 +662,7 @@ def solve_qp(p: Problem, opts: Options = Options(), x_init=None, y_init=None,
     r_anchor = None
     r_prev = None
     hist = []
+    rlog = []
     while True:
         if tape is not None:
             tape.append(("step", k, tau, sigma, x.copy(), y.copy(), xavg.copy(), yavg.copy()))
@@ -671,12 +676,13 @@ def solve_qp(p: Problem, opts: Options = Options(), x_init=None, y_init=None,
             if info["converged"] or total >= opts.iteration_limit:
                 status = "optimal" if info["converged"] else "iteration_limit"
                 return Result(Dc * xavg, Dr * yavg, status, total, restarts, info, omega,
-                              eta, nA, nQ, Dr, Dc, hist)
+                              eta, nA, nQ, Dr, Dc, hist, restart_log=rlog)
             r = info["rel_kkt"]
             if _restart_decision(r, r_anchor, r_prev, k, total, opts):
                 dx = float(np.linalg.norm(xavg - xa))
                 dy = float(np.linalg.norm(yavg - ya))
                 omega = _update_weight(omega, dx, dy, opts)
+                rlog.append((total, omega))
                 tau, sigma = step_sizes(eta, omega, nA, nQ, opts, True)
                 x, y = xavg.copy(), yavg.copy()
                 xa, ya = xavg.copy(), yavg.copy()

@@ -9,17 +9,20 @@ QPUnrolledLayer: the same solution map differentiated through the solver's
 LPValue: v = min c^T x  s.t.  lc <= A x <= uc, l <= x <= u, differentiable in
          (c, lc, uc) through the envelope theorem (dv/dc = x*, ...).
 SharedLPValues: v_k = min c_k^T x  s.t.  lc <= A x <= uc, l <= x <= u for the B rows
-         c_k of C with one dense A shared by the batch; dv_k/dc_k = x_k*.
+         c_k of C with one dense A shared by the batch (a SharedFeasibleSet, on the
+         device once); dv_k/dc_k = x_k*.
 SPOPlusLoss: the SPO+ surrogate loss of predicted costs c^_k against true costs c_k
          over the same shared feasible set, with subgradient 2 (x*(c_k) - x~_k),
-         x~_k = argmin (2 c^_k - c_k)^T x: one batched solve per forward.
+         x~_k = argmin (2 c^_k - c_k)^T x: one library call per forward forms the
+         costs, solves the batch and returns the losses and subgradients.
 SparseLPValues, SPOPlusLossSparse: the same two layers over one SPARSE feasible set
-         (for example the grid shortest-path LP of the paper's Warcraft experiment):
-         the B cost rows are solved as B instances of one ragged-batch launch.
+         (a SparseFeasibleSet: B copies of the set in one ragged batch, built on the
+         device once; for example the grid shortest-path LP of the paper's Warcraft
+         experiment).
+Every layer passes CUDA tensors to the library and gets CUDA tensors back.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import mpax as C
@@ -58,6 +61,15 @@ def _keep_if_needed(ctx, h):
     return None
 
 
+def _require_handle(ctx):
+    """The solve behind this node is freed by its first backward (its device
+    memory is the size of the problem); a second backward through the same graph
+    (retain_graph=True) has nothing left to differentiate."""
+    if ctx.h is None or ctx.h.h is None:
+        raise RuntimeError("the QP solve of this node was freed by an earlier backward; "
+                           "run the forward again to differentiate it again")
+
+
 class QPLayer(torch.autograd.Function):
     """forward(c, b, D, data, options) -> x*.
 
@@ -82,6 +94,7 @@ class QPLayer(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, gx):
+        _require_handle(ctx)
         try:
             dc, db, dD, _ = C.mpax_qp_adjoint(ctx.h.h, _f64(gx), ctx.m, ctx.n)
         finally:
@@ -115,6 +128,7 @@ class QPUnrolledLayer(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, gx):
+        _require_handle(ctx)
         try:
             g = C.mpax_qp_unrolled_grad(ctx.h.h, _f64(gx), ctx.m, ctx.n)
         finally:
@@ -148,104 +162,109 @@ class LPValue(torch.autograd.Function):
         return (gv * dc).to(gv.dtype), (gv * dlc).to(gv.dtype), (gv * duc).to(gv.dtype), None, None
 
 
-class SharedLPValues(torch.autograd.Function):
-    """forward(C, A, lc, uc, l, u, options, fp32_products) -> (B,) optimal values.
+class SharedFeasibleSet:
+    """{x : lc <= A x <= uc, l <= x <= u} with one dense A (m x n, FP32), held by
+    the library as a shared-matrix batch of B instances (A copied to the device
+    once), for layers that solve B cost vectors over it at every forward."""
 
-    C is (B, n); A is a dense (m, n) FP32 CUDA tensor shared by the batch.  Only C
-    is differentiable: dv_k/dc_k = x_k*."""
+    def __init__(self, A, lc, uc, l, u, B):
+        self.m, self.n = int(A.shape[0]), int(A.shape[1])
+        self.B = int(B)
+        zero = torch.zeros((self.B, self.n), dtype=torch.float64,
+                           device=A.device if torch.is_tensor(A) else "cpu")
+        self.h = C.mpax_lp_shared_create(self.m, self.n, self.B, A.detach() if torch.is_tensor(A)
+                                         else A, zero, _f64(lc), _f64(uc), _f64(l), _f64(u))
+
+    def close(self):
+        h, self.h = self.h, None
+        if h:
+            C.mpax_shared_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover - interpreter shutdown
+            pass
+
+
+class SparseFeasibleSet:
+    """{x : lc <= A x <= uc, l <= x <= u} with a sparse A, held by the library as
+    B copies in one ragged batch built on the device once (for example the grid
+    shortest-path LP of the paper's Warcraft experiment), for layers that solve B
+    cost vectors over it at every forward.  `data` holds m, n, row_ptr, col, val,
+    lc, uc, l, u (numpy arrays or CUDA tensors)."""
+
+    def __init__(self, data, B):
+        d = data
+        self.m, self.n, self.B = int(d["m"]), int(d["n"]), int(B)
+        self.h = C.mpax_lp_batch_create_replicated(self.B, self.m, self.n, d["row_ptr"],
+                                                   d["col"], d["val"], d["lc"], d["uc"],
+                                                   d["l"], d["u"])
+
+    def close(self):
+        h, self.h = self.h, None
+        if h:
+            C.mpax_batch_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover - interpreter shutdown
+            pass
+
+
+class SharedLPValues(torch.autograd.Function):
+    """forward(C, fs, options, fp32_products) -> (B,) optimal values v_k = min c_k^T x
+    over the SharedFeasibleSet fs; C is (B, n).  dv_k/dc_k = x_k*."""
 
     @staticmethod
-    def forward(ctx, Cm, A, lc, uc, l, u, options, fp32_products=False):
-        B, n = Cm.shape
-        m = A.shape[0]
-        h = C.mpax_lp_shared_create(m, n, B, A.detach(), _f64(Cm), _f64(lc), _f64(uc),
-                                    _f64(l), _f64(u))
-        try:
-            C.mpax_shared_solve(h, C.mpax_options_default(**(options or {})), fp32_products)
-            _, per = C.mpax_shared_get_stats(h, B)
-            X, _ = C.mpax_shared_get_solution(h, m, n, B, device=Cm)
-        finally:
-            C.mpax_shared_destroy(h)
+    def forward(ctx, Cm, fs, options, fp32_products=False):
+        C.mpax_shared_set_costs(fs.h, _f64(Cm))
+        C.mpax_shared_solve(fs.h, C.mpax_options_default(**(options or {})), fp32_products)
+        X, _ = C.mpax_shared_get_solution(fs.h, fs.m, fs.n, fs.B, device=Cm)
+        v = C.mpax_shared_get_objective(fs.h, fs.B, device=Cm)
         ctx.save_for_backward(X)
-        return torch.as_tensor(per["primal_obj"], dtype=Cm.dtype, device=Cm.device)
+        return v.to(Cm.dtype)
 
     @staticmethod
     def backward(ctx, gv):
         (X,) = ctx.saved_tensors
-        return (gv[:, None] * X).to(gv.dtype), None, None, None, None, None, None, None
+        return (gv[:, None] * X).to(gv.dtype), None, None, None
 
 
 class SPOPlusLoss(torch.autograd.Function):
-    """forward(C_hat, C_true, X_true, Z_true, A, lc, uc, l, u, options, fp32_products)
-    -> (B,) losses  l_k = -min (2 c^_k - c_k)^T x + 2 c^_k^T x*_k - z*_k.
-
-    X_true (B, n) and Z_true (B,) are the optima of the true costs (for example
-    from SharedLPValues); only C_hat is differentiable."""
+    """forward(C_hat, C_true, X_true, Z_true, fs, options, fp32_products) -> (B,)
+    SPO+ losses  l_k = -min (2 c^_k - c_k)^T x + 2 c^_k^T x*_k - z*_k  over the
+    SharedFeasibleSet fs, with subgradient 2 (x*_k - x~_k): one batched solve and
+    the loss formed in the library.  X_true (B, n) and Z_true (B,) are the optima
+    of the true costs (for example from SharedLPValues); only C_hat is
+    differentiable."""
 
     @staticmethod
-    def forward(ctx, C_hat, C_true, X_true, Z_true, A, lc, uc, l, u, options,
-                fp32_products=False):
-        B, n = C_hat.shape
-        m = A.shape[0]
-        Q = (2.0 * C_hat.detach() - C_true.detach()).to(torch.float64).contiguous()
-        h = C.mpax_lp_shared_create(m, n, B, A.detach(), Q, _f64(lc), _f64(uc), _f64(l),
-                                    _f64(u))
-        try:
-            C.mpax_shared_solve(h, C.mpax_options_default(**(options or {})), fp32_products)
-            _, per = C.mpax_shared_get_stats(h, B)
-            Xt, _ = C.mpax_shared_get_solution(h, m, n, B, device=C_hat)
-        finally:
-            C.mpax_shared_destroy(h)
-        Xs = X_true.detach().to(torch.float64)
-        v = torch.as_tensor(per["primal_obj"], dtype=torch.float64, device=C_hat.device)
-        loss = -v + 2.0 * (C_hat.detach().to(torch.float64) * Xs).sum(1) - Z_true.to(torch.float64)
-        ctx.save_for_backward(Xs - Xt)
+    def forward(ctx, C_hat, C_true, X_true, Z_true, fs, options, fp32_products=False):
+        loss, grad = C.mpax_shared_spo_plus(fs.h, C.mpax_options_default(**(options or {})),
+                                            _f64(C_hat), _f64(C_true), _f64(X_true),
+                                            _f64(Z_true), fp32_products)
+        ctx.save_for_backward(grad)
         return loss.to(C_hat.dtype)
 
     @staticmethod
     def backward(ctx, gl):
-        (D,) = ctx.saved_tensors
-        return ((2.0 * gl.to(torch.float64)[:, None] * D).to(gl.dtype),) + (None,) * 10
-
-
-# ---- one sparse feasible set, B cost vectors: the ragged batch ----------------
-
-def _batch_solve(data, Cm, options):
-    """Solve min c_k^T x over the sparse set `data` (numpy m, n, row_ptr, col,
-    val, lc, uc, l, u) for the B rows c_k of Cm as one ragged batch (B copies of
-    the CSR with local columns).  Returns (X (B, n) like Cm, values (B,) FP64)."""
-    B = int(Cm.shape[0])
-    m, n = int(data["m"]), int(data["n"])
-    rp = np.asarray(data["row_ptr"], dtype=np.int64)
-    nnz = int(rp[-1])
-    m_off = np.arange(B + 1, dtype=np.int64) * m
-    n_off = np.arange(B + 1, dtype=np.int64) * n
-    row_ptr = np.concatenate([[0], (rp[1:][None, :] + nnz * np.arange(B)[:, None]).ravel()])
-    tile = lambda a, t: np.tile(np.asarray(a, dtype=t), B)  # noqa: E731
-    c = Cm.detach().to(torch.float64).cpu().numpy().reshape(-1)
-    h = C.mpax_lp_batch_create(B, m_off, n_off, row_ptr, tile(data["col"], np.int32),
-                               tile(data["val"], np.float64), c, tile(data["lc"], np.float64),
-                               tile(data["uc"], np.float64), tile(data["l"], np.float64),
-                               tile(data["u"], np.float64))
-    try:
-        C.mpax_batch_solve(h, C.mpax_options_default(**(options or {})))
-        x, _ = C.mpax_batch_get_solution(h, B * m, B * n)
-        _, per = C.mpax_batch_get_stats(h, B)
-    finally:
-        C.mpax_batch_destroy(h)
-    X = torch.from_numpy(x.reshape(B, n)).to(device=Cm.device)
-    v = torch.from_numpy(per["primal_obj"].copy()).to(device=Cm.device)
-    return X, v
+        (G,) = ctx.saved_tensors
+        return ((gl[:, None] * G).to(gl.dtype),) + (None,) * 6
 
 
 class SparseLPValues(torch.autograd.Function):
-    """forward(C, data, options) -> (B,) optimal values v_k = min c_k^T x over the
-    sparse set `data` (see _batch_solve); dv_k/dc_k = x_k*."""
+    """forward(C, fs, options) -> (B,) optimal values v_k = min c_k^T x over the
+    SparseFeasibleSet fs (one ragged-batch solve); dv_k/dc_k = x_k*."""
 
     @staticmethod
-    def forward(ctx, Cm, data, options):
-        X, v = _batch_solve(data, Cm, options)
-        ctx.save_for_backward(X)
+    def forward(ctx, Cm, fs, options):
+        C.mpax_batch_set_costs(fs.h, _f64(Cm))
+        C.mpax_batch_solve(fs.h, C.mpax_options_default(**(options or {})))
+        x, _ = C.mpax_batch_get_solution(fs.h, fs.B * fs.m, fs.B * fs.n, device=Cm)
+        v = C.mpax_batch_get_objective(fs.h, fs.B, device=Cm)
+        ctx.save_for_backward(x.view(fs.B, fs.n))
         return v.to(Cm.dtype)
 
     @staticmethod
@@ -255,21 +274,20 @@ class SparseLPValues(torch.autograd.Function):
 
 
 class SPOPlusLossSparse(torch.autograd.Function):
-    """forward(C_hat, C_true, X_true, Z_true, data, options) -> (B,) SPO+ losses
-    -min (2 c^_k - c_k)^T x + 2 c^_k^T x*_k - z*_k over the sparse set `data`,
-    one ragged-batch solve; subgradient 2 (x*_k - x~_k).  Only C_hat is
+    """forward(C_hat, C_true, X_true, Z_true, fs, options) -> (B,) SPO+ losses over
+    the SparseFeasibleSet fs, one ragged-batch solve with the loss and its
+    subgradient 2 (x*_k - x~_k) formed in the library.  Only C_hat is
     differentiable."""
 
     @staticmethod
-    def forward(ctx, C_hat, C_true, X_true, Z_true, data, options):
-        Q = 2.0 * C_hat.detach().to(torch.float64) - C_true.detach().to(torch.float64)
-        Xt, v = _batch_solve(data, Q, options)
-        Xs = X_true.detach().to(torch.float64)
-        loss = -v + 2.0 * (C_hat.detach().to(torch.float64) * Xs).sum(1) - Z_true.to(torch.float64)
-        ctx.save_for_backward(Xs - Xt)
+    def forward(ctx, C_hat, C_true, X_true, Z_true, fs, options):
+        loss, grad = C.mpax_batch_spo_plus(fs.h, C.mpax_options_default(**(options or {})),
+                                           _f64(C_hat), _f64(C_true), _f64(X_true),
+                                           _f64(Z_true))
+        ctx.save_for_backward(grad)
         return loss.to(C_hat.dtype)
 
     @staticmethod
     def backward(ctx, gl):
-        (D,) = ctx.saved_tensors
-        return ((2.0 * gl.to(torch.float64)[:, None] * D).to(gl.dtype),) + (None,) * 5
+        (G,) = ctx.saved_tensors
+        return ((gl[:, None] * G).to(gl.dtype),) + (None,) * 5

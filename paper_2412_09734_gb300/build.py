@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmpax_gb300.so")
 SOURCES = ["api.cu", "pdhg.cu", "prep.cu", "sparse.cu", "noalloc.cu", "batch.cu", "adjoint.cu",
-           "shared.cu"]
+           "shared.cu", "umma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -63,8 +63,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if force or jobs or not _newer(LIB, objs):
         tmp = LIB + ".tmp"
         libdir = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
-        run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lcublas",
-             "-Xlinker", f"-rpath={libdir}"])
+        run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-Xlinker", f"-rpath={libdir}"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -30,6 +30,9 @@ namespace {
 mpax_status cuda_fail(cudaError_t e, const char* where) {
   if (e == cudaErrorMemoryAllocation)
     return fail(MPAX_ERR_OUT_OF_MEMORY, std::string(where) + ": out of device memory");
+  if (e == cudaErrorTimeout)  // the library's own bounded device waits
+    return fail(MPAX_ERR_DEVICE_TIMEOUT,
+                std::string(where) + ": a bounded wait of a SpMV kernel gave up");
   return fail(MPAX_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
@@ -277,7 +280,8 @@ mpax_status create_common(int32_t m, int32_t n, int64_t nnz, const int64_t* row_
   if (!e) e = dmalloc(&P.colred, n);
   if (!e) e = dmalloc(&P.rowred2, m);
   if (!e) e = dmalloc(&P.colred2, n);
-  if (!e) e = dmalloc(&P.tmp_rows, big);
+  // (also the 32-bin row-length histogram of the kernel autotuner)
+  if (!e) e = dmalloc(&P.tmp_rows, std::max<size_t>(big, 64));
   if (!e) e = dmalloc(&P.tmp_scan, scan_tmp_ints(big));
   if (!e) e = dmalloc(&P.red, kRedBlocks * 8);
   if (!e) e = dmalloc(&P.red_out, 16);
@@ -402,6 +406,8 @@ mpax_status check_options(const mpax_options* o) {
   if (!(o->time_limit >= 0)) return fail(MPAX_ERR_INVALID_ARGUMENT, "time_limit must be >= 0");
   if (o->fp64_continuation && o->stall_checks < 1)
     return fail(MPAX_ERR_INVALID_ARGUMENT, "stall_checks must be >= 1");
+  if (o->spmv_kernel < -1 || o->spmv_kernel >= kSpmvKinds)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "spmv_kernel must be -1, 0 or 1");
   if (o->record_tape && o->precision != MPAX_PREC_FP64)
     return fail(MPAX_ERR_UNSUPPORTED, "record_tape needs precision FP64");
   return MPAX_OK;
@@ -446,6 +452,7 @@ mpax_status do_prepare(mpax_problem* pb, const mpax_options* o, long long* launc
   EngineBase* eng = pb->eng[prec];
   TRY_CUDA(eng->load_values(), "load values");
   *launches += 9;
+  TRY_CUDA(eng->tune(*o, launches), "kernel tuning");
   TRY_CUDA(eng->init_state(*o, launches), "init state");
   pb->cur = prec;
   pb->prepared = true;
@@ -521,6 +528,7 @@ void mpax_options_default(mpax_options* o) {
   o->fp64_continuation = 1;
   o->stall_checks = 8;
   o->record_tape = 0;
+  o->spmv_kernel = -1;
 }
 
 mpax_status mpax_lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
@@ -742,6 +750,7 @@ mpax_status mpax_solve(mpax_problem* pb, const mpax_options* opts, const double*
   }
   S.fp64_iterations = fp64_iters;
   S.polish_iterations = polish_iters;
+  eng->tune_info(S.spmv_kernel, S.spmv_tune_us);
   if (pb->polished) {
     double k6[6];
     TRY_CUDA(cudaMemcpyAsync(k6, pb->d6, sizeof(k6), cudaMemcpyDeviceToHost, P.s), "kkt");
@@ -840,6 +849,22 @@ mpax_status mpax_get_stats(const mpax_problem* pb, mpax_stats* stats) {
   if (!pb || !stats) return fail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
   *stats = pb->stats;
   if (!pb->solved) return fail(MPAX_ERR_NOT_SOLVED, "call mpax_solve first");
+  return MPAX_OK;
+}
+
+mpax_status mpax_get_restart_history(const mpax_problem* cpb, int32_t cap, int64_t* iters,
+                                     double* omega, int32_t* count) {
+  mpax_problem* pb = const_cast<mpax_problem*>(cpb);
+  if (!pb || !count || cap < 0) return fail(MPAX_ERR_INVALID_ARGUMENT, "bad argument");
+  if (!pb->solved) return fail(MPAX_ERR_NOT_SOLVED, "call mpax_solve first");
+  DevState h;
+  TRY_CUDA(pb->eng[pb->cur]->read_state(&h), "read state");
+  *count = h.rs_count;
+  const int k = std::min(std::min(h.rs_count, cap), kRestartLog);
+  for (int i = 0; i < k; ++i) {
+    if (iters) iters[i] = h.rs_iter[i];
+    if (omega) omega[i] = h.rs_omega[i];
+  }
   return MPAX_OK;
 }
 

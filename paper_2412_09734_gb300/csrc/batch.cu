@@ -10,7 +10,8 @@
 // loop for it -- power iteration, initial primal weight, half-steps, relative
 // KKT checks, restarts, primal-weight updates, termination -- with the two
 // gathered vectors of the instance (y for the SpMV^T, the reflected primal point
-// for the SpMV) held in shared memory.  All reductions are fixed-order CTA
+// for the SpMV) held in shared memory, or, for an instance too large for that,
+// in global memory (the same code through generic pointers).  All reductions are fixed-order CTA
 // trees in FP64; no instance waits on another, so no grid-wide synchronisation
 // exists and a finished CTA simply takes the next instance.
 #include <algorithm>
@@ -76,9 +77,16 @@ struct BatchArgs {
   long long* restarts;
   double *relkkt, *pobj, *secs;
   int* next;
-  int smem_m;  // elements of y held in shared memory (>= max m_b)
-  int smem_n;  // elements of the primal vector held in shared memory (>= max n_b)
-  int rp_smem; // 1: the instance's row pointers are staged in shared memory
+  // Shared-memory pool of a CTA: smem_vec elements for the instance's two
+  // gathered vectors (y, m_b entries, then the primal vector, n_b entries) and
+  // then rp_cap ints for its row pointers.  An instance with m_b + n_b >
+  // smem_vec keeps both vectors in global memory instead (gys, gxs: its slices
+  // of two m- and n-vectors); one with m_b + n_b + 2 > rp_cap reads its row
+  // pointers in place.
+  int smem_vec;
+  int rp_cap;
+  T* gys;
+  T* gxs;
   double eps_abs, eps_rel, r_suff, r_nec, r_art, pw_smooth, step_safety, power_tol;
   long long iter_limit;
   long long time_limit_ns;  // from the start of the launch, on the device clock
@@ -156,8 +164,9 @@ __device__ __forceinline__ void rows_dot(const int* pp, const int* pe, const T* 
 }
 
 template <typename T>
-__device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, int* srp, double* sh,
-                               unsigned long long t_launch) {
+__device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs,
+                                               int* srp, double* sh,
+                                               unsigned long long t_launch) {
   const unsigned long long t_start = gtimer();
   __shared__ int s_late;
   const int m0 = (int)a.m_off[b], mb = (int)(a.m_off[b + 1] - a.m_off[b]);
@@ -168,7 +177,7 @@ __device__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs, int* 
   // global round trip less in every step of a half-step), else read in place.
   const int* rpl = a.rp + m0;
   const int* rptl = a.rpt + n0;
-  if (a.rp_smem) {
+  if (srp) {
     int* sa = srp;
     int* st = srp + (mb + 1);
     for (int i = threadIdx.x; i <= mb; i += blockDim.x) sa[i] = a.rp[m0 + i];
@@ -512,9 +521,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_lp_kernel(BatchArgs<T>
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ double sh[32];
   __shared__ int s_inst;
-  T* ys = reinterpret_cast<T*>(sm);
-  T* xs = ys + a.smem_m;
-  int* srp = reinterpret_cast<int*>(xs + a.smem_n);  // rp_smem only
+  T* pool = reinterpret_cast<T*>(sm);
+  int* rpool = reinterpret_cast<int*>(pool + a.smem_vec);
   const unsigned long long t_launch = gtimer();  // used by thread 0 only
   while (true) {
     if (threadIdx.x == 0) s_inst = atomicAdd(a.next, 1);
@@ -522,7 +530,12 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_lp_kernel(BatchArgs<T>
     const int w = s_inst;
     __syncthreads();
     if (w >= a.n_todo) return;
-    solve_instance<T>(a, a.todo ? a.todo[w] : w, ys, xs, srp, sh, t_launch);
+    const int b = a.todo ? a.todo[w] : w;
+    const int mb = (int)(a.m_off[b + 1] - a.m_off[b]), nb = (int)(a.n_off[b + 1] - a.n_off[b]);
+    int* srp = (mb + nb + 2 <= a.rp_cap) ? rpool : nullptr;
+    // two call sites: the shared-memory one keeps shared loads for the gathers
+    if (mb + nb <= a.smem_vec) solve_instance<T>(a, b, pool, pool + mb, srp, sh, t_launch);
+    else solve_instance<T>(a, b, a.gys + a.m_off[b], a.gxs + a.n_off[b], srp, sh, t_launch);
   }
 }
 
@@ -545,6 +558,58 @@ __global__ void k_globalize_cols(const long long* __restrict__ m_off,
     if (c < 0 || c >= nb) atomicOr(flags, 1);
     col[p] = (int)(n_off[lo] + c);
   }
+}
+
+// ---- B copies of one LP's constraints (the replicated batch) -----------------
+__global__ void k_rep_rowptr(const long long* __restrict__ rp, int m, long long nnz, int B,
+                             long long* __restrict__ out) {
+  const long long total = (long long)B * m;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / m, i = t - b * m;
+    out[t + 1] = rp[i + 1] + b * nnz;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+}
+
+template <typename V>
+__global__ void k_tile(const V* __restrict__ src, long long len, int B, V* __restrict__ dst) {
+  const long long total = len * B;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x)
+    dst[t] = src[t % len];
+}
+
+// ---- SPO+ (Sec. 3.4): the surrogate loss of predicted costs ------------------
+// c' = 2 c_hat - c_true, the costs of the solve that gives x~.
+__global__ void k_spo_costs(const double* __restrict__ c_hat, const double* __restrict__ c_true,
+                            long long len, double* __restrict__ out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
+       t += (long long)gridDim.x * blockDim.x)
+    out[t] = 2.0 * c_hat[t] - c_true[t];
+}
+
+// One block per instance b (coordinates [off[b], off[b+1]), or b*n.. with off
+// null): loss_b = -c'^T x~ + 2 c_hat^T x* - z*_b and grad = 2 (x* - x~), where
+// x~ minimises c'^T x (Elmachtoub and Grigas 2022).  Fixed-order FP64 sums.
+__global__ void k_spo_loss(const long long* __restrict__ off, int n, const double* __restrict__ cp,
+                           const double* __restrict__ c_hat, const double* __restrict__ x_true,
+                           const double* __restrict__ z_true, const double* __restrict__ x_tl,
+                           double* __restrict__ loss, double* __restrict__ grad) {
+  __shared__ double sh[32];
+  const int b = blockIdx.x;
+  const long long j0 = off ? off[b] : (long long)b * n, j1 = off ? off[b + 1] : j0 + n;
+  double v = 0.0, t = 0.0;
+  for (long long j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    const double xt = x_tl[j], xs = x_true[j];
+    v += cp[j] * xt;
+    t += c_hat[j] * xs;
+    grad[j] = 2.0 * (xs - xt);
+  }
+  v = block_sum(v, sh);
+  __syncthreads();
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) loss[b] = -v + 2.0 * t - z_true[b];
 }
 
 }  // namespace mpax
@@ -572,6 +637,7 @@ struct mpax_batch {
   long long launches = 0;
   int* todo = nullptr;     // device list of instances continued in FP64
   int fp64_instances = 0;  // instances of the last solve continued in FP64
+  double* spo = nullptr;   // SPO+ staging of host arguments: 3 sum(n) + B doubles
 };
 
 namespace mpax {
@@ -589,14 +655,20 @@ mpax_status bfail(mpax_status s, const std::string& m) {
   return s;
 }
 
+// Bytes of shared memory an instance's two vectors may take (larger instances
+// keep them in global memory).
+constexpr long long kBatchVecBytes = 200 * 1024;
+
 template <typename T>
 mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches,
-                      const int* todo, int n_todo, int warm, int stall_limit) {
+                      const int* todo, const int* todo_host, int n_todo, int warm,
+                      int stall_limit) {
   ProblemData& P = *problem_data(bt->prob);
   cudaStream_t s = P.s;
   const int m = P.m, n = P.n, nnz = P.nnz;
   // scaled data and iterate storage in the iteration precision
-  const size_t need = sizeof(T) * ((size_t)2 * (nnz + kPad) + 9 * (size_t)n + 7 * (size_t)m + 64);
+  const size_t need =
+      sizeof(T) * ((size_t)2 * (nnz + kPad) + 10 * (size_t)n + 8 * (size_t)m + 96);
   if (bt->work_bytes < need) {
     if (bt->work) cudaFree(bt->work);
     bt->work = nullptr;
@@ -615,6 +687,7 @@ mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches
   T *c = take(n), *l = take(n), *u = take(n), *lc = take(m), *uc = take(m);
   T *w = take(n), *xa = take(n), *xhat = take(n), *gbuf = take(n);
   T *ya = take(m), *yhat = take(m);
+  T *gys = take(m), *gxs = take(n);
   cudaError_t e;
   if ((e = cast_vec<T>(P.val_s, valA, nnz, s))) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
   if ((e = gather_cast<T>(P.val_s, P.permT, valAt, nnz, s)))
@@ -662,8 +735,8 @@ mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches
   a.pobj = bt->pobj;
   a.secs = bt->secs;
   a.next = bt->next;
-  a.smem_m = (bt->max_m + 3) / 4 * 4;
-  a.smem_n = (bt->max_n + 3) / 4 * 4;
+  a.gys = gys;
+  a.gxs = gxs;
   a.eps_abs = o->eps_abs;
   a.eps_rel = o->eps_rel;
   a.r_suff = o->restart_sufficient;
@@ -679,13 +752,22 @@ mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches
   a.check_every = o->check_every;
   a.power_max_iter = o->power_max_iter;
   a.power_cap = o->pock_chambolle ? 1.0 : INFINITY;
-  size_t smem = sizeof(T) * ((size_t)a.smem_m + (size_t)a.smem_n);
-  if (smem > 200 * 1024)
-    return bfail(MPAX_ERR_UNSUPPORTED,
-                 "batch instances too large for one CTA's shared memory (max_m + max_n)");
-  const size_t rp_bytes = sizeof(int) * ((size_t)bt->max_m + (size_t)bt->max_n + 2);
-  a.rp_smem = (MPAX_BATCH_SMEM_RP && smem + rp_bytes <= 100 * 1024) ? 1 : 0;
-  if (a.rp_smem) smem += rp_bytes;
+  // the shared pool fits the largest instance of this launch that fits in
+  // kBatchVecBytes; larger instances run from global memory
+  const long long vec_cap = kBatchVecBytes / (long long)sizeof(T);
+  long long vmax = 0, rmax = 0;
+  for (int w = 0; w < n_todo; ++w) {
+    const int b = todo_host ? todo_host[w] : w;
+    const long long v = (bt->h_moff[b + 1] - bt->h_moff[b]) + (bt->h_noff[b + 1] - bt->h_noff[b]);
+    if (v <= vec_cap) vmax = std::max(vmax, v);
+    rmax = std::max(rmax, v + 2);
+  }
+  a.smem_vec = (int)((vmax + 3) / 4 * 4);
+  size_t smem = sizeof(T) * (size_t)a.smem_vec;
+  // row pointers staged when two CTAs per SM still fit
+  a.rp_cap = (MPAX_BATCH_SMEM_RP && smem + sizeof(int) * (size_t)rmax <= 100 * 1024)
+                 ? (int)rmax : 0;
+  smem += sizeof(int) * (size_t)a.rp_cap;
   cudaFuncSetAttribute(batch_lp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   int occ = 0, dev = 0, sms = 0;
@@ -837,8 +919,9 @@ mpax_status mpax_batch_solve(mpax_batch* bt, const mpax_options* o) {
   const bool cont = o->precision == MPAX_PREC_MIXED && o->fp64_continuation;
   mpax_status st =
       o->precision == MPAX_PREC_FP64
-          ? run_batch<double>(bt, o, &launches, nullptr, bt->B, 0, 0)
-          : run_batch<float>(bt, o, &launches, nullptr, bt->B, 0, cont ? o->stall_checks : 0);
+          ? run_batch<double>(bt, o, &launches, nullptr, nullptr, bt->B, 0, 0)
+          : run_batch<float>(bt, o, &launches, nullptr, nullptr, bt->B, 0,
+                             cont ? o->stall_checks : 0);
   if (st) return st;
   if (cont) {
     // FP64 continuation of the instances that stalled in FP32, warm-started
@@ -856,7 +939,7 @@ mpax_status mpax_batch_solve(mpax_batch* bt, const mpax_options* o) {
       e = cudaMemcpyAsync(bt->todo, todo.data(), sizeof(int) * todo.size(),
                           cudaMemcpyHostToDevice, s);
       if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
-      st = run_batch<double>(bt, o, &launches, bt->todo, (int)todo.size(), 1, 0);
+      st = run_batch<double>(bt, o, &launches, bt->todo, todo.data(), (int)todo.size(), 1, 0);
       if (st) return st;
     }
   }
@@ -930,11 +1013,171 @@ mpax_status mpax_batch_get_stats(const mpax_batch* bt, mpax_batch_stats* stats, 
   return MPAX_OK;
 }
 
+mpax_status mpax_lp_batch_create_replicated(int32_t B, int32_t m, int32_t n, int64_t nnz,
+                                            const int64_t* row_ptr, const int32_t* col_idx,
+                                            const double* val, const double* lc,
+                                            const double* uc, const double* l, const double* u,
+                                            mpax_mem_kind kind, void* cuda_stream,
+                                            mpax_batch** out) {
+  if (!out) return bfail(MPAX_ERR_INVALID_ARGUMENT, "out must not be NULL");
+  *out = nullptr;
+  if (B < 1 || m < 0 || n < 0 || nnz < 0)
+    return bfail(MPAX_ERR_INVALID_ARGUMENT, "B >= 1 and non-negative sizes required");
+  if (!row_ptr || (nnz > 0 && (!col_idx || !val)) || (m > 0 && (!lc || !uc)) ||
+      (n > 0 && (!l || !u)))
+    return bfail(MPAX_ERR_INVALID_ARGUMENT, "a required array pointer is NULL");
+  if ((long long)B * m >= (1LL << 31) || (long long)B * n >= (1LL << 31) ||
+      (long long)B * nnz >= (1LL << 31))
+    return bfail(MPAX_ERR_UNSUPPORTED, "B copies must hold < 2^31 rows, columns and nonzeros");
+  const cudaMemcpyKind k = kind == MPAX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // one copy of the set on the device, then B copies of it (columns stay local)
+  const long long Bm = (long long)B * m, Bn = (long long)B * n, Bz = (long long)B * nnz;
+  long long *rp1 = nullptr, *rpB = nullptr, *moff = nullptr, *noff = nullptr;
+  int *col1 = nullptr, *colB = nullptr;
+  double* v1 = nullptr;  // nnz + 2m + 2n
+  double* vB = nullptr;  // B (nnz + 3n + 2m): values, c (zero), lc, uc, l, u
+  cudaError_t e = cudaMalloc(&rp1, sizeof(long long) * (m + 1));
+  if (!e) e = cudaMalloc(&rpB, sizeof(long long) * (Bm + 1));
+  if (!e) e = cudaMalloc(&moff, sizeof(long long) * (B + 1));
+  if (!e) e = cudaMalloc(&noff, sizeof(long long) * (B + 1));
+  if (!e) e = cudaMalloc(&col1, sizeof(int) * std::max<long long>(nnz, 1));
+  if (!e) e = cudaMalloc(&colB, sizeof(int) * std::max<long long>(Bz, 1));
+  if (!e) e = cudaMalloc(&v1, sizeof(double) * std::max<long long>(nnz + 2LL * m + 2LL * n, 1));
+  if (!e) e = cudaMalloc(&vB, sizeof(double) * std::max<long long>(Bz + 3 * Bn + 2 * Bm, 1));
+  double* valB = vB;
+  double* cB = vB + Bz;
+  double* lcB = cB + Bn;
+  double* ucB = lcB + Bm;
+  double* lB = ucB + Bm;
+  double* uB = lB + Bn;
+  if (!e) e = cudaMemcpyAsync(rp1, row_ptr, sizeof(long long) * (m + 1), k, s);
+  if (!e && nnz) e = cudaMemcpyAsync(col1, col_idx, sizeof(int) * nnz, k, s);
+  if (!e && nnz) e = cudaMemcpyAsync(v1, val, sizeof(double) * nnz, k, s);
+  if (!e && m) e = cudaMemcpyAsync(v1 + nnz, lc, sizeof(double) * m, k, s);
+  if (!e && m) e = cudaMemcpyAsync(v1 + nnz + m, uc, sizeof(double) * m, k, s);
+  if (!e && n) e = cudaMemcpyAsync(v1 + nnz + 2LL * m, l, sizeof(double) * n, k, s);
+  if (!e && n) e = cudaMemcpyAsync(v1 + nnz + 2LL * m + n, u, sizeof(double) * n, k, s);
+  std::vector<long long> hm(B + 1), hn(B + 1);
+  for (int b = 0; b <= B; ++b) {
+    hm[b] = (long long)b * m;
+    hn[b] = (long long)b * n;
+  }
+  if (!e) e = cudaMemcpyAsync(moff, hm.data(), sizeof(long long) * (B + 1), cudaMemcpyHostToDevice, s);
+  if (!e) e = cudaMemcpyAsync(noff, hn.data(), sizeof(long long) * (B + 1), cudaMemcpyHostToDevice, s);
+  if (!e) {
+    const int g = 1024;
+    k_rep_rowptr<<<g, 256, 0, s>>>(rp1, m, nnz, B, rpB);
+    if (nnz) k_tile<int><<<g, 256, 0, s>>>(col1, nnz, B, colB);
+    if (nnz) k_tile<double><<<g, 256, 0, s>>>(v1, nnz, B, valB);
+    if (m) k_tile<double><<<g, 256, 0, s>>>(v1 + nnz, m, B, lcB);
+    if (m) k_tile<double><<<g, 256, 0, s>>>(v1 + nnz + m, m, B, ucB);
+    if (n) k_tile<double><<<g, 256, 0, s>>>(v1 + nnz + 2LL * m, n, B, lB);
+    if (n) k_tile<double><<<g, 256, 0, s>>>(v1 + nnz + 2LL * m + n, n, B, uB);
+    if (Bn) e = cudaMemsetAsync(cB, 0, sizeof(double) * Bn, s);
+    if (!e) e = cudaGetLastError();
+    if (!e) e = cudaStreamSynchronize(s);
+  }
+  mpax_status st = MPAX_ERR_CUDA;
+  if (!e)
+    st = mpax_lp_batch_create(B, (const int64_t*)moff, (const int64_t*)noff,
+                              (const int64_t*)rpB, colB, valB, cB, lcB, ucB, lB, uB,
+                              MPAX_MEM_DEVICE, cuda_stream, out);
+  cudaStreamSynchronize(s);
+  for (void* p : {(void*)rp1, (void*)rpB, (void*)moff, (void*)noff, (void*)col1, (void*)colB,
+                  (void*)v1, (void*)vB})
+    if (p) cudaFree(p);
+  if (e) return bfail(e == cudaErrorMemoryAllocation ? MPAX_ERR_OUT_OF_MEMORY : MPAX_ERR_CUDA,
+                      cudaGetErrorString(e));
+  return st;
+}
+
+mpax_status mpax_batch_set_costs(mpax_batch* bt, const double* c, mpax_mem_kind kind) {
+  if (!bt || !c) return bfail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  ProblemData& P = *problem_data(bt->prob);
+  const long long n = bt->h_noff[bt->B];
+  problem_order_after_user(bt->prob);
+  const cudaMemcpyKind k = kind == MPAX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaError_t e = n ? cudaMemcpyAsync(P.c, c, sizeof(double) * n, k, P.s) : cudaSuccess;
+  if (!e) e = cudaStreamSynchronize(P.s);
+  if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  problem_order_user_after(bt->prob);
+  bt->solved = false;
+  return MPAX_OK;
+}
+
+mpax_status mpax_batch_get_objective(const mpax_batch* bt, double* v, mpax_mem_kind kind) {
+  if (!bt || !v) return bfail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  if (!bt->solved) return bfail(MPAX_ERR_NOT_SOLVED, "call mpax_batch_solve first");
+  const cudaMemcpyKind k = kind == MPAX_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  const cudaError_t e = cudaMemcpy(v, bt->pobj, sizeof(double) * bt->B, k);
+  if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  return MPAX_OK;
+}
+
+mpax_status mpax_batch_spo_plus(mpax_batch* bt, const mpax_options* o, const double* c_hat,
+                                const double* c_true, const double* x_true,
+                                const double* z_true, double* loss, double* grad,
+                                mpax_mem_kind kind) {
+  if (!bt || !o || !c_hat || !c_true || !x_true || !z_true || !loss || !grad)
+    return bfail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  ProblemData& P = *problem_data(bt->prob);
+  cudaStream_t s = P.s;
+  const int B = bt->B;
+  const long long n = bt->h_noff[B];
+  problem_order_after_user(bt->prob);
+  cudaError_t e = cudaSuccess;
+  if (kind == MPAX_MEM_HOST) {
+    // stage the host arguments: c_hat, c_true, x_true (sum n each), z_true (B)
+    if (!bt->spo) e = cudaMalloc(&bt->spo, sizeof(double) * (3 * std::max<long long>(n, 1) + B));
+    double* d = bt->spo;
+    if (!e && n) e = cudaMemcpyAsync(d, c_hat, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+    if (!e && n) e = cudaMemcpyAsync(d + n, c_true, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+    if (!e && n)
+      e = cudaMemcpyAsync(d + 2 * n, x_true, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d + 3 * n, z_true, sizeof(double) * B, cudaMemcpyHostToDevice, s);
+    c_hat = d;
+    c_true = d + n;
+    x_true = d + 2 * n;
+    z_true = d + 3 * n;
+  }
+  if (!e && n) {
+    k_spo_costs<<<(int)std::min<long long>(4096, (n + 255) / 256), 256, 0, s>>>(c_hat, c_true,
+                                                                              n, P.c);
+    e = cudaGetLastError();
+  }
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  problem_order_user_after(bt->prob);
+  bt->solved = false;
+  mpax_status st = mpax_batch_solve(bt, o);
+  if (st) return st;
+  problem_order_after_user(bt->prob);
+  double* dl = loss;
+  double* dg = grad;
+  if (kind == MPAX_MEM_HOST) {
+    // results go through the work area of the staged inputs (c_true is no longer needed)
+    dg = bt->spo + n;
+    dl = bt->spo + 3 * n;  // z_true is read before loss is written, block by block
+  }
+  k_spo_loss<<<B, 256, 0, s>>>(bt->n_off, 0, P.c, c_hat, x_true, z_true, bt->xout, dl, dg);
+  e = cudaGetLastError();
+  if (!e && kind == MPAX_MEM_HOST) {
+    if (n) e = cudaMemcpyAsync(grad, dg, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(loss, dl, sizeof(double) * B, cudaMemcpyDeviceToHost, s);
+  }
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  problem_order_user_after(bt->prob);
+  return MPAX_OK;
+}
+
 void mpax_batch_destroy(mpax_batch* bt) {
   if (!bt) return;
   if (bt->prob) mpax_destroy(bt->prob);
   void* bufs[] = {bt->m_off, bt->n_off, bt->next, bt->status, bt->iters, bt->restarts,
-                  bt->relkkt, bt->pobj, bt->secs, bt->xout, bt->yout, bt->work, bt->todo};
+                  bt->relkkt, bt->pobj, bt->secs, bt->xout, bt->yout, bt->work, bt->todo,
+                  bt->spo};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete bt;

@@ -69,6 +69,7 @@ constexpr int kLongRow = 64;    // rows longer than this are cut into slices
 constexpr int kItemRows = 64;   // at most this many short rows per item
 constexpr int kShortCap = kSliceNnz + kLongRow;  // nonzeros of a packed item, upper bound
 constexpr int kMaxCheckEvery = 1024;
+constexpr int kRestartLog = 256;  // restarts whose iteration and weight are kept
 
 // Number of FP64 partial-sum quantities kept per work item.
 constexpr int kPartQ = 10;
@@ -82,10 +83,17 @@ struct Sched {
   int rows = 0;
   int n_items = 0;
   int4* items = nullptr;
-  int* cnt = nullptr;      // arrival counters of sliced rows (self-resetting)
+  int* cnt = nullptr;      // arrival counters of sliced rows (self-resetting), then
+                           // one error word (cnt[n_items]) of the pipelined kernel
   void* carry = nullptr;   // per-item partial row sums of sliced rows (8 bytes each)
   double* part = nullptr;  // kPartQ * n_items FP64 partials
+  // Kernel that runs the items: 0 = spmv_fused (one warp per item), 1 =
+  // spmv_pipe (persistent warps, TMA-staged matrix).  Both give identical bits;
+  // the choice is the autotuner's (or the caller's).
+  int kind = 0;
 };
+// Kernel kinds of a schedule.
+constexpr int kSpmvItem = 0, kSpmvPipe = 1, kSpmvKinds = 2;
 
 struct Csr {
   int rows = 0, cols = 0, nnz = 0;
@@ -114,6 +122,11 @@ struct DevState {
   int tape_err;           // a taped block found no record to write
   int done, restart_flag, termination, have_anchor;
   int check_every, is_qp, nan_seen, pad;
+  // Restart log of the run: iteration count and primal weight after each of the
+  // first kRestartLog restarts (rs_count counts them all).
+  int rs_count, rs_pad;
+  long long rs_iter[kRestartLog];
+  double rs_omega[kRestartLog];
   // Halpern / averaging coefficient table for the current block:
   // coef_a[i], coef_b[i] for inner counter k' = k_base - 1 + i (i = 0..block).
   double coef_a[kMaxCheckEvery + 2];

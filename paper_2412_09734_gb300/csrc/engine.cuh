@@ -24,6 +24,12 @@ class EngineBase {
   // Power iterations for ||A~|| (and ||Q~||), initial primal weight, step
   // sizes, counters; Halpern/averaging tables for the first block.
   virtual cudaError_t init_state(const mpax_options& o, long long* launches) = 0;
+  // Kernel of the A and A^T schedules: o.spmv_kernel when >= 0, else the
+  // faster of the kinds timed on this matrix (cached by matrix signature).
+  // kind[0], kind[1]: A, A^T; us[2 * s + k]: average microseconds of kind k on
+  // schedule s (0 where not timed in this call).
+  virtual cudaError_t tune(const mpax_options& o, long long* launches) = 0;
+  virtual void tune_info(int* kind, double* us) const = 0;
   // Starting point from unscaled FP64 device vectors (nullable = zeros).
   virtual cudaError_t init_iterate(const double* x0, const double* y0) = 0;
   virtual cudaError_t run(const mpax_options& o, RunInfo* info) = 0;

@@ -19,6 +19,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "sync.cuh"
 
 namespace mpax {
 
@@ -260,6 +261,264 @@ __global__ void MPAX_SPMV_BOUNDS spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
       }
     }
   }
+}
+
+
+// ---------------------------------------------------------------------------
+// Pipelined schedule of the same work items (spmv_pipe)
+// ---------------------------------------------------------------------------
+// Warps are persistent and own contiguous ranges of the item list.  Lane 0
+// stages the values and column indices of each item in the warp's shared
+// memory with TMA bulk copies (cp.async.bulk, completion on an mbarrier), two
+// items ahead of the one being computed, so a warp's gathers of item i overlap
+// the matrix loads of items i+1 and i+2, and no register holds a value in
+// flight.  The arithmetic is that of spmv_fused item by item (the same products,
+// the same order of every sum), so both kernels return identical bits:
+//   * packed rows: products rounded to T in shared memory, then one lane per
+//     row sums them left to right;
+//   * slices of a long row: each lane's strided products accumulated (FMA),
+//     then the xor tree; the slices' sums are added in slice order.  A warp that
+//     holds every slice of a row keeps that running sum in a register; a row
+//     whose slices span two or more warps is finished, as in spmv_fused, by the
+//     warp that arrives last at the row's counter, which adds the slices'
+//     carries in slice order.
+// Every wait on a copy is bounded (kWaitNs of the device clock); a wait
+// that gives up sets the schedule's error word, waits (again bounded) for the
+// warp's other copy and returns.
+
+constexpr int kPipeWarps = 8;  // warps per CTA
+
+// Elements copied per staged array: an item's range rounded out to 16 bytes.
+template <typename T>
+struct PipeLayout {
+  static constexpr int kValV = 16 / (int)sizeof(T);  // elements per 16 bytes
+  static constexpr int kValCap = kShortCap + 2 * kValV;
+  static constexpr int kColCap = kShortCap + 8;
+  static constexpr int kStageBytes = kValCap * (int)sizeof(T) + kColCap * 4;
+  static constexpr int kWarpBytes = 2 * kStageBytes + 16;  // two stages + two mbarriers
+  static_assert(kStageBytes % 16 == 0, "stage size must keep 16-byte alignment");
+};
+
+// Lane 0: stage the values and columns of item `it` (nonzeros [p0, p1)),
+// rounded out to 16-byte boundaries, into one stage; returns nothing, the
+// offsets are recomputed by the consumer from p0.
+template <typename T>
+__device__ __forceinline__ void pipe_issue(const SpmvArgs<T>& a, const int4& it,
+                                           unsigned char* stage, unsigned long long* bar) {
+  using L = PipeLayout<T>;
+  int p0, p1;
+  item_range(it, p0, p1);
+  const int v0 = p0 & ~(L::kValV - 1), v1 = (p1 + L::kValV - 1) & ~(L::kValV - 1);
+  const int c0 = p0 & ~3, c1 = (p1 + 3) & ~3;
+  const unsigned vb = (unsigned)((v1 - v0) * (int)sizeof(T)), cb = (unsigned)((c1 - c0) * 4);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(vb + cb)
+               : "memory");
+  if (vb)
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(stage)),
+        "l"(a.val + v0), "r"(vb), "r"(smem_addr(bar))
+        : "memory");
+  if (cb)
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(stage + L::kValCap * sizeof(T))),
+        "l"(a.col + c0), "r"(cb), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Items of warp gw (of W): [lo, hi), contiguous, balanced by count.
+__device__ __forceinline__ void pipe_range(int n_items, int gw, int W, int& lo, int& hi) {
+  lo = (int)((long long)gw * n_items / W);
+  hi = (int)((long long)(gw + 1) * n_items / W);
+}
+
+template <typename T, class In, class Epi>
+__global__ void __launch_bounds__(kWarp* kPipeWarps, sizeof(T) == 4 ? 5 : 3)
+    spmv_pipe(SpmvArgs<T> a, In in, Epi epi, int* err) {
+  using L = PipeLayout<T>;
+  extern __shared__ __align__(128) unsigned char pipe_smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int W = gridDim.x * kPipeWarps;
+  int lo, hi;
+  pipe_range(a.n_items, blockIdx.x * kPipeWarps + wib, W, lo, hi);
+  if (lo >= hi) return;
+  if (epi.skip()) return;  // read before any copy is issued
+  if (*(volatile int*)err) return;  // an earlier wait gave up: the solve reports it
+  unsigned char* wsm = pipe_smem + (size_t)wib * L::kWarpBytes;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(wsm + 2 * L::kStageBytes);
+  unsigned pending = 0;  // bit s: stage s has a copy in flight (lane 0's view)
+  if (lane == 0) {
+    mbar_init(bar);
+    mbar_init(bar + 1);
+    mbar_init_fence();
+    pipe_issue<T>(a, a.items[lo], wsm, bar);
+    pending = 1u;
+    if (lo + 1 < hi) {
+      pipe_issue<T>(a, a.items[lo + 1], wsm + L::kStageBytes, bar + 1);
+      pending |= 2u;
+    }
+  }
+  __syncwarp();
+  in.load();
+  epi.load();
+  unsigned phase = 0;  // bit s: parity of stage s's next completion
+  bool failed = false;
+  T run = 0;  // running sum of the long row whose slices this warp is walking
+  int4 it = a.items[lo];
+  for (int i = lo; i < hi; ++i) {
+    const int sidx = (i - lo) & 1;
+    unsigned char* stage = wsm + sidx * L::kStageBytes;
+    T* sval = reinterpret_cast<T*>(stage);
+    const int* scol = reinterpret_cast<const int*>(stage + L::kValCap * sizeof(T));
+    const int4 it_next = (i + 1 < hi) ? a.items[i + 1] : it;
+    int4 nx = make_int4(0, 0, 0, 0);
+    if (lane == 0 && i + 2 < hi) nx = a.items[i + 2];
+    double acc[Epi::NQ];
+#pragma unroll
+    for (int q = 0; q < Epi::NQ; ++q) acc[q] = 0.0;
+    // operands of the item's rows, requested before waiting for its matrix
+    int r = 0, pa0 = 0, pa1 = 0, pb0 = 0, pb1 = 0, ra = 0, rb = 0;
+    bool ha = false, hb = false;
+    typename Epi::Pre pra, prb;
+    if (it.x >= 0) {
+      ra = it.x + lane;
+      rb = it.x + kWarp + lane;
+      ha = ra < it.y;
+      hb = rb < it.y;
+      const int sa = ha ? ra : it.x, sb = hb ? rb : it.x;
+      pa0 = a.rp[sa];
+      pa1 = a.rp[sa + 1];
+      pb0 = a.rp[sb];
+      pb1 = a.rp[sb + 1];
+      epi.pre(sa, pra);
+      epi.pre(sb, prb);
+    } else {
+      r = -(it.x + 1);
+      epi.pre(r, pra);
+    }
+    // lane 0 waits (bounded) and tells the warp; the others then find the phase
+    // complete, which also makes the staged bytes visible to them
+    const unsigned par = (phase >> sidx) & 1u;
+    bool ok = true;
+    if (lane == 0) ok = mbar_wait(bar + sidx, par);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) {
+      failed = true;
+      break;
+    }
+    if (lane != 0) mbar_wait(bar + sidx, par);
+    phase ^= 1u << sidx;
+    pending &= ~(1u << sidx);
+    if (it.x >= 0) {
+      // ---- packed short rows [r0, r1), nonzeros [base, end) ----------------
+      const int base = it.z;
+      const int cnt = it.w - base;
+      T* buf = sval + (base & (L::kValV - 1));  // buf[q - base] = product q
+      const int* cb = scol + (base & 3);
+#pragma unroll
+      for (int u = 0; u < kShortLoads; ++u) {
+        const int q = lane + u * kWarp;
+        if (q < cnt) buf[q] = buf[q] * in(cb[q]);
+      }
+      __syncwarp();
+      if (ha) {
+        T s = 0;
+        for (int q = pa0; q < pa1; ++q) s += buf[q - base];
+        epi.row(ra, s, pra, acc);
+      }
+      if (hb) {
+        T s = 0;
+        for (int q = pb0; q < pb1; ++q) s += buf[q - base];
+        epi.row(rb, s, prb, acc);
+      }
+      if (Epi::NQ > 0 && epi.check) {
+#pragma unroll
+        for (int q = 0; q < Epi::NQ; ++q) {
+          const double t = warp_sum(acc[q]);
+          if (lane == 0) a.part[(a.q0 + q) * a.n_items + i] = t;
+        }
+      }
+    } else {
+      // ---- slice si of S of the long row r: nonzeros [p0, p1) --------------
+      const int p0 = it.y, cnt = it.z - it.y;
+      const int si = it.w >> 16, S = it.w & 0xffff;
+      const int first = i - si;
+      const T* vb = sval + (p0 & (L::kValV - 1));
+      const int* cb = scol + (p0 & 3);
+      T s = 0;
+#pragma unroll
+      for (int u = 0; u < kSliceLoads; ++u) {
+        const int q = lane + u * kWarp;
+        if (q < cnt) s += vb[q] * in(cb[q]);
+      }
+      s = warp_sum(s);
+      // the row's sum in slice order, as spmv_fused forms it: a one-slice row
+      // is its slice's sum; otherwise 0 + c_0 + c_1 + ...  A warp whose range
+      // begins inside the row starts a partial (it goes through the carries).
+      if (si == 0 || i == lo) run = (S == 1) ? s : (T)0 + s;
+      else run += s;
+      const bool whole = first >= lo && first + S <= hi;  // every slice in this warp
+      if (whole) {
+        if (si == S - 1 && lane == 0) {
+          epi.row(r, run, pra, acc);
+          if (Epi::NQ > 0 && epi.check) {
+#pragma unroll
+            for (int q = 0; q < Epi::NQ; ++q) a.part[(a.q0 + q) * a.n_items + first] = acc[q];
+          }
+        }
+      } else if (lane == 0) {
+        // the row's slices span warps: every slice leaves its carry; the warp's
+        // last slice of the row arrives at the counter with this warp's count
+        a.carry[i] = s;
+        if (si == S - 1 || i == hi - 1) {
+          const int mine = i - max(first, lo) + 1;  // this warp's slices of the row
+          int prev;
+          asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                       : "=r"(prev)
+                       : "l"(a.cnt + first), "r"(mine)
+                       : "memory");
+          if (prev + mine == S) {
+            T tot = 0;
+            for (int t = 0; t < S; ++t) tot += __ldcg(a.carry + first + t);
+            a.cnt[first] = 0;  // ready for the next launch
+            epi.row(r, tot, pra, acc);
+            if (Epi::NQ > 0 && epi.check) {
+#pragma unroll
+              for (int q = 0; q < Epi::NQ; ++q) a.part[(a.q0 + q) * a.n_items + first] = acc[q];
+            }
+          }
+        }
+      }
+      // the finished row's contribution lands in slot `first`; the other
+      // slices' slots hold zero
+      if (Epi::NQ > 0 && epi.check && si != 0 && lane == 0) {
+#pragma unroll
+        for (int q = 0; q < Epi::NQ; ++q) a.part[(a.q0 + q) * a.n_items + i] = 0.0;
+      }
+    }
+    // the stage is free again: order this warp's generic accesses to it before
+    // the next bulk copy into it (async proxy), then refill it
+    if (i + 2 < hi) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        pipe_issue<T>(a, nx, stage, bar + sidx);
+        pending |= 1u << sidx;
+      }
+    }
+    it = it_next;
+  }
+  if (failed && lane == 0) {
+    atomicOr(err, 1);
+    // copies still in flight land in this warp's shared memory: wait for them
+    // (bounded) before the CTA may exit
+    for (int t = 0; t < 2; ++t)
+      if (pending & (1u << t)) mbar_wait(bar + t, (phase >> t) & 1u);
+  }
+  __syncwarp();
 }
 
 }  // namespace mpax

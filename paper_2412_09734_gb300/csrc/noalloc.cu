@@ -9,10 +9,11 @@
 // rows of A^T is covered by blocks of kRowsPerBlock rows, and every block owns
 // one slot per partial quantity, so m and n may not exceed
 // kMaxSlots * kRowsPerBlock (16,777,216).  Every GPU that loads the library
-// holds the array (2.5 MiB) until the process exits.
+// holds the array (3.5 MiB) until the process exits.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cmath>
 
 #include "../../include/mpax.h"
@@ -22,13 +23,24 @@ namespace {
 
 constexpr int kRowsPerBlock = 256;
 constexpr int kMaxSlots = 65536;  // blocks per pass
-constexpr int kQuant = 5;         // [0] r_p^2 [1] row dual terms [2] r_d^2 [3] c.x [4] bound terms
+// [0] r_p^2 [1] row dual terms [2] r_d^2 [3] c.x [4] bound terms [5] c^2 [6] b^2
+constexpr int kQuant = 7;
 constexpr int kMaxDevices = 64;
 
 // The scratch: kQuant slots per block, FP64.  Shared by every call on this device.
 static __device__ __align__(256) double g_scratch[kQuant * kMaxSlots];
 
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
+// Device address of g_scratch per device, looked up on the first call on that
+// device; concurrent first calls from several host threads store the same value.
+std::atomic<double*> g_scratch_ptr[kMaxDevices];
+
+__device__ __forceinline__ double bound_of(double lo, double hi) {
+  const bool fl = isfinite(lo), fu = isfinite(hi);
+  if (fl && fu) return (fabs(lo) >= fabs(hi)) ? lo : hi;
+  if (fl) return lo;
+  if (fu) return hi;
+  return 0.0;
+}
 
 // One warp per row of A: (A x)_i, r_p = Ax - proj_[lc,uc](Ax), lc y^+ - uc y^-.
 __global__ void k_rows(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -37,7 +49,7 @@ __global__ void k_rows(const int64_t* __restrict__ rp, const int32_t* __restrict
                        const double* __restrict__ y, double* __restrict__ scratch) {
   __shared__ double sh[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double a0 = 0.0, a1 = 0.0;
+  double a0 = 0.0, a1 = 0.0, a6 = 0.0;
   const int r_end = min(m, (int)(blockIdx.x + 1) * kRowsPerBlock);
   for (int i = blockIdx.x * kRowsPerBlock + w; i < r_end; i += blockDim.x >> 5) {
     double s = 0.0;
@@ -50,13 +62,17 @@ __global__ void k_rows(const int64_t* __restrict__ rp, const int32_t* __restrict
       const double yi = y[i];
       if (yi > 0.0 && isfinite(lo)) a1 += lo * yi;
       if (yi < 0.0 && isfinite(hi)) a1 += hi * yi;
+      const double b = bound_of(lo, hi);
+      a6 += b * b;
     }
   }
   const double r0 = mpax::block_sum(a0, sh);
   const double r1 = mpax::block_sum(a1, sh);
+  const double r6 = mpax::block_sum(a6, sh);
   if (threadIdx.x == 0) {
     scratch[0 * kMaxSlots + blockIdx.x] = r0;
     scratch[1 * kMaxSlots + blockIdx.x] = r1;
+    scratch[6 * kMaxSlots + blockIdx.x] = r6;
   }
 }
 
@@ -69,7 +85,7 @@ __global__ void k_cols(const int64_t* __restrict__ rpt, const int32_t* __restric
                        double* __restrict__ scratch) {
   __shared__ double sh[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double a2 = 0.0, a3 = 0.0, a4 = 0.0;
+  double a2 = 0.0, a3 = 0.0, a4 = 0.0, a5 = 0.0;
   const int r_end = min(n, (int)(blockIdx.x + 1) * kRowsPerBlock);
   for (int j = blockIdx.x * kRowsPerBlock + w; j < r_end; j += blockDim.x >> 5) {
     double t = 0.0;
@@ -87,47 +103,35 @@ __global__ void k_cols(const int64_t* __restrict__ rpt, const int32_t* __restric
       const double rd = lam - lh;
       a2 += rd * rd;
       a3 += c[j] * x[j];
+      a5 += c[j] * c[j];
       a4 += (lf ? lo * fmax(lh, 0.0) : 0.0) + (uf ? hi * fmin(lh, 0.0) : 0.0);
     }
   }
   const double r2 = mpax::block_sum(a2, sh);
   const double r3 = mpax::block_sum(a3, sh);
   const double r4 = mpax::block_sum(a4, sh);
+  const double r5 = mpax::block_sum(a5, sh);
   if (threadIdx.x == 0) {
     scratch[2 * kMaxSlots + blockIdx.x] = r2;
     scratch[3 * kMaxSlots + blockIdx.x] = r3;
     scratch[4 * kMaxSlots + blockIdx.x] = r4;
+    scratch[5 * kMaxSlots + blockIdx.x] = r5;
   }
 }
 
-__device__ __forceinline__ double bound_of(double lo, double hi) {
-  const bool fl = isfinite(lo), fu = isfinite(hi);
-  if (fl && fu) return (fabs(lo) >= fabs(hi)) ? lo : hi;
-  if (fl) return lo;
-  if (fu) return hi;
-  return 0.0;
-}
-
-// Norms of b and c, then the fixed-order reduction of every block slot.
+// The fixed-order reduction of every block slot (the norms of c and b included).
 __global__ void k_finish(const double* __restrict__ scratch, int nbr, int nbc,
-                         const double* __restrict__ c, int n, const double* __restrict__ lc,
-                         const double* __restrict__ uc, int m, double* __restrict__ out) {
+                         double* __restrict__ out) {
   __shared__ double sh[32];
   double v[kQuant];
-  const int nb[kQuant] = {nbr, nbr, nbc, nbc, nbc};
+  const int nb[kQuant] = {nbr, nbr, nbc, nbc, nbc, nbc, nbr};
   for (int q = 0; q < kQuant; ++q) {
     double s = 0.0;
     for (int b = threadIdx.x; b < nb[q]; b += blockDim.x) s += scratch[q * kMaxSlots + b];
     v[q] = mpax::block_sum(s, sh);
   }
-  double sc = 0.0, sb = 0.0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) sc += c[j] * c[j];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const double b = bound_of(lc[i], uc[i]);
-    sb += b * b;
-  }
-  const double nc = sqrt(mpax::block_sum(sc, sh));
-  const double nbn = sqrt(mpax::block_sum(sb, sh));
+  const double nc = sqrt(v[5]);
+  const double nbn = sqrt(v[6]);
   if (threadIdx.x == 0) {
     const double nrp = sqrt(v[0]), nrd = sqrt(v[2]);
     const double pobj = v[3];
@@ -173,19 +177,18 @@ extern "C" mpax_status mpax_lp_kkt_noalloc(int32_t m, int32_t n, int64_t nnz,
   // Host code must not hand `g_scratch` itself to a kernel: on the host that name
   // is a stand-in, not a device address.  Look the address up once per device,
   // with that device current.
-  if (!g_scratch_ptr[dev]) {
-    double* ptr = nullptr;
-    e = cudaGetSymbolAddress((void**)&ptr, g_scratch);
+  double* scratch = g_scratch_ptr[dev].load(std::memory_order_relaxed);
+  if (!scratch) {
+    e = cudaGetSymbolAddress((void**)&scratch, g_scratch);
     if (e != cudaSuccess) return noalloc_fail(MPAX_ERR_CUDA, cudaGetErrorString(e));
-    g_scratch_ptr[dev] = ptr;
+    g_scratch_ptr[dev].store(scratch, std::memory_order_relaxed);
   }
-  double* scratch = g_scratch_ptr[dev];
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const int nbr = (m + kRowsPerBlock - 1) / kRowsPerBlock;
   const int nbc = (n + kRowsPerBlock - 1) / kRowsPerBlock;
   if (nbr > 0) k_rows<<<nbr, 256, 0, s>>>(row_ptr, col_idx, val, m, lc, uc, x, y, scratch);
   if (nbc > 0) k_cols<<<nbc, 256, 0, s>>>(row_ptr_t, col_idx_t, val_t, n, c, l, u, x, y, scratch);
-  k_finish<<<1, 256, 0, s>>>(scratch, nbr, nbc, c, n, lc, uc, m, out);
+  k_finish<<<1, 256, 0, s>>>(scratch, nbr, nbc, out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return noalloc_fail(MPAX_ERR_CUDA, cudaGetErrorString(e));
   return MPAX_OK;

@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cstdio>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include <type_traits>
@@ -410,6 +411,11 @@ __global__ void k_finalize_check(const double* __restrict__ partAt, int nAt,
           st->omega = exp(th * log(dy / dx) + (1.0 - th) * log(st->omega));
         }
         set_step_sizes(st);
+        if (st->rs_count < kRestartLog) {
+          st->rs_iter[st->rs_count] = st->total;
+          st->rs_omega[st->rs_count] = st->omega;
+        }
+        st->rs_count += 1;
         st->k_base = 0;
         st->have_anchor = 1;
         st->r_anchor = r;
@@ -532,10 +538,56 @@ int resident_warps() {
   return w;
 }
 
+// Launch shape of spmv_pipe<T, In, Epi>: CTAs resident on the whole GPU and the
+// dynamic shared memory of one CTA (two stages per warp).
+struct PipeShape {
+  int grid = -1;
+  size_t smem = 0;
+};
+template <typename T, class In, class Epi>
+const PipeShape& pipe_shape() {
+  static PipeShape sh;
+  if (sh.grid < 0) {
+    const size_t smem = (size_t)kPipeWarps * PipeLayout<T>::kWarpBytes;
+    cudaFuncSetAttribute(spmv_pipe<T, In, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int blocks = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, spmv_pipe<T, In, Epi>,
+                                                  kWarp * kPipeWarps, smem);
+    sh.smem = smem;
+    sh.grid = std::max(1, blocks) * sms;
+  }
+  return sh;
+}
+// Items per warp below which spmv_pipe launches fewer warps than fit (a warp
+// needs a few items for its copies to run ahead of its gathers).
+constexpr int kPipeMinItems = 4;
+
 template <typename T, class In, class Epi>
 void launch_spmv(const Sched& sc, const Csr& K, const T* val, In in, Epi epi, int q0,
                  cudaStream_t s) {
   if (sc.n_items == 0) return;
+  if (sc.kind == kSpmvPipe) {
+    SpmvArgs<T> a;
+    a.items = sc.items;
+    a.n_items = sc.n_items;
+    a.pf_dist = 0;
+    a.rp = K.rp;
+    a.col = K.col;
+    a.val = val;
+    a.cnt = sc.cnt;
+    a.carry = reinterpret_cast<T*>(sc.carry);
+    a.part = sc.part;
+    a.q0 = q0;
+    const PipeShape& sh = pipe_shape<T, In, Epi>();
+    const int want = (sc.n_items + kPipeMinItems * kPipeWarps - 1) / (kPipeMinItems * kPipeWarps);
+    const int grid = std::max(1, std::min(sh.grid, want));
+    spmv_pipe<T, In, Epi><<<grid, kWarp * kPipeWarps, sh.smem, s>>>(a, in, epi,
+                                                                     sc.cnt + sc.n_items);
+    return;
+  }
   SpmvArgs<T> a;
   a.items = sc.items;
   a.n_items = sc.n_items;
@@ -563,6 +615,92 @@ void launch_spmv(const Sched& sc, const Csr& K, const T* val, In in, Epi epi, in
 #else
   spmv_fused<T, In, Epi><<<grid, kSpmvBlock, 0, s>>>(a, in, epi);
 #endif
+}
+
+// ---- autotuner helpers ------------------------------------------------------
+// Signature of a schedule's matrix: sizes, precision and the log2 histogram of
+// row lengths (bin b counts rows of length in [2^(b-1), 2^b), bin 0 empty rows).
+constexpr int kTuneBins = 32;
+constexpr int kTuneReps = 5;
+struct TuneKey {
+  long long v[5 + kTuneBins];
+  bool operator<(const TuneKey& o) const {
+    return std::lexicographical_compare(v, v + 5 + kTuneBins, o.v, o.v + 5 + kTuneBins);
+  }
+};
+
+__global__ void k_row_hist(const int* __restrict__ rp, int rows, int* __restrict__ hist) {
+  __shared__ int h[kTuneBins];
+  if (threadIdx.x < kTuneBins) h[threadIdx.x] = 0;
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
+    const int len = rp[i + 1] - rp[i];
+    atomicAdd(&h[len == 0 ? 0 : 32 - __clz(len)], 1);  // integer counts: order-free
+  }
+  __syncthreads();
+  if (threadIdx.x < kTuneBins && h[threadIdx.x]) atomicAdd(hist + threadIdx.x, h[threadIdx.x]);
+}
+
+cudaError_t tune_key(const Csr& K, int n_items, size_t tsize, int* scratch, cudaStream_t s,
+                     TuneKey* key) {
+  int h[kTuneBins];
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(h), s);
+  if (e) return e;
+  if (K.rows > 0) k_row_hist<<<grid1(K.rows), 256, 0, s>>>(K.rp, K.rows, scratch);
+  if ((e = cudaMemcpyAsync(h, scratch, sizeof(h), cudaMemcpyDeviceToHost, s))) return e;
+  if ((e = cudaStreamSynchronize(s))) return e;
+  key->v[0] = K.rows;
+  key->v[1] = K.cols;
+  key->v[2] = K.nnz;
+  key->v[3] = n_items;
+  key->v[4] = (long long)tsize;
+  for (int b = 0; b < kTuneBins; ++b) key->v[5 + b] = h[b];
+  return cudaSuccess;
+}
+
+std::mutex& tune_mutex() {
+  static std::mutex m;
+  return m;
+}
+std::map<TuneKey, int>& tune_cache() {
+  static std::map<TuneKey, int> c;
+  return c;
+}
+bool tune_lookup(const TuneKey& k, int* kind) {
+  std::lock_guard<std::mutex> g(tune_mutex());
+  auto it = tune_cache().find(k);
+  if (it == tune_cache().end()) return false;
+  *kind = it->second;
+  return true;
+}
+void tune_store(const TuneKey& k, int kind) {
+  std::lock_guard<std::mutex> g(tune_mutex());
+  tune_cache()[k] = kind;
+}
+
+// Average microseconds of `reps` launches of f (after one untimed launch),
+// CUDA events on the stream the launches use.
+template <class F>
+cudaError_t time_launches(cudaStream_t s, int reps, double* us, F f) {
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e) return e;
+  if ((e = cudaEventCreate(&e1))) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  f();
+  cudaEventRecord(e0, s);
+  for (int r = 0; r < reps; ++r) f();
+  cudaEventRecord(e1, s);
+  e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (!e) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *us = 1000.0 * ms / reps;
+  return e;
 }
 
 template <typename T>
@@ -737,6 +875,83 @@ class Engine final : public EngineBase {
       }
     }
     return cudaGetLastError();
+  }
+
+  // ---- autotuner: which kernel runs the A and A^T schedules -------------------
+  cudaError_t tune(const mpax_options& o, long long* launches) override {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    Sched* sc[2] = {&P.schedA, &P.schedAt};
+    const Csr* K[2] = {&P.A, &P.At};
+    const T* val[2] = {valA_, valAt_};
+    T* out[2] = {pw_, pg_};     // m and n entries (scratch of the power iteration)
+    const T* in[2] = {xbar_, y_};  // n and m entries
+    for (double& u : tune_us_) u = 0.0;
+    for (int q = 0; q < 2; ++q) {
+      int kind = kSpmvItem;
+      if (o.spmv_kernel >= 0) {
+        kind = o.spmv_kernel;
+      } else if (sc[q]->n_items > 0) {
+        TuneKey key;
+        cudaError_t e = tune_key(*K[q], sc[q]->n_items, sizeof(T), P.tmp_rows, s, &key);
+        if (e) return e;
+        if (!tune_lookup(key, &kind)) {
+          EpiStore<T> es{nullptr, out[q], nullptr, nullptr, nullptr, nullptr, 0};
+          double best = INFINITY;
+          for (int k = 0; k < kSpmvKinds; ++k) {
+            sc[q]->kind = k;
+            double us = 0.0;
+            e = time_launches(s, kTuneReps, &us, [&]() {
+              launch_spmv<T>(*sc[q], *K[q], val[q], InPlain<T>{in[q]}, es, 0, s);
+            });
+            if (e) return e;
+            *launches += kTuneReps + 1;
+            if (k == kSpmvPipe) {
+              // a bounded wait that gave up disqualifies the kernel (its error
+              // word is cleared so that the chosen kernel starts clean)
+              int herr = 0;
+              int* w = sc[q]->cnt + sc[q]->n_items;
+              if ((e = cudaMemcpyAsync(&herr, w, sizeof(int), cudaMemcpyDeviceToHost, s))) return e;
+              if ((e = cudaStreamSynchronize(s))) return e;
+              if (herr) {
+                if ((e = cudaMemsetAsync(w, 0, sizeof(int), s))) return e;
+                us = INFINITY;
+              }
+            }
+            tune_us_[2 * q + k] = us;
+            if (us < best) {
+              best = us;
+              kind = k;
+            }
+          }
+          tune_store(key, kind);
+        }
+      }
+      if (sc[q]->kind != kind) ++sched_generation;  // graphs captured the old kernel
+      sc[q]->kind = kind;
+      tune_kind_[q] = kind;
+    }
+    return cudaGetLastError();
+  }
+
+  // The error words of the pipelined SpMV (a bounded wait that gave up):
+  // cudaErrorTimeout when one is set.
+  cudaError_t pipe_errors() {
+    ProblemData& P = *P_;
+    const Sched* sc[2] = {&P.schedA, &P.schedAt};
+    for (const Sched* q : sc) {
+      if (!q->cnt || q->kind != kSpmvPipe) continue;
+      int h = 0;
+      cudaError_t e = cudaMemcpy(&h, q->cnt + q->n_items, sizeof(int), cudaMemcpyDeviceToHost);
+      if (e) return e;
+      if (h) return cudaErrorTimeout;
+    }
+    return cudaSuccess;
+  }
+
+  void tune_info(int* kind, double* us) const override {
+    for (int q = 0; q < 2; ++q) kind[q] = tune_kind_[q];
+    for (int i = 0; i < 2 * kSpmvKinds; ++i) us[i] = tune_us_[i];
   }
 
   cudaError_t init_state(const mpax_options& o, long long* launches) override {
@@ -929,6 +1144,9 @@ class Engine final : public EngineBase {
     prof_used_ = 0;
   }
 
+  int tune_kind_[2] = {0, 0};
+  double tune_us_[2 * kSpmvKinds] = {};
+
   cudaError_t block_graph(int len, cudaGraphExec_t* out) {
     if (graph_gen_ != sched_generation) {
       for (auto& kv : graphs_) cudaGraphExecDestroy(kv.second);
@@ -1036,6 +1254,7 @@ class Engine final : public EngineBase {
     cudaEventDestroy(ev[1]);
     if (e) return e;
     if ((e = cudaStreamSynchronize(s))) return e;
+    if ((e = pipe_errors())) return e;
     DevState h;
     if ((e = read_state(&h))) return e;
     if (tape_on_) {

@@ -21,7 +21,6 @@
 //
 // Layout: A is row-major m x n, i.e. column-major n x m; X, Y and every
 // per-instance vector are column-major (column k = instance k).
-#include <cublas_v2.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -33,6 +32,7 @@
 #include <vector>
 
 #include "../../include/mpax.h"
+#include "umma_host.h"
 #include "common.cuh"
 
 namespace mpax {
@@ -142,9 +142,10 @@ struct Vecs {
   const float *ct, *l, *u, *lc, *uc;  // scaled: ct n x B, l/u n, lc/uc m
   float *w, *xa, *xhat, *T;             // n x B
   float *y, *ya, *yhat, *S;             // m x B
-  __nv_bfloat16 *xh_hi, *xh_lo, *y_hi, *y_lo;
+  __nv_bfloat16 *xh_hi, *xh_lo, *y_hi, *y_lo;  // BF16 splits: B rows of ldx / ldy
   double* part;                          // per-column partials [q][k]
   Inst* inst;
+  long long ldx, ldy;                    // row strides of the splits (n, m rounded to 8)
 };
 
 // primal: T = A~^T Y; x = w + (anchor - w)/(k+1); x^ = proj(x - tau (c~ - T));
@@ -170,7 +171,7 @@ __global__ void k_primal(Vecs v, int check, const float* __restrict__ tpart, int
     const float xh = fminf(fmaxf(x - (float)I.tau * (v.ct[e] - t), v.l[j]), v.u[j]);
     const float wn = 2.0f * xh - x;
     v.w[e] = wn;
-    split_store(wn, v.xh_hi, v.xh_lo, e);
+    split_store(wn, v.xh_hi, v.xh_lo, (size_t)k * v.ldx + j);
     if (check) v.xhat[e] = xh;
   }
 }
@@ -200,7 +201,7 @@ __global__ void k_dual(Vecs v, int check, const float* __restrict__ spart, int s
     const float z = 2.0f * yh - y0;
     const float yn = z + hb * (v.ya[e] - z);
     v.y[e] = yn;
-    split_store(yn, v.y_hi, v.y_lo, e);
+    split_store(yn, v.y_hi, v.y_lo, (size_t)k * v.ldy + i);
     if (check) v.yhat[e] = yh;
   }
 }
@@ -369,7 +370,7 @@ __global__ void k_restart_apply(Vecs v) {
       const float xh = v.xhat[e];
       v.xa[e] = xh;
       v.w[e] = xh;
-      split_store(xh, v.xh_hi, v.xh_lo, e);
+      split_store(xh, v.xh_hi, v.xh_lo, (size_t)k * v.ldx + (e - (size_t)k * v.n));
     } else {
       const size_t f = e - tn;
       const int k = (int)(f / v.m);
@@ -377,7 +378,7 @@ __global__ void k_restart_apply(Vecs v) {
       const float yh = v.yhat[f];
       v.ya[f] = yh;
       v.y[f] = yh;
-      split_store(yh, v.y_hi, v.y_lo, f);
+      split_store(yh, v.y_hi, v.y_lo, (size_t)k * v.ldy + (f - (size_t)k * v.m));
     }
   }
 }
@@ -492,6 +493,38 @@ __global__ void k_scale_f(float* __restrict__ v, size_t n, const double* __restr
     v[i] = (float)((double)v[i] * inv);
 }
 
+// SPO+ (Sec. 3.4): c' = 2 c_hat - c_true; per instance k (one block),
+// loss_k = -c'_k^T x~_k + 2 c_hat_k^T x*_k - z*_k and grad_k = 2 (x*_k - x~_k),
+// fixed-order FP64 sums (Elmachtoub and Grigas 2022).
+__global__ void k_spo_costs2(const double* __restrict__ c_hat, const double* __restrict__ c_true,
+                             size_t len, double* __restrict__ out) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len;
+       t += (size_t)gridDim.x * blockDim.x)
+    out[t] = 2.0 * c_hat[t] - c_true[t];
+}
+__global__ void k_spo_loss2(int n, const double* __restrict__ cp, const double* __restrict__ c_hat,
+                            const double* __restrict__ x_true, const double* __restrict__ z_true,
+                            const double* __restrict__ x_tl, double* __restrict__ loss,
+                            double* __restrict__ grad) {
+  __shared__ double sh[32];
+  const size_t j0 = (size_t)blockIdx.x * n;
+  double v = 0.0, t = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double xt = x_tl[j0 + j], xs = x_true[j0 + j];
+    v += cp[j0 + j] * xt;
+    t += c_hat[j0 + j] * xs;
+    grad[j0 + j] = 2.0 * (xs - xt);
+  }
+  v = block_sum(v, sh);
+  __syncthreads();
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) loss[blockIdx.x] = -v + 2.0 * t - z_true[blockIdx.x];
+}
+__global__ void k_inst_pobj(const Inst* __restrict__ inst, int B, double* __restrict__ v) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < B) v[k] = inst[k].pobj;
+}
+
 }  // namespace
 }  // namespace mpax
 
@@ -500,7 +533,6 @@ using namespace mpax;
 struct mpax_shared {
   int m = 0, n = 0, B = 0;
   cudaStream_t user = nullptr, s = nullptr;
-  cublasHandle_t blas = nullptr;
   float* A0 = nullptr;   // original FP32, row-major m x n
   float* As = nullptr;   // scaled FP32
   __nv_bfloat16 *Ahi = nullptr, *Alo = nullptr;
@@ -524,6 +556,12 @@ struct mpax_shared {
   // the A w product over gemv_nchunks column chunks
   float* gpart = nullptr;
   float* gpart_n = nullptr;
+  double* spo = nullptr;  // SPO+ staging of host arguments: 3 n B + B doubles
+  // tensor-core products: BF16 splits are stored with row strides n8, m8 (n, m
+  // rounded up to 8, as TMA wants 16-byte strides; the pad columns stay zero)
+  long long n8 = 0, m8 = 0;
+  UmmaPlan plan_dual, plan_primal;  // S = A~ X (K = n), T = A~^T Y (K = m)
+  int* uerr = nullptr;              // set by a bounded wait of the product kernel
   int gemv_chunks = 1, gemv_nchunks = 1;
   long long gemv_launches = 0;
 };
@@ -538,10 +576,10 @@ void free_shared(mpax_shared* sh) {
                   sh->ct,  sh->lf,   sh->uf,    sh->lcf,   sh->ucf,  sh->w,    sh->xa,
                   sh->xhat, sh->T,   sh->xprev, sh->y,     sh->ya,   sh->yhat, sh->S,
                   sh->yprev, sh->xh_hi, sh->xh_lo, sh->y_hi, sh->y_lo, sh->part, sh->cn,
-                  sh->cns, sh->inst, sh->Xout, sh->Yout, sh->gpart, sh->gpart_n};
+                  sh->cns, sh->inst, sh->Xout, sh->Yout, sh->gpart, sh->gpart_n, sh->spo,
+                  sh->uerr};
   for (void* b : bufs)
     if (b) cudaFree(b);
-  if (sh->blas) cublasDestroy(sh->blas);
   if (sh->s) cudaStreamDestroy(sh->s);
   delete sh;
 }
@@ -673,6 +711,82 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv_n_part(const float* __res
   }
 }
 
+// ---- B > 1, FP32 products on the CUDA cores ----------------------------------------
+// C[n][m] = sum_k A_op[m][k] V[n][k] for the B instances' vectors V (rows of ldv):
+// A_op = A~ stored [M][K] (a_mn = 0, the dual step's A~ X) or A~^T of an A~ stored
+// [K][M] (a_mn = 1, the primal step's A~^T Y).  CTA tile 128 (M) x 64 (N) x 16
+// (K) staged in shared memory; each of 256 threads accumulates 8 x 4 outputs in
+// FP32, k in increasing order (one fixed order per output).
+constexpr int kSgBM = 128, kSgBN = 64, kSgBK = 16;
+
+template <int A_MN>
+__global__ void __launch_bounds__(256) k_sgemm(const float* __restrict__ A, long long lda,
+                                               const float* __restrict__ V, long long ldv,
+                                               float* __restrict__ Cm, long long ldc, int M,
+                                               int N, int K) {
+  __shared__ float As[kSgBK][kSgBM + 4];
+  __shared__ float Vs[kSgBK][kSgBN + 4];
+  const int tid = threadIdx.x;
+  const int tm = tid % 16, tn = tid / 16;  // 8 rows (m) and 4 instances (n) each
+  const int m0 = blockIdx.x * kSgBM, n0 = blockIdx.y * kSgBN;
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+  for (int k0 = 0; k0 < K; k0 += kSgBK) {
+    // A tile: 128 x 16 values, 8 per thread
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = tid + 256 * t;
+      int r, kk;
+      if (A_MN) {  // consecutive threads along m (contiguous in memory)
+        r = e % kSgBM;
+        kk = e / kSgBM;
+      } else {     // consecutive threads along k (contiguous in memory)
+        kk = e % kSgBK;
+        r = e / kSgBK;
+      }
+      const int gm = m0 + r, gk = k0 + kk;
+      float v = 0.0f;
+      if (gm < M && gk < K) v = A_MN ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+      As[kk][r] = v;
+    }
+    // V tile: 64 x 16 values, 4 per thread
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = tid + 256 * t;
+      const int kk = e % kSgBK, c = e / kSgBK;
+      const int gn = n0 + c, gk = k0 + kk;
+      Vs[kk][c] = (gn < N && gk < K) ? V[(long long)gn * ldv + gk] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kSgBK; ++kk) {
+      float a[8], b[4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = As[kk][tm * 8 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Vs[kk][tn * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int gn = n0 + tn * 4 + j;
+    if (gn >= N) continue;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int gm = m0 + tm * 8 + i;
+      if (gm < M) Cm[(long long)gn * ldc + gm] = acc[i][j];
+    }
+  }
+}
+
 }  // namespace mpax_gemv
 
 namespace {
@@ -705,39 +819,37 @@ void gemv_part(mpax_shared* sh, int trans, const float* vf, const float* Mf) {
 // C (rows x B, col-major) = op(M) V, M the stored column-major n x m matrix
 // (A row-major).  trans = 1: C = M^T V (= A V, rows = m, K = n); trans = 0:
 // C = M V (= A^T V, rows = n, K = m).  BF16x3 or FP32.
-cublasStatus_t product(mpax_shared* sh, int trans, const __nv_bfloat16* vhi,
+cudaError_t product(mpax_shared* sh, int trans, const __nv_bfloat16* vhi,
                        const __nv_bfloat16* vlo, const float* vf, float* C, bool bf16x3,
                        const float* Mf) {
   const int m = sh->m, n = sh->n, B = sh->B;
   const int rows = trans ? m : n, K = trans ? n : m;
-  const cublasOperation_t op = trans ? CUBLAS_OP_T : CUBLAS_OP_N;
-  const float one = 1.0f, zero = 0.0f;
-  cublasStatus_t st;
   if (!bf16x3 && B == 1) {
     gemv_part(sh, trans, vf, Mf);
     if (trans) k_gemv_t_sum<<<g1(m), 256, 0, sh->s>>>(sh->gpart_n, sh->gemv_nchunks, m, C);
     else k_gemv_t_sum<<<g1(n), 256, 0, sh->s>>>(sh->gpart, sh->gemv_chunks, n, C);
     sh->gemv_launches += 1;
-    return cudaGetLastError() == cudaSuccess ? CUBLAS_STATUS_SUCCESS : CUBLAS_STATUS_EXECUTION_FAILED;
+    return cudaGetLastError();
   }
   if (!bf16x3) {
-    st = cublasSgemm(sh->blas, op, CUBLAS_OP_N, rows, B, K, &one, Mf, n, vf, K, &zero, C, rows);
+    // FP32 on the CUDA cores: trans = 1 is A~ V (A~ [m][n] K-major), trans = 0
+    // is A~^T V (the same storage read M-major)
+    const dim3 grid((rows + kSgBM - 1) / kSgBM, (B + kSgBN - 1) / kSgBN);
+    if (trans) k_sgemm<0><<<grid, 256, 0, sh->s>>>(Mf, n, vf, K, C, rows, rows, B, K);
+    else k_sgemm<1><<<grid, 256, 0, sh->s>>>(Mf, n, vf, K, C, rows, rows, B, K);
     sh->gemms += 1;
     sh->gemm_flops += 2.0 * rows * (double)B * K;
-    return st;
+    return cudaGetLastError();
   }
-  // small terms first: A_hi v_lo, A_lo v_hi, then A_hi v_hi
-  const void* As[3] = {sh->Ahi, sh->Alo, sh->Ahi};
-  const void* Vs[3] = {vlo, vhi, vhi};
-  for (int t = 0; t < 3; ++t) {
-    st = cublasGemmEx(sh->blas, op, CUBLAS_OP_N, rows, B, K, &one, As[t], CUDA_R_16BF, n, Vs[t],
-                      CUDA_R_16BF, K, t == 0 ? &zero : &one, C, CUDA_R_32F, rows,
-                      CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-    if (st != CUBLAS_STATUS_SUCCESS) return st;
-  }
-  sh->gemms += 3;
-  sh->gemm_flops += 3 * 2.0 * rows * (double)B * K;
-  return CUBLAS_STATUS_SUCCESS;
+  // A_hi V_lo + A_lo V_hi + A_hi V_hi in one tensor-core kernel (umma.cuh); the
+  // plan of this direction holds the split buffers (vhi, vlo) and the output C
+  (void)vhi;
+  (void)vlo;
+  const UmmaPlan& p = trans ? sh->plan_dual : sh->plan_primal;
+  const cudaError_t e = umma_run(p, sh->s);
+  sh->gemms += 1;
+  sh->gemm_flops += p.flops;
+  return e;
 }
 
 }  // namespace
@@ -765,8 +877,10 @@ mpax_status mpax_lp_shared_create(int32_t m, int32_t n, int32_t B, const float* 
   };
   al(&sh->A0, mn);
   al(&sh->As, mn);
-  al(&sh->Ahi, mn);
-  al(&sh->Alo, mn);
+  sh->n8 = ((long long)n + 7) / 8 * 8;
+  sh->m8 = ((long long)m + 7) / 8 * 8;
+  al(&sh->Ahi, (size_t)m * sh->n8);
+  al(&sh->Alo, (size_t)m * sh->n8);
   al(&sh->C0, nB);
   al(&sh->lc, m);
   al(&sh->uc, m);
@@ -784,17 +898,19 @@ mpax_status mpax_lp_shared_create(int32_t m, int32_t n, int32_t B, const float* 
   al(&sh->ucf, m);
   for (float** p : {&sh->w, &sh->xa, &sh->xhat, &sh->T, &sh->xprev}) al(p, nB);
   for (float** p : {&sh->y, &sh->ya, &sh->yhat, &sh->S, &sh->yprev}) al(p, mB);
-  al(&sh->xh_hi, nB);
-  al(&sh->xh_lo, nB);
-  al(&sh->y_hi, mB);
-  al(&sh->y_lo, mB);
+  al(&sh->xh_hi, (size_t)B * sh->n8);
+  al(&sh->xh_lo, (size_t)B * sh->n8);
+  al(&sh->y_hi, (size_t)B * sh->m8);
+  al(&sh->y_lo, (size_t)B * sh->m8);
+  al(&sh->uerr, 1);
   al(&sh->part, 16 * (size_t)B);
   al(&sh->cn, B);
   al(&sh->cns, B);
   al(&sh->inst, B);
   al(&sh->Xout, nB);
   al(&sh->Yout, mB);
-  if (B == 1) {
+  {
+    // (every B: the power iteration's matrix-vector products use them too)
     // row chunks of the A^T y product: about four blocks per SM in all
     const long long tiles = (n + 4LL * kGemvThreads - 1) / (4LL * kGemvThreads);
     const long long want = (4LL * 152 + tiles - 1) / tiles;
@@ -807,6 +923,11 @@ mpax_status mpax_lp_shared_create(int32_t m, int32_t n, int32_t B, const float* 
     al(&sh->gpart_n, (size_t)sh->gemv_nchunks * m);
   }
   const cudaMemcpyKind k = kind == MPAX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  for (void* q : {(void*)sh->xh_hi, (void*)sh->xh_lo})
+    if (!e) e = cudaMemset(q, 0, sizeof(__nv_bfloat16) * (size_t)B * sh->n8);
+  for (void* q : {(void*)sh->y_hi, (void*)sh->y_lo})
+    if (!e) e = cudaMemset(q, 0, sizeof(__nv_bfloat16) * (size_t)B * sh->m8);
+  if (!e) e = cudaMemset(sh->uerr, 0, sizeof(int));
   if (!e) e = cudaMemcpy(sh->A0, A, sizeof(float) * mn, k);
   if (!e) e = cudaMemcpy(sh->C0, C, sizeof(double) * nB, k);
   if (!e) e = cudaMemcpy(sh->lc, lc, sizeof(double) * m, k);
@@ -818,13 +939,7 @@ mpax_status mpax_lp_shared_create(int32_t m, int32_t n, int32_t B, const float* 
     return sfail(e == cudaErrorMemoryAllocation ? MPAX_ERR_OUT_OF_MEMORY : MPAX_ERR_CUDA,
                  cudaGetErrorString(e));
   }
-  if (cublasCreate(&sh->blas) != CUBLAS_STATUS_SUCCESS ||
-      cublasSetStream(sh->blas, sh->s) != CUBLAS_STATUS_SUCCESS) {
-    free_shared(sh);
-    return sfail(MPAX_ERR_CUDA, "cuBLAS initialisation failed");
-  }
-  cublasSetMathMode(sh->blas, CUBLAS_DEFAULT_MATH);  // no TF32: the FP32 path stays FP32
-  *out = sh;
+*out = sh;
   return MPAX_OK;
 }
 
@@ -871,7 +986,19 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
     L += 4;
   }
   k_scale_dense<<<g1(mn), 256, 0, s>>>(sh->A0, sh->As, m, n, sh->Dr, sh->Dc);
-  k_split<<<g1(mn), 256, 0, s>>>(sh->As, sh->Ahi, sh->Alo, mn);
+  split_rows(sh->As, m, n, n, sh->Ahi, sh->Alo, sh->n8, s);
+  {
+    cudaError_t pe = umma_plan(&sh->plan_dual, sh->Ahi, sh->Alo, sh->n8, 0, sh->xh_hi, sh->xh_lo,
+                               sh->n8, m, B, n, sh->S, m, sh->uerr);
+    if (!pe)
+      pe = umma_plan(&sh->plan_primal, sh->Ahi, sh->Alo, sh->n8, 1, sh->y_hi, sh->y_lo, sh->m8, n,
+                     B, m, sh->T, n, sh->uerr);
+    if (pe) {
+      cudaEventDestroy(ev);
+      return sfail(MPAX_ERR_CUDA, std::string("tensor-core product plan: ") +
+                                      cudaGetErrorString(pe));
+    }
+  }
   k_scale_costs<<<g1(nB), 256, 0, s>>>(sh->C0, sh->Dc, n, nB, sh->ct);
   k_scale_vec<<<(n + 255) / 256, 256, 0, s>>>(sh->l, sh->Dc, 1, n, sh->lf);
   k_scale_vec<<<(n + 255) / 256, 256, 0, s>>>(sh->u, sh->Dc, 1, n, sh->uf);
@@ -888,11 +1015,13 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
     const double inv = 1.0 / std::sqrt(ss > 0.0 ? ss : 1.0);
     for (int j = 0; j < n; ++j) v0[j] = (float)(power_start_raw(j) * inv);
     cudaMemcpyAsync(v, v0.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s);
-    const float one = 1.0f, zero = 0.0f;
     double prev = 0.0, nu = 0.0, d_prev = 0.0;
     for (int t = 1; t <= o->power_max_iter; ++t) {
-      cublasSgemv(sh->blas, CUBLAS_OP_T, n, m, &one, sh->As, n, v, 1, &zero, wv, 1);
-      cublasSgemv(sh->blas, CUBLAS_OP_N, n, m, &one, sh->As, n, wv, 1, &zero, v, 1);
+      // wv = A~ v, v = A~^T wv with this file's matrix-vector kernels
+      gemv_part(sh, 1, v, sh->As);
+      k_gemv_t_sum<<<g1(m), 256, 0, s>>>(sh->gpart_n, sh->gemv_nchunks, m, wv);
+      gemv_part(sh, 0, wv, sh->As);
+      k_gemv_t_sum<<<g1(n), 256, 0, s>>>(sh->gpart, sh->gemv_chunks, n, v);
       k_vec_norm_part<<<1, 512, 0, s>>>(v, n, sh->scal);
       double nrm = 0.0;
       cudaMemcpyAsync(&nrm, sh->scal, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -926,17 +1055,18 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
     cudaMemsetAsync(p, 0, sizeof(float) * nB, s);
   for (void* p : {(void*)sh->y, (void*)sh->ya, (void*)sh->yhat})
     cudaMemsetAsync(p, 0, sizeof(float) * mB, s);
-  cudaMemsetAsync(sh->xh_hi, 0, sizeof(__nv_bfloat16) * nB, s);
-  cudaMemsetAsync(sh->xh_lo, 0, sizeof(__nv_bfloat16) * nB, s);
-  cudaMemsetAsync(sh->y_hi, 0, sizeof(__nv_bfloat16) * mB, s);
-  cudaMemsetAsync(sh->y_lo, 0, sizeof(__nv_bfloat16) * mB, s);
+  cudaMemsetAsync(sh->xh_hi, 0, sizeof(__nv_bfloat16) * B * sh->n8, s);
+  cudaMemsetAsync(sh->xh_lo, 0, sizeof(__nv_bfloat16) * B * sh->n8, s);
+  cudaMemsetAsync(sh->y_hi, 0, sizeof(__nv_bfloat16) * B * sh->m8, s);
+  cudaMemsetAsync(sh->y_lo, 0, sizeof(__nv_bfloat16) * B * sh->m8, s);
+  cudaMemsetAsync(sh->uerr, 0, sizeof(int), s);
   L += 4;
   bool bf = !fp32_products;
   long long switch_iter = -1;  // iteration at which BF16x3 gave way to FP32 products
   int switch_active = 0;
   Vecs V{m, n, B, sh->ct, sh->lf, sh->uf, sh->lcf, sh->ucf, sh->w, sh->xa, sh->xhat, sh->T,
          sh->y, sh->ya, sh->yhat, sh->S, sh->xh_hi, sh->xh_lo, sh->y_hi, sh->y_lo, sh->part,
-         sh->inst};
+         sh->inst, sh->n8, sh->m8};
   KktArgs K{m, n, B, sh->xhat, sh->yhat, sh->S, sh->T, nullptr, sh->xa, nullptr, sh->ya,
             sh->Dr, sh->Dc, sh->C0, sh->lc, sh->uc, sh->l, sh->u, sh->part};
   long long done_iters = 0;
@@ -965,13 +1095,13 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
         continue;
       }
       if (product(sh, 0, sh->y_hi, sh->y_lo, sh->y, sh->T, bf, sh->As)) {
-        result = sfail(MPAX_ERR_CUDA, "cuBLAS product failed");
+        result = sfail(MPAX_ERR_CUDA, "matrix product launch failed");
         break;
       }
       k_primal<<<g1(nB), 256, 0, s>>>(V, chk, nullptr, 0);
       // the dual product reads the reflected point w (FP32) or its BF16 split
       if (product(sh, 1, sh->xh_hi, sh->xh_lo, sh->w, sh->S, bf, sh->As)) {
-        result = sfail(MPAX_ERR_CUDA, "cuBLAS product failed");
+        result = sfail(MPAX_ERR_CUDA, "matrix product launch failed");
         break;
       }
       k_dual<<<g1(mB), 256, 0, s>>>(V, chk, nullptr, 0);
@@ -983,8 +1113,8 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
     ++check_no;
     // KKT products at (x^, y^): S = A~ x^, T = A~^T y^ (the x^/y^ splits reuse the
     // BF16 buffers; the iteration rewrites them before its next product)
-    k_split<<<g1(nB), 256, 0, s>>>(sh->xhat, sh->xh_hi, sh->xh_lo, nB);
-    k_split<<<g1(mB), 256, 0, s>>>(sh->yhat, sh->y_hi, sh->y_lo, mB);
+    split_rows(sh->xhat, B, n, n, sh->xh_hi, sh->xh_lo, sh->n8, s);
+    split_rows(sh->yhat, B, m, m, sh->y_hi, sh->y_lo, sh->m8, s);
     product(sh, 1, sh->xh_hi, sh->xh_lo, sh->xhat, sh->S, bf, sh->As);
     product(sh, 0, sh->y_hi, sh->y_lo, sh->yhat, sh->T, bf, sh->As);
     k_kkt_cols<<<B, 256, 0, s>>>(K, sh->inst);
@@ -998,8 +1128,8 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
                    tl_ns, B, check_no, (bf && o->fp64_continuation) ? o->stall_checks : 0};
     k_check_finalize<<<(B + 255) / 256, 256, 0, s>>>(sh->inst, sh->part, cp);
     // the BF16 splits of the iterates are rebuilt (restart copies x^, y^ into them)
-    k_split<<<g1(nB), 256, 0, s>>>(sh->w, sh->xh_hi, sh->xh_lo, nB);
-    k_split<<<g1(mB), 256, 0, s>>>(sh->y, sh->y_hi, sh->y_lo, mB);
+    split_rows(sh->w, B, n, n, sh->xh_hi, sh->xh_lo, sh->n8, s);
+    split_rows(sh->y, B, m, m, sh->y_hi, sh->y_lo, sh->m8, s);
     k_restart_apply<<<g1(nB + mB), 256, 0, s>>>(V);
     L += 8;
     cudaMemcpyAsync(hi.data(), sh->inst, sizeof(Inst) * B, cudaMemcpyDeviceToHost, s);
@@ -1020,6 +1150,13 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
   }
   cudaError_t e = cudaGetLastError();
   if (!result && e) result = sfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  {
+    int herr = 0;
+    cudaMemcpyAsync(&herr, sh->uerr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (!result && herr)
+      result = sfail(MPAX_ERR_DEVICE_TIMEOUT, "a bounded wait of the tensor-core product gave up");
+  }
   k_unscale_out<<<g1(nB), 256, 0, s>>>(sh->xhat, sh->Dc, n, nB, sh->Xout);
   k_unscale_out<<<g1(mB), 256, 0, s>>>(sh->yhat, sh->Dr, m, mB, sh->Yout);
   L += 2;
@@ -1087,6 +1224,88 @@ mpax_status mpax_shared_get_stats(const mpax_shared* sh, mpax_batch_stats* stats
     gemm_info[1] = sh->gemm_flops;
     gemm_info[2] = sh->norm_A;
   }
+  return MPAX_OK;
+}
+
+mpax_status mpax_shared_set_costs(mpax_shared* sh, const double* C, mpax_mem_kind kind) {
+  if (!sh || !C) return sfail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  const cudaMemcpyKind k = kind == MPAX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaEvent_t ev;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  cudaEventRecord(ev, sh->user);
+  cudaStreamWaitEvent(sh->s, ev, 0);
+  cudaError_t e = cudaMemcpyAsync(sh->C0, C, sizeof(double) * (size_t)sh->n * sh->B, k, sh->s);
+  if (!e) e = cudaStreamSynchronize(sh->s);
+  cudaEventDestroy(ev);
+  if (e) return sfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  sh->solved = false;
+  return MPAX_OK;
+}
+
+mpax_status mpax_shared_get_objective(const mpax_shared* sh, double* v, mpax_mem_kind kind) {
+  if (!sh || !v) return sfail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  if (!sh->solved) return sfail(MPAX_ERR_NOT_SOLVED, "call mpax_shared_solve first");
+  cudaError_t e;
+  if (kind == MPAX_MEM_HOST) {
+    for (int k = 0; k < sh->B; ++k) v[k] = sh->h_inst[k].pobj;
+    return MPAX_OK;
+  }
+  k_inst_pobj<<<(sh->B + 255) / 256, 256, 0, sh->s>>>(sh->inst, sh->B, v);
+  e = cudaGetLastError();
+  if (!e) e = cudaStreamSynchronize(sh->s);
+  if (e) return sfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  return MPAX_OK;
+}
+
+mpax_status mpax_shared_spo_plus(mpax_shared* sh, const mpax_options* o, int32_t fp32_products,
+                                 const double* C_hat, const double* C_true, const double* X_true,
+                                 const double* z_true, double* loss, double* grad,
+                                 mpax_mem_kind kind) {
+  if (!sh || !o || !C_hat || !C_true || !X_true || !z_true || !loss || !grad)
+    return sfail(MPAX_ERR_INVALID_ARGUMENT, "NULL argument");
+  const int B = sh->B, n = sh->n;
+  const size_t nB = (size_t)n * B;
+  cudaStream_t s = sh->s;
+  cudaEvent_t ev;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  cudaEventRecord(ev, sh->user);
+  cudaStreamWaitEvent(s, ev, 0);
+  cudaEventDestroy(ev);
+  cudaError_t e = cudaSuccess;
+  if (kind == MPAX_MEM_HOST) {
+    if (!sh->spo) e = cudaMalloc(&sh->spo, sizeof(double) * (3 * nB + B));
+    double* d = sh->spo;
+    if (!e) e = cudaMemcpyAsync(d, C_hat, sizeof(double) * nB, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d + nB, C_true, sizeof(double) * nB, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d + 2 * nB, X_true, sizeof(double) * nB, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d + 3 * nB, z_true, sizeof(double) * B, cudaMemcpyHostToDevice, s);
+    C_hat = d;
+    C_true = d + nB;
+    X_true = d + 2 * nB;
+    z_true = d + 3 * nB;
+  }
+  if (!e) {
+    k_spo_costs2<<<g1(nB), 256, 0, s>>>(C_hat, C_true, nB, sh->C0);
+    e = cudaGetLastError();
+  }
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return sfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  mpax_status st = mpax_shared_solve(sh, o, fp32_products);
+  if (st) return st;
+  double* dl = loss;
+  double* dg = grad;
+  if (kind == MPAX_MEM_HOST) {
+    dg = sh->spo + nB;      // C_true is no longer read
+    dl = sh->spo + 3 * nB;  // each block reads z_true[k] before writing loss[k]
+  }
+  k_spo_loss2<<<B, 256, 0, s>>>(n, sh->C0, C_hat, X_true, z_true, sh->Xout, dl, dg);
+  e = cudaGetLastError();
+  if (!e && kind == MPAX_MEM_HOST) {
+    e = cudaMemcpyAsync(grad, dg, sizeof(double) * nB, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(loss, dl, sizeof(double) * B, cudaMemcpyDeviceToHost, s);
+  }
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return sfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
   return MPAX_OK;
 }
 

@@ -193,10 +193,10 @@ cudaError_t build_schedule(const Csr& A, Sched& sc, cudaStream_t s, int* tmp_row
     sc.rows = A.rows;
     sc.n_items = n_items;
     if ((e = cudaMalloc(&sc.items, sizeof(int4) * std::max(n_items, 1)))) return e;
-    if ((e = cudaMalloc(&sc.cnt, sizeof(int) * std::max(n_items, 1)))) return e;
+    if ((e = cudaMalloc(&sc.cnt, sizeof(int) * (n_items + 1)))) return e;
     if ((e = cudaMalloc(&sc.carry, sizeof(double) * std::max(n_items, 1)))) return e;
     if ((e = cudaMalloc(&sc.part, sizeof(double) * kPartQ * std::max(n_items, 1)))) return e;
-    cudaMemsetAsync(sc.cnt, 0, sizeof(int) * std::max(n_items, 1), s);
+    cudaMemsetAsync(sc.cnt, 0, sizeof(int) * (n_items + 1), s);
     cudaMemsetAsync(sc.part, 0, sizeof(double) * kPartQ * std::max(n_items, 1), s);
     ++sched_generation;
   }

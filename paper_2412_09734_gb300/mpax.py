@@ -38,7 +38,10 @@ EXPORTED = ["mpax_version", "mpax_last_error", "mpax_status_string", "mpax_optio
             "mpax_lp_batch_create", "mpax_batch_solve", "mpax_batch_get_solution",
             "mpax_batch_get_stats", "mpax_batch_destroy", "mpax_lp_shared_create", "mpax_shared_solve",
             "mpax_shared_get_solution", "mpax_shared_get_stats", "mpax_shared_destroy",
-            "mpax_lp_kkt_noalloc"]
+            "mpax_lp_kkt_noalloc", "mpax_get_restart_history",
+            "mpax_lp_batch_create_replicated", "mpax_batch_set_costs",
+            "mpax_batch_get_objective", "mpax_batch_spo_plus", "mpax_shared_set_costs",
+            "mpax_shared_get_objective", "mpax_shared_spo_plus", "mpax_dense_bf16x3"]
 
 
 class MpaxError(RuntimeError):
@@ -63,7 +66,7 @@ class Options(ctypes.Structure):
         ("power_max_iter", ctypes.c_int32), ("power_tol", ctypes.c_double),
         ("use_graphs", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
         ("fp64_continuation", ctypes.c_int32), ("stall_checks", ctypes.c_int32),
-        ("record_tape", ctypes.c_int32),
+        ("record_tape", ctypes.c_int32), ("spmv_kernel", ctypes.c_int32),
     ]
 
 
@@ -82,6 +85,7 @@ class Stats(ctypes.Structure):
         ("profile_ms", ctypes.c_double * 4), ("profile_launches", ctypes.c_int64 * 4),
         ("fp64_iterations", ctypes.c_int64), ("polish_iterations", ctypes.c_int64),
         ("backward_launches", ctypes.c_int64),
+        ("spmv_kernel", ctypes.c_int32 * 2), ("spmv_tune_us", ctypes.c_double * 4),
     ]
 
     def as_dict(self):
@@ -133,6 +137,7 @@ _sig = {
     "mpax_solve": ([_P, ctypes.POINTER(Options), _P, _P, _INT], _INT),
     "mpax_get_solution": ([_P, _P, _P, _INT], _INT),
     "mpax_get_stats": ([_P, ctypes.POINTER(Stats)], _INT),
+    "mpax_get_restart_history": ([_P, ctypes.c_int32, _P, _P, _P], _INT),
     "mpax_destroy": ([_P], None),
     "mpax_prepare": ([_P, ctypes.POINTER(Options)], _INT),
     "mpax_get_scaling": ([_P, _P, _P, _P, _INT], _INT),
@@ -156,6 +161,15 @@ _sig = {
     "mpax_shared_get_solution": ([_P, _P, _P, _INT], _INT),
     "mpax_shared_get_stats": ([_P, ctypes.POINTER(BatchStats)] + [_P] * 6, _INT),
     "mpax_shared_destroy": ([_P], None),
+    "mpax_lp_batch_create_replicated": ([_I32, _I32, _I32, _I64] + [_P] * 7 +
+                                        [_INT, _P, ctypes.POINTER(_P)], _INT),
+    "mpax_batch_set_costs": ([_P, _P, _INT], _INT),
+    "mpax_batch_get_objective": ([_P, _P, _INT], _INT),
+    "mpax_batch_spo_plus": ([_P, ctypes.POINTER(Options)] + [_P] * 6 + [_INT], _INT),
+    "mpax_shared_set_costs": ([_P, _P, _INT], _INT),
+    "mpax_shared_get_objective": ([_P, _P, _INT], _INT),
+    "mpax_shared_spo_plus": ([_P, ctypes.POINTER(Options), _I32] + [_P] * 6 + [_INT], _INT),
+    "mpax_dense_bf16x3": ([_I32, _I32, _I32, _I32, _P, _P, _P, _INT, _P], _INT),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -355,6 +369,17 @@ def mpax_get_stats(h):
     return s.as_dict()
 
 
+def mpax_get_restart_history(h, cap=256):
+    """(iterations at each restart, primal weight after it) of the last run."""
+    it = np.zeros(cap, dtype=np.int64)
+    om = np.zeros(cap, dtype=np.float64)
+    cnt = ctypes.c_int32(0)
+    _check(_lib.mpax_get_restart_history(h, cap, it.ctypes.data_as(ctypes.c_void_p),
+                                         om.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)))
+    k = min(cnt.value, cap)
+    return it[:k].copy(), om[:k].copy(), cnt.value
+
+
 def mpax_destroy(h):
     if h:
         _lib.mpax_destroy(h)
@@ -435,11 +460,61 @@ def mpax_batch_solve(h, opts):
     _check(_lib.mpax_batch_solve(h, ctypes.byref(opts)))
 
 
-def mpax_batch_get_solution(h, m_total, n_total):
-    x = np.empty(n_total)
-    y = np.empty(m_total)
-    _check(_lib.mpax_batch_get_solution(h, _ptr_out(x), _ptr_out(y), MPAX_MEM_HOST))
+def _out(shape, device):
+    """An FP64 output buffer: a CUDA tensor on `device`'s device when `device` is a
+    CUDA tensor, else a numpy array; with its pointer and memory kind."""
+    if device is not None and _is_torch(device) and device.is_cuda:
+        import torch
+        t = torch.empty(shape, dtype=torch.float64, device=device.device)
+        return t, (t.data_ptr() if t.numel() else None), MPAX_MEM_DEVICE
+    a = np.empty(shape)
+    return a, (a.ctypes.data if a.size else None), MPAX_MEM_HOST
+
+
+def mpax_batch_get_solution(h, m_total, n_total, device=None):
+    x, px, kind = _out(n_total, device)
+    y, py, _ = _out(m_total, device)
+    _check(_lib.mpax_batch_get_solution(h, px, py, kind))
     return x, y
+
+
+def mpax_lp_batch_create_replicated(B, m, n, row_ptr, col_idx, val, lc, uc, l, u, stream=None):
+    kind = _kind_of(row_ptr, val)
+    k = _Keep(kind)
+    nnz = int(len(val)) if not _is_torch(val) else int(val.numel())
+    h = _P()
+    _check(_lib.mpax_lp_batch_create_replicated(
+        int(B), int(m), int(n), nnz, k.ptr(row_ptr, np.int64), k.ptr(col_idx, np.int32),
+        k.ptr(val, np.float64), k.ptr(lc, np.float64), k.ptr(uc, np.float64),
+        k.ptr(l, np.float64), k.ptr(u, np.float64), kind, _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def mpax_batch_set_costs(h, c):
+    kind = _kind_of(c)
+    k = _Keep(kind)
+    _check(_lib.mpax_batch_set_costs(h, k.ptr(c, np.float64), kind))
+
+
+def mpax_batch_get_objective(h, B, device=None):
+    v, pv, kind = _out(B, device)
+    _check(_lib.mpax_batch_get_objective(h, pv, kind))
+    return v
+
+
+def mpax_batch_spo_plus(h, opts, c_hat, c_true, x_true, z_true):
+    """(loss (B,), grad (like c_hat)) of SPO+; CUDA tensors in give CUDA tensors out."""
+    kind = _kind_of(c_hat)
+    k = _Keep(kind)
+    B = int(len(z_true)) if not _is_torch(z_true) else int(z_true.numel())
+    total = int(np.prod(c_hat.shape))
+    loss, pl, _ = _out(B, c_hat if kind == MPAX_MEM_DEVICE else None)
+    grad, pg, _ = _out(tuple(c_hat.shape), c_hat if kind == MPAX_MEM_DEVICE else None)
+    assert total == (grad.numel() if _is_torch(grad) else grad.size)
+    _check(_lib.mpax_batch_spo_plus(h, ctypes.byref(opts), k.ptr(c_hat, np.float64),
+                                    k.ptr(c_true, np.float64), k.ptr(x_true, np.float64),
+                                    k.ptr(z_true, np.float64), pl, pg, kind))
+    return loss, grad
 
 
 def mpax_batch_get_stats(h, B):
@@ -534,6 +609,32 @@ def mpax_shared_solve(h, opts, fp32_products=False):
     _check(_lib.mpax_shared_solve(h, ctypes.byref(opts), 1 if fp32_products else 0))
 
 
+def mpax_shared_set_costs(h, C):
+    kind = _kind_of(C)
+    k = _Keep(kind)
+    _check(_lib.mpax_shared_set_costs(h, k.ptr(C, np.float64), kind))
+
+
+def mpax_shared_get_objective(h, B, device=None):
+    v, pv, kind = _out(B, device)
+    _check(_lib.mpax_shared_get_objective(h, pv, kind))
+    return v
+
+
+def mpax_shared_spo_plus(h, opts, C_hat, C_true, X_true, z_true, fp32_products=False):
+    """(loss (B,), grad (B, n)) of SPO+ over the shared set; CUDA in, CUDA out."""
+    kind = _kind_of(C_hat)
+    k = _Keep(kind)
+    B = int(C_hat.shape[0])
+    loss, pl, _ = _out(B, C_hat if kind == MPAX_MEM_DEVICE else None)
+    grad, pg, _ = _out(tuple(C_hat.shape), C_hat if kind == MPAX_MEM_DEVICE else None)
+    _check(_lib.mpax_shared_spo_plus(h, ctypes.byref(opts), 1 if fp32_products else 0,
+                                     k.ptr(C_hat, np.float64), k.ptr(C_true, np.float64),
+                                     k.ptr(X_true, np.float64), k.ptr(z_true, np.float64),
+                                     pl, pg, kind))
+    return loss, grad
+
+
 def mpax_shared_get_solution(h, m, n, B, device=None):
     """Returns (X, Y) as (B, n) and (B, m) FP64 arrays; CUDA tensors when `device`
     is a CUDA tensor used as a template."""
@@ -568,3 +669,30 @@ def mpax_shared_get_stats(h, B):
 def mpax_shared_destroy(h):
     if h:
         _lib.mpax_shared_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# dense products of the shared-matrix batch
+# ---------------------------------------------------------------------------
+
+def mpax_dense_bf16x3(A, V, a_mn_major=False, stream=None):
+    """D (N x M) = rows of A_op V^T on the tensor cores (BF16x3); A is [M][K]
+    (or [K][M] with a_mn_major), V is [N][K].  CUDA tensors in, CUDA tensor out."""
+    kind = _kind_of(A, V)
+    if a_mn_major:
+        K, M = int(A.shape[0]), int(A.shape[1])
+    else:
+        M, K = int(A.shape[0]), int(A.shape[1])
+    N = int(V.shape[0])
+    k = _Keep(kind)
+    pa, pv = k.ptr(A, np.float32), k.ptr(V, np.float32)
+    if kind == MPAX_MEM_DEVICE:
+        import torch
+        D = torch.empty((N, M), dtype=torch.float32, device=A.device)
+        pd = D.data_ptr()
+    else:
+        D = np.empty((N, M), dtype=np.float32)
+        pd = D.ctypes.data
+    _check(_lib.mpax_dense_bf16x3(M, N, K, 1 if a_mn_major else 0, pa, pv, pd, kind,
+                                  _stream(stream)))
+    return D

@@ -207,42 +207,3 @@ def test_qp_layers_release_handles_on_every_path(C, monkeypatch):
         del x
         gc.collect()
         assert log == ["H"]
-
-
-def test_sparse_batch_layers_pack_a_block_diagonal_batch(C, monkeypatch):
-    """Host logic of SparseLPValues / SPOPlusLossSparse (no GPU, fake library): the B
-    cost rows become B copies of one CSR with local columns, i.e. the block-diagonal
-    matrix, and the packed solution comes back as B rows."""
-    import types
-
-    import scipy.sparse as sp
-    import torch
-
-    from paper_2412_09734_gb300 import autograd as AG
-    from synth import grid_shortest_path_lp, instance_seed
-    g = grid_shortest_path_lp(4, B=3, seed=instance_seed(1))
-    seen = {}
-
-    def create(B, m_off, n_off, row_ptr, col, val, c, lc, uc, l, u):
-        seen.update(B=B, m_off=m_off, n_off=n_off, row_ptr=row_ptr, col=col, val=val, c=c,
-                    lc=lc)
-        return "H"
-
-    fake = types.SimpleNamespace(
-        mpax_lp_batch_create=create, mpax_batch_solve=lambda h, o: None,
-        mpax_options_default=lambda **k: None,
-        mpax_batch_get_solution=lambda h, M, N: (np.arange(N, dtype=float), np.zeros(M)),
-        mpax_batch_get_stats=lambda h, B: ({}, dict(primal_obj=np.arange(B, dtype=float))),
-        mpax_batch_destroy=lambda h: None)
-    monkeypatch.setattr(AG, "C", fake)
-    X, v = AG._batch_solve(g, torch.from_numpy(g["C"]), {})
-    m, n, B = g["m"], g["n"], 3
-    glob = seen["col"] + np.repeat(np.arange(B) * n, g["nnz"])
-    Ab = sp.csr_matrix((seen["val"], glob, seen["row_ptr"]), shape=(B * m, B * n))
-    A = sp.csr_matrix((g["val"], g["col"], g["row_ptr"]), shape=(m, n))
-    assert abs(Ab - sp.block_diag([A] * B)).max() == 0
-    assert np.array_equal(seen["m_off"], [0, m, 2 * m, 3 * m])
-    assert np.array_equal(seen["c"], g["C"].ravel())
-    assert np.array_equal(seen["lc"], np.tile(g["lc"], B))
-    assert X.shape == (B, n) and np.array_equal(X[1].numpy(), np.arange(n, 2 * n))
-    assert v.tolist() == [0.0, 1.0, 2.0]

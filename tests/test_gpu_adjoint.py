@@ -67,15 +67,24 @@ def test_qp_adjoint_matches_oracle(C, case, eps, tol):
     h = create(C, d)
     try:
         C.mpax_solve(h, C.mpax_options_default(eps_abs=eps, eps_rel=eps, iteration_limit=10**6))
-        x, _ = C.mpax_get_solution(h, d["m"], d["n"])
+        x, y = C.mpax_get_solution(h, d["m"], d["n"])
         dc, db, dD, info = C.mpax_qp_adjoint(h, x - d["x_target"], d["m"], d["n"], tol=1e-12,
                                              max_iter=20000)
     finally:
         C.mpax_destroy(h)
     assert info["rel_residual"] <= 1e-10
+    # the adjoint at the oracle's own optimum: the two solves' points differ by
+    # the solve tolerance, which bounds this comparison
     assert rel_inf(dc, rdc) <= tol
     assert rel_inf(db, rdb) <= tol
     assert rel_inf(dD, rdD) <= tol
+    # the same linear system: the oracle's direct solve at the GPU's point (same
+    # active-set rule); MINRES to a 1e-12 residual must agree to 1e-6
+    free_g, rows_g = AD.active_sets(p, x, y, 1e-7, 1e-7)
+    gdc, gdb, gdD = AD.qp_adjoint(p, x, y, x - d["x_target"], free_g, rows_g)
+    assert rel_inf(dc, gdc) <= 1e-6
+    assert rel_inf(db, gdb) <= 1e-6
+    assert rel_inf(dD, gdD) <= 1e-6
 
 
 def test_qp_layer_autograd_matches_finite_differences(C):

@@ -5,7 +5,7 @@ import pytest
 
 from oracle import pdhg as O
 from synth import ragged_lp_batch
-from tests.gpu_util import lib
+from tests.gpu_util import lib, rel_inf
 
 pytestmark = pytest.mark.gpu
 
@@ -191,3 +191,122 @@ def test_batch_with_every_bound_type(C):
             assert chk["converged"], (prec, b, chk["rel_kkt"])
             assert chk["primal_obj"] == pytest.approx(inst["opt_value"], rel=30 * eps,
                                                       abs=30 * eps)
+
+
+def _pack(insts):
+    """Pack instance dictionaries like synth.ragged_lp_batch."""
+    B = len(insts)
+    m_off = np.zeros(B + 1, dtype=np.int64)
+    n_off = np.zeros(B + 1, dtype=np.int64)
+    nnz_off = np.zeros(B + 1, dtype=np.int64)
+    np.cumsum([d["m"] for d in insts], out=m_off[1:])
+    np.cumsum([d["n"] for d in insts], out=n_off[1:])
+    np.cumsum([d["nnz"] for d in insts], out=nnz_off[1:])
+    row_ptr = np.concatenate([[0]] + [d["row_ptr"][1:] + nnz_off[i] for i, d in enumerate(insts)])
+    cat = lambda k: np.concatenate([d[k] for d in insts])  # noqa: E731
+    return dict(B=B, m_off=m_off, n_off=n_off, row_ptr=row_ptr.astype(np.int64),
+                col=cat("col"), val=cat("val"), c=cat("c"), lc=cat("lc"), uc=cat("uc"),
+                l=cat("l"), u=cat("u"), instances=insts)
+
+
+def _iterate_batch():
+    from synth import instance_seed, lp_instance
+    ms = [20, 64, 150, 333, 700, 2000]
+    return _pack([lp_instance(m, 2 * m, seed=instance_seed(7000 + i), density=0.01 if m > 500
+                              else 0.05, variant="nondegenerate") for i, m in enumerate(ms)])
+
+
+@pytest.mark.parametrize("prec,k,tol", [(0, 192, 1e-12), (1, 64, 1e-5)],
+                         ids=["fp64_192", "mixed_64"])
+@pytest.mark.parametrize("pmax", [0, 1000])
+def test_batch_iterates_match_oracle(C, prec, k, tol, pmax):
+    """Iterate-level parity of the persistent batch kernel (eqs. 3-4, Algorithm 1
+    per instance): k iterations from zero, with the checks, restarts and
+    primal-weight updates they include, give the oracle's (x^, y^) of the last
+    check element by element (normwise relative in the inf-norm), with the same
+    number of restarts, for instances from m = 20 to m = 2000."""
+    d = _iterate_batch()
+    h = _create(C, d)
+    try:
+        C.mpax_batch_solve(h, C.mpax_options_default(precision=prec, iteration_limit=k,
+                                                     eps_abs=1e-14, eps_rel=1e-14,
+                                                     power_max_iter=pmax))
+        summary, per = C.mpax_batch_get_stats(h, d["B"])
+        x, y = C.mpax_batch_get_solution(h, int(d["m_off"][-1]), int(d["n_off"][-1]))
+    finally:
+        C.mpax_batch_destroy(h)
+    assert np.all(per["iterations"] == k)
+    restarts = 0
+    for b, inst in enumerate(d["instances"]):
+        p = O.problem_from_arrays(inst)
+        ref = O.solve_lp(p, O.Options(eps_abs=1e-14, eps_rel=1e-14, iteration_limit=k,
+                                      power_max_iter=pmax, eps_primal_infeasible=0.0,
+                                      eps_dual_infeasible=0.0))
+        xs = x[d["n_off"][b]:d["n_off"][b + 1]]
+        ys = y[d["m_off"][b]:d["m_off"][b + 1]]
+        assert ref.iterations == k
+        assert rel_inf(xs, ref.x) <= tol, (b, rel_inf(xs, ref.x))
+        assert rel_inf(ys, ref.y) <= tol, (b, rel_inf(ys, ref.y))
+        restarts += ref.restarts
+    assert summary["restarts_total"] == restarts
+
+
+def _oversized_batch():
+    from synth import instance_seed, lp_instance
+    small = [lp_instance(m, 2 * m, seed=instance_seed(7100 + i), density=0.05,
+                         variant="nondegenerate") for i, m in enumerate([40, 120, 300])]
+    # m + n = 36,000: shared memory in FP32 (<= 51,200), global memory in FP64 (> 25,600)
+    mid = lp_instance(12000, 24000, seed=instance_seed(7110), density=3e-4,
+                      variant="nondegenerate")
+    # m + n = 60,000: global memory in both precisions
+    big = lp_instance(20000, 40000, seed=instance_seed(7111), density=1.5e-4,
+                      variant="nondegenerate")
+    return _pack(small[:2] + [mid] + small[2:] + [big])
+
+
+def _check_batch(d, x, y, per, eps):
+    for b, inst in enumerate(d["instances"]):
+        p = O.problem_from_arrays(inst)
+        xs = x[d["n_off"][b]:d["n_off"][b + 1]]
+        ys = y[d["m_off"][b]:d["m_off"][b + 1]]
+        chk = O.kkt(p, xs, ys, eps, eps)
+        assert per["status"][b] == 1 and chk["converged"], (b, chk["rel_kkt"])
+        assert chk["primal_obj"] == pytest.approx(inst["opt_value"], rel=30 * eps, abs=30 * eps)
+
+
+def test_batch_instances_beyond_shared_memory_fp64(C):
+    """Instances whose vectors exceed a CTA's shared memory run from global
+    memory (m + n = 36,000 and 60,000 in FP64), beside shared-memory ones in the
+    same launch; with such an instance in the launch no row pointers are staged."""
+    d = _oversized_batch()
+    eps = 1e-6
+    h = _create(C, d)
+    try:
+        C.mpax_batch_solve(h, C.mpax_options_default(precision=0, eps_abs=eps, eps_rel=eps,
+                                                     iteration_limit=200000))
+        summary, per = C.mpax_batch_get_stats(h, d["B"])
+        x, y = C.mpax_batch_get_solution(h, int(d["m_off"][-1]), int(d["n_off"][-1]))
+    finally:
+        C.mpax_batch_destroy(h)
+    assert summary["n_optimal"] == d["B"]
+    _check_batch(d, x, y, per, eps)
+
+
+def test_batch_fp64_continuation_of_an_instance_beyond_shared_memory(C):
+    """A mixed solve below the FP32 floor stalls; its FP64 continuation launch
+    takes instances whose FP64 vectors no longer fit in shared memory (the
+    m + n = 36,000 one fits in FP32 but not in FP64), and every instance meets
+    the tolerance in the oracle's evaluation."""
+    d = _oversized_batch()
+    eps = 1e-7
+    h = _create(C, d)
+    try:
+        C.mpax_batch_solve(h, C.mpax_options_default(precision=1, eps_abs=eps, eps_rel=eps,
+                                                     iteration_limit=400000))
+        summary, per = C.mpax_batch_get_stats(h, d["B"])
+        x, y = C.mpax_batch_get_solution(h, int(d["m_off"][-1]), int(d["n_off"][-1]))
+    finally:
+        C.mpax_batch_destroy(h)
+    assert summary["fp64_instances"] >= 1
+    assert summary["n_optimal"] == d["B"]
+    _check_batch(d, x, y, per, eps)

@@ -416,3 +416,32 @@ def test_f32_create_and_reduced_costs(C):
     # lam is a difference of O(1) terms: rounding is relative to them
     assert np.max(np.abs(lam - ref)) <= 1e-13 * (np.max(np.abs(p.c)) + np.max(np.abs(aty)))
     assert np.max(np.abs(ref)) > 0.05
+
+
+# ----------------------------------------------------------------------------- restarts
+
+@pytest.mark.parametrize("case,eps", [("lp_200x400", 1e-8), ("zipf_20k_40k", 1e-6)])
+def test_restart_log_matches_oracle(C, case, eps):
+    """Restart rule and primal-weight update (Sec. 3's adaptive restarts and
+    primal-weight updates, in the written reading): in FP64 the GPU restarts at
+    the same iterations as the oracle and its primal weight after every restart
+    equals the oracle's."""
+    if case == "lp_200x400":
+        d = lp_instance(200, 400, seed=instance_seed(1), density=0.02, variant="nondegenerate")
+    else:
+        d = zipf_lp(20000, 40000, 400000, 102, variant="nondegenerate")
+    p = O.problem_from_arrays(d)
+    ref = O.solve_lp(p, O.Options(eps_abs=eps, eps_rel=eps, iteration_limit=400000))
+    h = create(C, d)
+    try:
+        C.mpax_solve(h, C.mpax_options_default(eps_abs=eps, eps_rel=eps, iteration_limit=400000))
+        stats = C.mpax_get_stats(h)
+        it, om, cnt = C.mpax_get_restart_history(h)
+    finally:
+        C.mpax_destroy(h)
+    assert ref.status == "optimal" and stats["termination_name"] == "optimal"
+    assert cnt == stats["restarts"] == ref.restarts == len(ref.restart_log)
+    k = min(cnt, 256)
+    assert list(it) == [t for t, _ in ref.restart_log[:k]]
+    np.testing.assert_allclose(om, [w for _, w in ref.restart_log[:k]], rtol=1e-9, atol=0)
+    assert stats["iterations"] == ref.iterations

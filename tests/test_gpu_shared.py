@@ -97,16 +97,16 @@ def test_shared_values_autograd(C):
     """d v_k / d c_k = x_k*: the backward of the value layer returns the solved
     primal rows, whose values match c_k^T x0 and whose KKT error the oracle checks."""
     import torch
-    from paper_2412_09734_gb300.autograd import SharedLPValues
+    from paper_2412_09734_gb300.autograd import SharedFeasibleSet, SharedLPValues
     # 3/4 of x0 on a bound leaves ~32 free coordinates against 64 equality rows:
     # a tall, well-conditioned system, so x0 is the unique optimum
     d = shared_dense_lp_batch(64, 128, 6, seed=4242, bound_frac=0.75)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
     Cm = dev(d["C"]).requires_grad_(True)
     w = torch.linspace(0.5, 1.5, d["B"], dtype=torch.float64, device="cuda")
-    v = SharedLPValues.apply(Cm, dev(d["A"]), dev(d["b"]), dev(d["b"]), dev(d["l"]),
-                             dev(d["u"]), dict(eps_abs=1e-4, eps_rel=1e-4,
-                                               iteration_limit=400000))
+    fs = SharedFeasibleSet(dev(d["A"]), dev(d["b"]), dev(d["b"]), dev(d["l"]), dev(d["u"]),
+                           d["B"])
+    v = SharedLPValues.apply(Cm, fs, dict(eps_abs=1e-4, eps_rel=1e-4, iteration_limit=400000))
     (w * v).sum().backward()
     np.testing.assert_allclose(v.detach().cpu().numpy(), d["opt_value"], rtol=1e-3, atol=1e-3)
     G = Cm.grad.cpu().numpy()
@@ -126,19 +126,20 @@ def test_spo_plus_loss_matches_oracle(C):
     inequality along random directions)."""
     import torch
     from oracle import spo
-    from paper_2412_09734_gb300.autograd import SharedLPValues, SPOPlusLoss
+    from paper_2412_09734_gb300.autograd import SharedFeasibleSet, SharedLPValues, SPOPlusLoss
     d = shared_dense_lp_batch(64, 128, 4, seed=777, bound_frac=0.75)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
     opts = dict(eps_abs=1e-6, eps_rel=1e-6, iteration_limit=400000)
     A, b, l, u = dev(d["A"]), dev(d["b"]), dev(d["l"]), dev(d["u"])
+    fs = SharedFeasibleSet(A, b, b, l, u, d["B"])
     Ct = dev(d["C"])
     with torch.no_grad():
-        zt = SharedLPValues.apply(Ct, A, b, b, l, u, opts, True)
+        zt = SharedLPValues.apply(Ct, fs, opts, True)
     # the true optimum is x0 (unique, reduced costs at the bounds)
     Xt = torch.from_numpy(np.tile(d["x0"], (d["B"], 1))).cuda()
     rng = np.random.default_rng(11)
     Ch = dev(d["C"] + rng.normal(0, 0.5, d["C"].shape)).requires_grad_(True)
-    loss = SPOPlusLoss.apply(Ch, Ct, Xt, zt, A, b, b, l, u, opts, True)
+    loss = SPOPlusLoss.apply(Ch, Ct, Xt, zt, fs, opts, True)
     loss.sum().backward()
     G = Ch.grad.cpu().numpy()
     Lg = loss.detach().cpu().numpy()

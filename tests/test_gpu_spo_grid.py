@@ -34,10 +34,11 @@ def _dijkstra(g, cost):
 
 def test_sparse_lp_values_are_shortest_path_lengths(C):
     import torch
-    from paper_2412_09734_gb300.autograd import SparseLPValues
+    from paper_2412_09734_gb300.autograd import SparseFeasibleSet, SparseLPValues
     g = grid_shortest_path_lp(8, B=6, seed=instance_seed(41))
+    fs = SparseFeasibleSet(g, g["B"])
     Cm = torch.from_numpy(g["C"]).cuda().requires_grad_(True)
-    v = SparseLPValues.apply(Cm, g, OPTS)
+    v = SparseLPValues.apply(Cm, fs, OPTS)
     v.sum().backward()
     X = Cm.grad.cpu().numpy()
     A = sp.csr_matrix((g["val"], g["col"], g["row_ptr"]), shape=(g["m"], g["n"]))
@@ -52,19 +53,21 @@ def test_sparse_lp_values_are_shortest_path_lengths(C):
 
 def test_sparse_spo_plus_matches_oracle(C):
     import torch
-    from paper_2412_09734_gb300.autograd import SparseLPValues, SPOPlusLossSparse
+    from paper_2412_09734_gb300.autograd import (SparseFeasibleSet, SparseLPValues,
+                                                 SPOPlusLossSparse)
     g = grid_shortest_path_lp(8, B=4, seed=instance_seed(42))
+    fs = SparseFeasibleSet(g, g["B"])
     rng = np.random.default_rng(5)
     Ct = torch.from_numpy(g["C"]).cuda()
     with torch.no_grad():
-        zt = SparseLPValues.apply(Ct, g, OPTS)
+        zt = SparseLPValues.apply(Ct, fs, OPTS)
     # the true optimal flows (GPU), for the GPU loss
     Ctg = Ct.clone().requires_grad_(True)
-    SparseLPValues.apply(Ctg, g, OPTS).sum().backward()
+    SparseLPValues.apply(Ctg, fs, OPTS).sum().backward()
     Xt = Ctg.grad.detach()
     Ch_np = g["C"] + rng.normal(0, 0.3, g["C"].shape)
     Ch = torch.from_numpy(Ch_np).cuda().requires_grad_(True)
-    loss = SPOPlusLossSparse.apply(Ch, Ct, Xt, zt, g, OPTS)
+    loss = SPOPlusLossSparse.apply(Ch, Ct, Xt, zt, fs, OPTS)
     loss.sum().backward()
     G = Ch.grad.cpu().numpy()
     Lg = loss.detach().cpu().numpy()
@@ -79,3 +82,63 @@ def test_sparse_spo_plus_matches_oracle(C):
             delta = rng.normal(0, 0.1, g["n"])
             l2 = spo.spo_plus(p, Ch_np[b] + delta, ref.x, ref.kkt["primal_obj"], oo)[0]
             assert l2 >= lo + G[b] @ delta - 1e-3 * (1 + abs(lo))
+
+
+def test_spo_plus_layers_stay_on_the_device(C, monkeypatch):
+    """SPO+ forward and backward with CUDA tensors move no tensor to the host: the
+    costs 2 c^ - c, the solve, the losses and the subgradients are formed in the
+    library on device pointers, and every tensor-to-host conversion is disabled
+    while the layers run."""
+    import torch
+    from paper_2412_09734_gb300.autograd import (SparseFeasibleSet, SparseLPValues,
+                                                 SPOPlusLossSparse)
+    g = grid_shortest_path_lp(6, B=3, seed=instance_seed(43))
+    fs = SparseFeasibleSet(g, g["B"])
+    Ct = torch.from_numpy(g["C"]).cuda()
+    Ch = (Ct + 0.2 * torch.randn_like(Ct)).requires_grad_(True)
+
+    def no_host(*a, **k):
+        raise AssertionError("a tensor was copied to the host")
+
+    with monkeypatch.context() as mp:
+        for name in ("cpu", "numpy", "item", "tolist"):
+            mp.setattr(torch.Tensor, name, no_host)
+        Ctg = Ct.clone().requires_grad_(True)
+        zt = SparseLPValues.apply(Ctg, fs, OPTS)
+        zt.sum().backward()
+        Xt = Ctg.grad.detach()
+        loss = SPOPlusLossSparse.apply(Ch, Ct, Xt, zt.detach(), fs, OPTS)
+        loss.sum().backward()
+        assert loss.is_cuda and Ch.grad.is_cuda and Xt.is_cuda
+    # the loss of the true costs is zero (x~ = x* when c^ = c)
+    with torch.no_grad():
+        l0 = SPOPlusLossSparse.apply(Ct, Ct, Xt, zt.detach(), fs, OPTS)
+    assert float(l0.abs().max()) <= 1e-5 * (1 + float(zt.abs().max()))
+
+
+def test_replicated_batch_equals_packed_copies(C):
+    """B copies built on the device (mpax_lp_batch_create_replicated) are the
+    block-diagonal batch that B host-packed copies give: identical solves in FP64."""
+    g = grid_shortest_path_lp(6, B=3, seed=instance_seed(44))
+    B, m, n = g["B"], g["m"], g["n"]
+    nnz = int(g["row_ptr"][-1])
+    rp = np.concatenate([[0], (g["row_ptr"][1:][None, :] + nnz * np.arange(B)[:, None]).ravel()])
+    tile = lambda a: np.tile(a, B)  # noqa: E731
+    opts = C.mpax_options_default(eps_abs=1e-8, eps_rel=1e-8, iteration_limit=10**6)
+    res = []
+    hp = C.mpax_lp_batch_create(B, np.arange(B + 1) * m, np.arange(B + 1) * n, rp,
+                                tile(g["col"]), tile(g["val"]), g["C"].ravel(), tile(g["lc"]),
+                                tile(g["uc"]), tile(g["l"]), tile(g["u"]))
+    hr = C.mpax_lp_batch_create_replicated(B, m, n, g["row_ptr"], g["col"], g["val"], g["lc"],
+                                           g["uc"], g["l"], g["u"])
+    try:
+        C.mpax_batch_set_costs(hr, g["C"].ravel())
+        for h in (hp, hr):
+            C.mpax_batch_solve(h, opts)
+            res.append(C.mpax_batch_get_solution(h, B * m, B * n)
+                       + (C.mpax_batch_get_objective(h, B),))
+    finally:
+        C.mpax_batch_destroy(hp)
+        C.mpax_batch_destroy(hr)
+    for a, b in zip(res[0], res[1]):
+        np.testing.assert_array_equal(a, b)

@@ -383,3 +383,34 @@ def test_restart_rule_and_primal_weight_update_by_hand():
     # omega <- exp(0.5 log(dy/dx) + 0.5 log omega): the geometric mean of dy/dx and omega
     assert O._update_weight(2.0, 1.0, 8.0, o) == pytest.approx(4.0, rel=1e-15)
     assert O._update_weight(2.0, 0.0, 8.0, o) == 2.0  # a zero move keeps omega
+
+
+@pytest.mark.parametrize("kind", ["bernoulli", "zipf", "empty_rows_cols", "qp_diag"])
+def test_pock_chambolle_bound_against_svd(kind):
+    """After the Pock-Chambolle round (alpha = 1) the scaled matrix has
+    ||A~||_2 <= 1 (Schur's test with weights sqrt(r_i), sqrt(c_j)); the batch path
+    uses that bound in place of the power iteration (power_max_iter = 0).  Pinned
+    against the exact 2-norm (SVD), for LPs and for a QP whose scaled diagonal
+    Q~_jj joins the column sums (which only enlarges c_j)."""
+    rng = np.random.default_rng({"bernoulli": 1, "zipf": 2, "empty_rows_cols": 3,
+                                 "qp_diag": 4}[kind])
+    m, n = 150, 260
+    if kind == "zipf":
+        d = lp_instance(m, n, seed=instance_seed(77), nnz=3000, rows="zipf")
+        A = sp.csr_matrix((d["val"], d["col"], d["row_ptr"]), shape=(m, n))
+    else:
+        A = sp.random(m, n, density=0.03, random_state=rng, format="csr",
+                      data_rvs=lambda k: rng.standard_normal(k))
+        if kind == "empty_rows_cols":
+            A = sp.lil_matrix(A)
+            A[:7, :] = 0.0
+            A[:, :11] = 0.0
+            A = sp.csr_matrix(A)
+            A.eliminate_zeros()
+    qd = rng.uniform(0.1, 1.0, size=n) if kind == "qp_diag" else None
+    for ruiz in (0, 10):
+        Dr, Dc = O.scaling_factors(A, ruiz, True, qd)
+        At = (sp.diags(Dr) @ A @ sp.diags(Dc)).toarray()
+        nrm = np.linalg.norm(At, 2)
+        assert nrm <= 1.0 + 1e-12, (ruiz, nrm)
+        assert nrm >= 0.3  # the bound is not vacuous on these matrices

@@ -64,7 +64,11 @@ def test_noalloc_kkt_matches_handle_kkt_twice(C):
         for seed in (1, 2):  # two calls in a row share the static scratch
             rng = np.random.default_rng(seed)
             x = np.clip(rng.standard_normal(d["n"]) * 4, d["l"], d["u"])
+            # y sign-consistent with the row bounds (<= 0 where lc = -inf, >= 0
+            # where uc = +inf), the points the solver returns
             y = rng.standard_normal(d["m"]) * seed
+            y = np.where(np.isinf(d["uc"]), np.abs(y), y)
+            y = np.where(np.isinf(d["lc"]), -np.abs(y), y)
             ref = C.mpax_kkt(h, x, y)
             got = _noalloc(C, d, dev, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
             scale = 1 + abs(ref["primal_obj"]) + abs(ref["dual_obj"])
