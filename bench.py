@@ -437,7 +437,7 @@ def run_ours(args):
     # the fused SpMVs: CUDA-event times of every launch in one profiled solve,
     # mixed precision (the headline kernel) and FP64 (the plain path's)
     pk, pk_src = peaks()
-    kname = {0: "spmv_fused", 1: "spmv_pipe"}
+    kname = {0: "spmv_fused", 1: "spmv_pipe", 2: "spmv_fused(wide)"}
     names = ["primal", "dual"]
     spmv = {}
     for prec, pname in ((C.MPAX_PREC_MIXED, "mixed"), (C.MPAX_PREC_FP64, "fp64")):
@@ -455,8 +455,8 @@ def run_ours(args):
                 "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": alg,
                 "achieved": alg / avg_s / 1e9, "frac": alg / avg_s / 1e9 / pk,
                 "launches": ps["profile_launches"][idx],
-                "autotuner_us": {"A": list(ps["spmv_tune_us"][:2]),
-                                 "A^T": list(ps["spmv_tune_us"][2:])}}
+                "autotuner_us": {"A": list(ps["spmv_tune_us"][:3]),
+                                 "A^T": list(ps["spmv_tune_us"][3:])}}
     mixed_ms = {w: spmv[f"mixed/{w}"]["avg_launch_us"] * spmv[f"mixed/{w}"]["launches"]
                 for w in names}
     which = max(names, key=lambda w: mixed_ms[w])
@@ -577,12 +577,35 @@ def run_subworkloads(args):
     return out
 
 
+def run_profile_umma():
+    """ncu target of the tensor-core product: two BF16x3 products of the shared
+    batch's shapes at half of its rows and columns (A 8192 x 16384, 512
+    instances; the BF16 operands, 512 MB, exceed L2), the dual (K-major A) then
+    the primal (MN-major A), one launch each after one warm-up launch each."""
+    import torch
+    torch.cuda.init()
+    from paper_2412_09734_gb300 import mpax as C
+    g = torch.Generator(device="cuda").manual_seed(5)
+    m, n, B = 8192, 16384, 512
+    A = torch.randn(m, n, device="cuda", generator=g) / n ** 0.5
+    X = torch.rand(B, n, device="cuda", generator=g)
+    Y = torch.randn(B, m, device="cuda", generator=g)
+    for _ in range(2):
+        C.mpax_dense_bf16x3(A, X)                  # S = A X   (M = m, K = n)
+        C.mpax_dense_bf16x3(A, Y, a_mn_major=True)  # T = A^T Y (M = n, K = m)
+    torch.cuda.synchronize()
+    print(json.dumps({"products": 4, "flops_each": 3 * 2 * m * n * B}))
+    return 0
+
+
 def run_profile_target(args):
     """Short solves of the bench workload for an ncu capture: 128 iterations in
     mixed precision, then 128 in FP64 (two check blocks each)."""
     import torch
     torch.cuda.init()
     from paper_2412_09734_gb300 import mpax as C
+    if args.workload == "shared_dense_512":
+        return run_profile_umma()
     d, _ = workload(args.workload)
     m, n, _ = WORKLOADS[args.workload]
     keys = ("row_ptr", "col", "val", "c", "lc", "uc", "l", "u")
@@ -984,6 +1007,8 @@ def main():
     single = {"next_rows_20k": run_next_rows, "ragged_lp_4096": run_batch,
               "shared_dense_512": run_shared, "qp_200k": run_qp,
               "knapsack_1000x100000": run_knapsack}
+    if args.profile_run:
+        return run_profile_target(args)
     if args.workload in single:
         print(json.dumps(single[args.workload](args)), flush=True)
         return 0

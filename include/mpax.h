@@ -140,14 +140,16 @@ typedef struct mpax_options {
                                  records stay in device memory until the next
                                  mpax_solve or mpax_destroy. */
   int32_t spmv_kernel;        /* -1: autotuned.  Kernel of the A and A^T products of
-                                 the iteration: 0 one warp per work item, 1 persistent
-                                 warps with TMA-staged matrix rows.  Both compute
-                                 every product and sum in the same order, so results
-                                 are identical bit for bit; -1 times both on the
+                                 the iteration: 0 one warp per work item (at least
+                                 20 CTAs of 2 warps per SM), 1 persistent warps with
+                                 TMA-staged matrix rows, 2 as 0 with a register
+                                 budget for 10 CTAs per SM.  All compute every
+                                 product and sum in the same order, so results are
+                                 identical bit for bit; -1 times each on the
                                  problem's own matrices at the first prepare (five
-                                 launches each) and keeps the faster, cached for the
-                                 process by matrix signature (rows, columns, nnz,
-                                 precision, histogram of log2 row lengths) */
+                                 launches each) and keeps the fastest, cached for
+                                 the process by matrix signature (rows, columns,
+                                 nnz, precision, histogram of log2 row lengths) */
 } mpax_options;
 
 typedef struct mpax_stats {
@@ -171,8 +173,8 @@ typedef struct mpax_stats {
   int64_t polish_iterations;         /* iterations of the two feasibility-polishing runs */
   int64_t backward_launches;         /* library kernels of the last mpax_qp_unrolled_grad */
   int32_t spmv_kernel[2];            /* kernel (mpax_options.spmv_kernel) of A, A^T */
-  double spmv_tune_us[4];            /* autotuner timings of the last prepare that timed:
-                                        A kind 0, A kind 1, A^T kind 0, A^T kind 1
+  double spmv_tune_us[6];            /* autotuner timings of the last prepare that timed:
+                                        A kinds 0, 1, 2, then A^T kinds 0, 1, 2
                                         (microseconds per launch; 0 = not timed) */
 } mpax_stats;
 

@@ -407,7 +407,7 @@ mpax_status check_options(const mpax_options* o) {
   if (o->fp64_continuation && o->stall_checks < 1)
     return fail(MPAX_ERR_INVALID_ARGUMENT, "stall_checks must be >= 1");
   if (o->spmv_kernel < -1 || o->spmv_kernel >= kSpmvKinds)
-    return fail(MPAX_ERR_INVALID_ARGUMENT, "spmv_kernel must be -1, 0 or 1");
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "spmv_kernel must be -1, 0, 1 or 2");
   if (o->record_tape && o->precision != MPAX_PREC_FP64)
     return fail(MPAX_ERR_UNSUPPORTED, "record_tape needs precision FP64");
   return MPAX_OK;

@@ -88,12 +88,15 @@ struct Sched {
   void* carry = nullptr;   // per-item partial row sums of sliced rows (8 bytes each)
   double* part = nullptr;  // kPartQ * n_items FP64 partials
   // Kernel that runs the items: 0 = spmv_fused (one warp per item), 1 =
-  // spmv_pipe (persistent warps, TMA-staged matrix).  Both give identical bits;
-  // the choice is the autotuner's (or the caller's).
+  // spmv_pipe (persistent warps, TMA-staged matrix), 2 = spmv_fused with more
+  // registers per thread.  All give identical bits; the choice is the
+  // autotuner's (or the caller's).
   int kind = 0;
 };
-// Kernel kinds of a schedule.
-constexpr int kSpmvItem = 0, kSpmvPipe = 1, kSpmvKinds = 2;
+// Kernel kinds of a schedule: spmv_fused with the default launch shape, spmv_pipe,
+// spmv_fused with the wide register budget (kSpmvWideMinB CTAs per SM).
+constexpr int kSpmvItem = 0, kSpmvPipe = 1, kSpmvItemWide = 2, kSpmvKinds = 3;
+constexpr int kSpmvWideMinB = 10;
 
 struct Csr {
   int rows = 0, cols = 0, nnz = 0;

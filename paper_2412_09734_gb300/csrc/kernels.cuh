@@ -100,8 +100,11 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"(size) : "memory");
 }
 
-template <typename T, class In, class Epi>
-__global__ void MPAX_SPMV_BOUNDS spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
+// MINB: resident CTAs per SM asked of the register allocator (the default
+// shape's MPAX_SPMV_MINB, or kSpmvWideMinB: more registers per thread, fewer
+// warps; the FP64 instances of the default shape spill at its 48-register cap).
+template <typename T, class In, class Epi, int MINB = MPAX_SPMV_MINB>
+__global__ void __launch_bounds__(kSpmvBlock, MINB) spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
   __shared__ T sbuf[kSpmvWarps][kShortCap];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;

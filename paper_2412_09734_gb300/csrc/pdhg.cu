@@ -523,16 +523,16 @@ __global__ void k_kkt_finalize(const double* __restrict__ partAt, int nAt,
 // launch helper
 // ---------------------------------------------------------------------------
 
-// Warps of spmv_fused<T, In, Epi> resident on the whole GPU (one wave).
-template <typename T, class In, class Epi>
+// Warps of spmv_fused<T, In, Epi, MINB> resident on the whole GPU (one wave).
+template <typename T, class In, class Epi, int MINB>
 int resident_warps() {
   static int w = -1;
   if (w < 0) {
     int blocks = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, spmv_fused<T, In, Epi>, kSpmvBlock,
-                                                  0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, spmv_fused<T, In, Epi, MINB>,
+                                                  kSpmvBlock, 0);
     w = std::max(1, blocks) * sms * kSpmvWarps;
   }
   return w;
@@ -591,7 +591,10 @@ void launch_spmv(const Sched& sc, const Csr& K, const T* val, In in, Epi epi, in
   SpmvArgs<T> a;
   a.items = sc.items;
   a.n_items = sc.n_items;
-  a.pf_dist = MPAX_SPMV_PREFETCH ? resident_warps<T, In, Epi>() : 0;
+  const bool wide = sc.kind == kSpmvItemWide;
+  a.pf_dist = !MPAX_SPMV_PREFETCH ? 0
+              : wide ? resident_warps<T, In, Epi, kSpmvWideMinB>()
+                     : resident_warps<T, In, Epi, MPAX_SPMV_MINB>();
   a.rp = K.rp;
   a.col = K.col;
   a.val = val;
@@ -600,6 +603,10 @@ void launch_spmv(const Sched& sc, const Csr& K, const T* val, In in, Epi epi, in
   a.part = sc.part;
   a.q0 = q0;
   const int grid = (sc.n_items + kSpmvWarps - 1) / kSpmvWarps;
+  if (wide) {
+    spmv_fused<T, In, Epi, kSpmvWideMinB><<<grid, kSpmvBlock, 0, s>>>(a, in, epi);
+    return;
+  }
 #if MPAX_SPMV_PDL
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
@@ -883,9 +890,6 @@ class Engine final : public EngineBase {
     cudaStream_t s = P.s;
     Sched* sc[2] = {&P.schedA, &P.schedAt};
     const Csr* K[2] = {&P.A, &P.At};
-    const T* val[2] = {valA_, valAt_};
-    T* out[2] = {pw_, pg_};     // m and n entries (scratch of the power iteration)
-    const T* in[2] = {xbar_, y_};  // n and m entries
     for (double& u : tune_us_) u = 0.0;
     for (int q = 0; q < 2; ++q) {
       int kind = kSpmvItem;
@@ -895,15 +899,16 @@ class Engine final : public EngineBase {
         TuneKey key;
         cudaError_t e = tune_key(*K[q], sc[q]->n_items, sizeof(T), P.tmp_rows, s, &key);
         if (e) return e;
+        key.v[4] += P.is_qp ? 100 : 0;  // the iteration's epilogues differ
         if (!tune_lookup(key, &kind)) {
-          EpiStore<T> es{nullptr, out[q], nullptr, nullptr, nullptr, nullptr, 0};
+          // a previous solve may have left `done` set, which makes every epilogue
+          // skip its work; init_state clears the state again after tuning
+          if ((e = cudaMemsetAsync(st_, 0, sizeof(DevState), s))) return e;
           double best = INFINITY;
           for (int k = 0; k < kSpmvKinds; ++k) {
             sc[q]->kind = k;
             double us = 0.0;
-            e = time_launches(s, kTuneReps, &us, [&]() {
-              launch_spmv<T>(*sc[q], *K[q], val[q], InPlain<T>{in[q]}, es, 0, s);
-            });
+            e = time_launches(s, kTuneReps, &us, [&]() { tune_launch(q); });
             if (e) return e;
             *launches += kTuneReps + 1;
             if (k == kSpmvPipe) {
@@ -918,7 +923,7 @@ class Engine final : public EngineBase {
                 us = INFINITY;
               }
             }
-            tune_us_[2 * q + k] = us;
+            tune_us_[kSpmvKinds * q + k] = us;
             if (us < best) {
               best = us;
               kind = k;
@@ -947,6 +952,32 @@ class Engine final : public EngineBase {
       if (h) return cudaErrorTimeout;
     }
     return cudaSuccess;
+  }
+
+  // One launch of the iteration's half-step on schedule q (0: A, the dual step;
+  // 1: A^T, the primal step) with its own epilogue, on the engine's iterate
+  // buffers: tuning runs before the iterate is initialised, so what these
+  // launches write is overwritten before the solve reads it.
+  void tune_launch(int q) {
+    ProblemData& P = *P_;
+    cudaStream_t s = P.s;
+    if (!P.is_qp) {
+      if (q == 0) {
+        EpiDualLP<T> ed{st_, y_, ya_, lc_, uc_, yhat_, yprev_, 0, 0, 0};
+        launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{xbar_}, ed, 0, s);
+      } else {
+        EpiPrimalLP<T> ep{st_, xbar_, xbar_, xa_, c_, l_, u_, nullptr, xhat_, xprev_, 0, 0, 0};
+        launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{y_}, ep, 0, s);
+      }
+    } else if (q == 0) {
+      EpiDualQP<T> ed{st_, y_, yavg_, yanc_, lc_, uc_, 0, 0};
+      launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{xref_}, ed, 0, s);
+    } else {
+      EpiPrimalQP<T> ep{st_, x_,  xavg_,   xref_,    xanc_, c_,    l_,     u_, Ds_, P.F.rp,
+                        P.F.col, fval_, uvec_, xprev_, 0,   0,   0,  nullptr, nullptr,
+                        P.q_general ? qvec_ : nullptr};
+      launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{y_}, ep, 0, s);
+    }
   }
 
   void tune_info(int* kind, double* us) const override {

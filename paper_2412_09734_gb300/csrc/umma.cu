@@ -96,7 +96,7 @@ cudaError_t umma_plan(UmmaPlan* p, const __nv_bfloat16* Ahi, const __nv_bfloat16
   if ((e = make_map(&p->vh, Vhi, K, N, ldv, bn))) return e;
   if ((e = make_map(&p->vl, Vlo, K, N, ldv, bn))) return e;
   p->args = UmmaArgs{M, N, K, a_mn_major, bn, D, ldd, err};
-  p->grid = dim3((unsigned)((M + kUmmaBM - 1) / kUmmaBM), (unsigned)((N + bn - 1) / bn));
+  p->grid = dim3((unsigned)((N + bn - 1) / bn), (unsigned)((M + kUmmaBM - 1) / kUmmaBM));
   p->flops = 3.0 * 2.0 * (double)M * N * K;
   return cudaSuccess;
 }

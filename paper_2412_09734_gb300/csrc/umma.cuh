@@ -111,7 +111,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   unsigned long long* accf = empty + kUmmaStages;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kUmmaBM, n0 = blockIdx.y * g.bn;
+  // instance tiles vary fastest: the CTAs that share an A tile run together, so
+  // all but the first read it from L2 (A is larger than L2 and streams from HBM)
+  const int m0 = blockIdx.y * kUmmaBM, n0 = blockIdx.x * g.bn;
   const int KB = (g.K + kUmmaBK - 1) / kUmmaBK;
   const uint32_t ncols = (uint32_t)g.bn;
   if (threadIdx.x == 0) {

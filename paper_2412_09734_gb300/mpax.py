@@ -85,7 +85,7 @@ class Stats(ctypes.Structure):
         ("profile_ms", ctypes.c_double * 4), ("profile_launches", ctypes.c_int64 * 4),
         ("fp64_iterations", ctypes.c_int64), ("polish_iterations", ctypes.c_int64),
         ("backward_launches", ctypes.c_int64),
-        ("spmv_kernel", ctypes.c_int32 * 2), ("spmv_tune_us", ctypes.c_double * 4),
+        ("spmv_kernel", ctypes.c_int32 * 2), ("spmv_tune_us", ctypes.c_double * 6),
     ]
 
     def as_dict(self):
@@ -460,7 +460,7 @@ def mpax_batch_solve(h, opts):
     _check(_lib.mpax_batch_solve(h, ctypes.byref(opts)))
 
 
-def _out(shape, device):
+def _out_buf(shape, device):
     """An FP64 output buffer: a CUDA tensor on `device`'s device when `device` is a
     CUDA tensor, else a numpy array; with its pointer and memory kind."""
     if device is not None and _is_torch(device) and device.is_cuda:
@@ -472,8 +472,8 @@ def _out(shape, device):
 
 
 def mpax_batch_get_solution(h, m_total, n_total, device=None):
-    x, px, kind = _out(n_total, device)
-    y, py, _ = _out(m_total, device)
+    x, px, kind = _out_buf(n_total, device)
+    y, py, _ = _out_buf(m_total, device)
     _check(_lib.mpax_batch_get_solution(h, px, py, kind))
     return x, y
 
@@ -497,7 +497,7 @@ def mpax_batch_set_costs(h, c):
 
 
 def mpax_batch_get_objective(h, B, device=None):
-    v, pv, kind = _out(B, device)
+    v, pv, kind = _out_buf(B, device)
     _check(_lib.mpax_batch_get_objective(h, pv, kind))
     return v
 
@@ -508,8 +508,8 @@ def mpax_batch_spo_plus(h, opts, c_hat, c_true, x_true, z_true):
     k = _Keep(kind)
     B = int(len(z_true)) if not _is_torch(z_true) else int(z_true.numel())
     total = int(np.prod(c_hat.shape))
-    loss, pl, _ = _out(B, c_hat if kind == MPAX_MEM_DEVICE else None)
-    grad, pg, _ = _out(tuple(c_hat.shape), c_hat if kind == MPAX_MEM_DEVICE else None)
+    loss, pl, _ = _out_buf(B, c_hat if kind == MPAX_MEM_DEVICE else None)
+    grad, pg, _ = _out_buf(tuple(c_hat.shape), c_hat if kind == MPAX_MEM_DEVICE else None)
     assert total == (grad.numel() if _is_torch(grad) else grad.size)
     _check(_lib.mpax_batch_spo_plus(h, ctypes.byref(opts), k.ptr(c_hat, np.float64),
                                     k.ptr(c_true, np.float64), k.ptr(x_true, np.float64),
@@ -616,7 +616,7 @@ def mpax_shared_set_costs(h, C):
 
 
 def mpax_shared_get_objective(h, B, device=None):
-    v, pv, kind = _out(B, device)
+    v, pv, kind = _out_buf(B, device)
     _check(_lib.mpax_shared_get_objective(h, pv, kind))
     return v
 
@@ -626,8 +626,8 @@ def mpax_shared_spo_plus(h, opts, C_hat, C_true, X_true, z_true, fp32_products=F
     kind = _kind_of(C_hat)
     k = _Keep(kind)
     B = int(C_hat.shape[0])
-    loss, pl, _ = _out(B, C_hat if kind == MPAX_MEM_DEVICE else None)
-    grad, pg, _ = _out(tuple(C_hat.shape), C_hat if kind == MPAX_MEM_DEVICE else None)
+    loss, pl, _ = _out_buf(B, C_hat if kind == MPAX_MEM_DEVICE else None)
+    grad, pg, _ = _out_buf(tuple(C_hat.shape), C_hat if kind == MPAX_MEM_DEVICE else None)
     _check(_lib.mpax_shared_spo_plus(h, ctypes.byref(opts), 1 if fp32_products else 0,
                                      k.ptr(C_hat, np.float64), k.ptr(C_true, np.float64),
                                      k.ptr(X_true, np.float64), k.ptr(z_true, np.float64),
