@@ -83,12 +83,36 @@ class Clocks:
         self.proc = None
         self.path = None
 
+    def gpu_id(self):
+        """The GPU to sample, named by its UUID (or PCI bus id): with
+        CUDA_VISIBLE_DEVICES set, a CUDA device index is not nvidia-smi's index."""
+        try:
+            import torch
+            props = torch.cuda.get_device_properties(self.index)
+            uuid = getattr(props, "uuid", None)
+            if uuid is not None:
+                u = str(uuid)
+                return u if u.startswith("GPU-") else "GPU-" + u
+            bus = getattr(props, "pci_bus_id", None)
+            dom = getattr(props, "pci_domain_id", 0)
+            dev = getattr(props, "pci_device_id", 0)
+            if bus is not None:
+                return f"{dom:08X}:{bus:02X}:{dev:02X}.0"
+        except Exception:  # no torch or no CUDA: fall back to the visible index
+            pass
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            parts = [v.strip() for v in vis.split(",") if v.strip()]
+            if self.index < len(parts):
+                return parts[self.index]
+        return str(self.index)
+
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                ["nvidia-smi", f"--id={self.gpu_id()}", f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
@@ -138,7 +162,7 @@ def algorithmic_bytes(m, n, nnz, n_items_unused, fp64, which):
 
 def kernel_source_hash():
     h = hashlib.sha1()
-    for f in ("kernels.cuh", "epilogues.cuh", "common.cuh"):
+    for f in ("kernels.cuh", "epilogues.cuh", "common.cuh", "sync.cuh"):
         with open(os.path.join(ROOT, "paper_2412_09734_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -746,9 +770,23 @@ def run_shared(args):
                          obj_rel_err_max=float(np.max(np.abs(per["primal_obj"] - d["opt_value"])
                                                       / (1 + np.abs(d["opt_value"])))),
                          switched_to_fp32_instances=summ["fp64_instances"],
+                         product_tile_k=summ.get("product_tile_k"),
                          clocks=clk, gpu_launches=summ["kernel_launches"])
+    # the products on their own: CUDA events around every iteration product of a
+    # short profiled solve (192 iterations)
+    h = C.mpax_lp_shared_create(m, n, B, dev["A"], dev["C"], dev["b"], dev["b"], dev["l"],
+                                dev["u"])
+    C.mpax_shared_solve(h, C.mpax_options_default(profile_kernels=1, iteration_limit=192),
+                        False)
+    summ_p, _ = C.mpax_shared_get_stats(h, B)
+    C.mpax_shared_destroy(h)
+    flops_each = 3 * 2.0 * m * n * B
+    prod = {}
+    for name, ms in zip(("dual A~X", "primal A~^T Y"), summ_p["product_ms"]):
+        prod[name] = {"avg_launch_ms": ms, "tflops": flops_each / (ms / 1e3) / 1e12 if ms else None}
     pk, src = bf16_peak()
     a = out["bf16x3"]["tensor_tflops_over_solve"]
+    slow = max(prod, key=lambda k: prod[k]["avg_launch_ms"])
     line = {"metric": "shared-matrix dense LP batch solves/s to rel KKT 1e-4",
             "value": out["bf16x3"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
@@ -757,10 +795,16 @@ def run_shared(args):
             "config": {"workload": f"dense A {m}x{n} FP32 N(0,1/n), box [0,1], equality rows, "
                                    f"{B} cost vectors (half of x0 at bounds), rel KKT 1e-4",
                        "l2": "A is 2.1 GB FP32 / 2 x 1.1 GB BF16, larger than L2"},
-            "roofline": {"bound": "tensor", "achieved": a, "peak": pk, "unit": "TFLOP/s",
-                         "frac": a / pk, "traffic": None,
-                         "note": "BF16 GEMM flops executed (3 per BF16x3 product) over the whole "
-                                 "solve time, so a lower bound on the GEMMs' own rate",
+            "roofline": {"bound": "tensor", "achieved": prod[slow]["tflops"], "peak": pk,
+                         "unit": "TFLOP/s", "frac": prod[slow]["tflops"] / pk, "traffic": None,
+                         "kernel": f"umma_bf16x3 ({slow}, tile_k "
+                                   f"{summ_p['product_tile_k'][0 if slow.startswith('dual') else 1]})",
+                         "algorithmic_flops_per_launch": flops_each,
+                         "avg_launch_ms": prod[slow]["avg_launch_ms"],
+                         "products": prod,
+                         "over_the_solve": {"achieved": a, "frac": a / pk,
+                                            "note": "BF16 flops of every product over the whole "
+                                                    "solve time (update kernels included)"},
                          "peak_source": src + ", of measured"},
             "bf16x3": out["bf16x3"], "fp32": out.get("fp32"),
             "speedup_vs_fp32_products": (out["fp32"]["ms_per_batch"] / out["bf16x3"]["ms_per_batch"]

@@ -475,8 +475,13 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* opts, int32_t
 mpax_status mpax_shared_get_solution(const mpax_shared* sh, double* X, double* Y,
                                      mpax_mem_kind kind);
 /* As mpax_batch_get_stats (seconds = host time from solve start to the check at
- * which the instance finished); gemm_info (HOST, 3 doubles, nullable) receives
- * the GEMM count, their flops, and ||A~||_2. */
+ * which the instance finished); gemm_info (HOST, 7 doubles, nullable) receives
+ * the count of product launches, their flops, ||A~||_2, the K block (64 or 32)
+ * of the dual and the primal product's pipeline (each direction's shape is
+ * chosen by timing both on the first solve of each (m, n, B) in the process),
+ * and, when the solve ran with profile_kernels = 1, the average milliseconds of
+ * one iteration product launch, dual (A~ X) then primal (A~^T Y), from CUDA
+ * events on the solve's stream (0 otherwise). */
 mpax_status mpax_shared_get_stats(const mpax_shared* sh, mpax_batch_stats* stats,
                                   int32_t* status, int64_t* iterations, double* rel_kkt,
                                   double* primal_obj, double* seconds, double* gemm_info);
@@ -505,14 +510,16 @@ mpax_status mpax_shared_spo_plus(mpax_shared* sh, const mpax_options* opts,
  * and D = A_hi V_lo + A_lo V_hi + A_hi V_hi is formed on the tensor cores
  * (tcgen05, FP32 accumulation), the kernel the shared batch uses.  Its error
  * against the exact product is at most (3 * 2^-18 + (3K + 2) * 2^-24) *
- * sum_k |A_op,mk| |V_nk| per entry.  D is [N][M] (row n = instance n).  All
- * pointers in `kind` memory; the call allocates its BF16 operand copies and
- * returns when D is written.  Errors: MPAX_ERR_INVALID_ARGUMENT,
- * MPAX_ERR_OUT_OF_MEMORY, MPAX_ERR_CUDA, MPAX_ERR_DEVICE_TIMEOUT (a bounded wait
- * of the kernel gave up). */
+ * sum_k |A_op,mk| |V_nk| per entry.  D is [N][M] (row n = instance n).
+ * tile_k: K block of the kernel's pipeline, 64 (two stages) or 32 (four
+ * stages); 0 = 32.  Both give the same sums in the same order.  All pointers in
+ * `kind` memory; the call allocates its BF16 operand copies and returns when D
+ * is written.  Errors: MPAX_ERR_INVALID_ARGUMENT, MPAX_ERR_OUT_OF_MEMORY,
+ * MPAX_ERR_CUDA, MPAX_ERR_DEVICE_TIMEOUT (a bounded wait of the kernel gave
+ * up). */
 mpax_status mpax_dense_bf16x3(int32_t M, int32_t N, int32_t K, int32_t a_mn_major,
-                              const float* A, const float* V, float* D, mpax_mem_kind kind,
-                              void* cuda_stream);
+                              int32_t tile_k, const float* A, const float* V, float* D,
+                              mpax_mem_kind kind, void* cuda_stream);
 
 /* ---- Evaluation without device allocation --------------------------------- */
 

@@ -28,7 +28,10 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/mpax.h"
@@ -562,6 +565,16 @@ struct mpax_shared {
   long long n8 = 0, m8 = 0;
   UmmaPlan plan_dual, plan_primal;  // S = A~ X (K = n), T = A~^T Y (K = m)
   int* uerr = nullptr;              // set by a bounded wait of the product kernel
+  float shape_ms[2][2] = {{0, 0}, {0, 0}};  // tuner: [dual, primal][K block 64, 32] ms
+  // profile_kernels: event pairs of the iteration products and their sums
+  struct ProdEvent {
+    cudaEvent_t e0, e1;
+    int trans;
+  };
+  bool profiling = false;
+  std::vector<ProdEvent> prof_events;
+  double prof_ms[2] = {0, 0};  // [primal (A~^T Y), dual (A~ X)]
+  long long prof_n[2] = {0, 0};
   int gemv_chunks = 1, gemv_nchunks = 1;
   long long gemv_launches = 0;
 };
@@ -819,9 +832,42 @@ void gemv_part(mpax_shared* sh, int trans, const float* vf, const float* Mf) {
 // C (rows x B, col-major) = op(M) V, M the stored column-major n x m matrix
 // (A row-major).  trans = 1: C = M^T V (= A V, rows = m, K = n); trans = 0:
 // C = M V (= A^T V, rows = n, K = m).  BF16x3 or FP32.
+cudaError_t product_impl(mpax_shared* sh, int trans, const __nv_bfloat16* vhi,
+                         const __nv_bfloat16* vlo, const float* vf, float* C, bool bf16x3,
+                         const float* Mf);
+
+// With profile_kernels set, every iteration product is bracketed by CUDA events
+// on the solve's stream; the host sums the times after each check block.
 cudaError_t product(mpax_shared* sh, int trans, const __nv_bfloat16* vhi,
-                       const __nv_bfloat16* vlo, const float* vf, float* C, bool bf16x3,
-                       const float* Mf) {
+                    const __nv_bfloat16* vlo, const float* vf, float* C, bool bf16x3,
+                    const float* Mf) {
+  if (!sh->profiling) return product_impl(sh, trans, vhi, vlo, vf, C, bf16x3, Mf);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, sh->s);
+  const cudaError_t e = product_impl(sh, trans, vhi, vlo, vf, C, bf16x3, Mf);
+  cudaEventRecord(e1, sh->s);
+  sh->prof_events.push_back({e0, e1, trans});
+  return e;
+}
+
+void collect_product_times(mpax_shared* sh) {
+  for (const auto& pe : sh->prof_events) {
+    float ms = 0.f;
+    cudaEventSynchronize(pe.e1);
+    cudaEventElapsedTime(&ms, pe.e0, pe.e1);
+    sh->prof_ms[pe.trans] += ms;
+    sh->prof_n[pe.trans] += 1;
+    cudaEventDestroy(pe.e0);
+    cudaEventDestroy(pe.e1);
+  }
+  sh->prof_events.clear();
+}
+
+cudaError_t product_impl(mpax_shared* sh, int trans, const __nv_bfloat16* vhi,
+                         const __nv_bfloat16* vlo, const float* vf, float* C, bool bf16x3,
+                         const float* Mf) {
   const int m = sh->m, n = sh->n, B = sh->B;
   const int rows = trans ? m : n, K = trans ? n : m;
   if (!bf16x3 && B == 1) {
@@ -850,6 +896,71 @@ cudaError_t product(mpax_shared* sh, int trans, const __nv_bfloat16* vhi,
   sh->gemms += 1;
   sh->gemm_flops += p.flops;
   return e;
+}
+
+// The two products' plans.  Their pipeline shape (K block 64 with two stages,
+// or 32 with four; the same sums in the same order) is chosen per direction by
+// timing both on this solve's own buffers, once per (m, n, B) for the process.
+std::mutex& shape_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+std::map<std::tuple<int, int, int>, std::pair<int, int>>& shape_cache() {
+  static std::map<std::tuple<int, int, int>, std::pair<int, int>> c;
+  return c;
+}
+
+cudaError_t plan_products(mpax_shared* sh, bool tune) {
+  const int m = sh->m, n = sh->n, B = sh->B;
+  auto make = [&](UmmaPlan* p, int dir, int bk) {
+    return dir == 0 ? umma_plan(p, sh->Ahi, sh->Alo, sh->n8, 0, sh->xh_hi, sh->xh_lo, sh->n8, m,
+                                B, n, sh->S, m, sh->uerr, bk)
+                    : umma_plan(p, sh->Ahi, sh->Alo, sh->n8, 1, sh->y_hi, sh->y_lo, sh->m8, n,
+                                B, m, sh->T, n, sh->uerr, bk);
+  };
+  const auto key = std::make_tuple(m, n, B);
+  std::pair<int, int> bk(32, 32);
+  bool have;
+  {
+    std::lock_guard<std::mutex> g(shape_mutex());
+    auto it = shape_cache().find(key);
+    have = it != shape_cache().end();
+    if (have) bk = it->second;
+  }
+  cudaError_t e;
+  if (!have && tune) {
+    // the products write S and T, scratch until the iteration starts
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best[2] = {32, 32};
+    for (int dir = 0; dir < 2; ++dir) {
+      float tbest = INFINITY;
+      for (int cand : {64, 32}) {
+        UmmaPlan p;
+        if ((e = make(&p, dir, cand))) return e;
+        if ((e = umma_run(p, sh->s))) return e;
+        cudaEventRecord(e0, sh->s);
+        for (int r = 0; r < 2; ++r) umma_run(p, sh->s);
+        cudaEventRecord(e1, sh->s);
+        if ((e = cudaEventSynchronize(e1))) return e;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        sh->shape_ms[dir][cand == 64 ? 0 : 1] = ms / 2;
+        if (ms < tbest) {
+          tbest = ms;
+          best[dir] = cand;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bk = std::make_pair(best[0], best[1]);
+    std::lock_guard<std::mutex> g(shape_mutex());
+    shape_cache()[key] = bk;
+  }
+  if ((e = make(&sh->plan_dual, 0, bk.first))) return e;
+  return make(&sh->plan_primal, 1, bk.second);
 }
 
 }  // namespace
@@ -959,6 +1070,9 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
   cudaStreamWaitEvent(s, ev, 0);
   long long L = 0;
   sh->gemms = 0;
+  sh->profiling = o->profile_kernels != 0;
+  sh->prof_ms[0] = sh->prof_ms[1] = 0.0;
+  sh->prof_n[0] = sh->prof_n[1] = 0;
   sh->gemm_flops = 0.0;
   sh->gemv_launches = 0;
   // ---- scaling of the shared matrix (Ruiz, Pock-Chambolle) ----------------------
@@ -988,11 +1102,7 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
   k_scale_dense<<<g1(mn), 256, 0, s>>>(sh->A0, sh->As, m, n, sh->Dr, sh->Dc);
   split_rows(sh->As, m, n, n, sh->Ahi, sh->Alo, sh->n8, s);
   {
-    cudaError_t pe = umma_plan(&sh->plan_dual, sh->Ahi, sh->Alo, sh->n8, 0, sh->xh_hi, sh->xh_lo,
-                               sh->n8, m, B, n, sh->S, m, sh->uerr);
-    if (!pe)
-      pe = umma_plan(&sh->plan_primal, sh->Ahi, sh->Alo, sh->n8, 1, sh->y_hi, sh->y_lo, sh->m8, n,
-                     B, m, sh->T, n, sh->uerr);
+    cudaError_t pe = plan_products(sh, !fp32_products);
     if (pe) {
       cudaEventDestroy(ev);
       return sfail(MPAX_ERR_CUDA, std::string("tensor-core product plan: ") +
@@ -1134,6 +1244,7 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
     L += 8;
     cudaMemcpyAsync(hi.data(), sh->inst, sizeof(Inst) * B, cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
+    if (sh->profiling) collect_product_times(sh);
     int active = 0, stalled = 0;
     for (const Inst& I : hi) {
       active += !I.done;
@@ -1148,6 +1259,7 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
       switch_active = active;
     }
   }
+  if (sh->profiling) collect_product_times(sh);
   cudaError_t e = cudaGetLastError();
   if (!result && e) result = sfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
   {
@@ -1223,6 +1335,10 @@ mpax_status mpax_shared_get_stats(const mpax_shared* sh, mpax_batch_stats* stats
     gemm_info[0] = (double)sh->gemms;
     gemm_info[1] = sh->gemm_flops;
     gemm_info[2] = sh->norm_A;
+    gemm_info[3] = sh->plan_dual.bk;
+    gemm_info[4] = sh->plan_primal.bk;
+    gemm_info[5] = sh->prof_n[1] ? sh->prof_ms[1] / sh->prof_n[1] : 0.0;
+    gemm_info[6] = sh->prof_n[0] ? sh->prof_ms[0] / sh->prof_n[0] : 0.0;
   }
   return MPAX_OK;
 }

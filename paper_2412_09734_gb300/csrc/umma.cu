@@ -36,20 +36,22 @@ EncodeTiled encode_tiled() {
 }
 
 // 2-D BF16 tensor map: inner dimension `inner` (contiguous), `outer` rows of
-// `ld` elements, box {64, box_rows}, 128-byte swizzle, out-of-range reads zero.
+// `ld` elements, box {box_inner, box_rows} (box_inner 64: 128-byte swizzle, 32:
+// 64-byte swizzle), out-of-range reads zero.
 cudaError_t make_map(CUtensorMap* m, const __nv_bfloat16* base, long long inner, long long outer,
-                     long long ld, int box_rows) {
+                     long long ld, int box_inner, int box_rows) {
   EncodeTiled fn = encode_tiled();
   if (!fn) return cudaErrorNotSupported;
   if ((ld * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0)
     return cudaErrorInvalidValue;
   const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
   const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1u, 1u};
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                         const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        box_inner == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -81,36 +83,44 @@ int umma_tile_n(int N) {
 cudaError_t umma_plan(UmmaPlan* p, const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo,
                       long long lda, int a_mn_major, const __nv_bfloat16* Vhi,
                       const __nv_bfloat16* Vlo, long long ldv, int M, int N, int K, float* D,
-                      long long ldd, int* err) {
+                      long long ldd, int* err, int bk) {
   std::memset(p, 0, sizeof(*p));
-  if (M < 1 || N < 1 || K < 1) return cudaErrorInvalidValue;
+  if (M < 1 || N < 1 || K < 1 || (bk != 64 && bk != 32)) return cudaErrorInvalidValue;
   const int bn = umma_tile_n(N);
   cudaError_t e;
   if (!a_mn_major) {
-    if ((e = make_map(&p->ah, Ahi, K, M, lda, kUmmaBM))) return e;
-    if ((e = make_map(&p->al, Alo, K, M, lda, kUmmaBM))) return e;
-  } else {
-    if ((e = make_map(&p->ah, Ahi, M, K, lda, 64))) return e;
-    if ((e = make_map(&p->al, Alo, M, K, lda, 64))) return e;
+    if ((e = make_map(&p->ah, Ahi, K, M, lda, bk, kUmmaBM))) return e;
+    if ((e = make_map(&p->al, Alo, K, M, lda, bk, kUmmaBM))) return e;
+  } else {  // MN-major: 64 rows of M per box (128-byte swizzle), bk rows of K
+    if ((e = make_map(&p->ah, Ahi, M, K, lda, 64, bk))) return e;
+    if ((e = make_map(&p->al, Alo, M, K, lda, 64, bk))) return e;
   }
-  if ((e = make_map(&p->vh, Vhi, K, N, ldv, bn))) return e;
-  if ((e = make_map(&p->vl, Vlo, K, N, ldv, bn))) return e;
+  if ((e = make_map(&p->vh, Vhi, K, N, ldv, bk, bn))) return e;
+  if ((e = make_map(&p->vl, Vlo, K, N, ldv, bk, bn))) return e;
+  p->bk = bk;
   p->args = UmmaArgs{M, N, K, a_mn_major, bn, D, ldd, err};
   p->grid = dim3((unsigned)((N + bn - 1) / bn), (unsigned)((M + kUmmaBM - 1) / kUmmaBM));
   p->flops = 3.0 * 2.0 * (double)M * N * K;
   return cudaSuccess;
 }
 
-cudaError_t umma_run(const UmmaPlan& p, cudaStream_t s) {
+template <int BK>
+cudaError_t umma_launch(const UmmaPlan& p, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(umma_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kUmmaSmem);
+    cudaError_t e = cudaFuncSetAttribute(umma_bf16x3<BK>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         UmmaShape<BK>::kSmem);
     if (e) return e;
     attr = true;
   }
-  umma_bf16x3<<<p.grid, kUmmaThreads, kUmmaSmem, s>>>(p.ah, p.al, p.vh, p.vl, p.args);
+  umma_bf16x3<BK><<<p.grid, kUmmaThreads, UmmaShape<BK>::kSmem, s>>>(p.ah, p.al, p.vh, p.vl,
+                                                                     p.args);
   return cudaGetLastError();
+}
+
+cudaError_t umma_run(const UmmaPlan& p, cudaStream_t s) {
+  return p.bk == 32 ? umma_launch<32>(p, s) : umma_launch<64>(p, s);
 }
 
 cudaError_t split_rows(const float* src, long long rows, long long cols, long long lds,
@@ -129,12 +139,17 @@ using namespace mpax;
 extern "C" {
 
 mpax_status mpax_dense_bf16x3(int32_t M, int32_t N, int32_t K, int32_t a_mn_major,
-                              const float* A, const float* V, float* D, mpax_mem_kind kind,
-                              void* cuda_stream) {
+                              int32_t tile_k, const float* A, const float* V, float* D,
+                              mpax_mem_kind kind, void* cuda_stream) {
   if (M < 1 || N < 1 || K < 1 || !A || !V || !D) {
     set_last_error("M, N, K must be >= 1 and A, V, D non-NULL");
     return MPAX_ERR_INVALID_ARGUMENT;
   }
+  if (tile_k != 0 && tile_k != 32 && tile_k != 64) {
+    set_last_error("tile_k must be 0 (default), 32 or 64");
+    return MPAX_ERR_INVALID_ARGUMENT;
+  }
+  const int bk = tile_k == 64 ? 64 : 32;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const long long arows = a_mn_major ? K : M, acols = a_mn_major ? M : K;
   const long long lda = (acols + 7) / 8 * 8, ldv = ((long long)K + 7) / 8 * 8;
@@ -162,7 +177,7 @@ mpax_status mpax_dense_bf16x3(int32_t M, int32_t N, int32_t K, int32_t a_mn_majo
   if (!e) e = split_rows(Ad, arows, acols, acols, ah, al, lda, s);
   if (!e) e = split_rows(Vd, N, K, K, vh, vl, ldv, s);
   UmmaPlan p;
-  if (!e) e = umma_plan(&p, ah, al, lda, a_mn_major, vh, vl, ldv, M, N, K, Dd, M, err);
+  if (!e) e = umma_plan(&p, ah, al, lda, a_mn_major, vh, vl, ldv, M, N, K, Dd, M, err, bk);
   if (!e) e = umma_run(p, s);
   int herr = 0;
   if (!e) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -12,7 +12,8 @@
 // A~ X of the dual step) or A^T (A stored [K][M], M contiguous: the product A~^T Y
 // of the primal step); the MMA reads the latter as an MN-major operand.
 //
-// CTA: 6 warps.  Warp 0 (one lane) issues the TMA loads of a two-stage pipeline;
+// CTA: 6 warps.  Warp 0 (one lane) issues the TMA loads of a two- or four-stage
+// pipeline (UmmaShape);
 // warp 1 allocates TMEM and (one lane) issues the MMAs, releasing each stage
 // with tcgen05.commit; warps 2-5 read the accumulator (tcgen05.ld, one 32-lane
 // quarter each) and store D.  Every mbarrier wait is bounded; a wait that gives
@@ -31,20 +32,33 @@ namespace mpax {
 
 constexpr int kUmmaBM = 128;      // rows (M) of an output tile: TMEM lanes
 constexpr int kUmmaBNMax = 256;   // instances (N) of an output tile, at most
-constexpr int kUmmaBK = 64;       // K per stage: 128 bytes of BF16, one swizzle row
-constexpr int kUmmaStages = 2;
 constexpr int kUmmaThreads = 192;
-constexpr int kUmmaATile = kUmmaBM * kUmmaBK * 2;     // 16 KB
-constexpr int kUmmaVTile = kUmmaBNMax * kUmmaBK * 2;  // 32 KB
-constexpr int kUmmaStage = 2 * kUmmaATile + 2 * kUmmaVTile;
-constexpr int kUmmaSmem = kUmmaStages * kUmmaStage + 1024 + 128;  // + alignment, barriers
+
+// Two pipeline shapes with the same 192 KB of stages: K blocks of 64 (128-byte
+// rows, 128-byte swizzle) in 2 stages, or K blocks of 32 (64-byte rows of the
+// K-major operands, 64-byte swizzle) in 4 stages, which keeps three stages in
+// flight while the MMAs read the fourth.
+template <int BK>
+struct UmmaShape {
+  static_assert(BK == 64 || BK == 32, "K block of 64 or 32");
+  static constexpr int kStages = BK == 64 ? 2 : 4;
+  static constexpr int kATile = kUmmaBM * BK * 2;     // 16 / 8 KB
+  static constexpr int kVTile = kUmmaBNMax * BK * 2;  // 32 / 16 KB
+  static constexpr int kStage = 2 * kATile + 2 * kVTile;
+  static constexpr int kSmem = kStages * kStage + 1024 + 256;  // + alignment, barriers
+  // K-major operands: rows of BK elements; 8-row atoms of 8 * 2 BK bytes
+  static constexpr uint32_t kKSwizzle = BK == 64 ? 2u : 4u;  // 128- / 64-byte swizzle
+  static constexpr uint32_t kKAtom = 8u * 2u * BK;
+};
 
 // Shared-memory matrix descriptor of a tcgen05 operand: start address, leading-
-// and stride-dimension byte offsets (all >> 4), descriptor version 1, 128-byte
-// swizzle.  Tiles start on 1024-byte boundaries (base offset 0).
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// and stride-dimension byte offsets (all >> 4), descriptor version 1, swizzle
+// mode (2: 128-byte, 4: 64-byte).  Tiles start on 1024-byte boundaries (base
+// offset 0).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo,
+                                              uint32_t swizzle) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)swizzle << 61);
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, A K-major
@@ -97,10 +111,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+template <int BK>
 __global__ void __launch_bounds__(kUmmaThreads, 1)
     umma_bf16x3(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                 const __grid_constant__ CUtensorMap tVh, const __grid_constant__ CUtensorMap tVl,
                 UmmaArgs g) {
+  using S = UmmaShape<BK>;
+  constexpr int kUmmaStages = S::kStages, kUmmaStage = S::kStage;
+  constexpr int kUmmaATile = S::kATile, kUmmaVTile = S::kVTile, kUmmaBK = BK;
   extern __shared__ unsigned char umma_raw[];
   __shared__ int s_fail;
   // the swizzled tiles need 1024-byte alignment in the shared window
@@ -184,18 +202,19 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
         const uint32_t vh = st + 2 * kUmmaATile, vl = vh + kUmmaVTile;
 #pragma unroll
         for (int ks = 0; ks < kUmmaBK / 16; ++ks) {
-          // K = 16 per MMA: 32 bytes along a K-major row; two 8-row atoms (2 KB)
-          // of an MN-major tile, whose two 64-row halves sit 8 KB apart
+          // K = 16 per MMA: 32 bytes along a K-major row (8-row atoms of S::kKAtom
+          // bytes); two 8-row atoms (2 KB) of an MN-major tile (128-byte swizzle),
+          // whose two 64-row halves sit half an A tile apart
           uint64_t dah, dal;
           if (!g.a_mn_major) {
-            dah = umma_desc(ah + 32 * ks, 16, 1024);
-            dal = umma_desc(al + 32 * ks, 16, 1024);
+            dah = umma_desc(ah + 32 * ks, 16, S::kKAtom, S::kKSwizzle);
+            dal = umma_desc(al + 32 * ks, 16, S::kKAtom, S::kKSwizzle);
           } else {
-            dah = umma_desc(ah + 2048 * ks, 8192, 1024);
-            dal = umma_desc(al + 2048 * ks, 8192, 1024);
+            dah = umma_desc(ah + 2048 * ks, kUmmaATile / 2, 1024, 2u);
+            dal = umma_desc(al + 2048 * ks, kUmmaATile / 2, 1024, 2u);
           }
-          const uint64_t dvh = umma_desc(vh + 32 * ks, 16, 1024);
-          const uint64_t dvl = umma_desc(vl + 32 * ks, 16, 1024);
+          const uint64_t dvh = umma_desc(vh + 32 * ks, 16, S::kKAtom, S::kKSwizzle);
+          const uint64_t dvl = umma_desc(vl + 32 * ks, 16, S::kKAtom, S::kKSwizzle);
           umma_mma(tmem, dah, dvl, idesc, (kb | ks) ? 1u : 0u);
           umma_mma(tmem, dal, dvh, idesc, 1u);
           umma_mma(tmem, dah, dvh, idesc, 1u);

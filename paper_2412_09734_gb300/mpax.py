@@ -169,7 +169,7 @@ _sig = {
     "mpax_shared_set_costs": ([_P, _P, _INT], _INT),
     "mpax_shared_get_objective": ([_P, _P, _INT], _INT),
     "mpax_shared_spo_plus": ([_P, ctypes.POINTER(Options), _I32] + [_P] * 6 + [_INT], _INT),
-    "mpax_dense_bf16x3": ([_I32, _I32, _I32, _I32, _P, _P, _P, _INT, _P], _INT),
+    "mpax_dense_bf16x3": ([_I32, _I32, _I32, _I32, _I32, _P, _P, _P, _INT, _P], _INT),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -657,12 +657,14 @@ def mpax_shared_get_stats(h, B):
     kk = np.empty(B)
     po = np.empty(B)
     sec = np.empty(B)
-    gi = np.zeros(3)
+    gi = np.zeros(7)
     _check(_lib.mpax_shared_get_stats(h, ctypes.byref(s), st.ctypes.data, it.ctypes.data,
                                       kk.ctypes.data, po.ctypes.data, sec.ctypes.data,
                                       gi.ctypes.data))
     d = s.as_dict()
-    d.update(gemms=int(gi[0]), gemm_flops=float(gi[1]), norm_A=float(gi[2]))
+    d.update(gemms=int(gi[0]), gemm_flops=float(gi[1]), norm_A=float(gi[2]),
+             product_tile_k=(int(gi[3]), int(gi[4])),
+             product_ms=(float(gi[5]), float(gi[6])))
     return d, dict(status=st, iterations=it, rel_kkt=kk, primal_obj=po, seconds=sec)
 
 
@@ -675,9 +677,10 @@ def mpax_shared_destroy(h):
 # dense products of the shared-matrix batch
 # ---------------------------------------------------------------------------
 
-def mpax_dense_bf16x3(A, V, a_mn_major=False, stream=None):
+def mpax_dense_bf16x3(A, V, a_mn_major=False, tile_k=0, stream=None):
     """D (N x M) = rows of A_op V^T on the tensor cores (BF16x3); A is [M][K]
-    (or [K][M] with a_mn_major), V is [N][K].  CUDA tensors in, CUDA tensor out."""
+    (or [K][M] with a_mn_major), V is [N][K]; tile_k 0 / 32 / 64 picks the
+    kernel's K block.  CUDA tensors in, CUDA tensor out."""
     kind = _kind_of(A, V)
     if a_mn_major:
         K, M = int(A.shape[0]), int(A.shape[1])
@@ -693,6 +696,6 @@ def mpax_dense_bf16x3(A, V, a_mn_major=False, stream=None):
     else:
         D = np.empty((N, M), dtype=np.float32)
         pd = D.ctypes.data
-    _check(_lib.mpax_dense_bf16x3(M, N, K, 1 if a_mn_major else 0, pa, pv, pd, kind,
-                                  _stream(stream)))
+    _check(_lib.mpax_dense_bf16x3(M, N, K, 1 if a_mn_major else 0, int(tile_k), pa, pv, pd,
+                                  kind, _stream(stream)))
     return D

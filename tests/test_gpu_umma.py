@@ -44,23 +44,26 @@ CASES = [  # (M, N, K, a_mn_major)
 ]
 
 
+@pytest.mark.parametrize("tile_k", [32, 64])
 @pytest.mark.parametrize("M,N,K,mn", CASES)
-def test_bf16x3_product_within_its_error_bound(C, M, N, K, mn):
+def test_bf16x3_product_within_its_error_bound(C, M, N, K, mn, tile_k):
     import torch
     rng = np.random.default_rng(M * 7 + N * 3 + K + mn)
     A = rng.standard_normal((K, M) if mn else (M, K)).astype(np.float32) / np.sqrt(K)
     V = rng.standard_normal((N, K)).astype(np.float32)
     D = C.mpax_dense_bf16x3(torch.from_numpy(A).cuda(), torch.from_numpy(V).cuda(),
-                            a_mn_major=bool(mn)).cpu().numpy()
+                            a_mn_major=bool(mn), tile_k=tile_k).cpu().numpy()
     Aop = A.T if mn else A
     exact = V.astype(np.float64) @ Aop.astype(np.float64).T  # N x M
     err = np.abs(D.astype(np.float64) - exact)
     bound = _bound(Aop, V)
     assert np.all(err <= bound), float(np.max(err / np.maximum(bound, 1e-300)))
-    # and far better than one BF16 product: the split keeps ~16 bits
-    one_bf16 = (V.astype(np.float32).astype(np.float64) @ Aop.astype(np.float64).T)
+    # far below one BF16 product's error (~2^-9 relative): the split keeps ~16 bits
     assert np.max(err) < 1e-3 * np.max(np.abs(exact)) + 1e-30
-    del one_bf16
+    if tile_k == 64:  # both pipeline shapes form the same sums in the same order
+        D32 = C.mpax_dense_bf16x3(torch.from_numpy(A).cuda(), torch.from_numpy(V).cuda(),
+                                  a_mn_major=bool(mn), tile_k=32).cpu().numpy()
+        assert np.array_equal(D, D32)
 
 
 def test_bf16x3_host_pointers_and_bad_sizes(C):
