@@ -146,10 +146,12 @@ typedef struct mpax_options {
                                  budget for 10 CTAs per SM.  All compute every
                                  product and sum in the same order, so results are
                                  identical bit for bit; -1 times each on the
-                                 problem's own matrices at the first prepare (five
-                                 launches each) and keeps the fastest, cached for
-                                 the process by matrix signature (rows, columns,
-                                 nnz, precision, histogram of log2 row lengths) */
+                                 problem's own matrices, with the iteration's own
+                                 half-step epilogues, at the first prepare (ten
+                                 launches each) and keeps the fastest (another
+                                 kind must beat 0 by 3%), cached for the process
+                                 by matrix signature (rows, columns, nnz, LP or
+                                 QP, precision, histogram of log2 row lengths) */
 } mpax_options;
 
 typedef struct mpax_stats {
