@@ -771,6 +771,7 @@ def run_shared(args):
                                                       / (1 + np.abs(d["opt_value"])))),
                          switched_to_fp32_instances=summ["fp64_instances"],
                          product_tile_k=summ.get("product_tile_k"),
+                         prepare_s=summ.get("prepare_s"), power_rounds=summ.get("power_rounds"),
                          clocks=clk, gpu_launches=summ["kernel_launches"])
     # the products on their own: CUDA events around every iteration product of a
     # short profiled solve (192 iterations)

@@ -477,13 +477,15 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* opts, int32_t
 mpax_status mpax_shared_get_solution(const mpax_shared* sh, double* X, double* Y,
                                      mpax_mem_kind kind);
 /* As mpax_batch_get_stats (seconds = host time from solve start to the check at
- * which the instance finished); gemm_info (HOST, 7 doubles, nullable) receives
+ * which the instance finished); gemm_info (HOST, 9 doubles, nullable) receives
  * the count of product launches, their flops, ||A~||_2, the K block (64 or 32)
  * of the dual and the primal product's pipeline (each direction's shape is
  * chosen by timing both on the first solve of each (m, n, B) in the process),
  * and, when the solve ran with profile_kernels = 1, the average milliseconds of
  * one iteration product launch, dual (A~ X) then primal (A~^T Y), from CUDA
- * events on the solve's stream (0 otherwise). */
+ * events on the solve's stream (0 otherwise); then the host seconds of the
+ * solve's preparation (scaling, BF16 splits, plans, norm estimate) and the
+ * rounds of its power iteration (9 doubles in all). */
 mpax_status mpax_shared_get_stats(const mpax_shared* sh, mpax_batch_stats* stats,
                                   int32_t* status, int64_t* iterations, double* rel_kkt,
                                   double* primal_obj, double* seconds, double* gemm_info);

@@ -43,6 +43,13 @@ namespace mpax {
 namespace {
 
 int g1(long long k) { return (int)std::max(1LL, std::min(8192LL, (k + 255) / 256)); }
+// Grid of the per-instance elementwise kernels: x over `len` coordinates (256
+// threads, up to 4 coordinates each), y over the B instances (65,535 at most; the
+// kernels loop over the rest).
+dim3 grid2d(long long len, int B) {
+  const long long bx = std::max(1LL, std::min(1024LL, (len + 1023) / 1024));
+  return dim3((unsigned)bx, (unsigned)std::max(1, std::min(B, 65535)));
+}
 
 mpax_status sfail(mpax_status s, const std::string& m) {
   set_last_error(m.c_str());
@@ -154,11 +161,11 @@ struct Vecs {
 // primal: T = A~^T Y; x = w + (anchor - w)/(k+1); x^ = proj(x - tau (c~ - T));
 // w <- 2 x^ - x (also split to BF16 for the next product)
 // tpart (B = 1 only): T is the sum of the GEMV's tchunks partials, in order.
+// Grid: x over the coordinates of an instance, y over instances (grid2d).
 __global__ void k_primal(Vecs v, int check, const float* __restrict__ tpart, int tchunks) {
-  const size_t total = (size_t)v.n * v.B;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const int k = (int)(e / v.n), j = (int)(e % v.n);
+  for (int k = blockIdx.y; k < v.B; k += gridDim.y)
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.n; j += gridDim.x * blockDim.x) {
+    const size_t e = (size_t)k * v.n + j;
     const Inst& I = v.inst[k];
     if (I.done) continue;
     float t;
@@ -183,10 +190,9 @@ __global__ void k_primal(Vecs v, int check, const float* __restrict__ tpart, int
 // y <- z + (anchor - z)/(k+2), z = 2 y^ - y (also split)
 // spart (B = 1 only): S is the sum of the GEMV's schunks partials, in order.
 __global__ void k_dual(Vecs v, int check, const float* __restrict__ spart, int schunks) {
-  const size_t total = (size_t)v.m * v.B;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const int k = (int)(e / v.m), i = (int)(e % v.m);
+  for (int k = blockIdx.y; k < v.B; k += gridDim.y)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.m; i += gridDim.x * blockDim.x) {
+    const size_t e = (size_t)k * v.m + i;
     const Inst& I = v.inst[k];
     if (I.done) continue;
     float sv;
@@ -364,24 +370,23 @@ __global__ void k_check_finalize(Inst* inst, const double* part, CheckParams p) 
 }
 
 __global__ void k_restart_apply(Vecs v) {
-  const size_t tn = (size_t)v.n * v.B, tm = (size_t)v.m * v.B;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tn + tm;
-       e += (size_t)gridDim.x * blockDim.x) {
-    if (e < tn) {
-      const int k = (int)(e / v.n);
-      if (!v.inst[k].restart) continue;
-      const float xh = v.xhat[e];
-      v.xa[e] = xh;
-      v.w[e] = xh;
-      split_store(xh, v.xh_hi, v.xh_lo, (size_t)k * v.ldx + (e - (size_t)k * v.n));
-    } else {
-      const size_t f = e - tn;
-      const int k = (int)(f / v.m);
-      if (!v.inst[k].restart) continue;
-      const float yh = v.yhat[f];
-      v.ya[f] = yh;
-      v.y[f] = yh;
-      split_store(yh, v.y_hi, v.y_lo, (size_t)k * v.ldy + (f - (size_t)k * v.m));
+  const int tot = v.n + v.m;
+  for (int k = blockIdx.y; k < v.B; k += gridDim.y) {
+    if (!v.inst[k].restart) continue;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+      if (t < v.n) {
+        const size_t e = (size_t)k * v.n + t;
+        const float xh = v.xhat[e];
+        v.xa[e] = xh;
+        v.w[e] = xh;
+        split_store(xh, v.xh_hi, v.xh_lo, (size_t)k * v.ldx + t);
+      } else {
+        const size_t f = (size_t)k * v.m + (t - v.n);
+        const float yh = v.yhat[f];
+        v.ya[f] = yh;
+        v.y[f] = yh;
+        split_store(yh, v.y_hi, v.y_lo, (size_t)k * v.ldy + (t - v.n));
+      }
     }
   }
 }
@@ -389,10 +394,9 @@ __global__ void k_restart_apply(Vecs v) {
 // x (before the check step) rebuilt for the fixed-point residual: x = w + (xa - w)/(k+1)
 __global__ void k_rebuild_x(const float* __restrict__ w, const float* __restrict__ xa,
                             float* __restrict__ out, int n, int B, const Inst* inst) {
-  const size_t total = (size_t)n * B;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const int k = (int)(e / n);
+  for (int k = blockIdx.y; k < B; k += gridDim.y)
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const size_t e = (size_t)k * n + j;
     const Inst& I = inst[k];
     const float rb = (float)(1.0 / (double)(I.k + 1));
     out[e] = (I.k == 0) ? xa[e] : w[e] + rb * (xa[e] - w[e]);
@@ -566,6 +570,8 @@ struct mpax_shared {
   UmmaPlan plan_dual, plan_primal;  // S = A~ X (K = n), T = A~^T Y (K = m)
   int* uerr = nullptr;              // set by a bounded wait of the product kernel
   float shape_ms[2][2] = {{0, 0}, {0, 0}};  // tuner: [dual, primal][K block 64, 32] ms
+  double prep_seconds = 0.0;   // last solve: scaling, splits, plans, power iteration
+  int power_rounds = 0;        // last solve: rounds of the power iteration
   // profile_kernels: event pairs of the iteration products and their sums
   struct ProdEvent {
     cudaEvent_t e0, e1;
@@ -726,71 +732,113 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv_n_part(const float* __res
 
 // ---- B > 1, FP32 products on the CUDA cores ----------------------------------------
 // C[n][m] = sum_k A_op[m][k] V[n][k] for the B instances' vectors V (rows of ldv):
-// A_op = A~ stored [M][K] (a_mn = 0, the dual step's A~ X) or A~^T of an A~ stored
-// [K][M] (a_mn = 1, the primal step's A~^T Y).  CTA tile 128 (M) x 64 (N) x 16
-// (K) staged in shared memory; each of 256 threads accumulates 8 x 4 outputs in
-// FP32, k in increasing order (one fixed order per output).
-constexpr int kSgBM = 128, kSgBN = 64, kSgBK = 16;
+// A_op = A~ stored [M][K] (A_MN = 0, the dual step's A~ X) or A~^T of an A~ stored
+// [K][M] (A_MN = 1, the primal step's A~^T Y).  CTA tile 128 (M) x 128 (N) x 8 (K),
+// 256 threads of 8 x 8 outputs each, accumulated in FP32 in increasing k (one
+// fixed order per output).  The next k-slab is read from global memory into
+// registers while the current one is multiplied, then stored into the other of
+// two shared-memory buffers (one barrier per slab).
+constexpr int kSgBM = 128, kSgBN = 128, kSgBK = 8;
+
+template <int A_MN>
+__device__ __forceinline__ void sg_load_a(const float* __restrict__ A, long long lda, int M, int K,
+                                          int m0, int k0, int tid, float* ra) {
+  // 128 x 8 values, 4 per thread
+  if (A_MN) {  // rows k0..k0+7 of 128 contiguous m values: thread -> (k, 4 m)
+    const int kk = tid / 32, mm = (tid % 32) * 4;
+    const int gk = k0 + kk;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int gm = m0 + mm + t;
+      ra[t] = (gk < K && gm < M) ? A[(long long)gk * lda + gm] : 0.0f;
+    }
+  } else {     // 128 rows m of 8 contiguous k values: thread -> (m, 4 k)
+    const int r = tid / 2, kq = (tid % 2) * 4;
+    const int gm = m0 + r;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int gk = k0 + kq + t;
+      ra[t] = (gm < M && gk < K) ? A[(long long)gm * lda + gk] : 0.0f;
+    }
+  }
+}
+
+template <int A_MN>
+__device__ __forceinline__ void sg_store_a(float (*As)[kSgBM + 4], int tid, const float* ra) {
+  if (A_MN) {
+    const int kk = tid / 32, mm = (tid % 32) * 4;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) As[kk][mm + t] = ra[t];
+  } else {
+    const int r = tid / 2, kq = (tid % 2) * 4;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) As[kq + t][r] = ra[t];
+  }
+}
 
 template <int A_MN>
 __global__ void __launch_bounds__(256) k_sgemm(const float* __restrict__ A, long long lda,
                                                const float* __restrict__ V, long long ldv,
                                                float* __restrict__ Cm, long long ldc, int M,
                                                int N, int K) {
-  __shared__ float As[kSgBK][kSgBM + 4];
-  __shared__ float Vs[kSgBK][kSgBN + 4];
+  __shared__ __align__(16) float As[2][kSgBK][kSgBM + 4];
+  __shared__ __align__(16) float Vs[2][kSgBK][kSgBN + 4];
   const int tid = threadIdx.x;
-  const int tm = tid % 16, tn = tid / 16;  // 8 rows (m) and 4 instances (n) each
+  const int tm = tid % 16, tn = tid / 16;  // 8 rows (m) and 8 instances (n) each
   const int m0 = blockIdx.x * kSgBM, n0 = blockIdx.y * kSgBN;
-  float acc[8][4];
+  float acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-  for (int k0 = 0; k0 < K; k0 += kSgBK) {
-    // A tile: 128 x 16 values, 8 per thread
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int e = tid + 256 * t;
-      int r, kk;
-      if (A_MN) {  // consecutive threads along m (contiguous in memory)
-        r = e % kSgBM;
-        kk = e / kSgBM;
-      } else {     // consecutive threads along k (contiguous in memory)
-        kk = e % kSgBK;
-        r = e / kSgBK;
-      }
-      const int gm = m0 + r, gk = k0 + kk;
-      float v = 0.0f;
-      if (gm < M && gk < K) v = A_MN ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
-      As[kk][r] = v;
-    }
-    // V tile: 64 x 16 values, 4 per thread
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+  // V slab: 128 rows n of 8 contiguous k values: thread -> (n, 4 k)
+  const int vr = tid / 2, vq = (tid % 2) * 4;
+  float ra[4], rv[4];
+  auto load_v = [&](int k0) {
+    const int gn = n0 + vr;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      const int e = tid + 256 * t;
-      const int kk = e % kSgBK, c = e / kSgBK;
-      const int gn = n0 + c, gk = k0 + kk;
-      Vs[kk][c] = (gn < N && gk < K) ? V[(long long)gn * ldv + gk] : 0.0f;
+      const int gk = k0 + vq + t;
+      rv[t] = (gn < N && gk < K) ? V[(long long)gn * ldv + gk] : 0.0f;
     }
-    __syncthreads();
+  };
+  sg_load_a<A_MN>(A, lda, M, K, m0, 0, tid, ra);
+  load_v(0);
+  sg_store_a<A_MN>(As[0], tid, ra);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) Vs[0][vq + t][vr] = rv[t];
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += kSgBK) {
+    const bool more = k0 + kSgBK < K;
+    if (more) {
+      sg_load_a<A_MN>(A, lda, M, K, m0, k0 + kSgBK, tid, ra);
+      load_v(k0 + kSgBK);
+    }
 #pragma unroll
     for (int kk = 0; kk < kSgBK; ++kk) {
-      float a[8], b[4];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) a[i] = As[kk][tm * 8 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Vs[kk][tn * 4 + j];
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][tm * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][tm * 8 + 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Vs[buf][kk][tn * 8]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Vs[buf][kk][tn * 8 + 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+      sg_store_a<A_MN>(As[buf ^ 1], tid, ra);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) Vs[buf ^ 1][vq + t][vr] = rv[t];
     }
     __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int gn = n0 + tn * 4 + j;
+  for (int j = 0; j < 8; ++j) {
+    const int gn = n0 + tn * 8 + j;
     if (gn >= N) continue;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -1126,7 +1174,9 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
     for (int j = 0; j < n; ++j) v0[j] = (float)(power_start_raw(j) * inv);
     cudaMemcpyAsync(v, v0.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s);
     double prev = 0.0, nu = 0.0, d_prev = 0.0;
+    sh->power_rounds = 0;
     for (int t = 1; t <= o->power_max_iter; ++t) {
+      sh->power_rounds = t;
       // wv = A~ v, v = A~^T wv with this file's matrix-vector kernels
       gemv_part(sh, 1, v, sh->As);
       k_gemv_t_sum<<<g1(m), 256, 0, s>>>(sh->gpart_n, sh->gemv_nchunks, m, wv);
@@ -1153,6 +1203,9 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
     sh->norm_A = nu;
   }
   const double eta = sh->norm_A > 0 ? o->step_safety / sh->norm_A : 1.0;
+  cudaStreamSynchronize(s);
+  sh->prep_seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   // ---- per-instance initial state --------------------------------------------------
   k_colnorm<<<B, 256, 0, s>>>(sh->C0, sh->Dc, n, sh->cns);
   k_colnorm<<<B, 256, 0, s>>>(sh->C0, nullptr, n, sh->cn);
@@ -1190,16 +1243,16 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
     for (int it = 0; it < len; ++it) {
       const int chk = (it == len - 1);
       if (chk) {  // the iterate before the check step, for the fixed-point residual
-        k_rebuild_x<<<g1(nB), 256, 0, s>>>(sh->w, sh->xa, sh->xprev, n, B, sh->inst);
+        k_rebuild_x<<<grid2d(n, B), 256, 0, s>>>(sh->w, sh->xa, sh->xprev, n, B, sh->inst);
         k_copy_f<<<g1(mB), 256, 0, s>>>(sh->y, sh->yprev, mB);
         L += 2;
       }
       if (B == 1 && !bf) {
         // one instance, FP32: GEMV partials, summed inside the update kernels
         gemv_part(sh, 0, sh->y, sh->As);
-        k_primal<<<g1(nB), 256, 0, s>>>(V, chk, sh->gpart, sh->gemv_chunks);
+        k_primal<<<grid2d(n, B), 256, 0, s>>>(V, chk, sh->gpart, sh->gemv_chunks);
         gemv_part(sh, 1, sh->w, sh->As);
-        k_dual<<<g1(mB), 256, 0, s>>>(V, chk, sh->gpart_n, sh->gemv_nchunks);
+        k_dual<<<grid2d(m, B), 256, 0, s>>>(V, chk, sh->gpart_n, sh->gemv_nchunks);
         k_advance<<<(B + 255) / 256, 256, 0, s>>>(sh->inst, B);
         L += 3;
         continue;
@@ -1208,13 +1261,13 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
         result = sfail(MPAX_ERR_CUDA, "matrix product launch failed");
         break;
       }
-      k_primal<<<g1(nB), 256, 0, s>>>(V, chk, nullptr, 0);
+      k_primal<<<grid2d(n, B), 256, 0, s>>>(V, chk, nullptr, 0);
       // the dual product reads the reflected point w (FP32) or its BF16 split
       if (product(sh, 1, sh->xh_hi, sh->xh_lo, sh->w, sh->S, bf, sh->As)) {
         result = sfail(MPAX_ERR_CUDA, "matrix product launch failed");
         break;
       }
-      k_dual<<<g1(mB), 256, 0, s>>>(V, chk, nullptr, 0);
+      k_dual<<<grid2d(m, B), 256, 0, s>>>(V, chk, nullptr, 0);
       k_advance<<<(B + 255) / 256, 256, 0, s>>>(sh->inst, B);
       L += 3;
     }
@@ -1240,7 +1293,7 @@ mpax_status mpax_shared_solve(mpax_shared* sh, const mpax_options* o, int32_t fp
     // the BF16 splits of the iterates are rebuilt (restart copies x^, y^ into them)
     split_rows(sh->w, B, n, n, sh->xh_hi, sh->xh_lo, sh->n8, s);
     split_rows(sh->y, B, m, m, sh->y_hi, sh->y_lo, sh->m8, s);
-    k_restart_apply<<<g1(nB + mB), 256, 0, s>>>(V);
+    k_restart_apply<<<grid2d(n + m, B), 256, 0, s>>>(V);
     L += 8;
     cudaMemcpyAsync(hi.data(), sh->inst, sizeof(Inst) * B, cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
@@ -1339,6 +1392,8 @@ mpax_status mpax_shared_get_stats(const mpax_shared* sh, mpax_batch_stats* stats
     gemm_info[4] = sh->plan_primal.bk;
     gemm_info[5] = sh->prof_n[1] ? sh->prof_ms[1] / sh->prof_n[1] : 0.0;
     gemm_info[6] = sh->prof_n[0] ? sh->prof_ms[0] / sh->prof_n[0] : 0.0;
+    gemm_info[7] = sh->prep_seconds;
+    gemm_info[8] = sh->power_rounds;
   }
   return MPAX_OK;
 }

@@ -657,14 +657,15 @@ def mpax_shared_get_stats(h, B):
     kk = np.empty(B)
     po = np.empty(B)
     sec = np.empty(B)
-    gi = np.zeros(7)
+    gi = np.zeros(9)
     _check(_lib.mpax_shared_get_stats(h, ctypes.byref(s), st.ctypes.data, it.ctypes.data,
                                       kk.ctypes.data, po.ctypes.data, sec.ctypes.data,
                                       gi.ctypes.data))
     d = s.as_dict()
     d.update(gemms=int(gi[0]), gemm_flops=float(gi[1]), norm_A=float(gi[2]),
              product_tile_k=(int(gi[3]), int(gi[4])),
-             product_ms=(float(gi[5]), float(gi[6])))
+             product_ms=(float(gi[5]), float(gi[6])), prepare_s=float(gi[7]),
+             power_rounds=int(gi[8]))
     return d, dict(status=st, iterations=it, rel_kkt=kk, primal_obj=po, seconds=sec)
 
 

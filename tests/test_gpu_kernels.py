@@ -100,8 +100,9 @@ def test_autotuner_times_once_and_reuses_its_choice(C):
     us = list(s_t["spmv_tune_us"])
     assert all(u > 0 for u in us), us
     kinds = list(s_t["spmv_kernel"])
-    for q in range(2):  # the fastest kind was kept
-        assert kinds[q] == int(np.argmin(us[3 * q:3 * q + 3]))
+    for q in range(2):  # the fastest kind was kept (another must beat kind 0 by 3%)
+        score = [us[3 * q], 1.03 * us[3 * q + 1], 1.03 * us[3 * q + 2]]
+        assert kinds[q] == int(np.argmin(score))
     x_c, y_c, s_c = solve(C, d, spmv_kernel=-1, **kw)  # same signature: cached
     assert list(s_c["spmv_tune_us"]) == [0.0] * 6
     assert list(s_c["spmv_kernel"]) == kinds
