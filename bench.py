@@ -859,13 +859,14 @@ def run_qp(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        its, bw, res, launches = [], [], [], 0
+        its, bw, res, mr, launches = [], [], [], [], 0
         for _ in range(steps):
             s, info, tb = step()
             assert s["termination_name"] == "optimal", s
             its.append(s["iterations"])
             bw.append(tb)
             res.append(info["rel_residual"])
+            mr.append(info["iterations"])
             launches += s["kernel_launches"]
         e1.record()
         torch.cuda.synchronize()
@@ -873,6 +874,7 @@ def run_qp(args):
         ms = e0.elapsed_time(e1) / steps
         out[name] = dict(steps_per_s=1e3 / ms, ms_per_step=ms, iterations=float(np.mean(its)),
                          backward_s=float(np.mean(bw)), adjoint_rel_residual=max(res),
+                         minres_iterations=float(np.mean(mr)),
                          clocks=clk, gpu_launches=launches)
     out["unrolled_fp64"] = None
     if not getattr(args, "sub", False):

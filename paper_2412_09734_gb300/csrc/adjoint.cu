@@ -22,7 +22,10 @@
 #include <vector>
 
 #include "../../include/mpax.h"
+#include "epilogues.cuh"
+#include "kernels.cuh"
 #include "problem.cuh"
+#include "spmv_launch.cuh"
 
 namespace mpax {
 ProblemData* problem_data(mpax_problem* p);
@@ -34,14 +37,20 @@ namespace {
 using namespace mpax;
 
 int g1(long long k) { return (int)std::max(1LL, std::min(4096LL, (k + 255) / 256)); }
+// MINRES: steps per captured graph (the period of the buffer rotations) and
+// graphs launched between two reads of the state by the host
+constexpr int kMinresGraphSteps = 3;
+constexpr int kMinresGraphsPerCheck = 8;
 int wgrid(long long rows) { return (int)std::max(1LL, std::min(152LL * 8, (rows * 32 + 255) / 256)); }
 
 // out_r = mask_r * (sum_p val[p] x[col[p]] + d_r x_r)   (d, mask nullable)
+// (skip nullable: a device flag that, when set, turns the launch into a no-op)
 __global__ void k_rows(const int* __restrict__ rp, const int* __restrict__ col,
                        const double* __restrict__ val, const int* __restrict__ perm, int rows,
                        const double* __restrict__ x, const double* __restrict__ d,
                        const double* __restrict__ xd, const unsigned char* __restrict__ mask,
-                       double* __restrict__ out, int accumulate) {
+                       double* __restrict__ out, int accumulate, const int* skip = nullptr) {
+  if (skip && *skip) return;
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += nw) {
@@ -105,15 +114,188 @@ __global__ void k_axpby(double* __restrict__ z, const double* __restrict__ a, do
     z[i] = alpha * a[i] + beta * (b ? b[i] : 0.0);
 }
 
-// w_new = (v - e w1 - dl w2) / g;  x += phi w_new;  (w1, w2, w) rotate on the host
-__global__ void k_minres_w(const double* __restrict__ v, const double* __restrict__ w1,
-                           const double* __restrict__ w2, double oldeps, double delta,
-                           double denom, double* __restrict__ wout, double* __restrict__ x,
-                           double phi, int n) {
+// ---- MINRES with its scalars resident on the device --------------------------
+// One MINRES step (Paige-Saunders, no preconditioner) on the masked KKT matrix
+//   K = [[mask_F (D~ + F~ F~^T + Q~) mask_F, mask_F A~^T mask_R], [mask_R A~ mask_F, 0]]
+// runs on the solver's row schedules of A, A^T, F, F^T and Q (the fused SpMV
+// kernels of kernels.cuh, FP64), none of the launches returning a scalar to the
+// host:
+//   u = F~^T v_top            (schedule of F^T; low-rank Q only)
+//   aux = F~ u, or Q~ v_top   (schedule of F, or of Q for a general Q)
+//   y_top = mask_F (A~^T v_bot + aux + D~ v_top)   (schedule of A^T)
+//   y_bot = mask_R A~ v_top                          (schedule of A, forked branch)
+//     both fused with the first Lanczos update y -= (beta / beta_old) r1 (from the
+//     second step on) and per-item partials of v.y
+//   k_mr_alpha  alpha = v.y from the partials of both products, in a fixed order
+//   k_mr_b      y -= (alpha / beta) r2; the last block to finish sums the
+//               partials of y.y, takes beta' = sqrt(y.y) and the Givens
+//               recurrences, and sets `done` when phibar <= tol beta1, beta' = 0
+//               or the step limit is reached
+//   k_mr_c      w' = (v - eps_old w1 - delta w2) / gamma;  x += phi w';  v = y / beta'
+// after which r1 <- r2, r2 <- y, w1 <- w2, w2 <- w' rotate buffers on the host.
+// The steps are captured as one CUDA graph and the host reads the state only
+// every few dozen steps; a step launched after convergence finds `done` set and
+// does nothing.  "Last block" is an arrival counter (atomicAdd after a fence, no
+// waiting); every sum runs in a fixed order, so results do not depend on the
+// number of steps between host checks.
+struct MinresState {
+  double beta1, tol;
+  double beta, oldb, dbar, epsln, cs, sn, phibar, alfa;
+  double oldeps, delta, inv_gamma, phi;  // the w update of the latest step
+  int itn, max_iter, done, w_applied;    // w_applied == itn: no w update pending
+};
+
+// Arrival at the end of a kernel: true in the whole of the block that arrives last.
+// The counter is reset for the next launch by that block.
+__device__ __forceinline__ bool arrive_last(unsigned* cnt, bool* flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    *flag = atomicAdd(cnt, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (*flag) __threadfence();
+  return *flag;
+}
+
+// Fixed-order sum of count partials written by other blocks or launches (read
+// through L2); the total in thread 0.
+__device__ __forceinline__ double sum_parts(const double* part, int count, double* sh) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) s += __ldcg(part + i);
+  return block_sum(s, sh);
+}
+
+// Row epilogues of the MINRES products (the interface of epilogues.cuh).
+// out_r = s: u = F~^T v_top and aux = F~ u (or Q~ v_top).
+struct EpiMrStore {
+  static constexpr int NQ = 1;  // no partials: check stays 0
+  struct Pre {};
+  const MinresState* st;
+  double* out;
+  int check = 0;
+  __device__ __forceinline__ bool skip() const { return st->done != 0; }
+  __device__ __forceinline__ void load() {}
+  __device__ __forceinline__ void pre(int, Pre&) const {}
+  __device__ __forceinline__ void row(int r, double s, const Pre&, double*) { out[r] = s; }
+};
+
+// One block row of y = K v (top: rows of A^T, bottom: rows of A), then
+// y -= (beta / beta_old) r1 and the partial [0] v.y.
+struct EpiMrRow {
+  static constexpr int NQ = 1;
+  struct Pre {
+    double v, r1, aux, d;
+    unsigned char keep;
+  };
+  MinresState* st;
+  const double* v;   // the stacked vector, offset to this block's rows
+  double* y;         // likewise
+  const double* r1;  // likewise
+  const double* aux;  // nullable (top only): F~ u or Q~ v_top
+  const double* ds;   // nullable (top only): D~
+  const unsigned char* mask;
+  int check = 1;
+  bool sub;
+  double c;
+  __device__ __forceinline__ bool skip() const { return st->done != 0; }
+  __device__ __forceinline__ void load() {
+    sub = st->itn >= 1;
+    c = sub ? -st->beta / st->oldb : 0.0;
+  }
+  __device__ __forceinline__ void pre(int r, Pre& p) const {
+    p.v = v[r];
+    p.r1 = sub ? r1[r] : 0.0;
+    p.aux = aux ? aux[r] : 0.0;
+    p.d = ds ? ds[r] : 0.0;
+    p.keep = mask[r];
+  }
+  __device__ __forceinline__ void row(int r, double s, const Pre& p, double* acc) {
+    double yi = p.keep ? s + p.aux + p.d * p.v : 0.0;
+    if (sub) yi += c * p.r1;
+    y[r] = yi;
+    acc[0] += p.v * yi;
+  }
+};
+
+// alpha = v.y from the per-item partials of the top product, then the bottom's:
+// block b sums a contiguous share of that sequence, the last block to finish
+// sums the blocks' totals in block order.
+constexpr int kAlphaBlocks = 32;
+__global__ void k_mr_alpha(MinresState* __restrict__ st, const double* __restrict__ pt, int nt,
+                           const double* __restrict__ pb, int nb, double* __restrict__ apart,
+                           unsigned* __restrict__ cnt) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->w_applied = st->itn;  // no w update pending
+  if (st->done) return;
+  const long long total = (long long)nt + nb;
+  const int lo = (int)(total * blockIdx.x / gridDim.x);
+  const int hi = (int)(total * (blockIdx.x + 1) / gridDim.x);
+  double t = 0.0;
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) t += __ldcg(i < nt ? pt + i : pb + (i - nt));
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) apart[blockIdx.x] = t;
+  if (!arrive_last(cnt, &last)) return;
+  const double a = sum_parts(apart, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    st->alfa = a;
+    *cnt = 0;
+  }
+}
+
+__global__ void k_mr_b(MinresState* __restrict__ st, double* __restrict__ y,
+                       const double* __restrict__ r2, int n, double* __restrict__ part,
+                       unsigned* __restrict__ cnt) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  if (st->done) return;
+  const double c = -st->alfa / st->beta;
+  double s = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double wn = (v[i] - oldeps * w1[i] - delta * w2[i]) * denom;
-    wout[i] = wn;
+    const double yi = y[i] + c * r2[i];
+    y[i] = yi;
+    s += yi * yi;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (!arrive_last(cnt, &last)) return;
+  const double bsq = sum_parts(part, gridDim.x, sh);
+  if (threadIdx.x != 0) return;
+  *cnt = 0;
+  const double alfa = st->alfa;
+  const double beta = sqrt(bsq);
+  const double cs = st->cs, sn = st->sn, dbar = st->dbar;
+  st->oldeps = st->epsln;
+  st->delta = cs * dbar + sn * alfa;
+  const double gbar = sn * dbar - cs * alfa;
+  st->epsln = sn * beta;
+  st->dbar = -cs * beta;
+  const double gamma = fmax(sqrt(gbar * gbar + beta * beta), 1e-300);
+  st->cs = gbar / gamma;
+  st->sn = beta / gamma;
+  st->inv_gamma = 1.0 / gamma;
+  st->phi = st->cs * st->phibar;
+  st->phibar = st->sn * st->phibar;
+  st->oldb = st->beta;
+  st->beta = beta;
+  st->itn += 1;
+  if (st->phibar <= st->tol * st->beta1 || beta == 0.0 || st->itn >= st->max_iter) st->done = 1;
+}
+
+__global__ void k_mr_c(const MinresState* __restrict__ st, double* __restrict__ v,
+                       const double* __restrict__ w1, const double* __restrict__ w2,
+                       double* __restrict__ w, double* __restrict__ x,
+                       const double* __restrict__ y, int n) {
+  if (st->w_applied == st->itn) return;  // no step ran since the last update
+  const double oldeps = st->oldeps, delta = st->delta, ig = st->inv_gamma, phi = st->phi;
+  const bool next = !st->done;
+  const double ib = next ? 1.0 / st->beta : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double wn = (v[i] - oldeps * w1[i] - delta * w2[i]) * ig;
+    w[i] = wn;
     x[i] += phi * wn;
+    if (next) v[i] = ib * y[i];
   }
 }
 
@@ -302,7 +484,11 @@ mpax_status mpax_qp_adjoint(mpax_problem* prob, const double* g, double* dc, dou
   double* Fts = B.get<double>(P.f_nnz, &e);  // scaled F^T values (transpose order)
   double* As_t = B.get<double>(P.nnz, &e);   // scaled A^T values
   double* part = B.get<double>(kRedBlocks, &e);
+  double* part_b = B.get<double>(kRedBlocks, &e);
+  double* u = B.get<double>(std::max(P.r, 1), &e);
+  unsigned* cnt = B.get<unsigned>(2, &e);
   double* one = B.get<double>(1, &e);
+  MinresState* mst = B.get<MinresState>(1, &e);
   if (e) return afail(MPAX_ERR_OUT_OF_MEMORY, "adjoint buffers");
   mpax_status st = mpax_get_solution(prob, x, y, MPAX_MEM_DEVICE);
   if (st) return st;
@@ -325,62 +511,106 @@ mpax_status mpax_qp_adjoint(mpax_problem* prob, const double* g, double* dc, dou
   // MINRES on K z = b, z = [w~; v~]
   double *xz = vb[0], *r1 = vb[1], *r2 = vb[2], *yv = vb[3], *v = vb[4], *w = vb[5], *w1 = vb[6],
          *w2 = vb[7];
-  auto matvec = [&](const double* in, double* out) {
-    // top: mask_F (Ds in_top + F~ (F~^T in_top) + A~^T in_bot)
-    k_rows<<<wgrid(P.r), 256, 0, s>>>(P.Ft.rp, P.Ft.col, Fts, nullptr, P.r, in, nullptr,
-                                       nullptr, nullptr, tmpr, 0);
-    k_rows<<<wgrid(n), 256, 0, s>>>(P.F.rp, P.F.col, P.fval_s, nullptr, n, tmpr, P.D_s, in,
-                                     nullptr, out, 0);
-    if (P.q_general)
-      k_rows<<<wgrid(n), 256, 0, s>>>(P.Q.rp, P.Q.col, P.qval_s, nullptr, n, in, nullptr,
-                                       nullptr, nullptr, out, 1);
-    k_rows<<<wgrid(n), 256, 0, s>>>(P.At.rp, P.At.col, As_t, nullptr, n, in + n, nullptr,
-                                     nullptr, freem, out, 1);
-    // bottom: mask_R A~ in_top
-    k_rows<<<wgrid(m), 256, 0, s>>>(P.A.rp, P.A.col, P.val_s, nullptr, m, in, nullptr, nullptr,
-                                     rowm, out + n, 0);
-  };
   k_rhs<<<g1(N), 256, 0, s>>>(gd, P.Dc, freem, n, m, r1);
   cudaMemsetAsync(xz, 0, sizeof(double) * N, s);
   cudaMemsetAsync(w, 0, sizeof(double) * N, s);
   cudaMemsetAsync(w2, 0, sizeof(double) * N, s);
   cudaMemcpyAsync(r2, r1, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
-  cudaMemcpyAsync(yv, r1, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
-  double beta1 = std::sqrt(dot(r1, r1, N, part, one, s));
-  int itn = 0;
-  double phibar = beta1;
+  cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 2, s);
+  const double beta1 = std::sqrt(dot(r1, r1, N, part, one, s));
+  MinresState hs{};
+  hs.beta1 = beta1;
+  hs.tol = tol;
+  hs.beta = beta1;
+  hs.cs = -1.0;
+  hs.phibar = beta1;
+  hs.max_iter = max_iter;
+  hs.done = beta1 > 0.0 ? 0 : 1;
+  if ((e = cudaMemcpyAsync(mst, &hs, sizeof(hs), cudaMemcpyHostToDevice, s)))
+    return afail(MPAX_ERR_CUDA, cudaGetErrorString(e));
   if (beta1 > 0.0) {
-    double oldb = 0.0, beta = beta1, dbar = 0.0, epsln = 0.0, cs = -1.0, sn = 0.0;
-    for (itn = 1; itn <= max_iter; ++itn) {
-      k_axpby<<<g1(N), 256, 0, s>>>(v, yv, 1.0 / beta, nullptr, 0.0, N);
-      matvec(v, yv);
-      if (itn >= 2) k_axpby<<<g1(N), 256, 0, s>>>(yv, yv, 1.0, r1, -beta / oldb, N);
-      const double alfa = dot(v, yv, N, part, one, s);
-      k_axpby<<<g1(N), 256, 0, s>>>(yv, yv, 1.0, r2, -alfa / beta, N);
-      std::swap(r1, r2);  // r1 <- r2
-      cudaMemcpyAsync(r2, yv, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
-      oldb = beta;
-      beta = std::sqrt(dot(r2, yv, N, part, one, s));
-      const double oldeps = epsln;
-      const double delta = cs * dbar + sn * alfa;
-      const double gbar = sn * dbar - cs * alfa;
-      epsln = sn * beta;
-      dbar = -cs * beta;
-      double gamma = std::sqrt(gbar * gbar + beta * beta);
-      gamma = std::max(gamma, 1e-300);
-      cs = gbar / gamma;
-      sn = beta / gamma;
-      const double phi = cs * phibar;
-      phibar = sn * phibar;
-      // w1 <- w2, w2 <- w, w <- (v - oldeps w1 - delta w2) / gamma, x += phi w
-      double* t = w1;
+    k_axpby<<<g1(N), 256, 0, s>>>(v, r2, 1.0 / beta1, nullptr, 0.0, N);
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+    if (!e) e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming);
+    struct Release {
+      cudaStream_t& s2;
+      cudaEvent_t &a, &b;
+      ~Release() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        if (s2) cudaStreamDestroy(s2);
+      }
+    } release{s2, ev_fork, ev_join};
+    if (e) return afail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+    const bool lowrank = !P.q_general && P.r > 0 && P.f_nnz > 0;
+    // the products run in FP64 with the wide register budget whatever kernel the
+    // solver's precision was tuned to
+    auto wide = [](const Sched& sc) {
+      Sched w = sc;
+      w.kind = kSpmvItemWide;
+      return w;
+    };
+    const Sched sA = wide(P.schedA), sAt = wide(P.schedAt), sF = wide(P.schedF),
+                sFt = wide(P.schedFt), sQ = wide(P.schedQ);
+    auto step = [&]() {
+      const double* aux = nullptr;
+      if (lowrank) {
+        launch_spmv<double>(sFt, P.Ft, Fts, InPlain<double>{v}, EpiMrStore{mst, u}, 0, s);
+        launch_spmv<double>(sF, P.F, P.fval_s, InPlain<double>{u}, EpiMrStore{mst, tmpn}, 0, s);
+        aux = tmpn;
+      } else if (P.q_general) {
+        launch_spmv<double>(sQ, P.Q, P.qval_s, InPlain<double>{v}, EpiMrStore{mst, tmpn}, 0, s);
+        aux = tmpn;
+      }
+      // the bottom block on a forked branch: it reads only v
+      cudaEventRecord(ev_fork, s);
+      cudaStreamWaitEvent(s2, ev_fork, 0);
+      EpiMrRow eb{mst, v + n, yv + n, r1 + n, nullptr, nullptr, rowm};
+      launch_spmv<double>(sA, P.A, P.val_s, InPlain<double>{v}, eb, 0, s2);
+      cudaEventRecord(ev_join, s2);
+      EpiMrRow et{mst, v, yv, r1, aux, P.D_s, freem};
+      launch_spmv<double>(sAt, P.At, As_t, InPlain<double>{v + n}, et, 0, s);
+      cudaStreamWaitEvent(s, ev_join, 0);
+      k_mr_alpha<<<kAlphaBlocks, 256, 0, s>>>(mst, sAt.part, sAt.n_items, sA.part, sA.n_items,
+                                              part, cnt);
+      k_mr_b<<<kRedBlocks, 256, 0, s>>>(mst, yv, r2, N, part_b, cnt + 1);
+      double* t = w1;  // w1 <- w2, w2 <- w, w <- (the free buffer)
       w1 = w2;
       w2 = w;
       w = t;
-      k_minres_w<<<g1(N), 256, 0, s>>>(v, w1, w2, oldeps, delta, 1.0 / gamma, w, xz, phi, N);
-      if (phibar <= tol * beta1 || beta == 0.0) break;
+      k_mr_c<<<g1(N), 256, 0, s>>>(mst, v, w1, w2, w, xz, yv, N);
+      t = r1;  // r1 <- r2, r2 <- y, y <- (the free buffer)
+      r1 = r2;
+      r2 = yv;
+      yv = t;
+    };
+    // Both rotations have period 3: a graph of three steps leaves every pointer
+    // where it found it, so one captured graph serves every launch.
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)))
+      return afail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+    for (int k = 0; k < kMinresGraphSteps; ++k) step();
+    e = cudaStreamEndCapture(s, &g);
+    if (!e) e = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    for (long long launched = 0; !e && launched < max_iter;) {
+      for (int k = 0; k < kMinresGraphsPerCheck && !e && launched < max_iter; ++k) {
+        e = cudaGraphLaunch(ge, s);
+        launched += kMinresGraphSteps;
+      }
+      if (!e) e = cudaMemcpyAsync(&hs, mst, sizeof(hs), cudaMemcpyDeviceToHost, s);
+      if (!e) e = cudaStreamSynchronize(s);
+      if (!e && hs.done) break;
     }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (e) return afail(MPAX_ERR_CUDA, cudaGetErrorString(e));
   }
+  const int itn = hs.itn;
+  const double phibar = hs.phibar;
   if ((e = cudaGetLastError())) return afail(MPAX_ERR_CUDA, cudaGetErrorString(e));
   double* odc = tmpn;
   double* odb = lam;  // reuse (m <= n not assumed: allocate when needed)

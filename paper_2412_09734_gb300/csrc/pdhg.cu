@@ -20,6 +20,7 @@
 #include "engine.cuh"
 #include "epilogues.cuh"
 #include "kernels.cuh"
+#include "spmv_launch.cuh"
 #include "unrolled.cuh"
 
 namespace mpax {
@@ -517,111 +518,6 @@ __global__ void k_kkt_finalize(const double* __restrict__ partAt, int nAt,
     out[5] = fmax(fmax(nrp / (1.0 + st->b_norm), nrd / (1.0 + st->c_norm)),
                   gap / (1.0 + fabs(pobj) + fabs(dobj)));
   }
-}
-
-// ---------------------------------------------------------------------------
-// launch helper
-// ---------------------------------------------------------------------------
-
-// Warps of spmv_fused<T, In, Epi, MINB> resident on the whole GPU (one wave).
-template <typename T, class In, class Epi, int MINB>
-int resident_warps() {
-  static int w = -1;
-  if (w < 0) {
-    int blocks = 0, dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, spmv_fused<T, In, Epi, MINB>,
-                                                  kSpmvBlock, 0);
-    w = std::max(1, blocks) * sms * kSpmvWarps;
-  }
-  return w;
-}
-
-// Launch shape of spmv_pipe<T, In, Epi>: CTAs resident on the whole GPU and the
-// dynamic shared memory of one CTA (two stages per warp).
-struct PipeShape {
-  int grid = -1;
-  size_t smem = 0;
-};
-template <typename T, class In, class Epi>
-const PipeShape& pipe_shape() {
-  static PipeShape sh;
-  if (sh.grid < 0) {
-    const size_t smem = (size_t)kPipeWarps * PipeLayout<T>::kWarpBytes;
-    cudaFuncSetAttribute(spmv_pipe<T, In, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    int blocks = 0, dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, spmv_pipe<T, In, Epi>,
-                                                  kWarp * kPipeWarps, smem);
-    sh.smem = smem;
-    sh.grid = std::max(1, blocks) * sms;
-  }
-  return sh;
-}
-// Items per warp below which spmv_pipe launches fewer warps than fit (a warp
-// needs a few items for its copies to run ahead of its gathers).
-constexpr int kPipeMinItems = 4;
-
-template <typename T, class In, class Epi>
-void launch_spmv(const Sched& sc, const Csr& K, const T* val, In in, Epi epi, int q0,
-                 cudaStream_t s) {
-  if (sc.n_items == 0) return;
-  if (sc.kind == kSpmvPipe) {
-    SpmvArgs<T> a;
-    a.items = sc.items;
-    a.n_items = sc.n_items;
-    a.pf_dist = 0;
-    a.rp = K.rp;
-    a.col = K.col;
-    a.val = val;
-    a.cnt = sc.cnt;
-    a.carry = reinterpret_cast<T*>(sc.carry);
-    a.part = sc.part;
-    a.q0 = q0;
-    const PipeShape& sh = pipe_shape<T, In, Epi>();
-    const int want = (sc.n_items + kPipeMinItems * kPipeWarps - 1) / (kPipeMinItems * kPipeWarps);
-    const int grid = std::max(1, std::min(sh.grid, want));
-    spmv_pipe<T, In, Epi><<<grid, kWarp * kPipeWarps, sh.smem, s>>>(a, in, epi,
-                                                                     sc.cnt + sc.n_items);
-    return;
-  }
-  SpmvArgs<T> a;
-  a.items = sc.items;
-  a.n_items = sc.n_items;
-  const bool wide = sc.kind == kSpmvItemWide;
-  a.pf_dist = !MPAX_SPMV_PREFETCH ? 0
-              : wide ? resident_warps<T, In, Epi, kSpmvWideMinB>()
-                     : resident_warps<T, In, Epi, MPAX_SPMV_MINB>();
-  a.rp = K.rp;
-  a.col = K.col;
-  a.val = val;
-  a.cnt = sc.cnt;
-  a.carry = reinterpret_cast<T*>(sc.carry);
-  a.part = sc.part;
-  a.q0 = q0;
-  const int grid = (sc.n_items + kSpmvWarps - 1) / kSpmvWarps;
-  if (wide) {
-    spmv_fused<T, In, Epi, kSpmvWideMinB><<<grid, kSpmvBlock, 0, s>>>(a, in, epi);
-    return;
-  }
-#if MPAX_SPMV_PDL
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(kSpmvBlock);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, spmv_fused<T, In, Epi>, a, in, epi);
-#else
-  spmv_fused<T, In, Epi><<<grid, kSpmvBlock, 0, s>>>(a, in, epi);
-#endif
 }
 
 // ---- autotuner helpers ------------------------------------------------------

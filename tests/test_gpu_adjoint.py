@@ -87,6 +87,40 @@ def test_qp_adjoint_matches_oracle(C, case, eps, tol):
     assert rel_inf(dD, gdD) <= 1e-6
 
 
+def test_qp_adjoint_step_limit_zero_gradient_and_determinism(C):
+    """The MINRES steps run in captured graphs of three steps with the host
+    reading the state every few dozen steps: a step limit that is not a
+    multiple of three must still stop exactly there, the MINRES residual must
+    not grow with the step count, a zero loss gradient takes no step and gives
+    zero, and two runs give identical bits (fixed-order reductions)."""
+    d = qp_instance(4000, 2000, seed=instance_seed(201), a_density=5e-3, f_cols=32,
+                    f_density=0.01)
+    h = create(C, d)
+    try:
+        C.mpax_solve(h, C.mpax_options_default(eps_abs=1e-8, eps_rel=1e-8,
+                                               iteration_limit=10**6))
+        x, _ = C.mpax_get_solution(h, d["m"], d["n"])
+        g = x - d["x_target"]
+        prev = np.inf
+        for k in (1, 2, 4, 7, 8):
+            _, _, _, info = C.mpax_qp_adjoint(h, g, d["m"], d["n"], tol=1e-14, max_iter=k)
+            assert info["iterations"] == k
+            assert info["rel_residual"] <= prev * (1 + 1e-12)
+            prev = info["rel_residual"]
+        a = C.mpax_qp_adjoint(h, g, d["m"], d["n"], tol=1e-10, max_iter=20000)
+        b = C.mpax_qp_adjoint(h, g, d["m"], d["n"], tol=1e-10, max_iter=20000)
+        assert a[3] == b[3] and a[3]["iterations"] < 20000
+        assert a[3]["rel_residual"] <= 1e-10
+        for u, v in zip(a[:3], b[:3]):
+            assert np.array_equal(u, v)
+        z = C.mpax_qp_adjoint(h, np.zeros(d["n"]), d["m"], d["n"])
+        assert z[3]["iterations"] == 0 and z[3]["rel_residual"] == 0.0
+        for u in z[:3]:
+            assert not np.any(u)
+    finally:
+        C.mpax_destroy(h)
+
+
 def test_qp_layer_autograd_matches_finite_differences(C):
     import torch
     from paper_2412_09734_gb300.autograd import QPLayer
