@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--workload", default="sparse_lp_500k",
                     choices=list(WORKLOADS) + ["ragged_lp_4096", "shared_dense_512",
                                                "qp_200k", "knapsack_1000x100000",
-                                               "next_rows_20k"])
+                                               "next_rows_20k", "small_lp_200x400"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-iters", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -158,6 +158,19 @@ def algorithmic_bytes(m, n, nnz, n_items_unused, fp64, which):
     if which == "primal":  # rows of A^T: n rows, gathers y (m)
         return nnz * (v + 4) + (n + 1) * 4 + m * v + n * 6 * v
     return nnz * (v + 4) + (m + 1) * 4 + n * v + m * 5 * v  # rows of A, gathers xbar (n)
+
+
+def qp_algorithmic_bytes(m, n, nnz, f_nnz, r, v=4):
+    """Bytes one rAPDHG iteration (Algorithm 2, Q = D + F F^T) must move at minimum,
+    per launch: aux = F^T x_md (F^T values + columns + row pointers, the x and x_avg
+    entries it gathers, u); primal = rows of A^T (matrix, one read of y) fused with
+    F u, D x_md and the projection (read x, x_avg, c, l, u, D and F's rows, write
+    x, x_ref, x_avg); dual = rows of A (matrix, one read of x_ref; read y, y_avg,
+    lc, uc, write y, y_avg)."""
+    aux = f_nnz * (v + 4) + (r + 1) * 4 + min(f_nnz, n) * 2 * v + r * v
+    primal = nnz * (v + 4) + (n + 1) * 4 + m * v + 9 * n * v + (n + 1) * 4 + f_nnz * (v + 4)
+    dual = nnz * (v + 4) + (m + 1) * 4 + n * v + 6 * m * v
+    return {"aux": aux, "primal": primal, "dual": dual, "total": aux + primal + dual}
 
 
 def kernel_source_hash():
@@ -567,6 +580,31 @@ def run_small_lp(args):
     finally:
         C.mpax_destroy(h)
     ms = e0.elapsed_time(e1) / steps
+    # the same LP as a one-instance batch: one persistent CTA runs the whole
+    # restarted loop with the instance staged in shared memory
+    one = [torch.tensor([0, k], dtype=torch.int64, device="cuda") for k in (200, 400)]
+    hb = C.mpax_lp_batch_create(1, *one, dev["row_ptr"].to(torch.int64),
+                                *[dev[k] for k in keys[1:]])
+    try:
+        for _ in range(max(1, args.warmup)):
+            C.mpax_batch_solve(hb, opts)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            C.mpax_batch_solve(hb, opts)
+        e1.record()
+        torch.cuda.synchronize()
+        _, per = C.mpax_batch_get_stats(hb, 1)
+    finally:
+        C.mpax_batch_destroy(hb)
+    ms_cta = e0.elapsed_time(e1) / steps
+    persistent = {"time_s": ms_cta / 1e3, "iterations": int(per["iterations"][0]),
+                  "in_kernel_s": float(per["seconds"][0]), "rel_kkt": float(per["rel_kkt"][0]),
+                  "iters_per_s": int(per["iterations"][0]) / (ms_cta / 1e3),
+                  "note": "mpax_lp_batch_create with one instance: one 512-thread CTA, "
+                          "device-side loop, matrices and iterates in shared memory; bound "
+                          "by the SM's FP64 pipe (FP64 runs at 1/64 of the FP32 rate on "
+                          "this GPU), not by memory"}
     return {"metric": "time to rel KKT 1e-8, FP64", "value": ms / 1e3, "unit": "s",
             "higher_is_better": False, "steps": steps,
             "config": {"workload": "LP m=200 n=400, 2% density, N(0,1), box [0,10], half "
@@ -574,7 +612,8 @@ def run_small_lp(args):
             "iterations": s["iterations"], "iters_per_s": s["iterations"] / (ms / 1e3),
             "rel_kkt": s["rel_kkt"], "kernel_launches_per_solve": s["kernel_launches"],
             "note": "launch-bound: about 40 KB of data; each 64-iteration block is one CUDA "
-                    "graph of ~134 launches, so the time is set by launch latency, not HBM"}
+                    "graph of ~134 launches, so the time is set by launch latency, not HBM",
+            "persistent_single_cta": persistent}
 
 
 def run_subworkloads(args):
@@ -905,6 +944,64 @@ def run_qp(args):
                                     tape_bytes=blocks * (64 + 8 * 2 * (n + m)),
                                     backward_launches=back_launches,
                                     dc_rel_diff_vs_implicit_adjoint=rel)
+    # the forward iteration against its roofline: kernel time per iteration from
+    # one profiled solve (CUDA events, no graphs) and wall time per iteration of
+    # the graph-replayed loop (two fixed-length solves, so preparation cancels);
+    # the difference is the launch overhead the graphs leave
+    h = C.mpax_qp_create_diag_lowrank(
+        m, n, dev["row_ptr"], dev["col"], dev["val"], dev["c"], dev["lc"], dev["uc"], dev["l"],
+        dev["u"], dev["D"], d["f_cols"], dev["f_row_ptr"], dev["f_col"], dev["f_val"])
+    try:
+        fixed = dict(precision=C.MPAX_PREC_MIXED, eps_abs=1e-13, eps_rel=1e-13,
+                     fp64_continuation=0, stall_checks=10**6)
+        walls = {}
+        for lim in (1024, 3072):
+            o = C.mpax_options_default(iteration_limit=lim, **fixed)
+            C.mpax_solve(h, o)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record()
+            C.mpax_solve(h, o)
+            f1.record()
+            torch.cuda.synchronize()
+            assert C.mpax_get_stats(h)["iterations"] == lim
+            walls[lim] = f0.elapsed_time(f1) / 1e3
+        C.mpax_solve(h, C.mpax_options_default(iteration_limit=1024, profile_kernels=1, **fixed))
+        ps = C.mpax_get_stats(h)
+    finally:
+        C.mpax_destroy(h)
+    its = ps["iterations"]
+    avg = [ps["profile_ms"][i] / max(1, ps["profile_launches"][i]) / 1e3 for i in range(2)]
+    avg_aux = ps["profile_ms_aux"] / max(1, ps["profile_launches_aux"]) / 1e3
+    kkt_it = (ps["profile_ms"][2] + ps["profile_ms"][3]) / 1e3 / its
+    kern_it = avg[0] + avg[1] + avg_aux + kkt_it
+    wall_it = (walls[3072] - walls[1024]) / 2048
+    qb = qp_algorithmic_bytes(m, n, int(d["row_ptr"][-1]), int(d["f_row_ptr"][-1]), d["f_cols"])
+    pk, pk_src = peaks()
+    roof = {"bound": "hbm", "achieved": qb["primal"] / avg[0] / 1e9, "peak": pk, "unit": "GB/s",
+            "frac": qb["primal"] / avg[0] / 1e9 / pk, "traffic": None,
+            "kernel": "spmv_fused<primal QP, float> (A^T rows + F rows + projection)",
+            "algorithmic_bytes_per_launch": qb["primal"], "avg_launch_us": avg[0] * 1e6,
+            "peak_source": pk_src + ", of measured",
+            "dual": {"avg_launch_us": avg[1] * 1e6, "frac": qb["dual"] / avg[1] / 1e9 / pk},
+            "aux_F^T x_md": {"avg_launch_us": avg_aux * 1e6,
+                             "frac": qb["aux"] / avg_aux / 1e9 / pk},
+            "iteration": {"algorithmic_bytes": qb["total"],
+                          "kernel_us_isolated": kern_it * 1e6, "wall_us": wall_it * 1e6,
+                          "frac_of_wall": qb["total"] / wall_it / 1e9 / pk,
+                          "graph_launch_overhead_us": max(0.0, wall_it - kern_it) * 1e6,
+                          "overlap_us": max(0.0, kern_it - wall_it) * 1e6,
+                          "launches": 3,
+                          "note": "kernel_us_isolated: the three products of an iteration "
+                                  "plus the KKT products of the checks (every 64 iterations), "
+                                  "each timed alone with CUDA events, no graphs (so each "
+                                  "carries its own start-up); wall_us: the graph-replayed "
+                                  "loop, where programmatic dependent launch starts each "
+                                  "product during the previous one's tail. overhead = wall - "
+                                  "isolated when positive, overlap = isolated - wall "
+                                  "otherwise"}}
+    out["mixed"]["roofline"] = roof
     line = {"metric": "differentiable QP forward (rel KKT 1e-4) + backward steps/s",
             "value": out["mixed"]["steps_per_s"], "unit": "steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["mixed"]["ms_per_step"],
@@ -912,6 +1009,7 @@ def run_qp(args):
             "data": "synthetic",
             "config": {"workload": f"QP n={n} m={m}, Q = diag(U[0.1,1]) + F F^T (F n x 32, 1%), "
                                    f"A 0.01% N(0,1), box [-1,1], b = A x0; loss 1/2||x*-x_t||^2"},
+            "roofline": out["mixed"]["roofline"],
             "mixed": out["mixed"], "fp64": out["fp64"], "unrolled_fp64": out["unrolled_fp64"],
             "speedup_vs_fp64": out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"],
             "clocks": out["mixed"]["clocks"], "gpu_launches": out["mixed"]["gpu_launches"]}
@@ -1053,14 +1151,12 @@ def main():
     args = parse()
     single = {"next_rows_20k": run_next_rows, "ragged_lp_4096": run_batch,
               "shared_dense_512": run_shared, "qp_200k": run_qp,
-              "knapsack_1000x100000": run_knapsack}
+              "knapsack_1000x100000": run_knapsack, "small_lp_200x400": run_small_lp}
     if args.profile_run:
         return run_profile_target(args)
     if args.workload in single:
         print(json.dumps(single[args.workload](args)), flush=True)
         return 0
-    if args.profile_run:
-        return run_profile_target(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -152,6 +152,13 @@ typedef struct mpax_options {
                                  kind must beat 0 by 3%), cached for the process
                                  by matrix signature (rows, columns, nnz, LP or
                                  QP, precision, histogram of log2 row lengths) */
+  int32_t batch_stage;        /* 1.  Ragged batch (mpax_batch_solve) with at most one
+                                 instance per SM: an instance whose matrices, scaled
+                                 data and iterates fit in 200 KB of shared memory is
+                                 copied there whole and iterates without global-memory
+                                 traffic.  0, or more instances than SMs: only each
+                                 instance's two gathered vectors and row pointers are
+                                 staged.  Results are identical bit for bit. */
 } mpax_options;
 
 typedef struct mpax_stats {
@@ -178,6 +185,10 @@ typedef struct mpax_stats {
   double spmv_tune_us[6];            /* autotuner timings of the last prepare that timed:
                                         A kinds 0, 1, 2, then A^T kinds 0, 1, 2
                                         (microseconds per launch; 0 = not timed) */
+  /* profile_kernels = 1, QP only: the same for the product ahead of the primal
+   * half-step (F~^T x_md for Q = D + F F^T, Q~ x_md for a general Q) */
+  double profile_ms_aux;
+  int64_t profile_launches_aux;
 } mpax_stats;
 
 typedef struct mpax_problem mpax_problem;

@@ -408,6 +408,8 @@ mpax_status check_options(const mpax_options* o) {
     return fail(MPAX_ERR_INVALID_ARGUMENT, "stall_checks must be >= 1");
   if (o->spmv_kernel < -1 || o->spmv_kernel >= kSpmvKinds)
     return fail(MPAX_ERR_INVALID_ARGUMENT, "spmv_kernel must be -1, 0, 1 or 2");
+  if (o->batch_stage != 0 && o->batch_stage != 1)
+    return fail(MPAX_ERR_INVALID_ARGUMENT, "batch_stage must be 0 or 1");
   if (o->record_tape && o->precision != MPAX_PREC_FP64)
     return fail(MPAX_ERR_UNSUPPORTED, "record_tape needs precision FP64");
   return MPAX_OK;
@@ -529,6 +531,7 @@ void mpax_options_default(mpax_options* o) {
   o->stall_checks = 8;
   o->record_tape = 0;
   o->spmv_kernel = -1;
+  o->batch_stage = 1;
 }
 
 mpax_status mpax_lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
@@ -680,7 +683,7 @@ mpax_status mpax_solve(mpax_problem* pb, const mpax_options* opts, const double*
     info64.restarts += info.restarts;
     info64.checks += info.checks;
     info64.launches += info.launches;
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 5; ++i) {
       info64.profile_ms[i] += info.profile_ms[i];
       info64.profile_launches[i] += info.profile_launches[i];
     }
@@ -748,6 +751,8 @@ mpax_status mpax_solve(mpax_problem* pb, const mpax_options* opts, const double*
     S.profile_ms[i] = info.profile_ms[i];
     S.profile_launches[i] = info.profile_launches[i];
   }
+  S.profile_ms_aux = info.profile_ms[4];
+  S.profile_launches_aux = info.profile_launches[4];
   S.fp64_iterations = fp64_iters;
   S.polish_iterations = polish_iters;
   eng->tune_info(S.spmv_kernel, S.spmv_tune_us);

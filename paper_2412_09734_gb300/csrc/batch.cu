@@ -96,6 +96,7 @@ struct BatchArgs {
   int warm;         // 1: start from the returned points (xout, yout) instead of zero
   double power_cap; // certified bound on ||A~_b||_2 (1 after Pock-Chambolle, else inf)
   int stall_limit;  // > 0: end an instance whose KKT error stops improving (FP32 floor)
+  long long stage_cap;  // bytes of the shared pool an instance may stage whole (0: none)
 };
 
 __device__ __forceinline__ double bsum(double v, double* sh) {
@@ -163,7 +164,55 @@ __device__ __forceinline__ void rows_dot(const int* pp, const int* pe, const T* 
   }
 }
 
-template <typename T>
+// Shared-memory pool of an instance run with kStage (T elements, then ints):
+// ys[mb] xs[nb] val[z] valt[z] c l u w xa xhat gbuf [nb each] lc uc ya yhat [mb each]
+// | rp[mb+1] rpt[nb+1] col[z] colt[z], z the instance's nonzeros.
+__host__ __device__ __forceinline__ long long stage_bytes(long long mb, long long nb, long long z,
+                                                          int tsize) {
+  return tsize * (5 * mb + 8 * nb + 2 * z) + 4 * (mb + nb + 2 + 2 * z);
+}
+
+// The arrays of one instance as the loop reads them.  Row pointers index val()
+// and col() (global offsets in place, local ones when staged); columns hold
+// global indices (less n0 for A, m0 for A^T); vectors are indexed locally.  In
+// place, every array is the kernel parameter's pointer plus the instance offset
+// (no register holds it); staged, it is the pool position that mb, nb and z fix.
+template <typename T, bool kStage>
+struct Inst {
+  const BatchArgs<T>& a;
+  int m0, n0, mb, nb, z;
+  const int *rp, *rpt;
+  T* sp;  // staged: the pool after ys and xs
+#define MPAX_INST_ARR(Type, name, staged, inplace) \
+  __device__ __forceinline__ Type* name() const {    \
+    if constexpr (kStage) return staged;             \
+    else return inplace;                             \
+  }
+  MPAX_INST_ARR(const T, val, sp, a.val)
+  MPAX_INST_ARR(const T, valt, sp + z, a.valt)
+  MPAX_INST_ARR(const T, c, sp + 2 * z, a.c + n0)
+  MPAX_INST_ARR(const T, l, sp + 2 * z + nb, a.l + n0)
+  MPAX_INST_ARR(const T, u, sp + 2 * z + 2 * nb, a.u + n0)
+  MPAX_INST_ARR(T, w, sp + 2 * z + 3 * nb, a.w + n0)
+  MPAX_INST_ARR(T, xa, sp + 2 * z + 4 * nb, a.xa + n0)
+  MPAX_INST_ARR(T, xhat, sp + 2 * z + 5 * nb, a.xhat + n0)
+  MPAX_INST_ARR(T, gbuf, sp + 2 * z + 6 * nb, a.gbuf + n0)
+  MPAX_INST_ARR(const T, lc, sp + 2 * z + 7 * nb, a.lc + m0)
+  MPAX_INST_ARR(const T, uc, sp + 2 * z + 7 * nb + mb, a.uc + m0)
+  MPAX_INST_ARR(T, ya, sp + 2 * z + 7 * nb + 2 * mb, a.ya + m0)
+  MPAX_INST_ARR(T, yhat, sp + 2 * z + 7 * nb + 3 * mb, a.yhat + m0)
+  MPAX_INST_ARR(int, srp, reinterpret_cast<int*>(sp + 2 * z + 7 * nb + 4 * mb), nullptr)
+  MPAX_INST_ARR(const int, col, srp() + (mb + 1) + (nb + 1), a.col)
+  MPAX_INST_ARR(const int, colt, srp() + (mb + 1) + (nb + 1) + z, a.colt)
+#undef MPAX_INST_ARR
+};
+
+// kStage: the whole instance -- both matrices, the scaled data and every
+// iterate vector -- is copied into the shared pool first, so the loop touches
+// global memory only at checks (the unscaled data) and at the end.  Otherwise
+// the two gathered vectors sit at ys, xs (shared or global) and the rest is
+// read in place, with the row pointers staged at srp when they fit.
+template <typename T, bool kStage>
 __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* ys, T* xs,
                                                int* srp, double* sh,
                                                unsigned long long t_launch) {
@@ -173,19 +222,55 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
   const int n0 = (int)a.n_off[b], nb = (int)(a.n_off[b + 1] - a.n_off[b]);
   const int grp = threadIdx.x / kLPR, gl = threadIdx.x % kLPR;
   const int G = blockDim.x / kLPR;
-  // Row pointers of A_b and A_b^T: staged in shared memory when they fit (one
-  // global round trip less in every step of a half-step), else read in place.
-  const int* rpl = a.rp + m0;
-  const int* rptl = a.rpt + n0;
-  if (srp) {
+  const int z0 = a.rp[m0];
+  Inst<T, kStage> v{a, m0, n0, mb, nb, a.rp[m0 + mb] - z0, a.rp + m0, a.rpt + n0, xs + nb};
+  if constexpr (kStage) {
+    // ys (the pool's start) and xs = ys + mb come first; copy the rest in
+    const int zt0 = a.rpt[n0];
+    int* srp_a = v.srp();
+    int* srp_t = srp_a + (mb + 1);
+    T* sval = const_cast<T*>(v.val());
+    T* svalt = const_cast<T*>(v.valt());
+    int* scol = const_cast<int*>(v.col());
+    int* scolt = const_cast<int*>(v.colt());
+    for (int i = threadIdx.x; i <= mb; i += blockDim.x) srp_a[i] = a.rp[m0 + i] - z0;
+    for (int j = threadIdx.x; j <= nb; j += blockDim.x) srp_t[j] = a.rpt[n0 + j] - zt0;
+    for (int p = threadIdx.x; p < v.z; p += blockDim.x) {
+      sval[p] = a.val[z0 + p];
+      scol[p] = a.col[z0 + p];
+      svalt[p] = a.valt[zt0 + p];
+      scolt[p] = a.colt[zt0 + p];
+    }
+    T* sc = const_cast<T*>(v.c());
+    T* sl = const_cast<T*>(v.l());
+    T* su = const_cast<T*>(v.u());
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+      sc[j] = a.c[n0 + j];
+      sl[j] = a.l[n0 + j];
+      su[j] = a.u[n0 + j];
+    }
+    T* slc = const_cast<T*>(v.lc());
+    T* suc = const_cast<T*>(v.uc());
+    for (int i = threadIdx.x; i < mb; i += blockDim.x) {
+      slc[i] = a.lc[m0 + i];
+      suc[i] = a.uc[m0 + i];
+    }
+    __syncthreads();
+    v.rp = srp_a;
+    v.rpt = srp_t;
+  } else if (srp) {
+    // Row pointers of A_b and A_b^T: staged in shared memory when they fit (one
+    // global round trip less in every step of a half-step), else read in place.
     int* sa = srp;
     int* st = srp + (mb + 1);
     for (int i = threadIdx.x; i <= mb; i += blockDim.x) sa[i] = a.rp[m0 + i];
     for (int j = threadIdx.x; j <= nb; j += blockDim.x) st[j] = a.rpt[n0 + j];
     __syncthreads();
-    rpl = sa;
-    rptl = st;
+    v.rp = sa;
+    v.rpt = st;
   }
+  const int* rpl = v.rp;
+  const int* rptl = v.rpt;
 
   // ---- power iteration for ||A~_b||_2 from the common start vector ----------
   double ss0 = 0.0;
@@ -205,7 +290,7 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
       const bool in_i = i < mb;
       T s = 0;
       for (int p = in_i ? rpl[i] + gl : 0; in_i && p < rpl[i + 1]; p += kLPR)
-        s += a.val[p] * xs[a.col[p] - n0];
+        s += v.val()[p] * xs[v.col()[p] - n0];
       s = group_sum(s);
       if (gl == 0 && in_i) ys[i] = s;
     }
@@ -216,10 +301,10 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
       const bool in_j = j < nb;
       T s = 0;
       for (int p = in_j ? rptl[j] + gl : 0; in_j && p < rptl[j + 1]; p += kLPR)
-        s += a.valt[p] * ys[a.colt[p] - m0];
+        s += v.valt()[p] * ys[v.colt()[p] - m0];
       s = group_sum(s);
       if (gl == 0 && in_j) {
-        a.gbuf[n0 + j] = s;
+        v.gbuf()[j] = s;
         acc += (double)s * (double)s;
       }
     }
@@ -229,7 +314,7 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
       break;
     }
     const double nu = sqrt(nrm);
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) xs[j] = (T)((double)a.gbuf[n0 + j] / nrm);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) xs[j] = (T)((double)v.gbuf()[j] / nrm);
     __syncthreads();
     nA = nu;
     double est = nu;
@@ -244,12 +329,12 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
   // ---- initial primal weight, norms of the unscaled data ------------------
   double s_cs = 0, s_bs = 0, s_c = 0, s_b = 0;
   for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-    const double cs = (double)a.c[n0 + j];
+    const double cs = (double)v.c()[j];
     s_cs += cs * cs;
     s_c += a.c0[n0 + j] * a.c0[n0 + j];
   }
   for (int i = threadIdx.x; i < mb; i += blockDim.x) {
-    const double bs = bound_val((double)a.lc[m0 + i], (double)a.uc[m0 + i]);
+    const double bs = bound_val((double)v.lc()[i], (double)v.uc()[i]);
     const double bo = bound_val(a.lc0[m0 + i], a.uc0[m0 + i]);
     s_bs += bs * bs;
     s_b += bo * bo;
@@ -263,16 +348,16 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
   // ---- start at zero, or (warm) at the returned point of an earlier launch,
   // taken back into the scaled space: anchor, reflected point, duals ---------
   for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-    const T v = a.warm ? (T)(a.xout[n0 + j] / a.Dc[n0 + j]) : (T)0;
-    a.xa[n0 + j] = v;
-    a.w[n0 + j] = v;
-    a.xhat[n0 + j] = v;
+    const T x = a.warm ? (T)(a.xout[n0 + j] / a.Dc[n0 + j]) : (T)0;
+    v.xa()[j] = x;
+    v.w()[j] = x;
+    v.xhat()[j] = x;
   }
   for (int i = threadIdx.x; i < mb; i += blockDim.x) {
-    const T v = a.warm ? (T)(a.yout[m0 + i] / a.Dr[m0 + i]) : (T)0;
-    ys[i] = v;
-    a.ya[m0 + i] = v;
-    a.yhat[m0 + i] = v;
+    const T y = a.warm ? (T)(a.yout[m0 + i] / a.Dr[m0 + i]) : (T)0;
+    ys[i] = y;
+    v.ya()[i] = y;
+    v.yhat()[i] = y;
   }
   __syncthreads();
 
@@ -305,30 +390,30 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
           pe[r] = in ? rptl[jr[r] + 1] : 0;
           sr[r] = 0;
           if (gl == 0 && in) {
-            const int g = n0 + jr[r];
-            x0r[r] = a.xa[g];
-            wr[r] = a.w[g];
-            cr[r] = a.c[g];
-            lr[r] = a.l[g];
-            ur[r] = a.u[g];
+            const int j = jr[r];
+            x0r[r] = v.xa()[j];
+            wr[r] = v.w()[j];
+            cr[r] = v.c()[j];
+            lr[r] = v.l()[j];
+            ur[r] = v.u()[j];
           }
         }
-        rows_dot<T>(pp, pe, a.valt, a.colt, ys, m0, sr);
+        rows_dot<T>(pp, pe, v.valt(), v.colt(), ys, m0, sr);
 #pragma unroll
         for (int r = 0; r < kBR; ++r) sr[r] = group_sum(sr[r]);
         if (gl == 0) {
 #pragma unroll
           for (int r = 0; r < kBR; ++r) {
             if (jr[r] >= nb) continue;
-            const int g = n0 + jr[r];
+            const int j = jr[r];
             const T x0 = x0r[r], wv = wr[r];
             const T x = (k == 0) ? x0 : wv + rb * (x0 - wv);
             const T xh = clampv<T>(x - tt * (cr[r] - sr[r]), lr[r], ur[r]);
             const T wn = (T)2 * xh - x;
-            a.w[g] = wn;
-            xs[jr[r]] = wn;
+            v.w()[j] = wn;
+            xs[j] = wn;
             if (chk) {
-              a.xhat[g] = xh;
+              v.xhat()[j] = xh;
               const double d0 = (double)xh - (double)x, d1 = (double)xh - (double)x0;
               P0 += d0 * d0;
               P1 += d1 * d1;
@@ -350,27 +435,27 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
           pe[r] = in ? rpl[ir[r] + 1] : 0;
           sr[r] = 0;
           if (gl == 0 && in) {
-            const int g = m0 + ir[r];
-            yar[r] = a.ya[g];
-            lcr[r] = a.lc[g];
-            ucr[r] = a.uc[g];
+            const int i = ir[r];
+            yar[r] = v.ya()[i];
+            lcr[r] = v.lc()[i];
+            ucr[r] = v.uc()[i];
           }
         }
-        rows_dot<T>(pp, pe, a.val, a.col, xs, n0, sr);
+        rows_dot<T>(pp, pe, v.val(), v.col(), xs, n0, sr);
 #pragma unroll
         for (int r = 0; r < kBR; ++r) sr[r] = group_sum(sr[r]);
         if (gl == 0) {
 #pragma unroll
           for (int r = 0; r < kBR; ++r) {
             if (ir[r] >= mb) continue;
-            const int g = m0 + ir[r];
-            const T y0 = ys[ir[r]], y0a = yar[r];
-            const T v = y0 * iss - sr[r];
-            const T yh = ss * (v - clampv<T>(v, -ucr[r], -lcr[r]));
+            const int i = ir[r];
+            const T y0 = ys[i], y0a = yar[r];
+            const T t = y0 * iss - sr[r];
+            const T yh = ss * (t - clampv<T>(t, -ucr[r], -lcr[r]));
             const T z = (T)2 * yh - y0;
-            ys[ir[r]] = z + hb * (y0a - z);
+            ys[i] = z + hb * (y0a - z);
             if (chk) {
-              a.yhat[g] = yh;
+              v.yhat()[i] = yh;
               const double d0 = (double)yh - (double)y0, d1 = (double)yh - (double)y0a;
               D0 += d0 * d0;
               D1 += d1 * d1;
@@ -383,7 +468,7 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
       ++total;
     }
     // ---- check: relative KKT error of (x^, y^) on the unscaled problem ----
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) xs[j] = a.xhat[n0 + j];
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) xs[j] = v.xhat()[j];
     __syncthreads();
     double K0 = 0, K1 = 0, C0 = 0, C1 = 0, C2 = 0;
     for (int i0 = 0; i0 < mb; i0 += G) {
@@ -391,7 +476,7 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
       const bool in_i = i < mb;
       T s = 0;
       for (int p = in_i ? rpl[i] + gl : 0; in_i && p < rpl[i + 1]; p += kLPR)
-        s += a.val[p] * xs[a.col[p] - n0];
+        s += v.val()[p] * xs[v.col()[p] - n0];
       s = group_sum(s);
       if (gl == 0 && in_i) {
         const int g = m0 + i;
@@ -399,7 +484,7 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
         const double lo = a.lc0[g], hi = a.uc0[g];
         const double r = ax - fmin(fmax(ax, lo), hi);
         K0 += r * r;
-        const double y = a.Dr[g] * (double)a.yhat[g];
+        const double y = a.Dr[g] * (double)v.yhat()[i];
         if (y > 0.0 && isfinite(lo)) K1 += lo * y;
         if (y < 0.0 && isfinite(hi)) K1 += hi * y;
       }
@@ -409,7 +494,7 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
       const bool in_j = j < nb;
       T s = 0;
       for (int p = in_j ? rptl[j] + gl : 0; in_j && p < rptl[j + 1]; p += kLPR)
-        s += a.valt[p] * a.yhat[a.colt[p]];
+        s += v.valt()[p] * v.yhat()[v.colt()[p] - m0];
       s = group_sum(s);
       if (gl == 0 && in_j) {
         const int g = n0 + j;
@@ -485,14 +570,14 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
       k = 0;
       ++restarts;
       for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        const T v = a.xhat[n0 + j];
-        a.xa[n0 + j] = v;
-        a.w[n0 + j] = v;
+        const T x = v.xhat()[j];
+        v.xa()[j] = x;
+        v.w()[j] = x;
       }
       for (int i = threadIdx.x; i < mb; i += blockDim.x) {
-        const T v = a.yhat[m0 + i];
-        a.ya[m0 + i] = v;
-        ys[i] = v;
+        const T y = v.yhat()[i];
+        v.ya()[i] = y;
+        ys[i] = y;
       }
     } else {
       r_prev = r;
@@ -501,9 +586,9 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
   }
   // ---- returned point (x^, y^), unscaled; per-instance statistics ---------
   for (int j = threadIdx.x; j < nb; j += blockDim.x)
-    a.xout[n0 + j] = a.Dc[n0 + j] * (double)a.xhat[n0 + j];
+    a.xout[n0 + j] = a.Dc[n0 + j] * (double)v.xhat()[j];
   for (int i = threadIdx.x; i < mb; i += blockDim.x)
-    a.yout[m0 + i] = a.Dr[m0 + i] * (double)a.yhat[m0 + i];
+    a.yout[m0 + i] = a.Dr[m0 + i] * (double)v.yhat()[i];
   if (threadIdx.x == 0) {
     // a warm launch continues an instance: its counts and time add to the earlier ones
     a.status[b] = term;
@@ -516,7 +601,9 @@ __device__ __forceinline__ void solve_instance(const BatchArgs<T>& a, int b, T* 
   __syncthreads();
 }
 
-template <typename T>
+// kStaging: the launch may stage whole instances (a separate instantiation, so
+// that the many-instance kernel carries only the two in-place call sites).
+template <typename T, bool kStaging>
 __global__ void __launch_bounds__(kBatchThreads, 2) batch_lp_kernel(BatchArgs<T> a) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ double sh[32];
@@ -532,11 +619,24 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_lp_kernel(BatchArgs<T>
     if (w >= a.n_todo) return;
     const int b = a.todo ? a.todo[w] : w;
     const int mb = (int)(a.m_off[b + 1] - a.m_off[b]), nb = (int)(a.n_off[b + 1] - a.n_off[b]);
+    const int z = a.rp[a.m_off[b + 1]] - a.rp[a.m_off[b]];
     int* srp = (mb + nb + 2 <= a.rp_cap) ? rpool : nullptr;
-    // two call sites: the shared-memory one keeps shared loads for the gathers
-    if (mb + nb <= a.smem_vec) solve_instance<T>(a, b, pool, pool + mb, srp, sh, t_launch);
-    else solve_instance<T>(a, b, a.gys + a.m_off[b], a.gxs + a.n_off[b], srp, sh, t_launch);
+    // three call sites: the whole instance in shared memory; its two gathered
+    // vectors in shared memory (shared loads for the gathers); everything global
+    if (kStaging && stage_bytes(mb, nb, z, (int)sizeof(T)) <= a.stage_cap)
+      solve_instance<T, true>(a, b, pool, pool + mb, nullptr, sh, t_launch);
+    else if (mb + nb <= a.smem_vec)
+      solve_instance<T, false>(a, b, pool, pool + mb, srp, sh, t_launch);
+    else
+      solve_instance<T, false>(a, b, a.gys + a.m_off[b], a.gxs + a.n_off[b], srp, sh, t_launch);
   }
+}
+
+// z[b] = rp[m_off[b]], b = 0..B
+__global__ void k_first_nnz(const long long* __restrict__ rp, const long long* __restrict__ m_off,
+                            int B, long long* __restrict__ z) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b <= B) z[b] = rp[m_off[b]];
 }
 
 // row -> instance via binary search in m_off; global column = n_off[b] + local
@@ -624,6 +724,7 @@ struct mpax_batch {
   long long* m_off = nullptr;  // device
   long long* n_off = nullptr;
   std::vector<long long> h_moff, h_noff;
+  std::vector<long long> h_zoff;  // row_ptr at each instance's first row
   int max_m = 0, max_n = 0;
   int* next = nullptr;
   int* status = nullptr;
@@ -658,6 +759,12 @@ mpax_status bfail(mpax_status s, const std::string& m) {
 // Bytes of shared memory an instance's two vectors may take (larger instances
 // keep them in global memory).
 constexpr long long kBatchVecBytes = 200 * 1024;
+// Shared-memory bytes an instance may stage whole (matrices, data and iterates)
+// when the launch has at most one instance per SM.  With more instances nothing
+// is staged whole: a pool of that size shrinks the L1 share of every CTA, and
+// on 4096 instances of the ragged recipe (about 15% small enough at 100 KB)
+// the batch took 0.57 s against 0.35 s without.
+constexpr long long kStageFew = 200 * 1024;
 
 template <typename T>
 mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches,
@@ -768,19 +875,31 @@ mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches
   a.rp_cap = (MPAX_BATCH_SMEM_RP && smem + sizeof(int) * (size_t)rmax <= 100 * 1024)
                  ? (int)rmax : 0;
   smem += sizeof(int) * (size_t)a.rp_cap;
-  cudaFuncSetAttribute(batch_lp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
   int occ = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_lp_kernel<T>, kBatchThreads, smem);
+  // whole-instance staging when every instance of the launch has an SM of its own
+  const long long cap = (o->batch_stage && n_todo <= sms) ? kStageFew : 0;
+  long long smax = 0;
+  for (int w = 0; w < n_todo; ++w) {
+    const int b = todo_host ? todo_host[w] : w;
+    const long long need = stage_bytes(bt->h_moff[b + 1] - bt->h_moff[b],
+                                       bt->h_noff[b + 1] - bt->h_noff[b],
+                                       bt->h_zoff[b + 1] - bt->h_zoff[b], (int)sizeof(T));
+    if (need <= cap) smax = std::max(smax, need);
+  }
+  a.stage_cap = smax;
+  smem = std::max(smem, (size_t)((smax + 15) / 16 * 16));
+  auto kernel = smax > 0 ? batch_lp_kernel<T, true> : batch_lp_kernel<T, false>;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kBatchThreads, smem);
   a.todo = todo;
   a.n_todo = n_todo;
   a.warm = warm;
   a.stall_limit = stall_limit;
   const int grid = std::min(n_todo, std::max(1, occ) * sms);
   cudaMemsetAsync(bt->next, 0, sizeof(int), s);
-  batch_lp_kernel<T><<<grid, kBatchThreads, smem, s>>>(a);
+  kernel<<<grid, kBatchThreads, smem, s>>>(a);
   *launches += 1;
   if ((e = cudaGetLastError())) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
   return MPAX_OK;
@@ -831,6 +950,13 @@ mpax_status mpax_lp_batch_create(int32_t B, const int64_t* m_off, const int64_t*
   const cudaMemcpyKind kin = kind == MPAX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   if (!e) e = cudaMemcpy(d_rp, row_ptr, sizeof(long long) * (m + 1), kin);
   if (!e && nnz > 0) e = cudaMemcpy(d_col, col_idx, sizeof(int) * nnz, kin);
+  // row_ptr at each instance's first row (sizes the whole-instance staging)
+  std::vector<long long> hz(B + 1);
+  long long* d_z = nullptr;
+  if (!e) e = cudaMalloc(&d_z, sizeof(long long) * (B + 1));
+  if (!e) k_first_nnz<<<(B + 256) / 256, 256>>>(d_rp, d_moff, B, d_z);
+  if (!e) e = cudaMemcpy(hz.data(), d_z, sizeof(long long) * (B + 1), cudaMemcpyDeviceToHost);
+  if (d_z) cudaFree(d_z);
   if (!e) e = cudaMemset(flags, 0, sizeof(int));
   if (!e && m > 0) k_globalize_cols<<<(m + 255) / 256, 256>>>(d_moff, d_noff, B, d_rp, m, d_col, flags);
   int hf = 0;
@@ -886,6 +1012,7 @@ mpax_status mpax_lp_batch_create(int32_t B, const int64_t* m_off, const int64_t*
   bt->n_off = d_noff;
   bt->h_moff = hm;
   bt->h_noff = hn;
+  bt->h_zoff = hz;
   bt->max_m = max_m;
   bt->max_n = max_n;
   if (e) {
@@ -903,7 +1030,7 @@ mpax_status mpax_batch_solve(mpax_batch* bt, const mpax_options* o) {
   if (o->check_every < 1 || o->iteration_limit < 1 || o->ruiz_iters < 0 ||
       !(o->step_safety > 0 && o->step_safety < 1) || o->power_max_iter < 0 ||
       (o->power_max_iter == 0 && !o->pock_chambolle) ||
-      !(o->time_limit >= 0))
+      !(o->time_limit >= 0) || (o->batch_stage != 0 && o->batch_stage != 1))
     return bfail(MPAX_ERR_INVALID_ARGUMENT, "invalid options");
   if (o->precision != MPAX_PREC_FP64 && o->precision != MPAX_PREC_MIXED)
     return bfail(MPAX_ERR_INVALID_ARGUMENT, "bad precision");

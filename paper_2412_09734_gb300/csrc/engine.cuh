@@ -10,8 +10,10 @@ struct RunInfo {
   int termination = 0;
   long long iterations = 0, restarts = 0, checks = 0;
   long long launches = 0;
-  double profile_ms[4] = {0, 0, 0, 0};
-  long long profile_launches[4] = {0, 0, 0, 0};
+  // [0] primal, [1] dual, [2] KKT SpMV, [3] KKT SpMV^T, [4] QP product ahead of
+  // the primal half-step
+  double profile_ms[5] = {0, 0, 0, 0, 0};
+  long long profile_launches[5] = {0, 0, 0, 0, 0};
   bool time_limit_hit = false;
 };
 

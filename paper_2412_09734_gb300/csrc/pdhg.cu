@@ -961,12 +961,16 @@ class Engine final : public EngineBase {
       } else {
         if (P.f_nnz > 0) {
           EpiStore<T> eu{&st_->done, uvec_, nullptr, nullptr, nullptr, nullptr, 0};
+          prof_begin(prof, 4);
           launch_spmv<T>(P.schedFt, P.Ft, ftval_, InMomentum<T>{x_, xavg_, st_, it}, eu, 0, s);
+          prof_end(prof, 4);
           launches_ += 1;
         }
         if (P.q_general) {
           EpiStore<T> eq{&st_->done, qvec_, nullptr, nullptr, nullptr, nullptr, 0};
+          prof_begin(prof, 4);
           launch_spmv<T>(P.schedQ, P.Q, qv_, InMomentum<T>{x_, xavg_, st_, it}, eq, 0, s);
+          prof_end(prof, 4);
           launches_ += 1;
         }
         EpiPrimalQP<T> ep{st_, x_,  xavg_,    xref_,    xanc_,  c_,     l_,    u_,

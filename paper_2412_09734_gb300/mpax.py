@@ -67,6 +67,7 @@ class Options(ctypes.Structure):
         ("use_graphs", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
         ("fp64_continuation", ctypes.c_int32), ("stall_checks", ctypes.c_int32),
         ("record_tape", ctypes.c_int32), ("spmv_kernel", ctypes.c_int32),
+        ("batch_stage", ctypes.c_int32),
     ]
 
 
@@ -86,6 +87,7 @@ class Stats(ctypes.Structure):
         ("fp64_iterations", ctypes.c_int64), ("polish_iterations", ctypes.c_int64),
         ("backward_launches", ctypes.c_int64),
         ("spmv_kernel", ctypes.c_int32 * 2), ("spmv_tune_us", ctypes.c_double * 6),
+        ("profile_ms_aux", ctypes.c_double), ("profile_launches_aux", ctypes.c_int64),
     ]
 
     def as_dict(self):

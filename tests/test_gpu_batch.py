@@ -313,3 +313,44 @@ def test_batch_fp64_continuation_of_an_instance_beyond_shared_memory(C):
     assert summary["fp64_instances"] >= 1
     assert summary["n_optimal"] == d["B"]
     _check_batch(d, x, y, per, eps)
+
+
+@pytest.mark.parametrize("many", [False, True], ids=["one_per_sm", "many_per_sm"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_whole_instance_staging_gives_identical_bits(C, prec, many):
+    """batch_stage = 1 copies every instance that fits (both matrices, data and
+    iterates) into shared memory before it iterates when each instance has an
+    SM (6 instances here); the arithmetic and its order are those of the
+    in-place path, so a fixed number of iterations (checks, restarts and
+    primal-weight updates included) gives the same bits.  With 200 instances
+    (more than the SMs) nothing is staged whole and the option changes nothing."""
+    if many:
+        d = ragged_lp_batch(200, seed=5151, m_lo=20, m_hi=300, density=0.05)
+    else:
+        d = _iterate_batch()
+    out = []
+    for stage in (1, 0):
+        h = _create(C, d)
+        try:
+            C.mpax_batch_solve(h, C.mpax_options_default(precision=prec, iteration_limit=320,
+                                                         eps_abs=1e-14, eps_rel=1e-14,
+                                                         batch_stage=stage))
+            summary, per = C.mpax_batch_get_stats(h, d["B"])
+            x, y = C.mpax_batch_get_solution(h, int(d["m_off"][-1]), int(d["n_off"][-1]))
+        finally:
+            C.mpax_batch_destroy(h)
+        out.append((x, y, per["iterations"], summary["restarts_total"]))
+    (x1, y1, i1, r1), (x0, y0, i0, r0) = out
+    assert np.array_equal(i1, i0) and r1 == r0
+    assert np.array_equal(x1, x0)
+    assert np.array_equal(y1, y0)
+
+
+def test_batch_stage_option_is_validated(C):
+    d = ragged_lp_batch(2, seed=5152, m_lo=20, m_hi=40, density=0.05)
+    h = _create(C, d)
+    try:
+        with pytest.raises(C.MpaxError):
+            C.mpax_batch_solve(h, C.mpax_options_default(batch_stage=2))
+    finally:
+        C.mpax_batch_destroy(h)
