@@ -170,3 +170,42 @@ def test_lp_value_layer_autograd(C):
     v.backward()
     assert float(v) == pytest.approx(d["opt_value"], rel=1e-8)
     np.testing.assert_allclose(c.grad.cpu().numpy(), d["x0"], atol=1e-6)
+
+
+def test_qp_adjoint_solves_its_system_at_full_size(C):
+    """The 200k-variable QP of the bench (n = 200,000, m = 100,000, Q = D + F F^T
+    with F 200,000 x 32): a direct solve of the adjoint system is out of reach there
+    (F F^T alone holds ~1.3e8 nonzeros), so the returned adjoint is checked against
+    the system itself, assembled on the host from the problem data.  With F, R the
+    active sets of the oracle's rule at the returned point (Sec. 3.4, the same
+    thresholds as the library), w = -dc_F and v = db_R must satisfy
+        Q_FF w + A_RF^T v = g_F,   A_RF w = 0
+    to the solve's tolerance, dc and db must vanish outside F and R, and
+    dD = -w x on F."""
+    import scipy.sparse as sp
+    d = qp_instance(200_000, 100_000, seed=instance_seed(3), a_density=1e-4, f_cols=32,
+                    f_density=0.01)
+    m, n = d["m"], d["n"]
+    h = create(C, d)
+    try:
+        C.mpax_solve(h, C.mpax_options_default(precision=C.MPAX_PREC_MIXED))
+        x, y = C.mpax_get_solution(h, m, n)
+        g = x - d["x_target"]
+        dc, db, dD, info = C.mpax_qp_adjoint(h, g, m, n, tol=1e-10, max_iter=20000)
+    finally:
+        C.mpax_destroy(h)
+    assert info["rel_residual"] <= 1e-10
+    p = O.problem_from_arrays(d)
+    free, rows = AD.active_sets(p, x, y, 1e-7, 1e-7)
+    assert not np.any(dc[~free]) and not np.any(db[~rows]) and not np.any(dD[~free])
+    A = sp.csr_matrix((d["val"], d["col"], d["row_ptr"]), shape=(m, n))
+    F = sp.csr_matrix((d["f_val"], d["f_col"], d["f_row_ptr"]), shape=(n, d["f_cols"]))
+    Fi, Ri = np.flatnonzero(free), np.flatnonzero(rows)
+    w, v = -dc[Fi], db[Ri]
+    ARF = A[Ri][:, Fi]
+    FF = F[Fi]
+    top = d["D"][Fi] * w + FF @ (FF.T @ w) + ARF.T @ v - g[Fi]
+    bot = ARF @ w
+    scale = np.linalg.norm(g[Fi])
+    assert np.linalg.norm(np.concatenate([top, bot])) <= 1e-6 * scale
+    np.testing.assert_array_equal(dD[Fi], -w * x[Fi])
