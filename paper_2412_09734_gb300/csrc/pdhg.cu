@@ -1336,6 +1336,12 @@ class Engine final : public EngineBase {
       // One block backwards: every launch reads its block's scalars from the
       // device state, so the sequence is captured once per block length as a
       // CUDA graph and replayed for every block.
+      // The reverse epilogues carry more state than the forward ones: in FP64 the
+      // default register budget (the forward kind the tuner may keep) spills them,
+      // so the reverse products run with the wide budget instead.
+      Sched sAtRev = P.schedAt, sARev = P.schedA;
+      if (sizeof(T) == 8 && sAtRev.kind == kSpmvItem) sAtRev.kind = kSpmvItemWide;
+      if (sizeof(T) == 8 && sARev.kind == kSpmvItem) sARev.kind = kSpmvItemWide;
       auto rev_block = [&](int L) {
         k_tape_open<<<1, 256, 0, s>>>(st_, tape_tab_);
         k_tape_restore<T><<<gN, 256, 0, s>>>(st_, tape_tab_, n, m, x_, xavg_, y_, yavg_, ax,
@@ -1351,7 +1357,7 @@ class Engine final : public EngineBase {
           EpiRevPrimal<T> ep{st_, ax, axa, uu, gc, gl, gu, gD, cx + (size_t)it * nn, Ds_,
                              P.F.rp, P.F.col, fval_, tq,
                              it < L - 1 ? xmd + (size_t)(it + 1) * nn : nullptr, it, 0, qu};
-          launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{ws}, ep, 0, s);
+          launch_spmv<T>(sAtRev, P.At, valAt_, InPlain<T>{ws}, ep, 0, s);
           if (P.f_nnz > 0) {
             EpiStore<T> eu{nullptr, tq, nullptr, nullptr, nullptr, nullptr, 0};
             launch_spmv<T>(P.schedFt, P.Ft, ftval_, InPlain<T>{uu}, eu, 0, s);
@@ -1364,7 +1370,7 @@ class Engine final : public EngineBase {
           }
           EpiRevDual<T> ed{st_, ay, aya, ws, glc, guc,
                            it > 0 ? cy + (size_t)(it - 1) * mm : nullptr, it, 0};
-          launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{uu}, ed, 0, s);
+          launch_spmv<T>(sARev, P.A, valA_, InPlain<T>{uu}, ed, 0, s);
           launches_ += 2;
         }
         k_rev_r4<T><<<grid1(n), 256, 0, s>>>(st_, 0, n, Ds_, P.F.rp, P.F.col, fval_, tq, uu, xmd,
