@@ -100,12 +100,34 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"(size) : "memory");
 }
 
+// Row sums of packed short rows.  FP32: the products are formed lane-parallel
+// into the warp's buffer and one lane adds a row's products in order.  FP64 runs
+// at a small fraction of the FP32 rate on this GPU (its pipe, not memory, bounds
+// the FP64 products), so there the buffer holds the values and, kShortCap
+// further, the gathered inputs, and the row's lane forms one fused multiply-add
+// chain: one FP64 instruction per nonzero instead of a multiply and an add.
+template <typename T>
+constexpr bool kFmaRows = sizeof(T) == 8;
+
+// buf: products (FP32) or values (FP64); bx: the gathered inputs (FP64 only).
+template <typename T>
+__device__ __forceinline__ T packed_row_sum(const T* buf, const T* bx, int q0, int q1) {
+  T s = 0;
+  if constexpr (kFmaRows<T>) {
+    for (int q = q0; q < q1; ++q) s = fma(buf[q], bx[q], s);
+  } else {
+    for (int q = q0; q < q1; ++q) s += buf[q];
+  }
+  return s;
+}
+
 // MINB: resident CTAs per SM asked of the register allocator (the default
 // shape's MPAX_SPMV_MINB, or kSpmvWideMinB: more registers per thread, fewer
 // warps; the FP64 instances of the default shape spill at its 48-register cap).
 template <typename T, class In, class Epi, int MINB = MPAX_SPMV_MINB>
 __global__ void __launch_bounds__(kSpmvBlock, MINB) spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
-  __shared__ T sbuf[kSpmvWarps][kShortCap];
+  // FP64 keeps values and gathered inputs apart (kFmaRows): twice the buffer
+  __shared__ T sbuf[kSpmvWarps][(kFmaRows<T> ? 2 : 1) * kShortCap];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int item = blockIdx.x * kSpmvWarps + wib;
@@ -148,10 +170,18 @@ __global__ void __launch_bounds__(kSpmvBlock, MINB) spmv_fused(SpmvArgs<T> a, In
     epi.pre(sa, pra);
     epi.pre(sb, prb);
     T* buf = sbuf[wib];
+    T* bufx = buf + kShortCap;  // FP64 only: the gathered inputs
 #pragma unroll
     for (int u = 0; u < kShortLoads; ++u) {
       const int q = base + lane + u * kWarp;
-      if (q < end) buf[q - base] = v[u] * in(c[u]);
+      if (q < end) {
+        if constexpr (kFmaRows<T>) {
+          buf[q - base] = v[u];
+          bufx[q - base] = in(c[u]);
+        } else {
+          buf[q - base] = v[u] * in(c[u]);
+        }
+      }
     }
     if (do_pf) {
       int q0, q1;
@@ -160,16 +190,8 @@ __global__ void __launch_bounds__(kSpmvBlock, MINB) spmv_fused(SpmvArgs<T> a, In
       prefetch_l2(a.col + q0, sizeof(int) * (size_t)(q1 - q0));
     }
     __syncwarp();
-    if (ha) {
-      T s = 0;
-      for (int q = pa0; q < pa1; ++q) s += buf[q - base];
-      epi.row(ra, s, pra, acc);
-    }
-    if (hb) {
-      T s = 0;
-      for (int q = pb0; q < pb1; ++q) s += buf[q - base];
-      epi.row(rb, s, prb, acc);
-    }
+    if (ha) epi.row(ra, packed_row_sum<T>(buf, bufx, pa0 - base, pa1 - base), pra, acc);
+    if (hb) epi.row(rb, packed_row_sum<T>(buf, bufx, pb0 - base, pb1 - base), prb, acc);
     if (Epi::NQ > 0 && epi.check) {
 #pragma unroll
       for (int q = 0; q < Epi::NQ; ++q) {
@@ -298,8 +320,12 @@ struct PipeLayout {
   static constexpr int kValCap = kShortCap + 2 * kValV;
   static constexpr int kColCap = kShortCap + 8;
   static constexpr int kStageBytes = kValCap * (int)sizeof(T) + kColCap * 4;
-  static constexpr int kWarpBytes = 2 * kStageBytes + 16;  // two stages + two mbarriers
+  // FP64: the gathered inputs of the current item (see packed_row_sum)
+  static constexpr int kXBytes = kFmaRows<T> ? kShortCap * (int)sizeof(T) : 0;
+  // two stages, the input buffer, two mbarriers
+  static constexpr int kWarpBytes = 2 * kStageBytes + kXBytes + 16;
   static_assert(kStageBytes % 16 == 0, "stage size must keep 16-byte alignment");
+  static_assert(kXBytes % 16 == 0, "input buffer must keep 16-byte alignment");
 };
 
 // Lane 0: stage the values and columns of item `it` (nonzeros [p0, p1)),
@@ -351,7 +377,9 @@ __global__ void __launch_bounds__(kWarp* kPipeWarps, sizeof(T) == 4 ? 5 : 3)
   if (epi.skip()) return;  // read before any copy is issued
   if (*(volatile int*)err) return;  // an earlier wait gave up: the solve reports it
   unsigned char* wsm = pipe_smem + (size_t)wib * L::kWarpBytes;
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(wsm + 2 * L::kStageBytes);
+  T* xbuf = reinterpret_cast<T*>(wsm + 2 * L::kStageBytes);  // FP64 only
+  unsigned long long* bar =
+      reinterpret_cast<unsigned long long*>(wsm + 2 * L::kStageBytes + L::kXBytes);
   unsigned pending = 0;  // bit s: stage s has a copy in flight (lane 0's view)
   if (lane == 0) {
     mbar_init(bar);
@@ -421,22 +449,19 @@ __global__ void __launch_bounds__(kWarp* kPipeWarps, sizeof(T) == 4 ? 5 : 3)
       const int cnt = it.w - base;
       T* buf = sval + (base & (L::kValV - 1));  // buf[q - base] = product q
       const int* cb = scol + (base & 3);
+      // xbuf is rewritten for every item: the previous item's sums have read it
+      if constexpr (kFmaRows<T>) __syncwarp();
 #pragma unroll
       for (int u = 0; u < kShortLoads; ++u) {
         const int q = lane + u * kWarp;
-        if (q < cnt) buf[q] = buf[q] * in(cb[q]);
+        if (q < cnt) {
+          if constexpr (kFmaRows<T>) xbuf[q] = in(cb[q]);
+          else buf[q] = buf[q] * in(cb[q]);
+        }
       }
       __syncwarp();
-      if (ha) {
-        T s = 0;
-        for (int q = pa0; q < pa1; ++q) s += buf[q - base];
-        epi.row(ra, s, pra, acc);
-      }
-      if (hb) {
-        T s = 0;
-        for (int q = pb0; q < pb1; ++q) s += buf[q - base];
-        epi.row(rb, s, prb, acc);
-      }
+      if (ha) epi.row(ra, packed_row_sum<T>(buf, xbuf, pa0 - base, pa1 - base), pra, acc);
+      if (hb) epi.row(rb, packed_row_sum<T>(buf, xbuf, pb0 - base, pb1 - base), prb, acc);
       if (Epi::NQ > 0 && epi.check) {
 #pragma unroll
         for (int q = 0; q < Epi::NQ; ++q) {
