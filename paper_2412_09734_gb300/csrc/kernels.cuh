@@ -121,16 +121,19 @@ __device__ __forceinline__ T packed_row_sum(const T* buf, const T* bx, int q0, i
   return s;
 }
 
-// MINB: resident CTAs per SM asked of the register allocator (the default
-// shape's MPAX_SPMV_MINB, or kSpmvWideMinB: more registers per thread, fewer
-// warps; the FP64 instances of the default shape spill at its 48-register cap).
-template <typename T, class In, class Epi, int MINB = MPAX_SPMV_MINB>
-__global__ void __launch_bounds__(kSpmvBlock, MINB) spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
-  // FP64 keeps values and gathered inputs apart (kFmaRows): twice the buffer
-  __shared__ T sbuf[kSpmvWarps][(kFmaRows<T> ? 2 : 1) * kShortCap];
+// The CTA's staging buffer: one row per warp; FP64 keeps values and gathered
+// inputs apart (kFmaRows), twice the length.
+template <typename T>
+using SpmvBuf = T[kSpmvWarps][(kFmaRows<T> ? 2 : 1) * kShortCap];
+
+// The work of CTA `cta` of a spmv_fused launch over the items of `a`: one item
+// per warp.
+template <typename T, class In, class Epi>
+__device__ __forceinline__ void spmv_fused_cta(const SpmvArgs<T>& a, In& in, Epi& epi, int cta,
+                                               SpmvBuf<T>& sbuf) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int item = blockIdx.x * kSpmvWarps + wib;
+  const int item = cta * kSpmvWarps + wib;
   // The next launch may start its CTAs as this grid drains (programmatic
   // dependent launch); it reads only the constant matrix arrays before its wait.
   pdl_launch_dependents();
@@ -286,6 +289,29 @@ __global__ void __launch_bounds__(kSpmvBlock, MINB) spmv_fused(SpmvArgs<T> a, In
       }
     }
   }
+}
+
+// MINB: resident CTAs per SM asked of the register allocator (the default
+// shape's MPAX_SPMV_MINB, or kSpmvWideMinB: more registers per thread, fewer
+// warps; the FP64 instances of the default shape spill at its 48-register cap).
+template <typename T, class In, class Epi, int MINB = MPAX_SPMV_MINB>
+__global__ void __launch_bounds__(kSpmvBlock, MINB) spmv_fused(SpmvArgs<T> a, In in, Epi epi) {
+  __shared__ SpmvBuf<T> sbuf;
+  spmv_fused_cta<T, In, Epi>(a, in, epi, blockIdx.x, sbuf);
+}
+
+// Two independent products in one launch: CTAs [0, grid1) take the items of
+// (a1, in1, epi1), the others those of (a2, in2, epi2), each item exactly as
+// spmv_fused computes it.  Saves a launch where the second product need not
+// wait for the first (the QP momentum product of the next step beside the dual
+// half-step of this one).
+template <typename T, class In1, class Epi1, class In2, class Epi2, int MINB = MPAX_SPMV_MINB>
+__global__ void __launch_bounds__(kSpmvBlock, MINB)
+    spmv_fused_pair(SpmvArgs<T> a1, In1 in1, Epi1 epi1, int grid1, SpmvArgs<T> a2, In2 in2,
+                    Epi2 epi2) {
+  __shared__ SpmvBuf<T> sbuf;
+  if ((int)blockIdx.x < grid1) spmv_fused_cta<T, In1, Epi1>(a1, in1, epi1, blockIdx.x, sbuf);
+  else spmv_fused_cta<T, In2, Epi2>(a2, in2, epi2, blockIdx.x - grid1, sbuf);
 }
 
 

@@ -942,6 +942,11 @@ class Engine final : public EngineBase {
           st_, tape_tab_, kTapeSlots, P.n, P.m, x_, xavg_, y_, yavg_, len);
       launches_ += 1;
     }
+    // QP: u = F~^T x_md (or Q~ x_md) of step it + 1 depends only on the point the
+    // primal half-step of step it wrote, so it rides in the dual half-step's launch
+    // (two independent schedules, one spmv_fused_pair); the first step of a block
+    // follows a check and a possible restart and launches it on its own.
+    bool aux_ready = false;
     for (int it = 0; it < len; ++it) {
       const bool last = (it == len - 1) && !plain;
       const int rec = (record_all || last) ? 1 : 0;
@@ -959,20 +964,21 @@ class Engine final : public EngineBase {
         prof_end(prof, 1);
         launches_ += 2;
       } else {
-        if (P.f_nnz > 0) {
+        if (P.f_nnz > 0 && !aux_ready) {
           EpiStore<T> eu{&st_->done, uvec_, nullptr, nullptr, nullptr, nullptr, 0};
           prof_begin(prof, 4);
           launch_spmv<T>(P.schedFt, P.Ft, ftval_, InMomentum<T>{x_, xavg_, st_, it}, eu, 0, s);
           prof_end(prof, 4);
           launches_ += 1;
         }
-        if (P.q_general) {
+        if (P.q_general && !aux_ready) {
           EpiStore<T> eq{&st_->done, qvec_, nullptr, nullptr, nullptr, nullptr, 0};
           prof_begin(prof, 4);
           launch_spmv<T>(P.schedQ, P.Q, qv_, InMomentum<T>{x_, xavg_, st_, it}, eq, 0, s);
           prof_end(prof, 4);
           launches_ += 1;
         }
+        aux_ready = false;
         EpiPrimalQP<T> ep{st_, x_,  xavg_,    xref_,    xanc_,  c_,     l_,    u_,
                           Ds_, P.F.rp, P.F.col, fval_, uvec_, xprev_, it,    rec, chk,
                           nullptr, nullptr, P.q_general ? qvec_ : nullptr};
@@ -980,9 +986,25 @@ class Engine final : public EngineBase {
         launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{y_}, ep, 0, s);
         prof_end(prof, 0);
         EpiDualQP<T> ed{st_, y_, yavg_, yanc_, lc_, uc_, it, chk};
-        prof_begin(prof, 1);
-        launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{xref_}, ed, 0, s);
-        prof_end(prof, 1);
+        // the pair launch when the next step's product exists and is not timed apart
+        const bool pair = !prof && it + 1 < len && (P.f_nnz > 0) != P.q_general;
+        if (pair) {
+          const InMomentum<T> nx{x_, xavg_, st_, it + 1};
+          if (P.f_nnz > 0) {
+            EpiStore<T> eu{&st_->done, uvec_, nullptr, nullptr, nullptr, nullptr, 0};
+            aux_ready = launch_spmv_pair<T>(P.schedA, P.A, valA_, InPlain<T>{xref_}, ed,
+                                            P.schedFt, P.Ft, ftval_, nx, eu, s);
+          } else {
+            EpiStore<T> eq{&st_->done, qvec_, nullptr, nullptr, nullptr, nullptr, 0};
+            aux_ready = launch_spmv_pair<T>(P.schedA, P.A, valA_, InPlain<T>{xref_}, ed,
+                                            P.schedQ, P.Q, qv_, nx, eq, s);
+          }
+        }
+        if (!aux_ready) {
+          prof_begin(prof, 1);
+          launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{xref_}, ed, 0, s);
+          prof_end(prof, 1);
+        }
         launches_ += 2;
       }
     }

@@ -111,4 +111,44 @@ void launch_spmv(const Sched& sc, const Csr& K, const T* val, In in, Epi epi, in
 #endif
 }
 
+// The arguments of a spmv_fused launch over schedule sc (no prefetch).
+template <typename T>
+SpmvArgs<T> fused_args(const Sched& sc, const Csr& K, const T* val, int q0) {
+  SpmvArgs<T> a;
+  a.items = sc.items;
+  a.n_items = sc.n_items;
+  a.pf_dist = 0;
+  a.rp = K.rp;
+  a.col = K.col;
+  a.val = val;
+  a.cnt = sc.cnt;
+  a.carry = reinterpret_cast<T*>(sc.carry);
+  a.part = sc.part;
+  a.q0 = q0;
+  return a;
+}
+
+// Two independent products in one spmv_fused_pair launch, with the first
+// schedule's register budget.  Returns false, launching nothing, when either
+// schedule runs the pipelined kernel or has no items: the caller then launches
+// the two apart.  Every item is computed as launch_spmv computes it, so the
+// results are the same bits.
+template <typename T, class In1, class Epi1, class In2, class Epi2>
+bool launch_spmv_pair(const Sched& s1, const Csr& K1, const T* v1, In1 in1, Epi1 e1,
+                      const Sched& s2, const Csr& K2, const T* v2, In2 in2, Epi2 e2,
+                      cudaStream_t s) {
+  if (s1.n_items == 0 || s2.n_items == 0 || s1.kind == kSpmvPipe || s2.kind == kSpmvPipe)
+    return false;
+  const SpmvArgs<T> a1 = fused_args<T>(s1, K1, v1, 0), a2 = fused_args<T>(s2, K2, v2, 0);
+  const int g1 = (s1.n_items + kSpmvWarps - 1) / kSpmvWarps;
+  const int g2 = (s2.n_items + kSpmvWarps - 1) / kSpmvWarps;
+  if (s1.kind == kSpmvItemWide)
+    spmv_fused_pair<T, In1, Epi1, In2, Epi2, kSpmvWideMinB>
+        <<<g1 + g2, kSpmvBlock, 0, s>>>(a1, in1, e1, g1, a2, in2, e2);
+  else
+    spmv_fused_pair<T, In1, Epi1, In2, Epi2><<<g1 + g2, kSpmvBlock, 0, s>>>(a1, in1, e1, g1, a2,
+                                                                          in2, e2);
+  return true;
+}
+
 }  // namespace mpax
