@@ -992,8 +992,11 @@ def run_qp(args):
                           "frac_of_wall": qb["total"] / wall_it / 1e9 / pk,
                           "graph_launch_overhead_us": max(0.0, wall_it - kern_it) * 1e6,
                           "overlap_us": max(0.0, kern_it - wall_it) * 1e6,
-                          "launches": 3,
-                          "note": "kernel_us_isolated: the three products of an iteration "
+                          "launches": 2 + 1 / 64,
+                          "note": "launches: the primal half-step and one launch holding "
+                                  "the dual half-step and the next step's F^T x_md, plus the "
+                                  "first step's own F^T x_md per 64-iteration block. "
+                                  "kernel_us_isolated: the three products of an iteration "
                                   "plus the KKT products of the checks (every 64 iterations), "
                                   "each timed alone with CUDA events, no graphs (so each "
                                   "carries its own start-up); wall_us: the graph-replayed "
