@@ -1275,23 +1275,35 @@ class Engine final : public EngineBase {
     ProblemData& P = *P_;
     cudaStream_t s = P.s;
     const size_t n = P.n, m = P.m;
+    bool aux_ready = false;  // the step's momentum product came with the last dual launch
     for (int it = 0; it < len; ++it) {
-      if (P.f_nnz > 0) {
+      if (P.f_nnz > 0 && !aux_ready) {
         EpiStore<T> eu{&st_->done, uvec_, nullptr, nullptr, nullptr, nullptr, 0};
         launch_spmv<T>(P.schedFt, P.Ft, ftval_, InMomentum<T>{x_, xavg_, st_, it}, eu, 0, s);
         launches_ += 1;
       }
-      if (P.q_general) {
+      if (P.q_general && !aux_ready) {
         EpiStore<T> eq{&st_->done, qvec_, nullptr, nullptr, nullptr, nullptr, 0};
         launch_spmv<T>(P.schedQ, P.Q, qv_, InMomentum<T>{x_, xavg_, st_, it}, eq, 0, s);
         launches_ += 1;
       }
+      aux_ready = false;
       EpiPrimalQP<T, true> ep{st_, x_,    xavg_,  xref_,  xanc_, c_,     l_,  u_,
                               Ds_, P.F.rp, P.F.col, fval_, uvec_, xprev_, it, 0,
                               0,   xmd + it * n, cx + it * n, P.q_general ? qvec_ : nullptr};
       launch_spmv<T>(P.schedAt, P.At, valAt_, InPlain<T>{y_}, ep, 0, s);
       EpiDualQP<T, true> ed{st_, y_, yavg_, yanc_, lc_, uc_, it, 0, cy + it * m};
-      launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{xref_}, ed, 0, s);
+      if (it + 1 < len && (P.f_nnz > 0) != P.q_general) {  // as in launch_block
+        const InMomentum<T> nx{x_, xavg_, st_, it + 1};
+        EpiStore<T> ea{&st_->done, P.f_nnz > 0 ? uvec_ : qvec_, nullptr, nullptr, nullptr,
+                       nullptr, 0};
+        aux_ready = P.f_nnz > 0
+                        ? launch_spmv_pair<T>(P.schedA, P.A, valA_, InPlain<T>{xref_}, ed,
+                                              P.schedFt, P.Ft, ftval_, nx, ea, s)
+                        : launch_spmv_pair<T>(P.schedA, P.A, valA_, InPlain<T>{xref_}, ed,
+                                              P.schedQ, P.Q, qv_, nx, ea, s);
+      }
+      if (!aux_ready) launch_spmv<T>(P.schedA, P.A, valA_, InPlain<T>{xref_}, ed, 0, s);
       launches_ += 2;
     }
   }
@@ -1380,19 +1392,28 @@ class Engine final : public EngineBase {
                              P.F.rp, P.F.col, fval_, tq,
                              it < L - 1 ? xmd + (size_t)(it + 1) * nn : nullptr, it, 0, qu};
           launch_spmv<T>(sAtRev, P.At, valAt_, InPlain<T>{ws}, ep, 0, s);
-          if (P.f_nnz > 0) {
-            EpiStore<T> eu{nullptr, tq, nullptr, nullptr, nullptr, nullptr, 0};
-            launch_spmv<T>(P.schedFt, P.Ft, ftval_, InPlain<T>{uu}, eu, 0, s);
-            launches_ += 1;
-          }
-          if (P.q_general) {
-            EpiStore<T> eq{nullptr, qu, nullptr, nullptr, nullptr, nullptr, 0};
-            launch_spmv<T>(P.schedQ, P.Q, qv_, InPlain<T>{uu}, eq, 0, s);
-            launches_ += 1;
-          }
+          // F~^T uu (or Q~ uu) and the reverse dual step both read only uu: one launch
           EpiRevDual<T> ed{st_, ay, aya, ws, glc, guc,
                            it > 0 ? cy + (size_t)(it - 1) * mm : nullptr, it, 0};
-          launch_spmv<T>(sARev, P.A, valA_, InPlain<T>{uu}, ed, 0, s);
+          bool paired = false;
+          if (P.f_nnz > 0) {
+            EpiStore<T> eu{nullptr, tq, nullptr, nullptr, nullptr, nullptr, 0};
+            paired = launch_spmv_pair<T>(sARev, P.A, valA_, InPlain<T>{uu}, ed, P.schedFt, P.Ft,
+                                         ftval_, InPlain<T>{uu}, eu, s);
+            if (!paired) {
+              launch_spmv<T>(P.schedFt, P.Ft, ftval_, InPlain<T>{uu}, eu, 0, s);
+              launches_ += 1;
+            }
+          } else if (P.q_general) {
+            EpiStore<T> eq{nullptr, qu, nullptr, nullptr, nullptr, nullptr, 0};
+            paired = launch_spmv_pair<T>(sARev, P.A, valA_, InPlain<T>{uu}, ed, P.schedQ, P.Q,
+                                         qv_, InPlain<T>{uu}, eq, s);
+            if (!paired) {
+              launch_spmv<T>(P.schedQ, P.Q, qv_, InPlain<T>{uu}, eq, 0, s);
+              launches_ += 1;
+            }
+          }
+          if (!paired) launch_spmv<T>(sARev, P.A, valA_, InPlain<T>{uu}, ed, 0, s);
           launches_ += 2;
         }
         k_rev_r4<T><<<grid1(n), 256, 0, s>>>(st_, 0, n, Ds_, P.F.rp, P.F.col, fval_, tq, uu, xmd,
