@@ -773,24 +773,35 @@ constexpr long long kBatchVecBytes = 200 * 1024;
 // the batch took 0.57 s against 0.35 s without.
 constexpr long long kStageFew = 200 * 1024;
 
+// The arguments and shared-memory size of one batch launch in precision T.
 template <typename T>
-mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches,
-                      const int* todo, const int* todo_host, int n_todo, int warm,
-                      int stall_limit) {
+struct BatchLaunch {
+  BatchArgs<T> a;
+  size_t smem = 0;
+};
+
+// Scaled data and iterate storage of the launch in T (in *work, grown to fit),
+// its arguments and its shared-memory pool; allow_stage: whole instances may be
+// staged.
+template <typename T>
+mpax_status batch_prepare(mpax_batch* bt, const mpax_options* o, long long* launches,
+                          const int* todo, const int* todo_host, int n_todo, int warm,
+                          int stall_limit, bool allow_stage, void** work, size_t* work_bytes,
+                          BatchLaunch<T>* L) {
   ProblemData& P = *problem_data(bt->prob);
   cudaStream_t s = P.s;
   const int m = P.m, n = P.n, nnz = P.nnz;
   // scaled data and iterate storage in the iteration precision
   const size_t need =
       sizeof(T) * ((size_t)2 * (nnz + kPad) + 10 * (size_t)n + 8 * (size_t)m + 96);
-  if (bt->work_bytes < need) {
-    if (bt->work) cudaFree(bt->work);
-    bt->work = nullptr;
-    bt->work_bytes = 0;
-    if (cudaMalloc(&bt->work, need) != cudaSuccess) return bfail(MPAX_ERR_OUT_OF_MEMORY, "batch work");
-    bt->work_bytes = need;
+  if (*work_bytes < need) {
+    if (*work) cudaFree(*work);
+    *work = nullptr;
+    *work_bytes = 0;
+    if (cudaMalloc(work, need) != cudaSuccess) return bfail(MPAX_ERR_OUT_OF_MEMORY, "batch work");
+    *work_bytes = need;
   }
-  T* p = reinterpret_cast<T*>(bt->work);
+  T* p = reinterpret_cast<T*>(*work);
   auto take = [&](size_t k) {
     T* r = p;
     p += (k + 15) / 16 * 16;
@@ -812,7 +823,7 @@ mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches
   scale_cast<T>(P.lc, P.Dr, false, lc, m, s);
   scale_cast<T>(P.uc, P.Dr, false, uc, m, s);
   *launches += 7;
-  BatchArgs<T> a;
+  BatchArgs<T>& a = L->a;
   a.B = bt->B;
   a.m_off = bt->m_off;
   a.n_off = bt->n_off;
@@ -882,11 +893,11 @@ mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches
   a.rp_cap = (MPAX_BATCH_SMEM_RP && smem + sizeof(int) * (size_t)rmax <= 100 * 1024)
                  ? (int)rmax : 0;
   smem += sizeof(int) * (size_t)a.rp_cap;
-  int occ = 0, dev = 0, sms = 0;
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // whole-instance staging when every instance of the launch has an SM of its own
-  const long long cap = (o->batch_stage && n_todo <= sms) ? kStageFew : 0;
+  const long long cap = (allow_stage && o->batch_stage && n_todo <= sms) ? kStageFew : 0;
   long long smax = 0;
   for (int w = 0; w < n_todo; ++w) {
     const int b = todo_host ? todo_host[w] : w;
@@ -896,19 +907,42 @@ mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches
     if (need <= cap) smax = std::max(smax, need);
   }
   a.stage_cap = smax;
-  smem = std::max(smem, (size_t)((smax + 15) / 16 * 16));
-  auto kernel = smax > 0 ? batch_lp_kernel<T, true> : batch_lp_kernel<T, false>;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kBatchThreads<T>, smem);
+  L->smem = std::max(smem, (size_t)((smax + 15) / 16 * 16));
   a.todo = todo;
   a.n_todo = n_todo;
   a.warm = warm;
   a.stall_limit = stall_limit;
-  const int grid = std::min(n_todo, std::max(1, occ) * sms);
-  cudaMemsetAsync(bt->next, 0, sizeof(int), s);
-  kernel<<<grid, kBatchThreads<T>, smem, s>>>(a);
-  *launches += 1;
   if ((e = cudaGetLastError())) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
+  return MPAX_OK;
+}
+
+// Resident CTAs of `kernel` on the whole GPU (at least one per SM).
+template <class K>
+int batch_grid(K kernel, int threads, size_t smem, int n_todo) {
+  int occ = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
+  return std::min(n_todo, std::max(1, occ) * sms);
+}
+
+template <typename T>
+mpax_status run_batch(mpax_batch* bt, const mpax_options* o, long long* launches,
+                      const int* todo, const int* todo_host, int n_todo, int warm,
+                      int stall_limit) {
+  BatchLaunch<T> L;
+  mpax_status st = batch_prepare<T>(bt, o, launches, todo, todo_host, n_todo, warm, stall_limit,
+                                    true, &bt->work, &bt->work_bytes, &L);
+  if (st) return st;
+  cudaStream_t s = problem_data(bt->prob)->s;
+  auto kernel = L.a.stage_cap > 0 ? batch_lp_kernel<T, true> : batch_lp_kernel<T, false>;
+  const int grid = batch_grid(kernel, kBatchThreads<T>, L.smem, n_todo);
+  cudaMemsetAsync(bt->next, 0, sizeof(int), s);
+  kernel<<<grid, kBatchThreads<T>, L.smem, s>>>(L.a);
+  *launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e) return bfail(MPAX_ERR_CUDA, cudaGetErrorString(e));
   return MPAX_OK;
 }
 
