@@ -763,6 +763,36 @@ def bf16_peak():
         return 1700.0, "fallback 1.7 PFLOP/s sustained"
 
 
+def bf16x3_product_error(C, A, cols=64):
+    """Error of the tensor-core BF16x3 product against the exact (FP64) product on
+    the workload's own matrix, both orientations, `cols` instance vectors each
+    (x ~ U[0, 1] like the box [0, 1]; y ~ N(0, 1)): the largest entry error
+    relative to sum_k |a_k| |v_k| (the stated bound is (3 2^-18 + (3K + 2) 2^-24)
+    times that sum) and the normwise relative error ||D - D_exact||_F / ||D_exact||_F."""
+    import torch
+    m, n = A.shape
+    g = torch.Generator(device="cuda").manual_seed(20241212)
+    A64 = A.double()
+    res = {}
+    for name, V, mn_major in (("dual A X", torch.rand(cols, n, device="cuda", generator=g), False),
+                              ("primal A^T Y", torch.randn(cols, m, device="cuda", generator=g),
+                               True)):
+        D = C.mpax_dense_bf16x3(A, V, a_mn_major=mn_major).double()
+        V64 = V.double()
+        exact = V64 @ (A64 if mn_major else A64.t())
+        mag = V64.abs() @ (A64.abs() if mn_major else A64.abs().t())
+        err = (D - exact).abs()
+        K = m if mn_major else n
+        res[name] = {"max_err_over_abs_sum": float((err / mag).max()),
+                     "rel_fro": float(torch.linalg.norm(D - exact) / torch.linalg.norm(exact)),
+                     "stated_bound_factor": 3 * 2.0 ** -18 + (3 * K + 2) * 2.0 ** -24,
+                     "columns": cols}
+        del D, exact, mag, err
+    del A64
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_shared(args):
     """Shared-matrix dense LP batch: A 16384 x 32768 FP32, 512 cost vectors solved
     together, K X and K^T Y as BF16x3 tensor-core GEMMs (FP32 accumulate) and,
@@ -824,6 +854,7 @@ def run_shared(args):
     prod = {}
     for name, ms in zip(("dual A~X", "primal A~^T Y"), summ_p["product_ms"]):
         prod[name] = {"avg_launch_ms": ms, "tflops": flops_each / (ms / 1e3) / 1e12 if ms else None}
+    out["bf16x3"]["product_error"] = bf16x3_product_error(C, dev["A"])
     pk, src = bf16_peak()
     a = out["bf16x3"]["tensor_tflops_over_solve"]
     slow = max(prod, key=lambda k: prod[k]["avg_launch_ms"])

@@ -6,7 +6,7 @@ import scipy.sparse as sp
 
 from oracle import pdhg as O
 from synth import shared_dense_lp_batch
-from tests.gpu_util import lib
+from tests.gpu_util import lib, rel_inf
 
 pytestmark = pytest.mark.gpu
 
@@ -181,3 +181,62 @@ def test_dense_single_knapsack_matches_highs(C):
     res = linprog(d["c"], A_ub=A, b_ub=d["uc"], bounds=(0, 1), method="highs")
     assert res.status == 0
     assert chk["primal_obj"] == pytest.approx(res.fun, rel=1e-5)
+
+
+@pytest.fixture(scope="module")
+def iterate_case():
+    """A shared batch whose products span several tiles with ragged edges in every
+    dimension (m = 2036 rows and n = 4100 columns are not multiples of the 128-row
+    output tile or the 32-wide K block; 500 instances fill one 256-wide instance
+    tile and part of a second), and the oracle's point after 192 iterations for
+    the first and last instance of each instance tile."""
+    d = shared_dense_lp_batch(2036, 4100, 500, seed=2412, bound_frac=0.5)
+    A = sp.csr_matrix(d["A"].astype(np.float64))
+    k_iter = 192
+    ref = {}
+    for k in (0, 255, 256, 499):
+        p = O.Problem(A, d["C"][k].copy(), d["b"].copy(), d["b"].copy(), d["l"], d["u"])
+        ref[k] = O.solve_lp(p, O.Options(eps_abs=1e-14, eps_rel=1e-14, iteration_limit=k_iter,
+                                         power_max_iter=0, eps_primal_infeasible=0.0,
+                                         eps_dual_infeasible=0.0))
+        assert ref[k].iterations == k_iter and ref[k].status == "iteration_limit"
+    assert any(r.restarts > 0 for r in ref.values())
+    return d, k_iter, ref
+
+
+# Tolerances.  The FP32 product path rounds the scaled matrix, the iterates and
+# every product to FP32; the mixed-precision batch kernel meets 1e-5 after 64
+# iterations, and 192 iterations with two restarts take 2e-5.  The BF16x3 path
+# forms each product from the split operands, which keep 2^-17 relative error
+# per element, and accumulates in FP32 on the tensor cores, whose error grows
+# with the length K of the sums (the (3K + 2) 2^-24 term of the product's stated
+# bound; on the 16384 x 32768 matrix of the dense bench the normwise product
+# error is 1.1e-4 at K = 32768, about 1.4e-5 when scaled to K = 4100).  Modelling
+# the split's rounding in FP64 on the CPU moves the oracle's point at iteration
+# 192 by 1.5e-5 here; 2e-4 leaves room for the accumulation, while a product
+# that drops one of its three terms (A_lo v_hi, say) moves the same point by
+# 3e-3 after only 64 iterations in that model.
+@pytest.mark.parametrize("fp32,tol", [(False, 2e-4), (True, 2e-5)], ids=["bf16x3", "fp32"])
+def test_shared_iterates_match_oracle(C, iterate_case, fp32, tol):
+    """Iterate-level parity of the shared-matrix batch (eqs. 3-4, Algorithm 1 per
+    column): 192 iterations from zero, with their checks, restarts and
+    primal-weight updates, give the oracle's (x^, y^) element by element for the
+    instances at the edges of both instance tiles, with the step sizes from the
+    certified bound ||A~||_2 <= 1 on both sides."""
+    d, k_iter, ref = iterate_case
+    h = C.mpax_lp_shared_create(d["m"], d["n"], d["B"], d["A"], d["C"], d["b"], d["b"],
+                                d["l"], d["u"])
+    try:
+        C.mpax_shared_solve(h, C.mpax_options_default(eps_abs=1e-14, eps_rel=1e-14,
+                                                      iteration_limit=k_iter, power_max_iter=0,
+                                                      fp64_continuation=0), fp32)
+        summ, per = C.mpax_shared_get_stats(h, d["B"])
+        X, Y = C.mpax_shared_get_solution(h, d["m"], d["n"], d["B"])
+    finally:
+        C.mpax_shared_destroy(h)
+    assert np.all(per["iterations"] == k_iter)
+    assert summ["fp64_instances"] == 0
+    assert summ["gemms"] > 0
+    for k, r in ref.items():
+        assert rel_inf(X[k], r.x) <= tol, (k, rel_inf(X[k], r.x))
+        assert rel_inf(Y[k], r.y) <= tol, (k, rel_inf(Y[k], r.y))
