@@ -102,29 +102,106 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
 
 // Row sums of packed short rows.  FP32: the products are formed lane-parallel
 // into the warp's buffer and one lane adds a row's products in order.  FP64 runs
-// at a small fraction of the FP32 rate on this GPU (its pipe, not memory, bounds
-// the FP64 products), so there the buffer holds the values and, kShortCap
-// further, the gathered inputs, and the row's lane forms one fused multiply-add
-// chain: one FP64 instruction per nonzero instead of a multiply and an add.
+// at a small fraction of the FP32 rate on this GPU (two FP64 lane operations per
+// SM and cycle: a warp-wide FP64 instruction holds the pipe for 16 cycles
+// however many of its lanes are active, so the FP64 pipe, not memory, bounds
+// these kernels).  There the buffer holds the values and, kShortCap further,
+// the gathered inputs, and the sums are fused multiply-add chains that keep
+// every lane busy (packed_rows_fma).
 template <typename T>
 constexpr bool kFmaRows = sizeof(T) == 8;
 
-// buf: products (FP32) or values (FP64); bx: the gathered inputs (FP64 only).
+// Shared-memory words of the row-start bit mask of an FP64 packed item (one bit
+// per nonzero position, kShortCap positions, plus a word read past the last).
+constexpr int kRowWords = (kShortCap + 31) / 32 + 1;
+
+// FP32 row sum: buf holds the products.
 template <typename T>
-__device__ __forceinline__ T packed_row_sum(const T* buf, const T* bx, int q0, int q1) {
+__device__ __forceinline__ T packed_row_sum(const T* buf, int q0, int q1) {
   T s = 0;
-  if constexpr (kFmaRows<T>) {
-    for (int q = q0; q < q1; ++q) s = fma(buf[q], bx[q], s);
-  } else {
-    for (int q = q0; q < q1; ++q) s += buf[q];
-  }
+  for (int q = q0; q < q1; ++q) s += buf[q];
   return s;
 }
 
-// The CTA's staging buffer: one row per warp; FP64 keeps values and gathered
-// inputs apart (kFmaRows), twice the length.
+// Sum of row [s, e) after the chunk walk of packed_rows_fma: a row inside one
+// chunk was stored whole at buf[s]; otherwise its pieces are added in chunk
+// order: its piece of chunk a (that chunk's last segment, at the chunk's last
+// position of bx), the whole chunks strictly between (their single segment, at
+// their first position), and its piece of chunk b (that chunk's first segment).
 template <typename T>
-using SpmvBuf = T[kSpmvWarps][(kFmaRows<T> ? 2 : 1) * kShortCap];
+__device__ __forceinline__ T packed_row_total(const T* buf, const T* bx, int L, int s, int e) {
+  if (s >= e) return T(0);
+  const int a = s / L, b = (e - 1) / L;
+  if (a == b) return buf[s];
+  T tot = bx[(a + 1) * L - 1];
+  for (int l = a + 1; l < b; ++l) tot += bx[l * L];
+  return tot + bx[b * L];
+}
+
+// FP64 row sums of a packed item with every lane busy.  The item's cnt
+// nonzeros (values in buf, gathered inputs in bx, both at offsets 0..cnt-1) are
+// cut into 32 chunks of L = ceil(cnt / 32) consecutive positions, chunk l
+// walked by lane l as one fused multiply-add chain that restarts at each row
+// start.  Every chain segment that is a whole row is stored at buf[its first
+// position]; the chunk's first and last segments are stored in bx at the
+// chunk's first and last position (positions the lane has already read; no
+// other lane reads them).  packed_row_total then assembles each row.  The
+// order of every sum depends only on the item, so all kernel kinds that stage
+// an item give the same bits.  The FP64 instructions per item are L chain steps
+// plus the chunk pieces of the longest row sum, against the longest row pair
+// of a lane when each lane sums its own rows.
+// Rows [a0, a1) and [b0, b1) (offsets from the item's first nonzero) are this
+// lane's two rows when ha / hb; words: kRowWords words of the warp's shared
+// memory.  Called by the whole warp.
+template <typename T>
+__device__ __forceinline__ void packed_rows_fma(T* buf, T* bx, unsigned* words, int cnt, int lane,
+                                                bool ha, int a0, int a1, bool hb, int b0, int b1,
+                                                T& sa, T& sb) {
+  if (lane < kRowWords) words[lane] = 0u;
+  __syncwarp();
+  if (ha && a0 < cnt) atomicOr(words + (a0 >> 5), 1u << (a0 & 31));
+  if (hb && b0 < cnt) atomicOr(words + (b0 >> 5), 1u << (b0 & 31));
+  __syncwarp();
+  const int L = (cnt + kWarp - 1) / kWarp;
+  const int c0 = lane * L, c1 = min(c0 + L, cnt);
+  if (c0 < c1) {
+    // bit t: position c0 + t starts a row (t <= L <= kShortCap / 32)
+    const unsigned long long two = (unsigned long long)words[c0 >> 5] |
+                                   ((unsigned long long)words[(c0 >> 5) + 1] << 32);
+    const unsigned m = (unsigned)(two >> (c0 & 31));
+    T acc = 0;
+    int s = c0;  // first position of the open segment
+#pragma unroll
+    for (int t = 0; t < kShortLoads; ++t) {
+      const int q = c0 + t;
+      if (q < c1) {
+        if (t > 0 && ((m >> t) & 1u)) {  // a row starts at q: close [s, q)
+          if (s == c0) bx[c0] = acc;
+          if ((m >> (s - c0)) & 1u) buf[s] = acc;  // [s, q) is a whole row
+          acc = 0;
+          s = q;
+        }
+        acc = fma(buf[q], bx[q], acc);
+      }
+    }
+    // the last segment [s, c1): a whole row if a row starts at s and the
+    // next row (or the item's end) at c1
+    if (((m >> (s - c0)) & 1u) && (c1 == cnt || ((m >> (c1 - c0)) & 1u))) buf[s] = acc;
+    if (s == c0) bx[c0] = acc;
+    bx[c1 - 1] = acc;
+  }
+  __syncwarp();
+  sa = ha ? packed_row_total(buf, bx, L, a0, a1) : T(0);
+  sb = hb ? packed_row_total(buf, bx, L, b0, b1) : T(0);
+}
+
+// The CTA's staging buffer: one row per warp; FP64 keeps values and gathered
+// inputs apart (kFmaRows), twice the length, followed by the row-start mask
+// (kRowWords words, rounded up to whole elements).
+template <typename T>
+constexpr int kSpmvBufLen = kFmaRows<T> ? 2 * kShortCap + (kRowWords * 4 + 7) / 8 : kShortCap;
+template <typename T>
+using SpmvBuf = T[kSpmvWarps][kSpmvBufLen<T>];
 
 // The work of CTA `cta` of a spmv_fused launch over the items of `a`: one item
 // per warp.
@@ -193,8 +270,16 @@ __device__ __forceinline__ void spmv_fused_cta(const SpmvArgs<T>& a, In& in, Epi
       prefetch_l2(a.col + q0, sizeof(int) * (size_t)(q1 - q0));
     }
     __syncwarp();
-    if (ha) epi.row(ra, packed_row_sum<T>(buf, bufx, pa0 - base, pa1 - base), pra, acc);
-    if (hb) epi.row(rb, packed_row_sum<T>(buf, bufx, pb0 - base, pb1 - base), prb, acc);
+    if constexpr (kFmaRows<T>) {
+      T sa, sb;
+      packed_rows_fma<T>(buf, bufx, reinterpret_cast<unsigned*>(bufx + kShortCap), end - base,
+                         lane, ha, pa0 - base, pa1 - base, hb, pb0 - base, pb1 - base, sa, sb);
+      if (ha) epi.row(ra, sa, pra, acc);
+      if (hb) epi.row(rb, sb, prb, acc);
+    } else {
+      if (ha) epi.row(ra, packed_row_sum<T>(buf, pa0 - base, pa1 - base), pra, acc);
+      if (hb) epi.row(rb, packed_row_sum<T>(buf, pb0 - base, pb1 - base), prb, acc);
+    }
     if (Epi::NQ > 0 && epi.check) {
 #pragma unroll
       for (int q = 0; q < Epi::NQ; ++q) {
@@ -346,8 +431,9 @@ struct PipeLayout {
   static constexpr int kValCap = kShortCap + 2 * kValV;
   static constexpr int kColCap = kShortCap + 8;
   static constexpr int kStageBytes = kValCap * (int)sizeof(T) + kColCap * 4;
-  // FP64: the gathered inputs of the current item (see packed_row_sum)
-  static constexpr int kXBytes = kFmaRows<T> ? kShortCap * (int)sizeof(T) : 0;
+  // FP64: the gathered inputs of the current item and the row-start mask (see
+  // packed_rows_fma)
+  static constexpr int kXBytes = kFmaRows<T> ? kShortCap * (int)sizeof(T) + kRowWords * 4 + 4 : 0;
   // two stages, the input buffer, two mbarriers
   static constexpr int kWarpBytes = 2 * kStageBytes + kXBytes + 16;
   static_assert(kStageBytes % 16 == 0, "stage size must keep 16-byte alignment");
@@ -486,8 +572,16 @@ __global__ void __launch_bounds__(kWarp* kPipeWarps, sizeof(T) == 4 ? 5 : 3)
         }
       }
       __syncwarp();
-      if (ha) epi.row(ra, packed_row_sum<T>(buf, xbuf, pa0 - base, pa1 - base), pra, acc);
-      if (hb) epi.row(rb, packed_row_sum<T>(buf, xbuf, pb0 - base, pb1 - base), prb, acc);
+      if constexpr (kFmaRows<T>) {
+        T sa, sb;
+        packed_rows_fma<T>(buf, xbuf, reinterpret_cast<unsigned*>(xbuf + kShortCap), cnt, lane,
+                           ha, pa0 - base, pa1 - base, hb, pb0 - base, pb1 - base, sa, sb);
+        if (ha) epi.row(ra, sa, pra, acc);
+        if (hb) epi.row(rb, sb, prb, acc);
+      } else {
+        if (ha) epi.row(ra, packed_row_sum<T>(buf, pa0 - base, pa1 - base), pra, acc);
+        if (hb) epi.row(rb, packed_row_sum<T>(buf, pb0 - base, pb1 - base), prb, acc);
+      }
       if (Epi::NQ > 0 && epi.check) {
 #pragma unroll
         for (int q = 0; q < Epi::NQ; ++q) {
