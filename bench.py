@@ -621,6 +621,80 @@ def run_small_lp(args):
             "persistent_single_cta": persistent}
 
 
+def oracle_sample_qp(d, iters):
+    """Time `iters` iterations of the oracle's rAPDHG loop (its own step and KKT
+    functions, KKT checked every 64 iterations) after its preprocessing, which is
+    not timed.  Returns (iters/s, seconds, prep seconds)."""
+    from oracle import pdhg as O
+    p = O.problem_from_arrays(d)
+    opts = O.Options()
+    t0 = time.perf_counter()
+    ps, Dr, Dc, nA, nQ, eta, omega = O.prepare(p, opts)
+    prep = time.perf_counter() - t0
+    tau, sigma = O.step_sizes(eta, omega, nA, nQ, opts, True)
+    x = np.zeros(p.n)
+    y = np.zeros(p.m)
+    xavg, yavg = x.copy(), y.copy()
+    t0 = time.perf_counter()
+    for k in range(iters):
+        x, y, xavg, yavg, _ = O.apdhg_step_qp(ps, x, y, xavg, yavg, k, tau, sigma)
+        if (k + 1) % opts.check_every == 0:
+            O.kkt(p, Dc * xavg, Dr * yavg)
+    dt = time.perf_counter() - t0
+    return iters / dt, dt, prep
+
+
+def oracle_leg(name):
+    """The FP64 oracle beside a workload of the default run, on one host core and
+    on a bounded sample of that workload (regenerated from the same seeds).
+    Returns a cpu_baseline object, or None where no bounded sample exists."""
+    from oracle import pdhg as O
+    from synth import instance_seed, lp_instance
+    if name == "small_lp_200x400":
+        d = lp_instance(200, 400, seed=instance_seed(1), density=0.02)
+        t0 = time.perf_counter()
+        r = O.solve_lp(O.problem_from_arrays(d), O.Options(eps_abs=1e-8, eps_rel=1e-8))
+        dt = time.perf_counter() - t0
+        return {"value": dt, "unit": "s", "cores": 1, "kind": "oracle",
+                "sample": f"one oracle solve of the same LP to rel KKT 1e-8 ({r.iterations} "
+                          f"iterations, {r.status}), preprocessing included"}
+    if name == "ragged_lp_4096":
+        from synth import ragged_lp_instances
+        k = 8
+        insts = ragged_lp_instances(4096, range(k))
+        t0 = time.perf_counter()
+        its = []
+        for inst in insts:
+            r = O.solve_lp(O.problem_from_arrays(inst),
+                           O.Options(eps_abs=1e-4, eps_rel=1e-4, power_max_iter=0))
+            its.append(r.iterations)
+        dt = time.perf_counter() - t0
+        return {"value": k / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                "sample": f"the first {k} of the 4096 instances (m = "
+                          f"{', '.join(str(i['m']) for i in insts)}), each solved to rel KKT "
+                          f"1e-4 with the certified bound ||A~||_2 <= 1 as on the GPU "
+                          f"({sum(its)} iterations in all), preprocessing included"}
+    if name == "qp_200k":
+        from synth import qp_instance
+        d = qp_instance(200_000, 100_000, seed=instance_seed(3), a_density=1e-4, f_cols=32,
+                        f_density=0.01)
+        rate, dt, prep = oracle_sample_qp(d, 64)
+        return {"value": rate, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                "sample": f"64 rAPDHG iterations of the oracle on the same QP after its "
+                          f"untimed preprocessing ({prep:.1f} s); on the GPU the mixed step runs "
+                          f"mixed.iterations iterations in ms_per_step, backward_s included"}
+    return None
+
+
+ORACLE_SKIPPED = {
+    "knapsack_1000x100000": "not sampled: the oracle holds A as CSR (1e8 nonzeros, 1.2 GB, and "
+                            "as much again for its transpose), so even one iteration after its "
+                            "scaling exceeds the few seconds a default run may spend",
+    "shared_dense_512": "not sampled: the 16384 x 32768 dense A as the oracle's CSR would take "
+                        "6.4 GB of host memory before its transpose",
+}
+
+
 def run_subworkloads(args):
     """The other workloads of the scope, measured in the default run with short
     step counts and attached to its JSON line (each keeps its own roofline,
@@ -640,6 +714,16 @@ def run_subworkloads(args):
         except Exception as exc:  # reported, not hidden: the line says what failed
             out[name] = {"error": f"{type(exc).__name__}: {exc}"}
         out[name]["driver_s"] = time.perf_counter() - t0
+        if not args.no_cpu_baseline:
+            t1 = time.perf_counter()
+            try:
+                cpu = oracle_leg(name)
+                out[name]["cpu_baseline"] = cpu if cpu is not None else {
+                    "kind": "oracle", "value": None, "note": ORACLE_SKIPPED.get(name, "")}
+            except Exception as exc:
+                out[name]["cpu_baseline"] = {"kind": "oracle", "value": None,
+                                             "error": f"{type(exc).__name__}: {exc}"}
+            out[name]["cpu_baseline_s"] = time.perf_counter() - t1
         print(f"[bench] {name}: {out[name].get('value')} {out[name].get('unit')} "
               f"({out[name]['driver_s']:.0f} s)", file=sys.stderr, flush=True)
     return out

@@ -12,6 +12,7 @@ from .generators import (  # noqa: F401
     qp_instance,
     qp_sparse_q_instance,
     ragged_lp_batch,
+    ragged_lp_instances,
     shared_dense_lp_batch,
     knapsack_lp,
     grid_shortest_path_lp,

@@ -288,6 +288,16 @@ def grid_shortest_path_lp(k: int, B: int = 1, *, seed: int = MASTER_SEED,
 # Ragged batch of independent LPs (packed CSR)
 # ----------------------------------------------------------------------------
 
+def ragged_lp_instances(B: int, which, *, seed: int = MASTER_SEED, m_lo: int = 50,
+                        m_hi: int = 2000, density: float = 0.01, lo: float = 0.0,
+                        hi: float = 10.0, variant: str = "literal") -> list:
+    """Instances `which` (indices into 0..B-1) of the B-instance ragged batch
+    below, each exactly as ragged_lp_batch builds it, without building the rest."""
+    ms = _rng(seed).integers(m_lo, m_hi + 1, size=B)
+    return [lp_instance(int(ms[i]), int(2 * ms[i]), seed=instance_seed(i, seed),
+                        density=density, lo=lo, hi=hi, variant=variant) for i in which]
+
+
 def ragged_lp_batch(B: int, *, seed: int = MASTER_SEED, m_lo: int = 50, m_hi: int = 2000,
                     density: float = 0.01, lo: float = 0.0, hi: float = 10.0,
                     variant: str = "literal") -> dict:
@@ -297,10 +307,8 @@ def ragged_lp_batch(B: int, *, seed: int = MASTER_SEED, m_lo: int = 50, m_hi: in
     sum(m)+1), column indices are local to their instance, vectors are
     concatenated; m_off / n_off / nnz_off are exclusive prefix offsets.
     """
-    rng = _rng(seed)
-    ms = rng.integers(m_lo, m_hi + 1, size=B)
-    insts = [lp_instance(int(mi), int(2 * mi), seed=instance_seed(i, seed), density=density,
-                         lo=lo, hi=hi, variant=variant) for i, mi in enumerate(ms)]
+    insts = ragged_lp_instances(B, range(B), seed=seed, m_lo=m_lo, m_hi=m_hi, density=density,
+                                lo=lo, hi=hi, variant=variant)
     m_off = np.zeros(B + 1, dtype=np.int64)
     n_off = np.zeros(B + 1, dtype=np.int64)
     nnz_off = np.zeros(B + 1, dtype=np.int64)

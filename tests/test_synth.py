@@ -94,3 +94,16 @@ def test_grid_shortest_path_lp_is_a_node_arc_incidence():
     assert g["n"] == 4 * 6 * 5 + 4 * 25
     assert g["lc"][0] == 1 and g["lc"][-1] == -1 and g["lc"].sum() == 0
     assert np.array_equal(g["C"], g["W"][:, g["heads"]])
+
+
+def test_ragged_instances_are_those_of_the_batch():
+    """A few instances of a ragged batch, built alone, equal the batch's own (the
+    bench's oracle sample of the 4096-instance batch relies on this)."""
+    from synth import ragged_lp_instances
+    b = ragged_lp_batch(12, seed=instance_seed(11), m_lo=20, m_hi=80)
+    picked = ragged_lp_instances(12, [0, 5, 11], seed=instance_seed(11), m_lo=20, m_hi=80)
+    for got, k in zip(picked, (0, 5, 11)):
+        ref = b["instances"][k]
+        assert got["m"] == ref["m"] and got["n"] == ref["n"]
+        for key in ("row_ptr", "col", "val", "c", "lc", "uc", "l", "u"):
+            np.testing.assert_array_equal(got[key], ref[key])
