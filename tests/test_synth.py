@@ -97,13 +97,26 @@ def test_grid_shortest_path_lp_is_a_node_arc_incidence():
 
 
 def test_ragged_instances_are_those_of_the_batch():
-    """A few instances of a ragged batch, built alone, equal the batch's own (the
-    bench's oracle sample of the 4096-instance batch relies on this)."""
+    """A few instances of a ragged batch, built alone, equal the slices of the
+    packed batch, and each is the recipe's instance: lp_instance(m_k, 2 m_k) with
+    instance_seed(k) (the bench's oracle sample of the 4096-instance batch relies
+    on this)."""
     from synth import ragged_lp_instances
-    b = ragged_lp_batch(12, seed=instance_seed(11), m_lo=20, m_hi=80)
-    picked = ragged_lp_instances(12, [0, 5, 11], seed=instance_seed(11), m_lo=20, m_hi=80)
+    seed = instance_seed(11)
+    b = ragged_lp_batch(12, seed=seed, m_lo=20, m_hi=80)
+    picked = ragged_lp_instances(12, [0, 5, 11], seed=seed, m_lo=20, m_hi=80)
     for got, k in zip(picked, (0, 5, 11)):
-        ref = b["instances"][k]
-        assert got["m"] == ref["m"] and got["n"] == ref["n"]
+        m0, m1 = b["m_off"][k], b["m_off"][k + 1]
+        n0, n1 = b["n_off"][k], b["n_off"][k + 1]
+        z0, z1 = b["nnz_off"][k], b["nnz_off"][k + 1]
+        assert got["m"] == m1 - m0 and got["n"] == n1 - n0 == 2 * got["m"]
+        np.testing.assert_array_equal(got["row_ptr"], b["row_ptr"][m0:m1 + 1] - z0)
+        np.testing.assert_array_equal(got["col"], b["col"][z0:z1])
+        np.testing.assert_array_equal(got["val"], b["val"][z0:z1])
+        for key, (o0, o1) in (("c", (n0, n1)), ("l", (n0, n1)), ("u", (n0, n1)),
+                              ("lc", (m0, m1)), ("uc", (m0, m1))):
+            np.testing.assert_array_equal(got[key], b[key][o0:o1])
+        ref = lp_instance(int(got["m"]), int(got["n"]), seed=instance_seed(k, seed),
+                          density=0.01, lo=0.0, hi=10.0)
         for key in ("row_ptr", "col", "val", "c", "lc", "uc", "l", "u"):
             np.testing.assert_array_equal(got[key], ref[key])
