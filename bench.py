@@ -687,9 +687,9 @@ def oracle_leg(name):
 
 
 ORACLE_SKIPPED = {
-    "knapsack_1000x100000": "not sampled: the oracle holds A as CSR (1e8 nonzeros, 1.2 GB, and "
-                            "as much again for its transpose), so even one iteration after its "
-                            "scaling exceeds the few seconds a default run may spend",
+    "knapsack_1000x100000": "not sampled: the oracle holds the dense 1000 x 100000 A as CSR "
+                            "(1e8 nonzeros, 1.2 GB, and as much again for its transpose) and "
+                            "scales it in ten Ruiz rounds before its first iteration",
     "shared_dense_512": "not sampled: the 16384 x 32768 dense A as the oracle's CSR would take "
                         "6.4 GB of host memory before its transpose",
 }
